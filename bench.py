@@ -1,0 +1,471 @@
+#!/usr/bin/env python
+"""Benchmark of the batched differentiable Gaussian rasteriser.
+
+Metric: fwd+bwd Mpix/s and mapping iterations/s of an 8-keyframe mapping
+window (8 x 640x480 views, 100k Gaussians, SH degree 3; the renderer's
+camera batch of the paper, Supp. Sec. 1.2), against the same window as 8
+per-view launches.  One step = forward render of the window + L1 colour and
+depth loss + backward to every Gaussian parameter and the 8 keyframe poses.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsr|reference]
+
+Under torchrun (N > 1) every rank renders its own copy of the window (the
+path does not shard here: replicas only); value = all pixels of all ranks /
+max step time over ranks.  --impl reference times the FP64 CPU oracle on a
+bounded crop of the same window (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s & mapping it/s (8-view batch) vs per-view launches; % FP32/SFU peak"
+FWD_OPS_PER_PAIR = 17   # FP32-pipe instructions per composited (pixel, Gaussian) pair, blend forward
+BWD_OPS_PER_PAIR = 48   # the same for the blend backward (before the per-warp reduction)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
+    p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-per-view", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2032.0), source="measured")
+    return dict(hbm_gbs=6400.0, sm_max_mhz=2032.0, source="fallback")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                     parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def dist_barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ workload
+def make_scene():
+    from paper_2411_17660_b300 import scenes
+    return scenes.config_window()
+
+
+def crop_pixels(scene, w, h):
+    pix = []
+    for c in scene.cameras:
+        x0, y0 = (c.W - w) // 2, (c.H - h) // 2
+        ys, xs = np.mgrid[y0:y0 + h, x0:x0 + w]
+        pix.append((ys * c.W + xs).reshape(-1).astype(np.int64))
+    return pix
+
+
+def oracle_step(scene, pix, gC, gD):
+    import oracle
+    gA = [np.zeros(len(p)) for p in pix]
+    oracle.render_backward(scene, gC, gD, gA, pixels=pix)
+
+
+def oracle_sample(scene, seconds):
+    """Picks a centred crop per view whose oracle fwd+bwd takes ~seconds."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(0)
+
+    def run(w, h):
+        pix = crop_pixels(scene, w, h)
+        gC = [rng.uniform(-1, 1, (3, len(p))) for p in pix]
+        gD = [rng.uniform(-0.1, 0.1, len(p)) for p in pix]
+        t0 = time.perf_counter()
+        oracle_step(scene, pix, gC, gD)
+        return time.perf_counter() - t0, pix, gC, gD
+
+    w, h = 32, 24
+    t, _, _, _ = run(w, h)
+    t0, _, _, _ = run(2, 2)                 # projection + binning cost, no pixels
+    per_px = max(t - t0, 1e-9) / (w * h * scene.V)
+    target_px = max((seconds - t0) / per_px / scene.V, 64)
+    side = int(np.sqrt(target_px * 4 / 3))
+    w = int(min(scene.cameras[0].W, max(8, side)))
+    h = int(min(scene.cameras[0].H, max(6, side * 3 // 4)))
+    return w, h, run
+
+
+def cpu_baseline(scene, seconds):
+    w, h, run = oracle_sample(scene, seconds)
+    t, pix, _, _ = run(w, h)
+    npx = sum(len(p) for p in pix)
+    return {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"fwd+bwd of a centred {w}x{h} crop of each of the {scene.V} views "
+                      f"({npx} px, all {scene.N} Gaussians projected), {t:.1f} s, FP64"}
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    scene = make_scene()
+    per_step = max(2.0, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
+    w, h, run = oracle_sample(scene, per_step)
+    for _ in range(args.warmup):
+        run(w, h)
+    times = []
+    npx = 0
+    for _ in range(args.steps):
+        t, pix, _, _ = run(w, h)
+        times.append(t)
+        npx = sum(len(p) for p in pix)
+    ms = 1000 * statistics.mean(times)
+    value = npx / (ms / 1000) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": scene.name, "views": scene.V, "resolution": "640x480", "gaussians": scene.N,
+                   "sh_degree": scene.sh_degree, "sample": f"{w}x{h} centred crop per view"},
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"fwd+bwd of a centred {w}x{h} crop of each view, per step"},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+class Window:
+    """Device state of one mapping window (inputs, outputs, workspace)."""
+
+    def __init__(self, scene, rast, views=None, dev="cuda"):
+        import torch
+        from paper_2411_17660_b300 import render as R
+        self.R, self.torch = R, torch
+        idx = list(range(scene.V)) if views is None else views
+        self.scene = scene
+        self.cams = [R.Intrinsics(scene.cameras[v].H, scene.cameras[v].W, scene.cameras[v].fx,
+                                  scene.cameras[v].fy, scene.cameras[v].cx, scene.cameras[v].cy) for v in idx]
+        self.params = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(dev)
+                       for k in R.PARAM_NAMES}
+        self.vm = torch.from_numpy(np.stack([scene.cameras[v].T_cw for v in idx]).astype(np.float32)).to(dev)
+        self.tc = torch.from_numpy(np.concatenate([scene.target_color[v].reshape(-1) for v in idx])).to(dev)
+        self.td = torch.from_numpy(np.concatenate([scene.target_depth[v].reshape(-1) for v in idx])).to(dev)
+        self.P = sum(c.H * c.W for c in self.cams)
+        self.rast = rast
+        self.color = torch.empty(3 * self.P, device=dev)
+        self.depth = torch.empty(self.P, device=dev)
+        self.alpha = torch.empty(self.P, device=dev)
+        self.dC = torch.empty_like(self.color)
+        self.dD = torch.empty_like(self.depth)
+        self.loss = torch.empty(1, device=dev)
+        self.grads = {k: torch.empty_like(v) for k, v in self.params.items()}
+        self.d_pose = torch.empty(len(self.cams), 6, device=dev)
+        _, _, _, self.ws = rast.render_forward(self.params, scene.sh_degree, self.cams, self.vm)
+        info = rast.info(self.ws)
+        # headroom so that the timed steps never re-grow
+        self.ws = rast.alloc_workspace(scene.N, self.cams, int(info.keys * 1.1) + 8192, dev)
+
+    def step(self, accumulate=False):
+        R, sc = self.R, self.scene
+        self.rast.forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
+                              self.alpha)
+        R.l1_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, 1.0, sc.depth_weight,
+                  self.dC, self.dD, self.loss)
+        self.rast.backward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.dC, self.dD, None,
+                               self.grads, self.d_pose, accumulate=accumulate)
+
+
+def launches_per_step(rast, win):
+    info = rast.info(win.ws)
+    tiles = info.tiles
+    tbits = 1
+    while (1 << tbits) < tiles:
+        tbits += 1
+    passes = (32 + tbits + 7) // 8
+    return 9 + passes + 1 + 3
+
+
+def time_steps(torch, fn, K, flush, events_per_step=None):
+    """Device time of K steps (CUDA events on the current stream), with an L2
+    flush before each step outside the timed events."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for k in range(K):
+        flush()
+        if events_per_step is not None:
+            events_per_step(k)
+        starts[k].record()
+        fn()
+        ends[k].record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_2411_17660_b300", "csrc", "blend.cu" if "blend" in kernel else "preprocess.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("source_sha") == sha:
+            return float(f["dram_bytes_per_launch"])
+    return None
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    import torch
+    from paper_2411_17660_b300 import binding as B
+    from paper_2411_17660_b300 import build as Build
+    from paper_2411_17660_b300 import render as R
+    Build.build()
+    torch.cuda.set_device(local)
+    scene = make_scene()
+    rast = R.GaussianRasterizer(args.tile)
+    win = Window(scene, rast)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = lambda: flush_buf.fill_(1.0)
+    K, W = args.steps, args.warmup
+
+    for _ in range(max(W, 3)):
+        flush()
+        win.step()
+    torch.cuda.synchronize()
+
+    # per-step stage events for the roofline (recorded inside the timed steps)
+    ev_sets = [[torch.cuda.Event(enable_timing=True) for _ in range(B.STAGE_EVENTS)] for _ in range(K)]
+    for s in ev_sets:
+        for e in s:
+            e.record()
+    torch.cuda.synchronize()
+    set_events = lambda k: rast.ctx.set_stage_events([e.cuda_event for e in ev_sets[k]])
+
+    sampler = ClockSampler(local)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    ms = time_steps(torch, win.step, K, flush, set_events)
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks = sampler.stop()
+    rast.ctx.set_stage_events(None)
+    ms_step = dist_max(world, statistics.mean(ms))
+
+    info = rast.info(win.ws)
+    if info.status != 0:
+        raise RuntimeError(f"device status {B.STATUS.get(info.status)} during the timed steps")
+    stage_ms = {}
+    for k, name in enumerate(B.STAGES):
+        a, b = B.STAGE_SPANS[k]
+        stage_ms[name] = statistics.mean(ev_sets[i][a].elapsed_time(ev_sets[i][b]) for i in range(K))
+
+    # the same window as 8 per-view launches
+    per_view = None
+    if not args.no_per_view:
+        wins = [Window(scene, rast, [v]) for v in range(scene.V)]
+
+        def per_view_step():
+            for i, w1 in enumerate(wins):
+                w1.step(accumulate=i > 0)
+
+        for _ in range(max(W, 3)):
+            flush()
+            per_view_step()
+        pv = time_steps(torch, per_view_step, K, flush)
+        per_view = dist_max(world, statistics.mean(pv))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(torch, R, scene, win, K, W, flush)
+        e2e["value"] = dist_max(world, -e2e["value"]) * -1 if world > 1 else e2e["value"]
+
+    peaks = load_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * peaks["sm_max_mhz"] * 1e6 / 1e9   # Gop/s (FP32 lanes x clock)
+    pairs = info.pairs_contributing
+    dominant = max(("blend_fwd", "blend_bwd", "sort", "preprocess", "preprocess_bwd"), key=lambda s: stage_ms[s])
+    ops = {"blend_fwd": FWD_OPS_PER_PAIR, "blend_bwd": BWD_OPS_PER_PAIR}
+    if dominant in ops:
+        achieved = pairs * ops[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved / alu_peak, "traffic": traffic_for(dominant),
+                "peak_note": f"FP32 lanes: {n_sm} SMs x 128 x {peaks['sm_max_mhz']:.0f} MHz (max clock)",
+                "work": f"{pairs} composited pairs x {ops[dominant]} FP32 ops"}
+    else:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": traffic_for(dominant)}
+
+    P_all = win.P * world
+    value = P_all / (ms_step / 1000) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": scene.name, "views": scene.V, "resolution": "640x480", "gaussians": scene.N,
+                   "sh_degree": scene.sh_degree, "tile": args.tile,
+                   "step": "forward + L1 colour/depth loss + backward (params + 8 poses)",
+                   "l2": "flushed before every step (256 MB write), outside the timed events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "mapping_it_per_s": 1000.0 / ms_step,
+        "per_view_launches": None if per_view is None else {
+            "ms_per_step": per_view, "value": P_all / (per_view / 1000) / 1e6, "unit": "Mpix/s",
+            "batched_speedup": per_view / ms_step},
+        "stages_ms": stage_ms,
+        "keys": info.keys, "pairs_contributing": pairs,
+        "roofline": roof,
+        "gpu_launches": launches_per_step(rast, win) * K,
+        "clocks": clocks,
+        "e2e": e2e,
+        "wall_s": wall,
+        "peaks_source": peaks["source"],
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_e2e(torch, R, scene, win, K, W, flush):
+    """Same step through the public API with pinned host inputs: H2D of the
+    parameters, poses and targets, the step, D2H of the loss and pose grads."""
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
+            for k in R.PARAM_NAMES}
+    h_vm = torch.from_numpy(np.stack([c.T_cw for c in scene.cameras]).astype(np.float32)).pin_memory()
+    h_tc = win.tc.cpu().pin_memory()
+    h_td = win.td.cpu().pin_memory()
+    out_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    out_pose = torch.empty(scene.V, 6, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host.values()) + h_vm.numel() * 4 + h_tc.numel() * 4 + h_td.numel() * 4
+    d2h = 4 + out_pose.numel() * 4
+
+    def e2e_step():
+        for k in R.PARAM_NAMES:
+            win.params[k].copy_(host[k], non_blocking=True)
+        win.vm.copy_(h_vm, non_blocking=True)
+        win.tc.copy_(h_tc, non_blocking=True)
+        win.td.copy_(h_td, non_blocking=True)
+        win.step()
+        out_loss.copy_(win.loss, non_blocking=True)
+        out_pose.copy_(win.d_pose, non_blocking=True)
+
+    for _ in range(max(W, 3)):
+        flush()
+        e2e_step()
+    torch.cuda.synchronize()
+    ms = time_steps(torch, e2e_step, K, flush)
+    m = statistics.mean(ms)
+    return {"value": win.P / (m / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": m,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * gsr.h -- C ABI of the B300 (sm_103a) differentiable Gaussian rasteriser.
+ *
+ * The library renders anisotropic 3-D Gaussians into a batch of keyframes and
+ * differentiates the result, following the rendering equation of
+ * DROID-Splat (arXiv 2411.17660), Sec. 3.3, Eq. "rendering":
+ *     C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j),   alpha_i = sigma_i G_i,
+ * where c_i is the colour converted from the spherical harmonics and G_i the
+ * Gaussian projected with the keyframe pose (R, t).  gsr_render produces the
+ * image I', the depth Z' and the opacity of every keyframe of a batch;
+ * gsr_render_backward backpropagates dL/d(images) to every Gaussian parameter
+ * (Sec. 3.3: "optimized via backpropagation") and to each keyframe pose
+ * (Sec. 3.3, pose finetuning; Supp. Sec. 1.3 "Feedback").
+ *
+ * Memory: every pointer in the structs below is a DEVICE pointer owned by the
+ * caller, except where marked "host".  The library allocates no device
+ * memory: the caller provides one workspace buffer per render (size from
+ * gsr_workspace_size) and must pass the same workspace, Gaussians and views
+ * to gsr_render_backward as to the gsr_render it differentiates.  All calls
+ * enqueue work on the given stream and return without synchronising, except
+ * gsr_read_info, which waits for the stream.
+ *
+ * Errors: argument errors are returned synchronously (GSR_EINVAL, with a
+ * message in gsr_last_error).  Launch failures return GSR_ECUDA.  Errors
+ * found on the device (key capacity exceeded, a bounded wait that ran out)
+ * are recorded in the workspace and reported by gsr_read_info; the outputs of
+ * such a call are undefined.
+ *
+ * Parameter layout is planar ("[K][N]": component k of Gaussian g at k*N+g).
+ * Conventions (readings of the paper, which inherits them from 3DGS):
+ * pinhole camera with pixel centres at integer (x, y), u = fx x/z + cx;
+ * T_cw = [W | t] maps world to camera (camera looks down +z); quaternions are
+ * (w, x, y, z) and need not be normalised; scales are log-scales; opacity is
+ * sigmoid(logit); colour = max(0, sum_k SH_k Y_k(dir) + 0.5) with real SH of
+ * degree <= 3 (Condon-Shortley phase), dir from the camera centre to the mean.
+ * Rules: cull z <= 0.2; Sigma' = J W Sigma W^T J^T + 0.3 I (J with x/z, y/z
+ * clamped to 1.3x the half field of view); per pixel, Gaussians with
+ * Mahalanobis d^2 <= 9 in depth order; alpha = min(0.99, sigma exp(-d^2/2));
+ * alpha < 1/255 skipped; stop before the Gaussian that would take the
+ * transmittance below 1e-4.  Depth output = sum_i w_i z_i, opacity output =
+ * 1 - T_final.  Everything is computed in FP32.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSR_ABI_VERSION 1
+#define GSR_MAX_VIEWS 64
+
+typedef enum {
+    GSR_OK = 0,
+    GSR_EINVAL = -1,     /* bad argument (synchronous) */
+    GSR_ECAPACITY = -2,  /* device: more tile keys than the workspace holds */
+    GSR_ECUDA = -3,      /* a CUDA call or launch failed */
+    GSR_ETIMEOUT = -4,   /* device: a bounded inter-block wait gave up */
+    GSR_ENOTREADY = -5,  /* backward called without a matching forward */
+    GSR_EINTERNAL = -6   /* device: an internal consistency check failed */
+} gsr_status;
+
+/* Same handle type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *gsr_stream;
+
+typedef struct gsr_ctx gsr_ctx;
+
+/* Library configuration, fixed for the lifetime of a context. */
+typedef struct {
+    int tile;              /* screen tile edge in pixels: 8, 16 or 32 (0 = 16) */
+    uint32_t spin_limit;   /* iterations before a bounded device wait gives up (0 = default) */
+    int flags;             /* 0, or GSR_TEST_STALL_SORT (test hook, see below) */
+} gsr_config;
+
+/* Test hook for the bounded-wait path: the first tile of the first radix-sort
+ * pass never publishes its digit counts, so the next tile's look-back wait
+ * runs out after spin_limit iterations and the call reports GSR_ETIMEOUT
+ * (outputs undefined).  Never set outside tests. */
+#define GSR_TEST_STALL_SORT 1
+
+/* The Gaussian map (Sec. 3.3: position P, rotation r, scale s, density
+ * sigma, SH coefficients).  Device pointers, float32, planar. */
+typedef struct {
+    int N;                        /* number of Gaussians, >= 0 */
+    int sh_degree;                /* 0..3 */
+    const float *means;           /* [3][N] world position */
+    const float *log_scales;      /* [3][N] log of the axis scales */
+    const float *quats;           /* [4][N] (w, x, y, z), unnormalised */
+    const float *opacity_logits;  /* [N] sigma = sigmoid(logit) */
+    const float *sh;              /* [(deg+1)^2 * 3][N], row = coeff*3 + channel */
+} gsr_gaussians;
+
+/* One keyframe: intrinsics (host values), pose and outputs (device). */
+typedef struct {
+    int H, W;                 /* image size, 1..16384 each */
+    float fx, fy, cx, cy;     /* pinhole intrinsics (host values) */
+    const float *T_cw;        /* device, 12 floats, row-major [W | t] world->camera */
+    float *color;             /* device out [3][H][W] */
+    float *depth;             /* device out [H][W] (may be NULL) */
+    float *alpha;             /* device out [H][W] (may be NULL) */
+} gsr_view;
+
+/* Upstream gradients of one keyframe (device; NULL means zero) and the
+ * output pose gradient: dL/dxi for the left perturbation T_cw <- Exp(xi) T_cw,
+ * xi = (rho, phi), at xi = 0. */
+typedef struct {
+    const float *d_color;     /* [3][H][W] or NULL */
+    const float *d_depth;     /* [H][W] or NULL */
+    const float *d_alpha;     /* [H][W] or NULL */
+    float *d_pose;            /* out [6] or NULL */
+} gsr_view_grad;
+
+/* Output parameter gradients (device, same layouts as gsr_gaussians),
+ * summed over the views of the batch.  accumulate != 0 adds into the arrays
+ * (also for d_pose); otherwise they are overwritten. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+    int accumulate;
+} gsr_grads;
+
+/* Device-side state of the last call on a workspace (gsr_read_info). */
+typedef struct {
+    int32_t status;              /* first device error (gsr_status), 0 = none */
+    uint32_t keys;               /* (Gaussian, tile) keys the last render produced */
+    uint32_t key_capacity;       /* keys the workspace holds */
+    uint32_t tiles;              /* screen tiles over all views */
+    uint64_t pairs_contributing; /* (pixel, Gaussian) pairs composited by the last render */
+} gsr_info;
+
+/* Target images for the L1 loss front end (device). */
+typedef struct {
+    const float *target_color;   /* [3][H][W] */
+    const float *target_depth;   /* [H][W] or NULL (no depth term) */
+    float *d_color;              /* out [3][H][W] dL/dcolor */
+    float *d_depth;              /* out [H][W] dL/ddepth, or NULL */
+} gsr_l1_view;
+
+/* Creates a context (host memory only).  cfg may be NULL for defaults.
+ * Returns GSR_EINVAL for an unsupported tile size. */
+gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out);
+
+/* Frees a context.  NULL is ignored. */
+gsr_status gsr_destroy(gsr_ctx *ctx);
+
+/* Bytes of workspace for N Gaussians, these V views and room for
+ * key_capacity (Gaussian, tile) keys (0 = a default estimate of 8 keys per
+ * (view, Gaussian) pair, at least 1M).  Host only. */
+gsr_status gsr_workspace_size(gsr_ctx *ctx, int N, const gsr_view *views, int V,
+                              size_t key_capacity, size_t *bytes);
+
+/* Forward render of V keyframes (1..GSR_MAX_VIEWS) in one batched pass:
+ * projection (EWA, SH colour), tile binning with a depth-keyed radix sort,
+ * front-to-back compositing (Sec. 3.3, Eq. "rendering").  Writes each view's
+ * color/depth/alpha and keeps in the workspace what the backward needs.
+ * ws must be 256-byte aligned and ws_bytes >= gsr_workspace_size(..., cap)
+ * for some cap; the key capacity is derived from ws_bytes. */
+gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
+                      void *ws, size_t ws_bytes, gsr_stream stream);
+
+/* Backward of the last gsr_render on ws: back-to-front replay from the stored
+ * final transmittance and contributor index, then projection/SH backward and
+ * the per-view SE(3) pose reduction.  grads[v] gives view v's upstream
+ * gradients and pose output.  Returns GSR_ENOTREADY if ws was not rendered
+ * with the same N, views and tile size. */
+gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                               const gsr_view_grad *grads, int V, const gsr_grads *out,
+                               void *ws, size_t ws_bytes, gsr_stream stream);
+
+/* Waits for stream, then copies the workspace's device state into *info
+ * (host).  Use it to detect GSR_ECAPACITY (grow key_capacity to info->keys
+ * and render again) or GSR_ETIMEOUT. */
+gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info *info,
+                         gsr_stream stream);
+
+/* L1 loss front end (the L1 terms of Eq. "rnd_loss"): for each view,
+ * loss += color_weight * mean|C - C*| + depth_weight * mean|D - D*| over its
+ * pixels (colour mean over 3 channels), and writes dL/dC, dL/dD.  Reads the
+ * rendered color/depth of views[v].  loss: device float, overwritten. */
+gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V,
+                       float color_weight, float depth_weight, float *loss, gsr_stream stream);
+
+/* Stage events (a profiling aid).  events holds GSR_STAGE_EVENTS cudaEvent_t
+ * handles created by the caller (copied at this call), or is NULL to stop.
+ * While set, gsr_render records events[0] on its stream before its first
+ * launch and events[1+k] after forward stage k (0 preprocess, 1 scan + key
+ * duplication, 2 radix sort, 3 tile ranges, 4 blend); gsr_render_backward
+ * records events[6] before its first launch and events[7+k] after backward
+ * stage k (0 gradient clear, 1 blend backward, 2 preprocess backward with the
+ * pose reduction).  Elapsed times between consecutive events are the stage
+ * durations on the device. */
+#define GSR_STAGE_EVENTS 10
+gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events);
+
+/* Message of the last synchronous error on ctx (host string owned by ctx). */
+const char *gsr_last_error(const gsr_ctx *ctx);
+
+/* Name of a status code. */
+const char *gsr_status_string(gsr_status s);
+
+/* GSR_ABI_VERSION of the built library. */
+int gsr_abi_version(void);
+
+/* sizeof of the ABI structs, for binding checks: 0 gsr_config, 1
+ * gsr_gaussians, 2 gsr_view, 3 gsr_view_grad, 4 gsr_grads, 5 gsr_info,
+ * 6 gsr_l1_view; 0 for other values. */
+size_t gsr_abi_sizeof(int which);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

@@ -1,0 +1,171 @@
+"""ctypes binding of libgsr.so (include/gsr.h): argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels; this module converts
+Python/torch objects into the C structs and raises on any non-OK status.  It
+fails loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libgsr.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
+
+MAX_VIEWS = 64
+STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
+          -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
+OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+TEST_STALL_SORT = 1
+STAGE_EVENTS = 10
+# stage k lasts from event STAGE_SPANS[k][0] to STAGE_SPANS[k][1]
+STAGES = ("preprocess", "scan_duplicate", "sort", "ranges", "blend_fwd", "clear", "blend_bwd", "preprocess_bwd")
+STAGE_SPANS = ((0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (6, 7), (7, 8), (8, 9))
+
+_p = ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("flags", ctypes.c_int)]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("sh_degree", ctypes.c_int), ("means", _p), ("log_scales", _p),
+                ("quats", _p), ("opacity_logits", _p), ("sh", _p)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("T_cw", _p), ("color", _p), ("depth", _p),
+                ("alpha", _p)]
+
+
+class ViewGrad(ctypes.Structure):
+    _fields_ = [("d_color", _p), ("d_depth", _p), ("d_alpha", _p), ("d_pose", _p)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("means", _p), ("log_scales", _p), ("quats", _p), ("opacity_logits", _p), ("sh", _p),
+                ("accumulate", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("keys", ctypes.c_uint32), ("key_capacity", ctypes.c_uint32),
+                ("tiles", ctypes.c_uint32), ("pairs_contributing", ctypes.c_uint64)]
+
+
+class L1View(ctypes.Structure):
+    _fields_ = [("target_color", _p), ("target_depth", _p), ("d_color", _p), ("d_depth", _p)]
+
+
+ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View]
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class GsrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def declared_functions() -> list:
+    """Names of the functions include/gsr.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(gsr_[a-z_0-9]+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgsr.so is not built ({path}); run `python -m paper_2411_17660_b300.build`")
+    lib = ctypes.CDLL(path)
+    c_int, c_size = ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "gsr_create": (c_int, [ctypes.POINTER(Config), ctypes.POINTER(_p)]),
+        "gsr_destroy": (c_int, [_p]),
+        "gsr_workspace_size": (c_int, [_p, c_int, ctypes.POINTER(View), c_int, c_size, ctypes.POINTER(c_size)]),
+        "gsr_render": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, _p, c_size, _p]),
+        "gsr_render_backward": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
+                                         ctypes.POINTER(ViewGrad), c_int, ctypes.POINTER(Grads), _p, c_size, _p]),
+        "gsr_read_info": (c_int, [_p, _p, c_size, ctypes.POINTER(Info), _p]),
+        "gsr_l1_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
+                                ctypes.c_float, _p, _p]),
+        "gsr_set_stage_events": (c_int, [_p, ctypes.POINTER(_p)]),
+        "gsr_last_error": (ctypes.c_char_p, [_p]),
+        "gsr_status_string": (ctypes.c_char_p, [c_int]),
+        "gsr_abi_version": (c_int, []),
+        "gsr_abi_sizeof": (c_size, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Context:
+    """Owns one gsr_ctx (host memory only)."""
+
+    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0):
+        self.lib = load()
+        cfg = Config(tile, spin_limit, flags)
+        h = _p()
+        st = self.lib.gsr_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise GsrError(st, f"gsr_create(tile={tile})")
+        self.h = h
+        self.tile = tile
+
+    def __del__(self):
+        lib, h = getattr(self, "lib", None), getattr(self, "h", None)
+        if lib is not None and h:
+            lib.gsr_destroy(h)
+            self.h = None
+
+    def check(self, st: int, what: str):
+        if st != OK:
+            raise GsrError(st, f"{what}: {self.lib.gsr_last_error(self.h).decode()}")
+
+    def workspace_size(self, N: int, views, key_capacity: int = 0) -> int:
+        arr = (View * len(views))(*views)
+        out = ctypes.c_size_t()
+        self.check(self.lib.gsr_workspace_size(self.h, N, arr, len(views), key_capacity, ctypes.byref(out)),
+                   "gsr_workspace_size")
+        return out.value
+
+    def render(self, g: Gaussians, views, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        arr = (View * len(views))(*views)
+        return self.lib.gsr_render(self.h, ctypes.byref(g), arr, len(views), ws_ptr, ws_bytes, stream)
+
+    def render_backward(self, g: Gaussians, views, vgrads, out: Grads, ws_ptr: int, ws_bytes: int,
+                        stream: int) -> int:
+        arr = (View * len(views))(*views)
+        garr = (ViewGrad * len(vgrads))(*vgrads)
+        return self.lib.gsr_render_backward(self.h, ctypes.byref(g), arr, garr, len(views), ctypes.byref(out),
+                                            ws_ptr, ws_bytes, stream)
+
+    def read_info(self, ws_ptr: int, ws_bytes: int, stream: int) -> Info:
+        info = Info()
+        self.check(self.lib.gsr_read_info(self.h, ws_ptr, ws_bytes, ctypes.byref(info), stream), "gsr_read_info")
+        return info
+
+    def set_stage_events(self, handles):
+        """handles: GSR_STAGE_EVENTS raw cudaEvent_t values, or None to stop."""
+        if handles is None:
+            self.check(self.lib.gsr_set_stage_events(self.h, None), "gsr_set_stage_events")
+            return
+        arr = (_p * STAGE_EVENTS)(*handles)
+        self.check(self.lib.gsr_set_stage_events(self.h, arr), "gsr_set_stage_events")
+
+    def l1_loss(self, views, targets, color_weight: float, depth_weight: float, loss_ptr: int, stream: int):
+        arr = (View * len(views))(*views)
+        tarr = (L1View * len(targets))(*targets)
+        self.check(self.lib.gsr_l1_loss(self.h, arr, tarr, len(views), color_weight, depth_weight, loss_ptr,
+                                        stream), "gsr_l1_loss")

@@ -1,0 +1,475 @@
+// api.cu -- the C ABI of include/gsr.h: argument checks, the workspace
+// layout, and the launch sequence of the forward and backward passes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <new>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct gsr_ctx {
+    int tile = 16;
+    uint32_t spin = gsr::kDefaultSpin;
+    int flags = 0;
+    int sm_count = 0;
+    std::string err;
+    struct Rec {
+        const void *ws;
+        size_t bytes;
+        int N, V, deg;
+        std::vector<int> dims;
+    };
+    std::vector<Rec> recs;  // recent forwards, for the backward's checks
+    // caller-provided stage events (gsr_set_stage_events), 0..9
+    bool timing = false;
+    cudaEvent_t ev[GSR_STAGE_EVENTS] = {};
+    void mark(int slot, cudaStream_t st) {
+        if (timing && ev[slot]) cudaEventRecord(ev[slot], st);
+    }
+};
+
+namespace gsr {
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3;
+    size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, vg_grads, pose_partials;
+    size_t total;
+    uint64_t VN;
+    uint32_t cap, lb_tiles, scan_blocks, pose_blocks, total_pixels, total_tiles;
+    int passes;
+};
+
+void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layout &L) {
+    L.VN = (uint64_t)V * (uint64_t)N;
+    uint64_t px = 0, tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        px += (uint64_t)views[v].H * views[v].W;
+        tiles += (uint64_t)((views[v].W + tile - 1) / tile) * ((views[v].H + tile - 1) / tile);
+    }
+    L.total_pixels = (uint32_t)px;
+    L.total_tiles = (uint32_t)tiles;
+    int tbits = 1;
+    while ((1ull << tbits) < tiles) ++tbits;
+    L.passes = (32 + tbits + 7) / 8;
+    L.cap = (uint32_t)cap;
+    L.lb_tiles = (uint32_t)((cap + kSortTile - 1) / kSortTile);
+    L.scan_blocks = (uint32_t)((L.VN + kScanChunk - 1) / kScanChunk);
+    if (L.scan_blocks == 0) L.scan_blocks = 1;
+    L.pose_blocks = (uint32_t)((N + 255) / 256);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    L.hdr = take(sizeof(WsHeader));
+    L.counts = take(4 * L.VN);
+    L.offsets = take(4 * L.VN);
+    L.scan_partials = take(8ull * L.scan_blocks);
+    L.rec0 = take(16 * L.VN);
+    L.rec1 = take(16 * L.VN);
+    L.rec2 = take(16 * L.VN);
+    L.rec3 = take(16 * L.VN);
+    L.hist = take(4ull * kMaxPasses * kRadix);
+    L.ranges = take(8ull * L.total_tiles);
+    L.T_final = take(4ull * L.total_pixels);
+    L.last = take(4ull * L.total_pixels);
+    L.vg_grads = take(4ull * kVGGrads * L.VN);
+    L.pose_partials = take(24ull * V * (L.pose_blocks ? L.pose_blocks : 1));
+    L.keys0 = take(8 * cap);
+    L.keys1 = take(8 * cap);
+    L.vals0 = take(4 * cap);
+    L.vals1 = take(4 * cap);
+    L.lookback = take(2ull * L.lb_tiles * kRadix * 4);
+    L.total = o;
+}
+
+// Largest key capacity (a multiple of the sort tile) whose layout fits.
+uint32_t capacity_for(int N, const gsr_view *views, int V, int tile, size_t bytes) {
+    Layout L0;
+    make_layout(N, views, V, tile, 0, L0);
+    if (bytes <= L0.total + 8 * 256) return 0;
+    const double per_key = 24.0 + 2.0 * kRadix * 4 / kSortTile;
+    uint64_t cap = (uint64_t)((double)(bytes - L0.total - 8 * 256) / per_key);
+    cap = cap / kSortTile * kSortTile;
+    const uint64_t kMaxCap = ((1ull << 30) - 1) / kSortTile * kSortTile;
+    if (cap > kMaxCap) cap = kMaxCap;
+    while (cap > 0) {
+        Layout L;
+        make_layout(N, views, V, tile, cap, L);
+        if (L.total <= bytes) break;
+        cap -= kSortTile;
+    }
+    return (uint32_t)cap;
+}
+
+Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) {
+    char *b = static_cast<char *>(base);
+    Ws w;
+    w.hdr = reinterpret_cast<WsHeader *>(b + L.hdr);
+    w.counts = reinterpret_cast<uint32_t *>(b + L.counts);
+    w.offsets = reinterpret_cast<uint32_t *>(b + L.offsets);
+    w.scan_partials = reinterpret_cast<unsigned long long *>(b + L.scan_partials);
+    w.rec0 = reinterpret_cast<float4 *>(b + L.rec0);
+    w.rec1 = reinterpret_cast<float4 *>(b + L.rec1);
+    w.rec2 = reinterpret_cast<float4 *>(b + L.rec2);
+    w.rec3 = reinterpret_cast<float4 *>(b + L.rec3);
+    w.keys[0] = reinterpret_cast<unsigned long long *>(b + L.keys0);
+    w.keys[1] = reinterpret_cast<unsigned long long *>(b + L.keys1);
+    w.vals[0] = reinterpret_cast<uint32_t *>(b + L.vals0);
+    w.vals[1] = reinterpret_cast<uint32_t *>(b + L.vals1);
+    w.hist = reinterpret_cast<uint32_t *>(b + L.hist);
+    w.lookback = reinterpret_cast<uint32_t *>(b + L.lookback);
+    w.ranges = reinterpret_cast<uint2 *>(b + L.ranges);
+    w.T_final = reinterpret_cast<float *>(b + L.T_final);
+    w.last = reinterpret_cast<uint32_t *>(b + L.last);
+    w.vg_grads = reinterpret_cast<float *>(b + L.vg_grads);
+    w.pose_partials = reinterpret_cast<float *>(b + L.pose_partials);
+    w.N = (uint32_t)N;
+    w.V = (uint32_t)V;
+    w.VN = (uint32_t)L.VN;
+    w.cap = L.cap;
+    w.lb_tiles = L.lb_tiles;
+    w.scan_blocks = L.scan_blocks;
+    w.pose_blocks = L.pose_blocks;
+    w.total_pixels = L.total_pixels;
+    w.total_tiles = L.total_tiles;
+    w.passes = L.passes;
+    w.spin_limit = spin;
+    w.test_flags = flags;
+    return w;
+}
+
+__global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles) {
+    uint32_t *p = reinterpret_cast<uint32_t *>(h);
+    for (int i = threadIdx.x; i < (int)(sizeof(WsHeader) / 4); i += blockDim.x) p[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        h->key_capacity = cap;
+        h->tiles = tiles;
+    }
+}
+
+gsr_status fail(gsr_ctx *ctx, gsr_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+gsr_status fail(gsr_ctx *ctx, gsr_status s, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+gsr_status cuda_fail(gsr_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, GSR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+gsr_status check_views(gsr_ctx *ctx, const gsr_view *views, int V, bool need_outputs) {
+    if (!views) return fail(ctx, GSR_EINVAL, "views is NULL");
+    if (V < 1 || V > GSR_MAX_VIEWS) return fail(ctx, GSR_EINVAL, "V=%d outside 1..%d", V, GSR_MAX_VIEWS);
+    uint64_t px = 0;
+    for (int v = 0; v < V; ++v) {
+        const gsr_view &w = views[v];
+        if (w.H < 1 || w.W < 1 || w.H > 16384 || w.W > 16384)
+            return fail(ctx, GSR_EINVAL, "view %d: size %dx%d outside 1..16384", v, w.W, w.H);
+        if (!(w.fx > 0.f) || !(w.fy > 0.f) || !std::isfinite(w.fx) || !std::isfinite(w.fy) ||
+            !std::isfinite(w.cx) || !std::isfinite(w.cy))
+            return fail(ctx, GSR_EINVAL, "view %d: intrinsics must be finite with fx, fy > 0", v);
+        if (!w.T_cw) return fail(ctx, GSR_EINVAL, "view %d: T_cw is NULL", v);
+        if (need_outputs && !w.color) return fail(ctx, GSR_EINVAL, "view %d: color output is NULL", v);
+        px += (uint64_t)w.H * w.W;
+    }
+    if (px >= (1ull << 32)) return fail(ctx, GSR_EINVAL, "more than 2^32 pixels in the batch");
+    return GSR_OK;
+}
+
+gsr_status check_gaussians(gsr_ctx *ctx, const gsr_gaussians *gs, int V) {
+    if (!gs) return fail(ctx, GSR_EINVAL, "gaussians is NULL");
+    if (gs->N < 0) return fail(ctx, GSR_EINVAL, "N=%d is negative", gs->N);
+    if (gs->sh_degree < 0 || gs->sh_degree > 3) return fail(ctx, GSR_EINVAL, "sh_degree=%d outside 0..3", gs->sh_degree);
+    if ((uint64_t)gs->N * (uint64_t)V >= (1ull << 31)) return fail(ctx, GSR_EINVAL, "N*V must be below 2^31");
+    if (gs->N > 0 && (!gs->means || !gs->log_scales || !gs->quats || !gs->opacity_logits || !gs->sh))
+        return fail(ctx, GSR_EINVAL, "a Gaussian parameter pointer is NULL");
+    return GSR_OK;
+}
+
+GaussianPtrs gaussian_ptrs(const gsr_gaussians *gs) {
+    GaussianPtrs g;
+    g.N = gs->N;
+    g.sh_degree = gs->sh_degree;
+    g.means = gs->means;
+    g.log_scales = gs->log_scales;
+    g.quats = gs->quats;
+    g.opacity_logits = gs->opacity_logits;
+    g.sh = gs->sh;
+    return g;
+}
+
+void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile) {
+    memset(&vt, 0, sizeof vt);
+    vt.V = V;
+    vt.tile = tile;
+    uint32_t toff = 0, poff = 0;
+    for (int v = 0; v < V; ++v) {
+        ViewParams &p = vt.v[v];
+        const gsr_view &w = views[v];
+        p.H = w.H;
+        p.W = w.W;
+        p.fx = w.fx;
+        p.fy = w.fy;
+        p.cx = w.cx;
+        p.cy = w.cy;
+        p.T_cw = w.T_cw;
+        p.color = w.color;
+        p.depth = w.depth;
+        p.alpha = w.alpha;
+        if (grads) {
+            p.d_color = grads[v].d_color;
+            p.d_depth = grads[v].d_depth;
+            p.d_alpha = grads[v].d_alpha;
+            p.d_pose = grads[v].d_pose;
+        }
+        p.tiles_x = (w.W + tile - 1) / tile;
+        p.tiles_y = (w.H + tile - 1) / tile;
+        p.tile_offset = toff;
+        p.pixel_offset = poff;
+        toff += (uint32_t)(p.tiles_x * p.tiles_y);
+        poff += (uint32_t)(w.H * w.W);
+    }
+    vt.total_tiles = toff;
+    vt.total_pixels = poff;
+}
+
+int sm_count(gsr_ctx *ctx) {
+    if (ctx->sm_count == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            ctx->sm_count = n;
+        else
+            ctx->sm_count = 148;
+    }
+    return ctx->sm_count;
+}
+
+}  // namespace
+}  // namespace gsr
+
+using namespace gsr;
+
+extern "C" {
+
+gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
+    if (!out) return GSR_EINVAL;
+    *out = nullptr;
+    int tile = 16, flags = 0;
+    uint32_t spin = kDefaultSpin;
+    if (cfg) {
+        if (cfg->tile != 0) tile = cfg->tile;
+        if (cfg->spin_limit != 0) spin = cfg->spin_limit;
+        if (cfg->flags & ~GSR_TEST_STALL_SORT) return GSR_EINVAL;
+        flags = cfg->flags;
+    }
+    if (tile != 8 && tile != 16 && tile != 32) return GSR_EINVAL;
+    gsr_ctx *c = new (std::nothrow) gsr_ctx;
+    if (!c) return GSR_EINVAL;
+    c->tile = tile;
+    c->spin = spin;
+    c->flags = flags;
+    *out = c;
+    return GSR_OK;
+}
+
+gsr_status gsr_destroy(gsr_ctx *ctx) {
+    delete ctx;
+    return GSR_OK;
+}
+
+gsr_status gsr_workspace_size(gsr_ctx *ctx, int N, const gsr_view *views, int V, size_t key_capacity, size_t *bytes) {
+    if (!ctx || !bytes) return fail(ctx, GSR_EINVAL, "ctx and bytes must be non-NULL");
+    gsr_status s = check_views(ctx, views, V, false);
+    if (s != GSR_OK) return s;
+    if (N < 0) return fail(ctx, GSR_EINVAL, "N=%d is negative", N);
+    if (key_capacity == 0) {
+        key_capacity = (size_t)8 * V * (size_t)N;
+        if (key_capacity < (1u << 20)) key_capacity = 1u << 20;
+    }
+    key_capacity = (key_capacity + kSortTile - 1) / kSortTile * kSortTile;
+    if (key_capacity >= (1u << 30)) return fail(ctx, GSR_EINVAL, "key_capacity must be below 2^30");
+    Layout L;
+    make_layout(N, views, V, ctx->tile, key_capacity, L);
+    *bytes = L.total + 8 * 256;
+    return GSR_OK;
+}
+
+gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, void *ws_ptr,
+                      size_t ws_bytes, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, true);
+    if (s != GSR_OK) return s;
+    if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
+    if (!ws_ptr || (reinterpret_cast<uintptr_t>(ws_ptr) & 255))
+        return fail(ctx, GSR_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    const uint32_t cap = capacity_for(gs->N, views, V, ctx->tile, ws_bytes);
+    if (cap == 0) return fail(ctx, GSR_EINVAL, "workspace of %zu bytes holds no tile keys", ws_bytes);
+    Layout L;
+    make_layout(gs->N, views, V, ctx->tile, cap, L);
+    ViewTable vt;
+    fill_views(vt, views, nullptr, V, ctx->tile);
+    const Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    const GaussianPtrs gp = gaussian_ptrs(gs);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    ctx->mark(0, st);
+    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, L.total_tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
+    if ((e = launch_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
+    ctx->mark(1, st);
+    if ((e = launch_scan_duplicate(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "scan/duplicate");
+    ctx->mark(2, st);
+    if ((e = launch_sort(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
+    ctx->mark(3, st);
+    if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
+    ctx->mark(4, st);
+    if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
+    ctx->mark(5, st);
+
+    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}};
+    for (int v = 0; v < V; ++v) {
+        r.dims.push_back(views[v].H);
+        r.dims.push_back(views[v].W);
+    }
+    for (auto it = ctx->recs.begin(); it != ctx->recs.end(); ++it)
+        if (it->ws == ws_ptr) {
+            ctx->recs.erase(it);
+            break;
+        }
+    ctx->recs.push_back(r);
+    if (ctx->recs.size() > 64) ctx->recs.erase(ctx->recs.begin());
+    return GSR_OK;
+}
+
+gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                               const gsr_view_grad *grads, int V, const gsr_grads *out, void *ws_ptr,
+                               size_t ws_bytes, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, false);
+    if (s != GSR_OK) return s;
+    if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
+    if (!grads) return fail(ctx, GSR_EINVAL, "grads is NULL");
+    if (!out || (gs->N > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh)))
+        return fail(ctx, GSR_EINVAL, "an output gradient pointer is NULL");
+    const gsr_ctx::Rec *rec = nullptr;
+    for (const auto &r : ctx->recs)
+        if (r.ws == ws_ptr) rec = &r;
+    bool match = rec && rec->bytes == ws_bytes && rec->N == gs->N && rec->V == V && rec->deg == gs->sh_degree;
+    for (int v = 0; match && v < V; ++v)
+        match = rec->dims[2 * v] == views[v].H && rec->dims[2 * v + 1] == views[v].W;
+    if (!match) return fail(ctx, GSR_ENOTREADY, "no forward with these Gaussians and views on this workspace");
+    const uint32_t cap = capacity_for(gs->N, views, V, ctx->tile, ws_bytes);
+    Layout L;
+    make_layout(gs->N, views, V, ctx->tile, cap, L);
+    ViewTable vt;
+    fill_views(vt, views, grads, V, ctx->tile);
+    const Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    const GaussianPtrs gp = gaussian_ptrs(gs);
+    GradPtrs gout;
+    gout.means = out->means;
+    gout.log_scales = out->log_scales;
+    gout.quats = out->quats;
+    gout.opacity_logits = out->opacity_logits;
+    gout.sh = out->sh;
+    gout.accumulate = out->accumulate;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    ctx->mark(6, st);
+    cudaError_t e = cudaMemsetAsync(w.vg_grads, 0, sizeof(float) * kVGGrads * L.VN, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear");
+    ctx->mark(7, st);
+    if ((e = launch_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
+    ctx->mark(8, st);
+    if ((e = launch_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess backward");
+    ctx->mark(9, st);
+    return GSR_OK;
+}
+
+gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info *info, gsr_stream stream) {
+    if (!ctx || !ws || !info || ws_bytes < sizeof(WsHeader)) return fail(ctx, GSR_EINVAL, "bad arguments");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    WsHeader h;
+    e = cudaMemcpy(&h, ws, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read header");
+    info->status = h.status;
+    info->keys = h.keys;
+    info->key_capacity = h.key_capacity;
+    info->tiles = h.tiles;
+    info->pairs_contributing = h.pairs_contrib;
+    return GSR_OK;
+}
+
+gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V, float color_weight,
+                       float depth_weight, float *loss, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, true);
+    if (s != GSR_OK) return s;
+    if (!targets || !loss) return fail(ctx, GSR_EINVAL, "targets and loss must be non-NULL");
+    for (int v = 0; v < V; ++v)
+        if (!targets[v].target_color || !targets[v].d_color)
+            return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
+    ViewTable vt;
+    fill_views(vt, views, nullptr, V, ctx->tile);
+    cudaError_t e = launch_l1_loss(vt, targets, color_weight, depth_weight, loss, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "l1 loss");
+    return GSR_OK;
+}
+
+gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events) {
+    if (!ctx) return GSR_EINVAL;
+    ctx->timing = events != nullptr;
+    for (int k = 0; k < GSR_STAGE_EVENTS; ++k) ctx->ev[k] = events ? static_cast<cudaEvent_t>(events[k]) : nullptr;
+    return GSR_OK;
+}
+
+const char *gsr_last_error(const gsr_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+const char *gsr_status_string(gsr_status s) {
+    switch (s) {
+        case GSR_OK: return "GSR_OK";
+        case GSR_EINVAL: return "GSR_EINVAL";
+        case GSR_ECAPACITY: return "GSR_ECAPACITY";
+        case GSR_ECUDA: return "GSR_ECUDA";
+        case GSR_ETIMEOUT: return "GSR_ETIMEOUT";
+        case GSR_ENOTREADY: return "GSR_ENOTREADY";
+        case GSR_EINTERNAL: return "GSR_EINTERNAL";
+    }
+    return "unknown";
+}
+
+int gsr_abi_version(void) { return GSR_ABI_VERSION; }
+
+size_t gsr_abi_sizeof(int which) {
+    switch (which) {
+        case 0: return sizeof(gsr_config);
+        case 1: return sizeof(gsr_gaussians);
+        case 2: return sizeof(gsr_view);
+        case 3: return sizeof(gsr_view_grad);
+        case 4: return sizeof(gsr_grads);
+        case 5: return sizeof(gsr_info);
+        case 6: return sizeof(gsr_l1_view);
+    }
+    return 0;
+}
+
+}  // extern "C"

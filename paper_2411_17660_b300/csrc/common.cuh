@@ -1,0 +1,203 @@
+// common.cuh -- constants, launch-parameter structs and small numeric helpers
+// shared by the rasteriser kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsr.h"
+
+namespace gsr {
+
+// ---------------------------------------------------------------- rules
+// Readings of the rendering rules (3DGS conventions the paper inherits,
+// Sec. 3.3): near plane, low-pass dilation, 3-sigma cutoff, alpha skip and
+// clamp, transmittance stop, Jacobian clamp.
+constexpr float kNearZ = 0.2f;
+constexpr float kDilation = 0.3f;
+constexpr float kCutoffD2 = 9.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kFovClamp = 1.3f;
+// The blend works with s = 0.5*log2(e)*d^2, so exp(-d^2/2) = 2^-s.
+constexpr float kHalfLog2e = 0.721347520444481703680f;      // 0.5 / ln 2
+constexpr float kSqrtHalfLog2e = 0.849321800288019133f;     // sqrt(0.5 / ln 2)
+constexpr float kLn2 = 0.693147180559945309417f;
+constexpr float kLog2_255 = 7.99435343685885793f;           // log2(255)
+
+constexpr int kMaxPasses = 8;     // 8-bit radix digits of a 64-bit key
+constexpr int kRadix = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 12;    // keys per thread per sort tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kVGGrads = 10;      // per (view, Gaussian) screen-space grads
+constexpr uint32_t kDefaultSpin = 1u << 24;
+
+// ---------------------------------------------------------------- params
+struct ViewParams {
+    int H, W;
+    float fx, fy, cx, cy;
+    const float *T_cw;
+    float *color, *depth, *alpha;
+    const float *d_color, *d_depth, *d_alpha;
+    float *d_pose;
+    int tiles_x, tiles_y;
+    uint32_t tile_offset;   // first global tile id of this view
+    uint32_t pixel_offset;  // first pixel in the concatenated per-pixel buffers
+};
+
+// Passed by value (__grid_constant__) so that a captured CUDA graph replays
+// it without any host-side copy.
+struct ViewTable {
+    int V;
+    int tile;
+    uint32_t total_tiles;
+    uint32_t total_pixels;
+    ViewParams v[GSR_MAX_VIEWS];
+};
+
+struct GaussianPtrs {
+    int N, sh_degree;
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+};
+
+// Device-side state at the start of the workspace.
+struct WsHeader {
+    int32_t status;                 // first device error (gsr_status)
+    uint32_t keys;                  // keys produced by the scan (clamped to 2^32-1)
+    uint32_t key_capacity;
+    uint32_t tiles;
+    unsigned long long pairs_contrib;
+    uint32_t sort_final;            // key buffer holding the sorted result
+    uint32_t sort_counter[kMaxPasses];
+    uint32_t pad[64 - 7 - kMaxPasses];
+};
+static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
+
+// Typed views of one workspace; offsets come from the host layout code.
+struct Ws {
+    WsHeader *hdr;
+    uint32_t *counts;        // [V*N] tiles touched by (view, Gaussian)
+    uint32_t *offsets;       // [V*N] exclusive scan of counts
+    unsigned long long *scan_partials;  // [scan_blocks]
+    float4 *rec0;            // [V*N] (u_hi, v_hi, u_lo, v_lo)
+    float4 *rec1;            // [V*N] (m00, m01, m11, s_max)
+    float4 *rec2;            // [V*N] (r, g, b, z)
+    float4 *rec3;            // [V*N] (log2 opacity, Sxx, Sxy, Syy)
+    unsigned long long *keys[2];
+    uint32_t *vals[2];
+    uint32_t *hist;          // [kMaxPasses][256]
+    uint32_t *lookback;      // [kMaxPasses][lb_tiles][256]
+    uint2 *ranges;           // [total_tiles]
+    float *T_final;          // [total_pixels]
+    uint32_t *last;          // [total_pixels] last contributor index + 1
+    float *vg_grads;         // [V][10][N]
+    float *pose_partials;    // [V][pose_blocks][6]
+    uint32_t N, V, VN;
+    uint32_t cap, lb_tiles, scan_blocks, pose_blocks;
+    uint32_t total_pixels, total_tiles;
+    int passes;
+    uint32_t spin_limit;
+    int test_flags;
+};
+
+__device__ __forceinline__ void set_status(WsHeader *h, int code) {
+    atomicCAS(reinterpret_cast<int *>(&h->status), 0, code);
+}
+
+// ---------------------------------------------------------------- numerics
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProd) written with
+// round-to-nearest intrinsics so that no contraction or reassociation can
+// change them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// w.x + t with a compensated dot product (Ogita-Rump-Oishi Dot2): result as
+// hi + lo, accurate to about one FP32 rounding of the exact value.
+__device__ __forceinline__ void dot3_plus(float w0, float w1, float w2, float t, float x0, float x1,
+                                          float x2, float &hi, float &lo) {
+    float p, s, h, r, q;
+    two_prod(w0, x0, p, s);
+    two_prod(w1, x1, h, r);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    two_prod(w2, x2, h, r);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    two_sum(p, t, p, q);
+    s = __fadd_rn(s, q);
+    hi = __fadd_rn(p, s);
+    lo = __fsub_rn(s, __fsub_rn(hi, p));
+}
+
+// f*(xh+xl)/(zh+zl) + c as hi + lo (double-float), for pixel coordinates
+// whose fractional part must survive |u| up to thousands of pixels.
+__device__ __forceinline__ void project_coord(float f, float c, float xh, float xl, float zh, float zl,
+                                              float &hi, float &lo) {
+    const float q1 = __fdiv_rn(xh, zh);
+    float r = __fmaf_rn(-q1, zh, xh);          // exact remainder xh - q1*zh
+    r = __fadd_rn(r, __fsub_rn(xl, __fmul_rn(q1, zl)));
+    const float q2 = __fdiv_rn(r, zh);
+    float p, pe;
+    two_prod(f, q1, p, pe);
+    pe = __fmaf_rn(f, q2, pe);
+    float s, se;
+    two_sum(p, c, s, se);
+    se = __fadd_rn(se, pe);
+    hi = __fadd_rn(s, se);
+    lo = __fsub_rn(se, __fsub_rn(hi, s));
+}
+
+// a*d - b*c with the FMA trick (Kahan): accurate even under cancellation.
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = __fmul_rn(b, c);
+    const float e = __fmaf_rn(-b, c, w);
+    const float f = __fmaf_rn(a, d, -w);
+    return __fadd_rn(f, e);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Relaxed GPU-scope accesses for inter-block flags.
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, uint32_t tile) {
+    int v = 0;
+    while (v + 1 < vt.V && tile >= vt.v[v + 1].tile_offset) ++v;
+    return v;
+}
+
+}  // namespace gsr

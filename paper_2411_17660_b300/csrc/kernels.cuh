@@ -1,0 +1,31 @@
+// kernels.cuh -- launch wrappers of the rasteriser stages (host side).
+#pragma once
+
+#include "common.cuh"
+
+namespace gsr {
+
+struct GradPtrs {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+    int accumulate;
+};
+
+// preprocess.cu
+cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
+                                  cudaStream_t st);
+
+// binning.cu
+cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_t st);
+cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st);
+cudaError_t launch_ranges(const Ws &ws, int sm_count, cudaStream_t st);
+
+// blend.cu
+cudaError_t launch_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
+cudaError_t launch_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
+
+// loss.cu
+cudaError_t launch_l1_loss(const ViewTable &vt, const gsr_l1_view *targets, float color_weight, float depth_weight,
+                           float *loss, cudaStream_t st);
+
+}  // namespace gsr

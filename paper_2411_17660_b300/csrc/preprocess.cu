@@ -1,0 +1,389 @@
+// preprocess.cu -- per-Gaussian forward projection (activation, camera
+// transform, EWA projection, SH colour, exact tile count) and its backward
+// (projection/SH chain rule, per-view SE(3) pose reduction).  One thread per
+// Gaussian loops over the views of the batch, so the 59 parameters of a
+// Gaussian are read once per batch, not once per view.
+#include "kernels.cuh"
+#include "project.cuh"
+#include "sh.cuh"
+#include "spans.cuh"
+
+namespace gsr {
+
+__device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
+    for (int i = threadIdx.x; i < vt.V * 12; i += blockDim.x) {
+        const int v = i / 12, k = i % 12;
+        const float x = vt.v[v].T_cw[k];
+        if (k % 4 == 3)
+            s_pose[v].t[k / 4] = x;
+        else
+            s_pose[v].W[k / 4][k % 4] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)vt.V) {
+        Pose &p = s_pose[threadIdx.x];
+        for (int j = 0; j < 3; ++j) p.C[j] = -(p.W[0][j] * p.t[0] + p.W[1][j] * p.t[1] + p.W[2][j] * p.t[2]);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ forward
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
+                                                             const GaussianPtrs gp, const Ws ws) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ Pose s_pose[GSR_MAX_VIEWS];
+    load_poses(vt, s_pose);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= gp.N) return;
+    const size_t N = (size_t)gp.N;
+    GaussPre G;
+    gauss_pre(gp, g, G);
+    float sh[3 * K];
+    bool sh_loaded = false;
+    for (int v = 0; v < vt.V; ++v) {
+        const ViewParams &vp = vt.v[v];
+        const size_t i = (size_t)v * N + g;
+        uint32_t count = 0;
+        Proj p;
+        if (G.alive && project_view(G, s_pose[v], vp, p)) {
+            const float m00 = kSqrtHalfLog2e * p.l00, m01 = kSqrtHalfLog2e * p.l01, m11 = kSqrtHalfLog2e * p.l11;
+            float uh, ul, vh, vl;
+            project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
+            project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
+            if (isfinite(uh) && isfinite(vh))
+                count = visit_tile_spans(uh, vh, p.sxx, p.sxy, p.syy, m00, G.smax, vp.W, vp.H, vt.tile,
+                                         [](int, int, int) {});
+            if (count) {
+                if (!sh_loaded) {
+#pragma unroll
+                    for (int k = 0; k < 3 * K; ++k) sh[k] = gp.sh[(size_t)k * N + g];
+                    sh_loaded = true;
+                }
+                const Pose &ps = s_pose[v];
+                float dx = G.mx - ps.C[0], dy = G.my - ps.C[1], dz = G.mz - ps.C[2];
+                const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+                dx *= rn;
+                dy *= rn;
+                dz *= rn;
+                float Y[K];
+                sh_eval<DEG>(dx, dy, dz, Y);
+                float rgb[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.5f;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc = fmaf(sh[k * 3 + c], Y[k], acc);
+                    rgb[c] = fmaxf(acc, 0.f);
+                }
+                ws.rec0[i] = make_float4(uh, vh, ul, vl);
+                ws.rec1[i] = make_float4(m00, m01, m11, G.smax);
+                ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], p.zh);
+                ws.rec3[i] = make_float4(G.log2o, p.sxx, p.sxy, p.syy);
+            }
+        }
+        ws.counts[i] = count;
+    }
+}
+
+// ------------------------------------------------------------------ backward
+template <int DEG>
+__global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
+                                                             const GaussianPtrs gp, const Ws ws,
+                                                             const GradPtrs out) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int WARPS = 256 / 32;
+    __shared__ Pose s_pose[GSR_MAX_VIEWS];
+    __shared__ float s_part[GSR_MAX_VIEWS][WARPS][6];
+    load_poses(vt, s_pose);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = g < gp.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t N = (size_t)gp.N;
+    GaussPre G;
+    if (active) gauss_pre(gp, g, G);
+    float sh[3 * K], dsh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+    bool sh_loaded = false;
+    float dmu[3] = {0.f, 0.f, 0.f}, dM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float dop = 0.f;
+
+    for (int v = 0; v < vt.V; ++v) {
+        const ViewParams &vp = vt.v[v];
+        const Pose &ps = s_pose[v];
+        float pose6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const size_t i = (size_t)v * N + g;
+        bool vis = active && ws.counts[i] > 0;
+        Proj p;
+        if (vis) vis = project_view(G, ps, vp, p);
+        if (vis) {
+            float sg[kVGGrads];
+#pragma unroll
+            for (int c = 0; c < kVGGrads; ++c) sg[c] = ws.vg_grads[((size_t)v * kVGGrads + c) * N + g];
+            float dpc[3] = {0.f, 0.f, 0.f};
+
+            // colour -> SH coefficients and the view direction
+            if (!sh_loaded) {
+#pragma unroll
+                for (int k = 0; k < 3 * K; ++k) sh[k] = gp.sh[(size_t)k * N + g];
+                sh_loaded = true;
+            }
+            const float ex = G.mx - ps.C[0], ey = G.my - ps.C[1], ez = G.mz - ps.C[2];
+            const float rn = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
+            const float dx = ex * rn, dy = ey * rn, dz = ez * rn;
+            float Y[K];
+            sh_eval<DEG>(dx, dy, dz, Y);
+            float dr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc = fmaf(sh[k * 3 + c], Y[k], acc);
+                dr[c] = acc > 0.f ? sg[6 + c] : 0.f;
+            }
+            float wk[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                dsh[k * 3 + 0] = fmaf(dr[0], Y[k], dsh[k * 3 + 0]);
+                dsh[k * 3 + 1] = fmaf(dr[1], Y[k], dsh[k * 3 + 1]);
+                dsh[k * 3 + 2] = fmaf(dr[2], Y[k], dsh[k * 3 + 2]);
+                wk[k] = dr[0] * sh[k * 3] + dr[1] * sh[k * 3 + 1] + dr[2] * sh[k * 3 + 2];
+            }
+            float gdx, gdy, gdz;
+            sh_grad<DEG>(dx, dy, dz, wk, gdx, gdy, gdz);
+            const float radial = gdx * dx + gdy * dy + gdz * dz;
+            const float dv0 = (gdx - dx * radial) * rn, dv1 = (gdy - dy * radial) * rn,
+                        dv2 = (gdz - dz * radial) * rn;
+            dmu[0] += dv0;
+            dmu[1] += dv1;
+            dmu[2] += dv2;
+            // the camera centre moves by -W^T rho: dL/drho gets -W dL/dC with dL/dC = -dv
+            pose6[0] += ps.W[0][0] * dv0 + ps.W[0][1] * dv1 + ps.W[0][2] * dv2;
+            pose6[1] += ps.W[1][0] * dv0 + ps.W[1][1] * dv1 + ps.W[1][2] * dv2;
+            pose6[2] += ps.W[2][0] * dv0 + ps.W[2][1] * dv1 + ps.W[2][2] * dv2;
+
+            // the blend returns dL/d ln(sigma); the logit chain is applied once at the end
+            dop += sg[5];
+
+            // pixel mean and depth
+            const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
+            dpc[0] += sg[0] * vp.fx * rz;
+            dpc[1] += sg[1] * vp.fy * rz;
+            dpc[2] += -(sg[0] * vp.fx * x + sg[1] * vp.fy * y) * rz * rz + sg[9];
+
+            // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
+            const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;
+            const float dl00 = kSqrtHalfLog2e * sg[2], dl01 = kSqrtHalfLog2e * sg[3], dl11 = kSqrtHalfLog2e * sg[4];
+            const float rdc = 1.0f / sqrtf(det * C);
+            const float dA = -0.5f * C * idet * (dl00 * p.l00 + dl01 * p.l01);
+            const float dB = dl00 * p.l00 * B * idet + dl01 * (p.l01 * B * idet - rdc);
+            const float dC = dl00 * 0.5f * p.l00 * (iC - A * idet) - dl01 * 0.5f * p.l01 * (A * idet + iC) -
+                             dl11 * 0.5f * p.l11 * iC;
+            // Sigma' = P P^T + 0.3 I
+            float dP[2][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                dP[0][j] = 2.f * dA * p.P[0][j] + dB * p.P[1][j];
+                dP[1][j] = dB * p.P[0][j] + 2.f * dC * p.P[1][j];
+            }
+            // P = T M
+            float dT[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    dT[r][k] = dP[r][0] * G.M[k][0] + dP[r][1] * G.M[k][1] + dP[r][2] * G.M[k][2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dM[k][j] += p.T[0][k] * dP[0][j] + p.T[1][k] * dP[1][j];
+            // T = J W  (J = [[J00, 0, J02], [0, J11, J12]])
+            const float dJ00 = dT[0][0] * ps.W[0][0] + dT[0][1] * ps.W[0][1] + dT[0][2] * ps.W[0][2];
+            const float dJ02 = dT[0][0] * ps.W[2][0] + dT[0][1] * ps.W[2][1] + dT[0][2] * ps.W[2][2];
+            const float dJ11 = dT[1][0] * ps.W[1][0] + dT[1][1] * ps.W[1][1] + dT[1][2] * ps.W[1][2];
+            const float dJ12 = dT[1][0] * ps.W[2][0] + dT[1][1] * ps.W[2][1] + dT[1][2] * ps.W[2][2];
+            float dW[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                dW[0][j] = p.J00 * dT[0][j];
+                dW[1][j] = p.J11 * dT[1][j];
+                dW[2][j] = p.J02 * dT[0][j] + p.J12 * dT[1][j];
+            }
+            // J(p) with clamped x/z, y/z
+            const float rz2 = rz * rz;
+            dpc[2] += -(dJ00 * vp.fx + dJ11 * vp.fy) * rz2;
+            if (p.clx) {
+                dpc[2] += dJ02 * vp.fx * p.txz * rz2;
+            } else {
+                dpc[0] += -dJ02 * vp.fx * rz2;
+                dpc[2] += 2.f * dJ02 * vp.fx * x * rz2 * rz;
+            }
+            if (p.cly) {
+                dpc[2] += dJ12 * vp.fy * p.tyz * rz2;
+            } else {
+                dpc[1] += -dJ12 * vp.fy * rz2;
+                dpc[2] += 2.f * dJ12 * vp.fy * y * rz2 * rz;
+            }
+            // p = W mu + t
+#pragma unroll
+            for (int j = 0; j < 3; ++j) dmu[j] += ps.W[0][j] * dpc[0] + ps.W[1][j] * dpc[1] + ps.W[2][j] * dpc[2];
+            // pose twist of T_cw <- Exp(rho, phi) T_cw
+            pose6[0] += dpc[0];
+            pose6[1] += dpc[1];
+            pose6[2] += dpc[2];
+            pose6[3] += y * dpc[2] - z * dpc[1];
+            pose6[4] += z * dpc[0] - x * dpc[2];
+            pose6[5] += x * dpc[1] - y * dpc[0];
+            float Am[3][3];  // dW W^T
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    Am[r][k] = dW[r][0] * ps.W[k][0] + dW[r][1] * ps.W[k][1] + dW[r][2] * ps.W[k][2];
+            pose6[3] += Am[2][1] - Am[1][2];
+            pose6[4] += Am[0][2] - Am[2][0];
+            pose6[5] += Am[1][0] - Am[0][1];
+        }
+        // per-warp partial of the view's pose gradient (deterministic order)
+        if (__any_sync(0xffffffffu, vis)) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float x = pose6[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                pose6[c] = x;
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) s_part[v][warp][c] = pose6[c];
+        } else if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s_part[v][warp][c] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < vt.V * 6; t += blockDim.x) {
+        const int v = t / 6, c = t % 6;
+        float acc = 0.f;
+        for (int w = 0; w < WARPS; ++w) acc += s_part[v][w][c];
+        ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + c] = acc;
+    }
+    if (!active) return;
+
+    // M = R diag(s) -> log-scales and the rotation
+    float dR[3][3], dls[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float ds = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ds += dM[r][j] * G.R[r][j];
+            dR[r][j] = dM[r][j] * G.s[j];
+        }
+        dls[j] = ds * G.s[j];
+    }
+    const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
+    // dR/dq for the unit quaternion (w, x, y, z)
+    float dq[4];
+    dq[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    dq[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
+                   w * dR[2][1] - 2.f * x * dR[2][2]);
+    dq[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
+                   z * dR[2][1] - 2.f * y * dR[2][2]);
+    dq[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                   y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    const float qu[4] = {w, x, y, z};
+    float dqr[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
+    const float dlogit = dop * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
+
+    const bool acc = out.accumulate != 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float *pm = out.means + (size_t)j * N + g;
+        float *pl = out.log_scales + (size_t)j * N + g;
+        *pm = acc ? *pm + dmu[j] : dmu[j];
+        *pl = acc ? *pl + dls[j] : dls[j];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float *pq = out.quats + (size_t)k * N + g;
+        *pq = acc ? *pq + dqr[k] : dqr[k];
+    }
+    float *po = out.opacity_logits + g;
+    *po = acc ? *po + dlogit : dlogit;
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) {
+        float *ps2 = out.sh + (size_t)k * N + g;
+        *ps2 = acc ? *ps2 + dsh[k] : dsh[k];
+    }
+}
+
+// Sum of the per-block pose partials of each view, in a fixed order.
+__global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant__ ViewTable vt, const Ws ws,
+                                                          int accumulate) {
+    __shared__ float s[256][6];
+    const int v = blockIdx.x;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t b = threadIdx.x; b < ws.pose_blocks; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += ws.pose_partials[((size_t)v * ws.pose_blocks + b) * 6 + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if (threadIdx.x < (unsigned)stride)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s[threadIdx.x][c] += s[threadIdx.x + stride][c];
+        __syncthreads();
+    }
+    float *dst = vt.v[v].d_pose;
+    if (threadIdx.x < 6 && dst) dst[threadIdx.x] = accumulate ? dst[threadIdx.x] + s[0][threadIdx.x] : s[0][threadIdx.x];
+}
+
+// ------------------------------------------------------------------ launchers
+template <int DEG>
+static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st) {
+    const int blocks = (gp.N + 255) / 256;
+    preprocess_fwd_kernel<DEG><<<blocks, 256, 0, st>>>(vt, gp, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st) {
+    if (gp.N == 0) return cudaSuccess;
+    switch (gp.sh_degree) {
+        case 0: return launch_pre_fwd<0>(vt, gp, ws, st);
+        case 1: return launch_pre_fwd<1>(vt, gp, ws, st);
+        case 2: return launch_pre_fwd<2>(vt, gp, ws, st);
+        default: return launch_pre_fwd<3>(vt, gp, ws, st);
+    }
+}
+
+template <int DEG>
+static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
+                                  cudaStream_t st) {
+    const int blocks = (gp.N + 255) / 256;
+    preprocess_bwd_kernel<DEG><<<blocks, 256, 0, st>>>(vt, gp, ws, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
+                                  cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (gp.N > 0) {
+        switch (gp.sh_degree) {
+            case 0: e = launch_pre_bwd<0>(vt, gp, ws, out, st); break;
+            case 1: e = launch_pre_bwd<1>(vt, gp, ws, out, st); break;
+            case 2: e = launch_pre_bwd<2>(vt, gp, ws, out, st); break;
+            default: e = launch_pre_bwd<3>(vt, gp, ws, out, st); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

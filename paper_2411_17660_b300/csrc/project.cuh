@@ -1,0 +1,130 @@
+// project.cuh -- per (view, Gaussian) projection shared by the forward
+// preprocess and its backward: activation and 3-D covariance factor,
+// camera transform, EWA projection to the dilated 2-D covariance Sigma', and
+// the Cholesky factor of Sigma'^-1 that the blend evaluates (Sec. 3.3,
+// alpha_i = sigma_i G(R, t, P_i, r_i, s_i)).
+//
+// FP32 throughout.  Two choices keep FP32 close to the exact result where the
+// textbook formulas lose digits:
+//  * det(Sigma') is formed as sum of squared 2x2 minors of P = J W R S
+//    (Cauchy-Binet) + 0.3 tr + 0.09, all non-negative terms, instead of
+//    a*c - b^2, which cancels for elongated footprints;
+//  * the blend evaluates d^2 = (l00 dx + l01 dy)^2 + (l11 dy)^2 with
+//    l11 = 1/sqrt(Syy), l00 = sqrt(Syy/det), l01 = -Sxy/sqrt(det Syy), which
+//    does not cancel the way a*dx^2 + 2b*dx*dy + c*dy^2 does far along the
+//    long axis of a thin ellipse.
+#pragma once
+
+#include "common.cuh"
+
+namespace gsr {
+
+struct GaussPre {
+    float mx, my, mz;
+    float qw, qx, qy, qz, qinv;   // unit quaternion and 1/|q|
+    float s[3];
+    float R[3][3];
+    float M[3][3];                // R diag(s)
+    float o, log2o, smax;
+    bool alive;                   // 255 o > 1: can pass the alpha skip somewhere
+};
+
+__device__ __forceinline__ void gauss_pre(const GaussianPtrs &gp, int g, GaussPre &G) {
+    const int N = gp.N;
+    G.mx = gp.means[g];
+    G.my = gp.means[N + g];
+    G.mz = gp.means[2 * N + g];
+    const float q0 = gp.quats[g], q1 = gp.quats[N + g], q2 = gp.quats[2 * N + g], q3 = gp.quats[3 * N + g];
+    const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+    G.qinv = 1.0f / sqrtf(qn2);
+    G.qw = q0 * G.qinv;
+    G.qx = q1 * G.qinv;
+    G.qy = q2 * G.qinv;
+    G.qz = q3 * G.qinv;
+    const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
+    G.R[0][0] = 1.f - 2.f * (y * y + z * z);
+    G.R[0][1] = 2.f * (x * y - w * z);
+    G.R[0][2] = 2.f * (x * z + w * y);
+    G.R[1][0] = 2.f * (x * y + w * z);
+    G.R[1][1] = 1.f - 2.f * (x * x + z * z);
+    G.R[1][2] = 2.f * (y * z - w * x);
+    G.R[2][0] = 2.f * (x * z - w * y);
+    G.R[2][1] = 2.f * (y * z + w * x);
+    G.R[2][2] = 1.f - 2.f * (x * x + y * y);
+    for (int k = 0; k < 3; ++k) G.s[k] = expf(gp.log_scales[k * N + g]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) G.M[i][j] = G.R[i][j] * G.s[j];
+    const float l = gp.opacity_logits[g];
+    G.o = 1.0f / (1.0f + expf(-l));
+    G.log2o = log2f(G.o);
+    // alpha = o 2^-s >= 1/255  <=>  s <= log2(255 o);  d^2 <= 9  <=>  s <= 9 kHalfLog2e
+    G.smax = fminf(kCutoffD2 * kHalfLog2e, G.log2o + kLog2_255);
+    G.alive = G.smax >= 0.f && isfinite(G.smax) && isfinite(G.mx + G.my + G.mz) &&
+              isfinite(G.s[0] + G.s[1] + G.s[2]) && qn2 > 0.f && isfinite(qn2);
+}
+
+// Camera pose in shared memory: W row-major (9), t (3), centre C = -W^T t (3).
+struct Pose {
+    float W[3][3];
+    float t[3];
+    float C[3];
+};
+
+struct Proj {
+    float xh, yh, zh, xl, yl, zl;  // camera-frame mean, hi + lo
+    bool clx, cly;
+    float txz, tyz;                // clamped x/z, y/z
+    float J00, J02, J11, J12;
+    float T[2][3];                 // J W
+    float P[2][3];                 // T M
+    float sxx, sxy, syy;           // Sigma' including the dilation
+    float det;
+    float l00, l01, l11;           // Cholesky factor of Sigma'^-1
+};
+
+// Returns false when the Gaussian is culled in this view (near plane, bad
+// determinant or non-finite values).
+__device__ __forceinline__ bool project_view(const GaussPre &G, const Pose &ps, const ViewParams &vp, Proj &p) {
+    dot3_plus(ps.W[0][0], ps.W[0][1], ps.W[0][2], ps.t[0], G.mx, G.my, G.mz, p.xh, p.xl);
+    dot3_plus(ps.W[1][0], ps.W[1][1], ps.W[1][2], ps.t[1], G.mx, G.my, G.mz, p.yh, p.yl);
+    dot3_plus(ps.W[2][0], ps.W[2][1], ps.W[2][2], ps.t[2], G.mx, G.my, G.mz, p.zh, p.zl);
+    const float z = p.zh;
+    if (!(z > kNearZ) || !isfinite(z)) return false;
+    const float limx = kFovClamp * 0.5f * (float)vp.W / vp.fx;
+    const float limy = kFovClamp * 0.5f * (float)vp.H / vp.fy;
+    const float rz = 1.0f / z;
+    float tx = p.xh * rz, ty = p.yh * rz;
+    p.clx = (tx < -limx) || (tx > limx);
+    p.cly = (ty < -limy) || (ty > limy);
+    tx = fminf(fmaxf(tx, -limx), limx);
+    ty = fminf(fmaxf(ty, -limy), limy);
+    p.txz = tx;
+    p.tyz = ty;
+    p.J00 = vp.fx * rz;
+    p.J02 = -vp.fx * tx * rz;      // -fx * xc / z^2 with xc = tx * z
+    p.J11 = vp.fy * rz;
+    p.J12 = -vp.fy * ty * rz;
+    for (int j = 0; j < 3; ++j) {
+        p.T[0][j] = p.J00 * ps.W[0][j] + p.J02 * ps.W[2][j];
+        p.T[1][j] = p.J11 * ps.W[1][j] + p.J12 * ps.W[2][j];
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) p.P[i][j] = p.T[i][0] * G.M[0][j] + p.T[i][1] * G.M[1][j] + p.T[i][2] * G.M[2][j];
+    const float a0 = p.P[0][0] * p.P[0][0] + p.P[0][1] * p.P[0][1] + p.P[0][2] * p.P[0][2];
+    const float c0 = p.P[1][0] * p.P[1][0] + p.P[1][1] * p.P[1][1] + p.P[1][2] * p.P[1][2];
+    const float b0 = p.P[0][0] * p.P[1][0] + p.P[0][1] * p.P[1][1] + p.P[0][2] * p.P[1][2];
+    const float m01 = det2(p.P[0][0], p.P[0][1], p.P[1][0], p.P[1][1]);
+    const float m02 = det2(p.P[0][0], p.P[0][2], p.P[1][0], p.P[1][2]);
+    const float m12 = det2(p.P[0][1], p.P[0][2], p.P[1][1], p.P[1][2]);
+    p.sxx = a0 + kDilation;
+    p.sxy = b0;
+    p.syy = c0 + kDilation;
+    p.det = (m01 * m01 + m02 * m02 + m12 * m12) + kDilation * (a0 + c0) + kDilation * kDilation;
+    if (!(p.det > 0.f) || !isfinite(p.det) || !isfinite(p.sxx + p.syy + p.sxy)) return false;
+    p.l11 = 1.0f / sqrtf(p.syy);
+    p.l00 = sqrtf(p.syy / p.det);
+    p.l01 = -p.sxy / sqrtf(p.det * p.syy);
+    return isfinite(p.l00) && isfinite(p.l01);
+}
+
+}  // namespace gsr
