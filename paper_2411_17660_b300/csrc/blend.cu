@@ -2,27 +2,31 @@
 // "rendering": C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j)) and its
 // back-to-front backward.
 //
-// One CTA per screen tile (all views concatenated), one warp per 8x4 block
-// of pixels, one pixel per lane.  Each warp walks its tile's depth-sorted
+// One CTA per screen tile (all views concatenated), one warp per 8x8 block
+// of pixels, two pixels per lane.  Each warp walks its tile's depth-sorted
 // list in chunks of 32 entries: the 32 lanes load one entry each, keep only
-// the Gaussians whose cutoff ellipse reaches the warp's 8x4 block (an exact
+// the Gaussians whose cutoff ellipse reaches the warp's 8x8 block (an exact
 // convex minimum of d^2 over the block), compact the survivors into the
 // warp's shared-memory slots with a ballot, and then every lane composites
-// them for its pixel.  A warp leaves as soon as all its lanes have hit the
+// them for its two pixels.  A warp leaves as soon as all its lanes have hit the
 // transmittance stop; warps never wait for each other.
 //
 // The backward recomputes the blend state from the stored final
 // transmittance and last contributor: walking back, T_i = T_{i+1}/(1-alpha_i)
 // and the colour/depth behind each entry accumulate as B <- B(1-a) + c a.
-// Per-Gaussian gradients of the 32 pixels of a warp are summed with warp
-// shuffles before one set of global atomics per (warp, Gaussian).
+// Per-Gaussian gradients of the 64 pixels of a warp are summed in registers
+// (two pixels per lane) and with a transposing warp butterfly before one set
+// of global atomics per (warp, Gaussian); when at most two lanes touch a
+// Gaussian they issue their atomics directly instead.
 #include "kernels.cuh"
 
 namespace gsr {
 
 namespace {
 
-constexpr int kSubW = 8, kSubH = 4;
+// A warp covers an 8x8 block of pixels: lane (x, y), y < 4, owns pixel rows
+// y and y + 4 of column x.
+constexpr int kSubW = 8, kSubH = 8, kPPL = 2, kRowStep = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int TS>
@@ -66,11 +70,54 @@ __device__ __forceinline__ bool touches_block(float ur, float vr, float m00, flo
     return smin <= smax + 1e-3f * (1.f + smax) + 1e-2f;
 }
 
+// One level of a transposing butterfly: L values per lane become ceil(L/2)
+// values, each summed over the lane pair (lane, lane ^ LEVEL).  The lower
+// lane keeps the first half, the upper lane the second (zero-padded).
+template <int L, int LEVEL>
+__device__ __forceinline__ void butterfly_level(const float *in, float *out, int lane) {
+    constexpr int H = (L + 1) / 2;
+    const bool hi = (lane & LEVEL) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float lo_keep = in[i];
+        const float hi_keep = (H + i < L) ? in[H + i] : 0.f;
+        const float send = hi ? lo_keep : hi_keep;
+        out[i] = (hi ? hi_keep : lo_keep) + __shfl_xor_sync(kFull, send, LEVEL);
+    }
+}
+
+// Sums 10 per-lane values over the warp with 12 shuffles (instead of 50):
+// afterwards lane l holds the total of component comp (valid = true) and
+// its partner lane l^1 holds the same total.
+__device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane, int &comp, bool &valid) {
+    static_assert(kVGGrads == 10, "butterfly is laid out for 10 values");
+    float a[5], b[3], c[2];
+    butterfly_level<10, 16>(v, a, lane);
+    butterfly_level<5, 8>(a, b, lane);
+    butterfly_level<3, 4>(b, c, lane);
+    float d;
+    butterfly_level<2, 2>(c, &d, lane);
+    d += __shfl_xor_sync(kFull, d, 1);
+    int base = 0, left = 10;
+    const int lev[4] = {16, 8, 4, 2}, half[4] = {5, 3, 2, 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (lane & lev[k]) {
+            base += half[k];
+            left = max(0, left - half[k]);
+        } else {
+            left = min(left, half[k]);
+        }
+    }
+    comp = base;
+    valid = left == 1;
+    return d;
+}
+
 struct WarpTile {
     int v;
-    int X0, Y0;       // pixel of lane 0
-    int px, py;       // this lane's pixel
-    bool inside;
+    int X0, Y0;         // pixel of lane 0 (origin of the warp's block)
+    int px, py;         // this lane's first pixel; the others sit kRowStep rows below
     uint2 range;
 };
 
@@ -88,7 +135,6 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     w.Y0 = ty * TS + (warp / S::WX) * kSubH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
-    w.inside = w.px < vp.W && w.py < vp.H;
     w.range = ws.ranges[tile];
     return w;
 }
@@ -136,31 +182,44 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    uint32_t last = 0, ncon = 0;
-    bool done = !wt.inside;
+    float T[kPPL], C0[kPPL], C1[kPPL], C2[kPPL], D[kPPL];
+    uint32_t last[kPPL], ncon = 0;
+    bool done[kPPL];
+#pragma unroll
+    for (int q = 0; q < kPPL; ++q) {
+        T[q] = 1.f;
+        C0[q] = C1[q] = C2[q] = D[q] = 0.f;
+        last[q] = 0;
+        done[q] = !(wt.px < vp.W && wt.py + q * kRowStep < vp.H);
+    }
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
-        if (__all_sync(kFull, done)) break;
+        bool all_done = true;
+#pragma unroll
+        for (int q = 0; q < kPPL; ++q) all_done &= done[q];
+        if (__all_sync(kFull, all_done)) break;
         const int n = stage_chunk(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0, sA[warp], sB[warp], sC[warp]);
         for (int j = 0; j < n; ++j) {
             const float4 a = sA[warp][j], b = sB[warp][j];
-            if (!done) {
+            const float dx = __fsub_rn(lxf, a.x);
+#pragma unroll
+            for (int q = 0; q < kPPL; ++q) {
+                if (done[q]) continue;
                 float p1, p2;
-                const float s = pair_s(__fsub_rn(lxf, a.x), __fsub_rn(lyf, a.y), a.z, a.w, b.x, p1, p2);
+                const float s = pair_s(dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.z, a.w, b.x, p1, p2);
                 if (s <= b.y) {
                     const float alpha = fminf(kAlphaMax, ex2_approx(__fsub_rn(b.z, s)));
-                    const float Tn = T * (1.f - alpha);
+                    const float Tn = T[q] * (1.f - alpha);
                     if (Tn < kTStop) {
-                        done = true;
+                        done[q] = true;
                     } else {
                         const float4 c = sC[warp][j];
-                        const float w = alpha * T;
-                        C0 = fmaf(w, c.x, C0);
-                        C1 = fmaf(w, c.y, C1);
-                        C2 = fmaf(w, c.z, C2);
-                        D = fmaf(w, b.w, D);
-                        T = Tn;
-                        last = __float_as_uint(c.w) + 1u;
+                        const float w = alpha * T[q];
+                        C0[q] = fmaf(w, c.x, C0[q]);
+                        C1[q] = fmaf(w, c.y, C1[q]);
+                        C2[q] = fmaf(w, c.z, C2[q]);
+                        D[q] = fmaf(w, b.w, D[q]);
+                        T[q] = Tn;
+                        last[q] = __float_as_uint(c.w) + 1u;
                         ++ncon;
                     }
                 }
@@ -168,15 +227,19 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
         }
         __syncwarp();
     }
-    if (wt.inside) {
-        const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)wt.py * vp.W + wt.px;
-        vp.color[pix] = C0;
-        vp.color[HW + pix] = C1;
-        vp.color[2 * HW + pix] = C2;
-        if (vp.depth) vp.depth[pix] = D;
-        if (vp.alpha) vp.alpha[pix] = 1.f - T;
-        ws.T_final[vp.pixel_offset + pix] = T;
-        ws.last[vp.pixel_offset + pix] = last;
+#pragma unroll
+    for (int q = 0; q < kPPL; ++q) {
+        const int py = wt.py + q * kRowStep;
+        if (wt.px < vp.W && py < vp.H) {
+            const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
+            vp.color[pix] = C0[q];
+            vp.color[HW + pix] = C1[q];
+            vp.color[2 * HW + pix] = C2[q];
+            if (vp.depth) vp.depth[pix] = D[q];
+            if (vp.alpha) vp.alpha[pix] = 1.f - T[q];
+            ws.T_final[vp.pixel_offset + pix] = T[q];
+            ws.last[vp.pixel_offset + pix] = last[q];
+        }
     }
     const uint32_t tot = __reduce_add_sync(kFull, ncon);
     if (lane == 0 && tot) atomicAdd(&ws.hdr->pairs_contrib, (unsigned long long)tot);
@@ -195,22 +258,31 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
     const size_t vN = (size_t)wt.v * N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
-    float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gATf = 0.f;
-    uint32_t last = 0;
-    if (wt.inside) {
-        const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)wt.py * vp.W + wt.px;
-        T = ws.T_final[vp.pixel_offset + pix];
-        last = ws.last[vp.pixel_offset + pix];
-        if (vp.d_color) {
-            gC0 = vp.d_color[pix];
-            gC1 = vp.d_color[HW + pix];
-            gC2 = vp.d_color[2 * HW + pix];
+    float T[kPPL], gC0[kPPL], gC1[kPPL], gC2[kPPL], gD[kPPL], gATf[kPPL];
+    float BC0[kPPL], BC1[kPPL], BC2[kPPL], BD[kPPL];
+    uint32_t last[kPPL], lmax = 0;
+#pragma unroll
+    for (int q = 0; q < kPPL; ++q) {
+        T[q] = 1.f;
+        gC0[q] = gC1[q] = gC2[q] = gD[q] = gATf[q] = 0.f;
+        BC0[q] = BC1[q] = BC2[q] = BD[q] = 0.f;
+        last[q] = 0;
+        const int py = wt.py + q * kRowStep;
+        if (wt.px < vp.W && py < vp.H) {
+            const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
+            T[q] = ws.T_final[vp.pixel_offset + pix];
+            last[q] = ws.last[vp.pixel_offset + pix];
+            if (vp.d_color) {
+                gC0[q] = vp.d_color[pix];
+                gC1[q] = vp.d_color[HW + pix];
+                gC2[q] = vp.d_color[2 * HW + pix];
+            }
+            if (vp.d_depth) gD[q] = vp.d_depth[pix];
+            if (vp.d_alpha) gATf[q] = vp.d_alpha[pix] * T[q];
         }
-        if (vp.d_depth) gD = vp.d_depth[pix];
-        if (vp.d_alpha) gATf = vp.d_alpha[pix] * T;
+        lmax = max(lmax, last[q]);
     }
-    const uint32_t wlast = __reduce_max_sync(kFull, last);
-    float BC0 = 0.f, BC1 = 0.f, BC2 = 0.f, BD = 0.f;
+    const uint32_t wlast = __reduce_max_sync(kFull, lmax);
     float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads * N;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
@@ -219,57 +291,66 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
         for (int j = n - 1; j >= 0; --j) {
             const float4 a = sA[warp][j], b = sB[warp][j], c = sC[warp][j];
             const uint32_t eidx = __float_as_uint(c.w);
+            const float dx = __fsub_rn(lxf, a.x);
+            float p1[kPPL], p2[kPPL], dy[kPPL], sv[kPPL];
+            bool contrib[kPPL], any = false;
+#pragma unroll
+            for (int q = 0; q < kPPL; ++q) {
+                dy[q] = __fsub_rn(lyf + (float)(q * kRowStep), a.y);
+                sv[q] = pair_s(dx, dy[q], a.z, a.w, b.x, p1[q], p2[q]);
+                contrib[q] = eidx < last[q] && sv[q] <= b.y;
+                any |= contrib[q];
+            }
+            const unsigned cmask = __ballot_sync(kFull, any);
+            if (cmask == 0u) continue;
             float gv[kVGGrads];
 #pragma unroll
             for (int k = 0; k < kVGGrads; ++k) gv[k] = 0.f;
-            bool contrib = false;
-            if (eidx < last) {
-                float p1, p2;
-                const float dx = __fsub_rn(lxf, a.x), dy = __fsub_rn(lyf, a.y);
-                const float s = pair_s(dx, dy, a.z, a.w, b.x, p1, p2);
-                if (s <= b.y) {
-                    contrib = true;
-                    const float raw = ex2_approx(__fsub_rn(b.z, s));
-                    const float alpha = fminf(kAlphaMax, raw);
-                    const float rom = 1.f / (1.f - alpha);
-                    const float Ti = T * rom;
-                    const float w = alpha * Ti;
-                    gv[6] = gC0 * w;
-                    gv[7] = gC1 * w;
-                    gv[8] = gC2 * w;
-                    gv[9] = gD * w;
-                    const float dcr = c.x - BC0, dcg = c.y - BC1, dcb = c.z - BC2, dzz = b.w - BD;
-                    const float dA = Ti * (dcr * gC0 + dcg * gC1 + dcb * gC2 + dzz * gD) + gATf * rom;
-                    BC0 = fmaf(alpha, dcr, BC0);
-                    BC1 = fmaf(alpha, dcg, BC1);
-                    BC2 = fmaf(alpha, dcb, BC2);
-                    BD = fmaf(alpha, dzz, BD);
-                    T = Ti;
-                    if (raw <= kAlphaMax) {
-                        gv[5] = dA * raw;                      // dL/d ln(sigma)
-                        const float ds2 = -2.f * kLn2 * raw * dA;  // 2 dL/ds
-                        const float dp1 = p1 * ds2, dp2 = p2 * ds2;
-                        gv[2] = dp1 * dx;
-                        gv[3] = dp1 * dy;
-                        gv[4] = dp2 * dy;
-                        gv[0] = -dp1 * a.z;
-                        gv[1] = -(dp1 * a.w + dp2 * b.x);
-                    }
-                }
+#pragma unroll
+            for (int q = 0; q < kPPL; ++q) {
+                // Branch-free: a pixel without a contribution runs with
+                // alpha = 0, which leaves its T and accumulated colour
+                // unchanged and makes every gradient term zero.
+                const float raw = contrib[q] ? ex2_approx(__fsub_rn(b.z, sv[q])) : 0.f;
+                const float alpha = fminf(kAlphaMax, raw);
+                const float rom = rcp_approx(1.f - alpha);
+                const float Ti = T[q] * rom;
+                const float w = alpha * Ti;
+                gv[6] = fmaf(gC0[q], w, gv[6]);
+                gv[7] = fmaf(gC1[q], w, gv[7]);
+                gv[8] = fmaf(gC2[q], w, gv[8]);
+                gv[9] = fmaf(gD[q], w, gv[9]);
+                const float dcr = c.x - BC0[q], dcg = c.y - BC1[q], dcb = c.z - BC2[q], dzz = b.w - BD[q];
+                const float dA = Ti * (dcr * gC0[q] + dcg * gC1[q] + dcb * gC2[q] + dzz * gD[q]) + gATf[q] * rom;
+                BC0[q] = fmaf(alpha, dcr, BC0[q]);
+                BC1[q] = fmaf(alpha, dcg, BC1[q]);
+                BC2[q] = fmaf(alpha, dcb, BC2[q]);
+                BD[q] = fmaf(alpha, dzz, BD[q]);
+                T[q] = Ti;
+                // no gradient to position or opacity through the 0.99 clamp
+                const float glo = raw <= kAlphaMax ? dA * raw : 0.f;   // dL/d ln(sigma)
+                const float ds2 = (-2.f * kLn2) * glo;                  // 2 dL/ds
+                const float dp1 = p1[q] * ds2, dp2 = p2[q] * ds2;
+                gv[5] += glo;
+                gv[0] += dp1;                                          // du, dv follow from these and m
+                gv[1] += dp2;
+                gv[2] = fmaf(dp1, dx, gv[2]);
+                gv[3] = fmaf(dp1, dy[q], gv[3]);
+                gv[4] = fmaf(dp2, dy[q], gv[4]);
             }
-            if (__any_sync(kFull, contrib)) {
-#pragma unroll
-                for (int k = 0; k < kVGGrads; ++k) {
-                    float x = gv[k];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                    gv[k] = x;
-                }
-                const uint32_t g = vals[eidx];
-                if (lane == 0 && g < N) {
+            const uint32_t g = vals[eidx];
+            if (g >= N) continue;
+            if (__popc(cmask) <= 2) {
+                // one or two lanes: their own atomics are cheaper than a reduction
+                if (any) {
 #pragma unroll
                     for (int k = 0; k < kVGGrads; ++k) atomicAdd(grads + (size_t)k * N + g, gv[k]);
                 }
+            } else {
+                int comp;
+                bool valid;
+                const float sum = warp_sum10(gv, lane, comp, valid);
+                if (valid && (lane & 1) == 0) atomicAdd(grads + (size_t)comp * N + g, sum);
             }
         }
         __syncwarp();

@@ -166,11 +166,15 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
             // the blend returns dL/d ln(sigma); the logit chain is applied once at the end
             dop += sg[5];
 
-            // pixel mean and depth
+            // pixel mean and depth: the blend returns the sums of dL/dp1 and
+            // dL/dp2 (p = m d, d = pixel - mean), so dL/du = -m00 S1 and
+            // dL/dv = -(m01 S1 + m11 S2)
             const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
-            dpc[0] += sg[0] * vp.fx * rz;
-            dpc[1] += sg[1] * vp.fy * rz;
-            dpc[2] += -(sg[0] * vp.fx * x + sg[1] * vp.fy * y) * rz * rz + sg[9];
+            const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
+            const float dv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
+            dpc[0] += du * vp.fx * rz;
+            dpc[1] += dv * vp.fy * rz;
+            dpc[2] += -(du * vp.fx * x + dv * vp.fy * y) * rz * rz + sg[9];
 
             // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
             const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;

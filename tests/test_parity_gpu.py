@@ -93,9 +93,12 @@ def test_permutation_invariance():
 
 
 def test_capacity_overflow_is_reported_then_grown():
-    sc = REDUCED["room"]()
+    sc = REDUCED["uneven"]()
     rast = R.GaussianRasterizer(16)
     params, cams, vm = U.to_device(sc)
+    _, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+    assert rast.info(ws).keys > 2 * 3072, "needs more keys than the smallest capacity"
+    rast = R.GaussianRasterizer(16)
     small = rast.alloc_workspace(sc.N, cams, key_capacity=3072)
     P = sum(c.H * c.W for c in cams)
     color = torch.empty(3 * P, device="cuda")
@@ -104,8 +107,9 @@ def test_capacity_overflow_is_reported_then_grown():
     assert info.status == B.ECAPACITY and info.keys > info.key_capacity
     c2, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
     assert rast.info(ws).status == B.OK
-    ref = U.gpu_forward(sc)[0][0]["color"]
-    np.testing.assert_array_equal(c2.view(3, cams[0].H, cams[0].W).cpu().numpy(), ref)
+    ref = U.gpu_forward(sc)[0]
+    for v, c in enumerate(R.split_views(c2, cams, 3)):
+        np.testing.assert_array_equal(c.cpu().numpy(), ref[v]["color"])
 
 
 def test_bounded_lookback_gives_up_with_status():
