@@ -62,7 +62,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.lb_tiles = (uint32_t)((cap + kSortTile - 1) / kSortTile);
     L.scan_blocks = (uint32_t)((L.VN + kScanChunk - 1) / kScanChunk);
     if (L.scan_blocks == 0) L.scan_blocks = 1;
-    L.pose_blocks = (uint32_t)((N + 255) / 256);
+    L.pose_blocks = (uint32_t)((N + 31) / 32);   // one pose partial per 32-Gaussian block
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;

@@ -247,22 +247,34 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int
         s_tile_ex[d_own] = tile_ex;
 
         // bounded decoupled look-back
+        // The flags of kLookBatch predecessors are loaded at once, so the
+        // walk costs one memory round trip per kLookBatch tiles.
         uint32_t prefix = 0;
         if (t > 0) {
-            uint32_t j = t - 1, spins = 0;
-            for (;;) {
-                const uint32_t s = ld_relaxed_gpu(lb + (size_t)j * kRadix + d_own);
-                const uint32_t flag = s & ~kCountMask;
-                if (flag == 0u) {
-                    if (++spins > ws.spin_limit) {
-                        set_status(ws.hdr, GSR_ETIMEOUT);
-                        break;
-                    }
-                    continue;
+            int j = (int)t - 1;
+            uint32_t spins = 0;
+            bool found = false;
+            while (!found) {
+                uint32_t f[kLookBatch];
+#pragma unroll
+                for (int k = 0; k < kLookBatch; ++k)
+                    f[k] = j - k >= 0 ? ld_relaxed_gpu(lb + (size_t)(j - k) * kRadix + d_own) : kFlagInc;
+                int k = 0;
+#pragma unroll
+                for (int q = 0; q < kLookBatch; ++q) {
+                    if (found || k != q) continue;   // stop at the first inclusive or not-ready flag
+                    const uint32_t flag = f[q] & ~kCountMask;
+                    if (flag == 0u) continue;
+                    prefix += f[q] & kCountMask;
+                    if (flag == kFlagInc) found = true;
+                    ++k;
                 }
-                prefix += s & kCountMask;
-                if (flag == kFlagInc || j == 0) break;
-                --j;
+                if (found) break;
+                j -= k;
+                if (k < kLookBatch && ++spins > ws.spin_limit) {  // waited on a flag that never came
+                    set_status(ws.hdr, GSR_ETIMEOUT);
+                    break;
+                }
             }
             st_relaxed_gpu(my, kFlagInc | ((prefix + cnt) & kCountMask));
         }

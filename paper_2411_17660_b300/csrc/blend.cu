@@ -258,14 +258,15 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
     const size_t vN = (size_t)wt.v * N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
-    float T[kPPL], gC0[kPPL], gC1[kPPL], gC2[kPPL], gD[kPPL], gATf[kPPL];
-    float BC0[kPPL], BC1[kPPL], BC2[kPPL], BD[kPPL];
+    // Q = gC . (colour behind) + gD (depth behind), normalised by the
+    // transmittance in front of the current entry
+    float T[kPPL], gC0[kPPL], gC1[kPPL], gC2[kPPL], gD[kPPL], gATf[kPPL], Q[kPPL];
     uint32_t last[kPPL], lmax = 0;
 #pragma unroll
     for (int q = 0; q < kPPL; ++q) {
         T[q] = 1.f;
         gC0[q] = gC1[q] = gC2[q] = gD[q] = gATf[q] = 0.f;
-        BC0[q] = BC1[q] = BC2[q] = BD[q] = 0.f;
+        Q[q] = 0.f;
         last[q] = 0;
         const int py = wt.py + q * kRowStep;
         if (wt.px < vp.W && py < vp.H) {
@@ -320,12 +321,12 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
                 gv[7] = fmaf(gC1[q], w, gv[7]);
                 gv[8] = fmaf(gC2[q], w, gv[8]);
                 gv[9] = fmaf(gD[q], w, gv[9]);
-                const float dcr = c.x - BC0[q], dcg = c.y - BC1[q], dcb = c.z - BC2[q], dzz = b.w - BD[q];
-                const float dA = Ti * (dcr * gC0[q] + dcg * gC1[q] + dcb * gC2[q] + dzz * gD[q]) + gATf[q] * rom;
-                BC0[q] = fmaf(alpha, dcr, BC0[q]);
-                BC1[q] = fmaf(alpha, dcg, BC1[q]);
-                BC2[q] = fmaf(alpha, dcb, BC2[q]);
-                BD[q] = fmaf(alpha, dzz, BD[q]);
+                // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
+                // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
+                const float gc = fmaf(gC0[q], c.x, fmaf(gC1[q], c.y, fmaf(gC2[q], c.z, gD[q] * b.w)));
+                const float dgq = gc - Q[q];
+                const float dA = fmaf(Ti, dgq, gATf[q] * rom);
+                Q[q] = fmaf(alpha, dgq, Q[q]);
                 T[q] = Ti;
                 // no gradient to position or opacity through the 0.99 clamp
                 const float glo = raw <= kAlphaMax ? dA * raw : 0.f;   // dL/d ln(sigma)

@@ -29,6 +29,7 @@ constexpr int kMaxPasses = 8;     // 8-bit radix digits of a 64-bit key
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 12;    // keys per thread per sort tile
+constexpr int kLookBatch = 8;     // predecessor flags read per look-back round
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -175,6 +176,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

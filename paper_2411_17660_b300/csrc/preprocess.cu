@@ -1,14 +1,23 @@
-// preprocess.cu -- per-Gaussian forward projection (activation, camera
-// transform, EWA projection, SH colour, exact tile count) and its backward
-// (projection/SH chain rule, per-view SE(3) pose reduction).  One thread per
-// Gaussian loops over the views of the batch, so the 59 parameters of a
-// Gaussian are read once per batch, not once per view.
+// preprocess.cu -- forward projection of every (view, Gaussian) pair
+// (activation, camera transform, EWA projection, SH colour, exact tile count)
+// and its backward (projection/SH chain rule, per-view SE(3) pose reduction).
+//
+// A block has kPreWarps warps in groups of VW = min(V, kPreWarps) (a power of
+// two); each group owns 32 Gaussians (one per lane) and its warps take the
+// views round-robin.  The warps of a group read the same Gaussians, so the
+// parameters come from DRAM once and from L1 after that, while the
+// (view, Gaussian) work is spread over many warps.  The backward sums each
+// Gaussian's gradient over the views in shared memory, in a fixed order, so
+// the result does not depend on timing.
 #include "kernels.cuh"
 #include "project.cuh"
 #include "sh.cuh"
 #include "spans.cuh"
 
 namespace gsr {
+
+constexpr int kPreWarps = 8;
+constexpr int kPreThreads = 32 * kPreWarps;
 
 __device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
     for (int i = threadIdx.x; i < vt.V * 12; i += blockDim.x) {
@@ -27,21 +36,34 @@ __device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
     __syncthreads();
 }
 
+// Unit view direction from the camera centre to the mean and its length.
+__device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, float &dx, float &dy, float &dz,
+                                         float &rn) {
+    dx = G.mx - ps.C[0];
+    dy = G.my - ps.C[1];
+    dz = G.mz - ps.C[2];
+    rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= rn;
+    dy *= rn;
+    dz *= rn;
+}
+
 // ------------------------------------------------------------------ forward
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
-                                                             const GaussianPtrs gp, const Ws ws) {
+__global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                     const GaussianPtrs gp, const Ws ws,
+                                                                     int vw_log2) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
     load_poses(vt, s_pose);
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int VW = 1 << vw_log2, slot = warp & (VW - 1);
+    const int g = (blockIdx.x * (kPreWarps >> vw_log2) + (warp >> vw_log2)) * 32 + lane;
     if (g >= gp.N) return;
     const size_t N = (size_t)gp.N;
     GaussPre G;
     gauss_pre(gp, g, G);
-    float sh[3 * K];
-    bool sh_loaded = false;
-    for (int v = 0; v < vt.V; ++v) {
+    for (int v = slot; v < vt.V; v += VW) {
         const ViewParams &vp = vt.v[v];
         const size_t i = (size_t)v * N + g;
         uint32_t count = 0;
@@ -55,30 +77,26 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(const __grid_consta
                 count = visit_tile_spans(uh, vh, p.sxx, p.sxy, p.syy, m00, G.smax, vp.W, vp.H, vt.tile,
                                          [](int, int, int) {});
             if (count) {
-                if (!sh_loaded) {
-#pragma unroll
-                    for (int k = 0; k < 3 * K; ++k) sh[k] = gp.sh[(size_t)k * N + g];
-                    sh_loaded = true;
-                }
-                const Pose &ps = s_pose[v];
-                float dx = G.mx - ps.C[0], dy = G.my - ps.C[1], dz = G.mz - ps.C[2];
-                const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-                dx *= rn;
-                dy *= rn;
-                dz *= rn;
+                float dx, dy, dz, rn;
+                view_dir(G, s_pose[v], dx, dy, dz, rn);
                 float Y[K];
                 sh_eval<DEG>(dx, dy, dz, Y);
-                float rgb[3];
-#pragma unroll
+                float rgb0 = 0.f, rgb1 = 0.f, rgb2 = 0.f;
+                // one channel at a time keeps few coefficients live in registers
+#pragma unroll 1
                 for (int c = 0; c < 3; ++c) {
+                    const float *shc = gp.sh + (size_t)c * N + g;
                     float acc = 0.5f;
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc = fmaf(sh[k * 3 + c], Y[k], acc);
-                    rgb[c] = fmaxf(acc, 0.f);
+                    for (int k = 0; k < K; ++k) acc = fmaf(__ldg(shc + (size_t)k * 3 * N), Y[k], acc);
+                    acc = fmaxf(acc, 0.f);
+                    if (c == 0) rgb0 = acc;
+                    else if (c == 1) rgb1 = acc;
+                    else rgb2 = acc;
                 }
                 ws.rec0[i] = make_float4(uh, vh, ul, vl);
                 ws.rec1[i] = make_float4(m00, m01, m11, G.smax);
-                ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], p.zh);
+                ws.rec2[i] = make_float4(rgb0, rgb1, rgb2, p.zh);
                 ws.rec3[i] = make_float4(G.log2o, p.sxx, p.sxy, p.syy);
             }
         }
@@ -87,29 +105,41 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(const __grid_consta
 }
 
 // ------------------------------------------------------------------ backward
+// Per-Gaussian partial gradients summed over views: dmu (3), dM (9, the
+// gradient of M = R diag(s)), d ln(sigma) (1), dSH (3K).
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
-                                                             const GaussianPtrs gp, const Ws ws,
-                                                             const GradPtrs out) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int WARPS = 256 / 32;
+struct BwdAcc {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+    static constexpr int NV = 13 + 3 * K;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                     const GaussianPtrs gp, const Ws ws,
+                                                                     const GradPtrs out, int vw_log2) {
+    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV;
+    extern __shared__ float s_red[];   // [kPreWarps][NV][32]
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
-    __shared__ float s_part[GSR_MAX_VIEWS][WARPS][6];
     load_poses(vt, s_pose);
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = g < gp.N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int VW = 1 << vw_log2, slot = warp & (VW - 1), group = warp >> vw_log2;
+    const uint32_t gblock = blockIdx.x * (kPreWarps >> vw_log2) + group;   // 32-Gaussian group index
+    const int g = (int)gblock * 32 + lane;
+    const bool active = g < gp.N;
     const size_t N = (size_t)gp.N;
     GaussPre G;
     if (active) gauss_pre(gp, g, G);
-    float sh[3 * K], dsh[3 * K];
+    // registers: dmu (3), dM (9), d ln(sigma) (1); the 3K SH gradients live
+    // in this warp's shared-memory columns (lane-private, no conflicts)
+    float acc[13];
 #pragma unroll
-    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
-    bool sh_loaded = false;
-    float dmu[3] = {0.f, 0.f, 0.f}, dM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float dop = 0.f;
+    for (int k = 0; k < 13; ++k) acc[k] = 0.f;
+    float *dmu = acc, *dM = acc + 3;
+    float *my_red = s_red + warp * NV * 32 + lane;   // element k at my_red[k * 32]
+#pragma unroll
+    for (int k = 13; k < NV; ++k) my_red[k * 32] = 0.f;
 
-    for (int v = 0; v < vt.V; ++v) {
+    for (int v = slot; v < vt.V; v += VW) {
         const ViewParams &vp = vt.v[v];
         const Pose &ps = s_pose[v];
         float pose6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -124,31 +154,32 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
             float dpc[3] = {0.f, 0.f, 0.f};
 
             // colour -> SH coefficients and the view direction
-            if (!sh_loaded) {
-#pragma unroll
-                for (int k = 0; k < 3 * K; ++k) sh[k] = gp.sh[(size_t)k * N + g];
-                sh_loaded = true;
-            }
-            const float ex = G.mx - ps.C[0], ey = G.my - ps.C[1], ez = G.mz - ps.C[2];
-            const float rn = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
-            const float dx = ex * rn, dy = ey * rn, dz = ez * rn;
+            float dx, dy, dz, rn;
+            view_dir(G, ps, dx, dy, dz, rn);
             float Y[K];
             sh_eval<DEG>(dx, dy, dz, Y);
-            float dr[3];
-#pragma unroll
+            float dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
+#pragma unroll 1
             for (int c = 0; c < 3; ++c) {
-                float acc = 0.5f;
+                const float *shc = gp.sh + (size_t)c * N + g;
+                float raw = 0.5f;
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc = fmaf(sh[k * 3 + c], Y[k], acc);
-                dr[c] = acc > 0.f ? sg[6 + c] : 0.f;
+                for (int k = 0; k < K; ++k) raw = fmaf(__ldg(shc + (size_t)k * 3 * N), Y[k], raw);
+                const float d = raw > 0.f ? sg[6 + c] : 0.f;   // no gradient through the clamp at 0
+                if (c == 0) dr0 = d;
+                else if (c == 1) dr1 = d;
+                else dr2 = d;
             }
             float wk[K];
+            const float *shg = gp.sh + g;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                dsh[k * 3 + 0] = fmaf(dr[0], Y[k], dsh[k * 3 + 0]);
-                dsh[k * 3 + 1] = fmaf(dr[1], Y[k], dsh[k * 3 + 1]);
-                dsh[k * 3 + 2] = fmaf(dr[2], Y[k], dsh[k * 3 + 2]);
-                wk[k] = dr[0] * sh[k * 3] + dr[1] * sh[k * 3 + 1] + dr[2] * sh[k * 3 + 2];
+                float *r = my_red + (13 + k * 3) * 32;
+                r[0] = fmaf(dr0, Y[k], r[0]);
+                r[32] = fmaf(dr1, Y[k], r[32]);
+                r[64] = fmaf(dr2, Y[k], r[64]);
+                wk[k] = dr0 * __ldg(shg + (size_t)(k * 3) * N) + dr1 * __ldg(shg + (size_t)(k * 3 + 1) * N) +
+                        dr2 * __ldg(shg + (size_t)(k * 3 + 2) * N);
             }
             float gdx, gdy, gdz;
             sh_grad<DEG>(dx, dy, dz, wk, gdx, gdy, gdz);
@@ -164,17 +195,17 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
             pose6[2] += ps.W[2][0] * dv0 + ps.W[2][1] * dv1 + ps.W[2][2] * dv2;
 
             // the blend returns dL/d ln(sigma); the logit chain is applied once at the end
-            dop += sg[5];
+            acc[12] += sg[5];
 
             // pixel mean and depth: the blend returns the sums of dL/dp1 and
             // dL/dp2 (p = m d, d = pixel - mean), so dL/du = -m00 S1 and
             // dL/dv = -(m01 S1 + m11 S2)
             const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
             const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
-            const float dv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
+            const float dvv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
             dpc[0] += du * vp.fx * rz;
-            dpc[1] += dv * vp.fy * rz;
-            dpc[2] += -(du * vp.fx * x + dv * vp.fy * y) * rz * rz + sg[9];
+            dpc[1] += dvv * vp.fy * rz;
+            dpc[2] += -(du * vp.fx * x + dvv * vp.fy * y) * rz * rz + sg[9];
 
             // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
             const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;
@@ -201,7 +232,7 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) dM[k][j] += p.T[0][k] * dP[0][j] + p.T[1][k] * dP[1][j];
+                for (int j = 0; j < 3; ++j) dM[k * 3 + j] += p.T[0][k] * dP[0][j] + p.T[1][k] * dP[1][j];
             // T = J W  (J = [[J00, 0, J02], [0, J11, J12]])
             const float dJ00 = dT[0][0] * ps.W[0][0] + dT[0][1] * ps.W[0][1] + dT[0][2] * ps.W[0][2];
             const float dJ02 = dT[0][0] * ps.W[2][0] + dT[0][1] * ps.W[2][1] + dT[0][2] * ps.W[2][2];
@@ -249,31 +280,53 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
             pose6[4] += Am[0][2] - Am[2][0];
             pose6[5] += Am[1][0] - Am[0][1];
         }
-        // per-warp partial of the view's pose gradient (deterministic order)
-        if (__any_sync(0xffffffffu, vis)) {
+        // this warp owns view v for its 32 Gaussians: its sum is their partial
+        float part[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float x = pose6[c];
+        for (int c = 0; c < 6; ++c) {
+            float x = pose6[c];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                pose6[c] = x;
-            }
-            if (lane == 0)
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            part[c] = x;
+        }
+        if (lane < 6) {
+            float x = part[0];
 #pragma unroll
-                for (int c = 0; c < 6; ++c) s_part[v][warp][c] = pose6[c];
-        } else if (lane == 0) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) s_part[v][warp][c] = 0.f;
+            for (int c = 1; c < 6; ++c) x = lane == c ? part[c] : x;
+            if (gblock < ws.pose_blocks) ws.pose_partials[((size_t)v * ws.pose_blocks + gblock) * 6 + lane] = x;
         }
     }
+
+    // sum each group's per-Gaussian partials over its warps (views) in a
+    // fixed order, into the group's first warp
+#pragma unroll
+    for (int k = 0; k < 13; ++k) my_red[k * 32] = acc[k];
     __syncthreads();
-    for (int t = threadIdx.x; t < vt.V * 6; t += blockDim.x) {
-        const int v = t / 6, c = t % 6;
-        float acc = 0.f;
-        for (int w = 0; w < WARPS; ++w) acc += s_part[v][w][c];
-        ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + c] = acc;
+    if (VW > 1) {
+        const int groups = kPreWarps >> vw_log2;
+        for (int idx = threadIdx.x; idx < groups * NV * 32; idx += kPreThreads) {
+            const int grp = idx / (NV * 32), rest = idx - grp * NV * 32;
+            float *first = s_red + (grp * VW) * NV * 32 + rest;
+            float x = first[0];
+            for (int s = 1; s < VW; ++s) x += first[s * NV * 32];
+            first[0] = x;
+        }
+        __syncthreads();
     }
     if (!active) return;
+    const float *gsum = s_red + (group * VW) * NV * 32 + lane;   // element k at gsum[k * 32]
+    // every warp of the group writes its share of the SH gradient rows
+    {
+        const bool ac = out.accumulate != 0;
+        for (int k = slot; k < 3 * K; k += VW) {
+            float *ps2 = out.sh + (size_t)k * N + g;
+            const float x = gsum[(13 + k) * 32];
+            *ps2 = ac ? *ps2 + x : x;
+        }
+    }
+    if (slot != 0) return;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) acc[k] = gsum[k * 32];
 
     // M = R diag(s) -> log-scales and the rotation
     float dR[3][3], dls[3];
@@ -282,8 +335,8 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
         float ds = 0.f;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            ds += dM[r][j] * G.R[r][j];
-            dR[r][j] = dM[r][j] * G.s[j];
+            ds += dM[r * 3 + j] * G.R[r][j];
+            dR[r][j] = dM[r * 3 + j] * G.s[j];
         }
         dls[j] = ds * G.s[j];
     }
@@ -302,28 +355,23 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(const __grid_consta
     float dqr[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
-    const float dlogit = dop * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
+    const float dlogit = acc[12] * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
 
-    const bool acc = out.accumulate != 0;
+    const bool ac = out.accumulate != 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         float *pm = out.means + (size_t)j * N + g;
         float *pl = out.log_scales + (size_t)j * N + g;
-        *pm = acc ? *pm + dmu[j] : dmu[j];
-        *pl = acc ? *pl + dls[j] : dls[j];
+        *pm = ac ? *pm + dmu[j] : dmu[j];
+        *pl = ac ? *pl + dls[j] : dls[j];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float *pq = out.quats + (size_t)k * N + g;
-        *pq = acc ? *pq + dqr[k] : dqr[k];
+        *pq = ac ? *pq + dqr[k] : dqr[k];
     }
     float *po = out.opacity_logits + g;
-    *po = acc ? *po + dlogit : dlogit;
-#pragma unroll
-    for (int k = 0; k < 3 * K; ++k) {
-        float *ps2 = out.sh + (size_t)k * N + g;
-        *ps2 = acc ? *ps2 + dsh[k] : dsh[k];
-    }
+    *po = ac ? *po + dlogit : dlogit;
 }
 
 // Sum of the per-block pose partials of each view, in a fixed order.
@@ -349,10 +397,23 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------------ launchers
+// log2 of the warps that share one group of 32 Gaussians: as many as there
+// are views, up to the block's kPreWarps (a power of two).
+static int views_log2(int V) {
+    int l = 0;
+    while ((2 << l) <= V && (2 << l) <= kPreWarps) ++l;
+    return l;
+}
+
+static int pre_blocks(int N, int vw_log2) {
+    const int per_block = 32 * (kPreWarps >> vw_log2);
+    return (N + per_block - 1) / per_block;
+}
+
 template <int DEG>
 static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st) {
-    const int blocks = (gp.N + 255) / 256;
-    preprocess_fwd_kernel<DEG><<<blocks, 256, 0, st>>>(vt, gp, ws);
+    const int l = views_log2(vt.V);
+    preprocess_fwd_kernel<DEG><<<pre_blocks(gp.N, l), kPreThreads, 0, st>>>(vt, gp, ws, l);
     return cudaGetLastError();
 }
 
@@ -369,8 +430,12 @@ cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
 template <int DEG>
 static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st) {
-    const int blocks = (gp.N + 255) / 256;
-    preprocess_bwd_kernel<DEG><<<blocks, 256, 0, st>>>(vt, gp, ws, out);
+    const int l = views_log2(vt.V);
+    const size_t smem = sizeof(float) * kPreWarps * BwdAcc<DEG>::NV * 32;
+    cudaError_t e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    preprocess_bwd_kernel<DEG><<<pre_blocks(gp.N, l), kPreThreads, smem, st>>>(vt, gp, ws, out, l);
     return cudaGetLastError();
 }
 
