@@ -198,6 +198,29 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
 #define GSR_STAGE_EVENTS 10
 gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events);
 
+/* Forward render without a caller-provided workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory (plug-ins running inside another framework's execution
+ * phase, where only that framework owns the allocator, and real-time loops
+ * that must not allocate).  It renders exactly as gsr_render, but its scratch
+ * is a static device array of GSR_NOALLOC_SCRATCH_BYTES inside the library,
+ * held on every device that loads the library until the process exits.  No
+ * device memory is allocated by the call.
+ * - Scenes whose smallest workspace (gsr_workspace_size with key_capacity 1)
+ *   exceeds GSR_NOALLOC_SCRATCH_BYTES are rejected with GSR_EINVAL.  The key
+ *   capacity is whatever fits in the rest of the array.
+ * - status: device pointer to one int32 that receives the call's device-side
+ *   status (0, or GSR_ECAPACITY when the tile keys did not fit); may be NULL.
+ * - The first call on a device looks up the array's device address; make it
+ *   before any stream capture on that device.
+ * - All calls share the one array and each leaves its contents behind; calls
+ *   that can overlap on the GPU (different streams, or threads) race.
+ * - There is no backward for this render: use gsr_render when gradients are
+ *   needed. */
+#define GSR_NOALLOC_SCRATCH_BYTES (64u << 20)
+gsr_status gsr_render_noalloc(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
+                              int32_t *status, gsr_stream stream);
+
 /* Message of the last synchronous error on ctx (host string owned by ctx). */
 const char *gsr_last_error(const gsr_ctx *ctx);
 

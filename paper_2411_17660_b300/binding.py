@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_l1_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
                                 ctypes.c_float, _p, _p]),
         "gsr_set_stage_events": (c_int, [_p, ctypes.POINTER(_p)]),
+        "gsr_render_noalloc": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, _p, _p]),
         "gsr_last_error": (ctypes.c_char_p, [_p]),
         "gsr_status_string": (ctypes.c_char_p, [c_int]),
         "gsr_abi_version": (c_int, []),
@@ -150,6 +151,12 @@ class Context:
         garr = (ViewGrad * len(vgrads))(*vgrads)
         return self.lib.gsr_render_backward(self.h, ctypes.byref(g), arr, garr, len(views), ctypes.byref(out),
                                             ws_ptr, ws_bytes, stream)
+
+    def render_noalloc(self, g: Gaussians, views, status_ptr: int, stream: int) -> int:
+        """Forward render into the library's static scratch (no allocation);
+        status_ptr: device int32 receiving the device-side status, or 0."""
+        arr = (View * len(views))(*views)
+        return self.lib.gsr_render_noalloc(self.h, ctypes.byref(g), arr, len(views), status_ptr or None, stream)
 
     def read_info(self, ws_ptr: int, ws_bytes: int, stream: int) -> Info:
         info = Info()

@@ -262,6 +262,11 @@ int sm_count(gsr_ctx *ctx) {
 }
 
 }  // namespace
+
+void set_ctx_error(gsr_ctx *ctx, const char *msg) {
+    if (ctx) ctx->err = msg;
+}
+
 }  // namespace gsr
 
 using namespace gsr;

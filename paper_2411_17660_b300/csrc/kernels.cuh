@@ -24,6 +24,9 @@ cudaError_t launch_ranges(const Ws &ws, int sm_count, cudaStream_t st);
 cudaError_t launch_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
 cudaError_t launch_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
 
+// api.cu: sets the message gsr_last_error returns
+void set_ctx_error(gsr_ctx *ctx, const char *msg);
+
 // loss.cu
 cudaError_t launch_l1_loss(const ViewTable &vt, const gsr_l1_view *targets, float color_weight, float depth_weight,
                            float *loss, cudaStream_t st);
