@@ -305,6 +305,8 @@ def traffic_for(kernel: str):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     for line in open(path):
+        if line.startswith("#"):
+            continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel and f.get("source_sha") == sha:
             return float(f["dram_bytes_per_launch"])
