@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
     p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--workload", default="window", choices=["small", "room", "window", "uneven", "outdoor"],
+                   help="window (8 x 640x480, 100k Gaussians) is the metric's workload; the others are for reports")
+    p.add_argument("--autotune", action="store_true", help="pick the tile size with the autotuner first")
+    p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
@@ -146,16 +150,22 @@ def dist_max(ws, x: float) -> float:
 
 
 # ------------------------------------------------------------------ workload
-def make_scene():
+def make_scene(name="window"):
     from paper_2411_17660_b300 import scenes
-    return scenes.config_window()
+    return scenes.make(name)
+
+
+def resolution(scene):
+    sizes = sorted({f"{c.W}x{c.H}" for c in scene.cameras})
+    return sizes[0] if len(sizes) == 1 else "mixed:" + ",".join(sizes)
 
 
 def crop_pixels(scene, w, h):
     pix = []
     for c in scene.cameras:
-        x0, y0 = (c.W - w) // 2, (c.H - h) // 2
-        ys, xs = np.mgrid[y0:y0 + h, x0:x0 + w]
+        cw, ch = min(w, c.W), min(h, c.H)
+        x0, y0 = (c.W - cw) // 2, (c.H - ch) // 2
+        ys, xs = np.mgrid[y0:y0 + ch, x0:x0 + cw]
         pix.append((ys * c.W + xs).reshape(-1).astype(np.int64))
     return pix
 
@@ -196,14 +206,14 @@ def cpu_baseline(scene, seconds):
     t, pix, _, _ = run(w, h)
     npx = sum(len(p) for p in pix)
     return {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"fwd+bwd of a centred {w}x{h} crop of each of the {scene.V} views "
+            "sample": f"fwd+bwd of a centred {w}x{h} crop (or less) of each of the {scene.V} views "
                       f"({npx} px, all {scene.N} Gaussians projected), {t:.1f} s, FP64"}
 
 
 def reference_arm(args, ws, rank):
     if rank != 0:
         return
-    scene = make_scene()
+    scene = make_scene(args.workload)
     per_step = max(2.0, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
     w, h, run = oracle_sample(scene, per_step)
     for _ in range(args.warmup):
@@ -220,7 +230,7 @@ def reference_arm(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": scene.name, "views": scene.V, "resolution": "640x480", "gaussians": scene.N,
+        "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
                    "sh_degree": scene.sh_degree, "sample": f"{w}x{h} centred crop per view"},
         "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"fwd+bwd of a centred {w}x{h} crop of each view, per step"},
@@ -325,8 +335,15 @@ def main():
     from paper_2411_17660_b300 import render as R
     Build.build()
     torch.cuda.set_device(local)
-    scene = make_scene()
-    rast = R.GaussianRasterizer(args.tile)
+    scene = make_scene(args.workload)
+    tile, tuned = args.tile, None
+    if args.autotune:
+        from paper_2411_17660_b300 import autotune as A
+        w0 = Window(scene, R.GaussianRasterizer(16))
+        tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
+        tile = tuned["tile"]
+        del w0
+    rast = R.GaussianRasterizer(tile)
     win = Window(scene, rast)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
@@ -381,6 +398,24 @@ def main():
         pv = time_steps(torch, per_view_step, K, flush)
         per_view = dist_max(world, statistics.mean(pv))
 
+    # the same step captured once in a CUDA graph and replayed
+    graph_ms = None
+    if not args.no_graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            win.step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            win.step()
+        for _ in range(3):
+            flush()
+            graph.replay()
+        gm = time_steps(torch, graph.replay, K, flush)
+        graph_ms = dist_max(world, statistics.mean(gm))
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -409,8 +444,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": scene.name, "views": scene.V, "resolution": "640x480", "gaussians": scene.N,
-                   "sh_degree": scene.sh_degree, "tile": args.tile,
+        "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
+                   "sh_degree": scene.sh_degree, "tile": tile, "autotune": tuned,
                    "step": "forward + L1 colour/depth loss + backward (params + 8 poses)",
                    "l2": "flushed before every step (256 MB write), outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -421,6 +456,8 @@ def main():
         "stages_ms": stage_ms,
         "keys": info.keys, "pairs_contributing": pairs,
         "roofline": roof,
+        "graph_replay": None if graph_ms is None else {
+            "ms_per_step": graph_ms, "value": P_all / (graph_ms / 1000) / 1e6, "unit": "Mpix/s"},
         "gpu_launches": launches_per_step(rast, win) * K,
         "clocks": clocks,
         "e2e": e2e,

@@ -168,7 +168,9 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
  * final transmittance and contributor index, then projection/SH backward and
  * the per-view SE(3) pose reduction.  grads[v] gives view v's upstream
  * gradients and pose output.  Returns GSR_ENOTREADY if ws was not rendered
- * with the same N, views and tile size. */
+ * with the same N, views and tile size.  The first backward on a device also
+ * raises a kernel's shared-memory limit (a host-side setting), so make one
+ * backward call before capturing the stream into a CUDA graph. */
 gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
                                const gsr_view_grad *grads, int V, const gsr_grads *out,
                                void *ws, size_t ws_bytes, gsr_stream stream);

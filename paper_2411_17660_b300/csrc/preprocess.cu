@@ -9,6 +9,8 @@
 // (view, Gaussian) work is spread over many warps.  The backward sums each
 // Gaussian's gradient over the views in shared memory, in a fixed order, so
 // the result does not depend on timing.
+#include <mutex>
+
 #include "kernels.cuh"
 #include "project.cuh"
 #include "sh.cuh"
@@ -432,9 +434,22 @@ static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, c
                                   cudaStream_t st) {
     const int l = views_log2(vt.V);
     const size_t smem = sizeof(float) * kPreWarps * BwdAcc<DEG>::NV * 32;
-    cudaError_t e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // More than 48 KB of dynamic shared memory needs an opt-in, set once per
+    // device (the first backward on a device, which should precede capture).
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64 || !done[dev]) {
+            e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) done[dev] = true;
+        }
+    }
     preprocess_bwd_kernel<DEG><<<pre_blocks(gp.N, l), kPreThreads, smem, st>>>(vt, gp, ws, out, l);
     return cudaGetLastError();
 }

@@ -218,3 +218,60 @@ def test_full_size_sampled_pixels(name):
     gpu = U.gpu_backward(sc, state, gC, gD, gA)
     _, orc = oracle.render_backward(sc, gCs, [g * 0.1 for g in gDs], gAs, pixels=pix, brute=True)
     U.compare_grads(orc, gpu, label=name)
+
+
+def test_cuda_graph_replay_matches_eager():
+    """Forward + loss + backward captured once in a CUDA graph, replayed on
+    changed inputs (same buffers), equals the eager calls on those inputs."""
+    sc = REDUCED["window"]()
+    rast = R.GaussianRasterizer(16)
+    params, cams, vm = U.to_device(sc)
+    color, depth, alpha, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+    ws = rast.alloc_workspace(sc.N, cams, int(rast.info(ws).keys * 2) + 8192)
+    tc = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc.target_color])).cuda()
+    td = torch.from_numpy(np.concatenate([t.reshape(-1) for t in sc.target_depth])).cuda()
+    dC, dD = torch.empty_like(color), torch.empty_like(depth)
+    loss = torch.empty(1, device="cuda")
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    d_pose = torch.empty(len(cams), 6, device="cuda")
+
+    def step():
+        rast.forward_raw(params, sc.sh_degree, cams, vm, ws, color, depth, alpha)
+        R.l1_loss(rast, cams, vm, color, depth, tc, td, 1.0, 0.1, dC, dD, loss)
+        rast.backward_raw(params, sc.sh_degree, cams, vm, ws, dC, dD, None, grads, d_pose)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    # new inputs in the same buffers: move the Gaussians and the cameras a bit
+    with torch.no_grad():
+        params["means"].add_(0.01)
+        vm[:, :, 3].add_(0.02)
+    graph.replay()
+    torch.cuda.synchronize()
+    got = {k: v.clone() for k, v in grads.items()}
+    got_img, got_pose, got_loss = color.clone(), d_pose.clone(), loss.clone()
+    assert rast.info(ws).status == B.OK
+    step()
+    torch.cuda.synchronize()
+    assert torch.equal(color, got_img)
+    assert torch.allclose(loss, got_loss, rtol=1e-5)
+    for k in R.PARAM_NAMES:
+        assert U.rel_l2(got[k].cpu().numpy().astype(np.float64), grads[k].cpu().numpy().astype(np.float64)) < 1e-5
+    assert U.rel_l2(got_pose.cpu().numpy().astype(np.float64), d_pose.cpu().numpy().astype(np.float64)) < 1e-5
+
+
+def test_autotuner_picks_a_candidate_and_caches(tmp_path):
+    from paper_2411_17660_b300 import autotune as A
+    sc = REDUCED["uneven"]()
+    params, cams, vm = U.to_device(sc)
+    cache = A.TileCache(str(tmp_path / "tiles.json"))
+    r = A.tune(params, sc.sh_degree, cams, vm, cache=cache, reps=2)
+    assert r["tile"] in A.CANDIDATES and set(r["ms"]) == set(A.CANDIDATES)
+    assert A.tune(params, sc.sh_degree, cams, vm, cache=cache) == r
