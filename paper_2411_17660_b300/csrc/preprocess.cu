@@ -2,13 +2,15 @@
 // (activation, camera transform, EWA projection, SH colour, exact tile count)
 // and its backward (projection/SH chain rule, per-view SE(3) pose reduction).
 //
-// A block has kPreWarps warps in groups of VW = min(V, kPreWarps) (a power of
-// two); each group owns 32 Gaussians (one per lane) and its warps take the
-// views round-robin.  The warps of a group read the same Gaussians, so the
-// parameters come from DRAM once and from L1 after that, while the
-// (view, Gaussian) work is spread over many warps.  The backward sums each
-// Gaussian's gradient over the views in shared memory, in a fixed order, so
-// the result does not depend on timing.
+// Forward: a block has kPreWarps warps in groups of VW = min(V, kPreWarps) (a
+// power of two); each group owns 32 Gaussians (one per lane) and its warps
+// take the views round-robin.  The warps of a group read the same Gaussians,
+// so the parameters come from DRAM once and from L1 after that, while the
+// (view, Gaussian) work is spread over many warps.
+// Backward: a block owns 32 Gaussians; it compacts the visible (view,
+// Gaussian) pairs so that its warps work on visible pairs only, and sums the
+// per-pair gradients over views in shared memory in a fixed order, so the
+// result does not depend on timing.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -107,228 +109,299 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __gri
 }
 
 // ------------------------------------------------------------------ backward
-// Per-Gaussian partial gradients summed over views: dmu (3), dM (9, the
-// gradient of M = R diag(s)), d ln(sigma) (1), dSH (3K).
+// A block owns 256/VW Gaussians and takes the views VW at a time (VW a power
+// of two, as many as there are views, up to 8).  Of the 256 candidate
+// (view, Gaussian) pairs of a chunk, the visible ones are compacted with a
+// block-wide scan (in candidate order) so that warps work on visible pairs
+// only; each pair's partial gradients go to its shared-memory column, and are
+// then summed per Gaussian (in view order) and per view (in Gaussian order).
+// Deterministic.
 template <int DEG>
 struct BwdAcc {
     static constexpr int K = (DEG + 1) * (DEG + 1);
-    static constexpr int NV = 13 + 3 * K;
+    static constexpr int NV = 13 + 3 * K;   // dmu (3), dM (9), d ln(sigma) (1), dSH (3K)
 };
 
+// Backward of one visible (view, Gaussian) pair; writes its NV partials to
+// part[k * kPreThreads] and its pose twist to pose[k * kPreThreads].
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                     const GaussianPtrs gp, const Ws ws,
-                                                                     const GradPtrs out, int vw_log2) {
-    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV;
-    extern __shared__ float s_red[];   // [kPreWarps][NV][32]
-    __shared__ Pose s_pose[GSR_MAX_VIEWS];
-    load_poses(vt, s_pose);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int VW = 1 << vw_log2, slot = warp & (VW - 1), group = warp >> vw_log2;
-    const uint32_t gblock = blockIdx.x * (kPreWarps >> vw_log2) + group;   // 32-Gaussian group index
-    const int g = (int)gblock * 32 + lane;
-    const bool active = g < gp.N;
+__device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &ws, const ViewParams &vp,
+                                              const Pose &ps, int v, int g, float *part, float *pose) {
+    constexpr int K = BwdAcc<DEG>::K;
     const size_t N = (size_t)gp.N;
+    const size_t i = (size_t)v * N + g;
     GaussPre G;
-    if (active) gauss_pre(gp, g, G);
-    // registers: dmu (3), dM (9), d ln(sigma) (1); the 3K SH gradients live
-    // in this warp's shared-memory columns (lane-private, no conflicts)
-    float acc[13];
+    gauss_pre(gp, g, G);
+    Proj p;
+    float pose6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float dmu[3] = {0.f, 0.f, 0.f}, dM[9];
 #pragma unroll
-    for (int k = 0; k < 13; ++k) acc[k] = 0.f;
-    float *dmu = acc, *dM = acc + 3;
-    float *my_red = s_red + warp * NV * 32 + lane;   // element k at my_red[k * 32]
+    for (int k = 0; k < 9; ++k) dM[k] = 0.f;
+    float dlno = 0.f;
+    if (!project_view(G, ps, vp, p)) {   // same decision as the forward; kept for safety
 #pragma unroll
-    for (int k = 13; k < NV; ++k) my_red[k * 32] = 0.f;
-
-    for (int v = slot; v < vt.V; v += VW) {
-        const ViewParams &vp = vt.v[v];
-        const Pose &ps = s_pose[v];
-        float pose6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const size_t i = (size_t)v * N + g;
-        bool vis = active && ws.counts[i] > 0;
-        Proj p;
-        if (vis) vis = project_view(G, ps, vp, p);
-        if (vis) {
-            float sg[kVGGrads];
+        for (int k = 0; k < BwdAcc<DEG>::NV; ++k) part[k * kPreThreads] = 0.f;
 #pragma unroll
-            for (int c = 0; c < kVGGrads; ++c) sg[c] = ws.vg_grads[((size_t)v * kVGGrads + c) * N + g];
-            float dpc[3] = {0.f, 0.f, 0.f};
-
-            // colour -> SH coefficients and the view direction
-            float dx, dy, dz, rn;
-            view_dir(G, ps, dx, dy, dz, rn);
-            float Y[K];
-            sh_eval<DEG>(dx, dy, dz, Y);
-            float dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
-#pragma unroll 1
-            for (int c = 0; c < 3; ++c) {
-                const float *shc = gp.sh + (size_t)c * N + g;
-                float raw = 0.5f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) raw = fmaf(__ldg(shc + (size_t)k * 3 * N), Y[k], raw);
-                const float d = raw > 0.f ? sg[6 + c] : 0.f;   // no gradient through the clamp at 0
-                if (c == 0) dr0 = d;
-                else if (c == 1) dr1 = d;
-                else dr2 = d;
-            }
-            float wk[K];
-            const float *shg = gp.sh + g;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float *r = my_red + (13 + k * 3) * 32;
-                r[0] = fmaf(dr0, Y[k], r[0]);
-                r[32] = fmaf(dr1, Y[k], r[32]);
-                r[64] = fmaf(dr2, Y[k], r[64]);
-                wk[k] = dr0 * __ldg(shg + (size_t)(k * 3) * N) + dr1 * __ldg(shg + (size_t)(k * 3 + 1) * N) +
-                        dr2 * __ldg(shg + (size_t)(k * 3 + 2) * N);
-            }
-            float gdx, gdy, gdz;
-            sh_grad<DEG>(dx, dy, dz, wk, gdx, gdy, gdz);
-            const float radial = gdx * dx + gdy * dy + gdz * dz;
-            const float dv0 = (gdx - dx * radial) * rn, dv1 = (gdy - dy * radial) * rn,
-                        dv2 = (gdz - dz * radial) * rn;
-            dmu[0] += dv0;
-            dmu[1] += dv1;
-            dmu[2] += dv2;
-            // the camera centre moves by -W^T rho: dL/drho gets -W dL/dC with dL/dC = -dv
-            pose6[0] += ps.W[0][0] * dv0 + ps.W[0][1] * dv1 + ps.W[0][2] * dv2;
-            pose6[1] += ps.W[1][0] * dv0 + ps.W[1][1] * dv1 + ps.W[1][2] * dv2;
-            pose6[2] += ps.W[2][0] * dv0 + ps.W[2][1] * dv1 + ps.W[2][2] * dv2;
-
-            // the blend returns dL/d ln(sigma); the logit chain is applied once at the end
-            acc[12] += sg[5];
-
-            // pixel mean and depth: the blend returns the sums of dL/dp1 and
-            // dL/dp2 (p = m d, d = pixel - mean), so dL/du = -m00 S1 and
-            // dL/dv = -(m01 S1 + m11 S2)
-            const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
-            const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
-            const float dvv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
-            dpc[0] += du * vp.fx * rz;
-            dpc[1] += dvv * vp.fy * rz;
-            dpc[2] += -(du * vp.fx * x + dvv * vp.fy * y) * rz * rz + sg[9];
-
-            // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
-            const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;
-            const float dl00 = kSqrtHalfLog2e * sg[2], dl01 = kSqrtHalfLog2e * sg[3], dl11 = kSqrtHalfLog2e * sg[4];
-            const float rdc = 1.0f / sqrtf(det * C);
-            const float dA = -0.5f * C * idet * (dl00 * p.l00 + dl01 * p.l01);
-            const float dB = dl00 * p.l00 * B * idet + dl01 * (p.l01 * B * idet - rdc);
-            const float dC = dl00 * 0.5f * p.l00 * (iC - A * idet) - dl01 * 0.5f * p.l01 * (A * idet + iC) -
-                             dl11 * 0.5f * p.l11 * iC;
-            // Sigma' = P P^T + 0.3 I
-            float dP[2][3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                dP[0][j] = 2.f * dA * p.P[0][j] + dB * p.P[1][j];
-                dP[1][j] = dB * p.P[0][j] + 2.f * dC * p.P[1][j];
-            }
-            // P = T M
-            float dT[2][3];
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    dT[r][k] = dP[r][0] * G.M[k][0] + dP[r][1] * G.M[k][1] + dP[r][2] * G.M[k][2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) dM[k * 3 + j] += p.T[0][k] * dP[0][j] + p.T[1][k] * dP[1][j];
-            // T = J W  (J = [[J00, 0, J02], [0, J11, J12]])
-            const float dJ00 = dT[0][0] * ps.W[0][0] + dT[0][1] * ps.W[0][1] + dT[0][2] * ps.W[0][2];
-            const float dJ02 = dT[0][0] * ps.W[2][0] + dT[0][1] * ps.W[2][1] + dT[0][2] * ps.W[2][2];
-            const float dJ11 = dT[1][0] * ps.W[1][0] + dT[1][1] * ps.W[1][1] + dT[1][2] * ps.W[1][2];
-            const float dJ12 = dT[1][0] * ps.W[2][0] + dT[1][1] * ps.W[2][1] + dT[1][2] * ps.W[2][2];
-            float dW[3][3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                dW[0][j] = p.J00 * dT[0][j];
-                dW[1][j] = p.J11 * dT[1][j];
-                dW[2][j] = p.J02 * dT[0][j] + p.J12 * dT[1][j];
-            }
-            // J(p) with clamped x/z, y/z
-            const float rz2 = rz * rz;
-            dpc[2] += -(dJ00 * vp.fx + dJ11 * vp.fy) * rz2;
-            if (p.clx) {
-                dpc[2] += dJ02 * vp.fx * p.txz * rz2;
-            } else {
-                dpc[0] += -dJ02 * vp.fx * rz2;
-                dpc[2] += 2.f * dJ02 * vp.fx * x * rz2 * rz;
-            }
-            if (p.cly) {
-                dpc[2] += dJ12 * vp.fy * p.tyz * rz2;
-            } else {
-                dpc[1] += -dJ12 * vp.fy * rz2;
-                dpc[2] += 2.f * dJ12 * vp.fy * y * rz2 * rz;
-            }
-            // p = W mu + t
-#pragma unroll
-            for (int j = 0; j < 3; ++j) dmu[j] += ps.W[0][j] * dpc[0] + ps.W[1][j] * dpc[1] + ps.W[2][j] * dpc[2];
-            // pose twist of T_cw <- Exp(rho, phi) T_cw
-            pose6[0] += dpc[0];
-            pose6[1] += dpc[1];
-            pose6[2] += dpc[2];
-            pose6[3] += y * dpc[2] - z * dpc[1];
-            pose6[4] += z * dpc[0] - x * dpc[2];
-            pose6[5] += x * dpc[1] - y * dpc[0];
-            float Am[3][3];  // dW W^T
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    Am[r][k] = dW[r][0] * ps.W[k][0] + dW[r][1] * ps.W[k][1] + dW[r][2] * ps.W[k][2];
-            pose6[3] += Am[2][1] - Am[1][2];
-            pose6[4] += Am[0][2] - Am[2][0];
-            pose6[5] += Am[1][0] - Am[0][1];
-        }
-        // this warp owns view v for its 32 Gaussians: its sum is their partial
-        float part[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            float x = pose6[c];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            part[c] = x;
-        }
-        if (lane < 6) {
-            float x = part[0];
-#pragma unroll
-            for (int c = 1; c < 6; ++c) x = lane == c ? part[c] : x;
-            if (gblock < ws.pose_blocks) ws.pose_partials[((size_t)v * ws.pose_blocks + gblock) * 6 + lane] = x;
-        }
+        for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = 0.f;
+        return;
     }
-
-    // sum each group's per-Gaussian partials over its warps (views) in a
-    // fixed order, into the group's first warp
+    float sg[kVGGrads];
 #pragma unroll
-    for (int k = 0; k < 13; ++k) my_red[k * 32] = acc[k];
-    __syncthreads();
-    if (VW > 1) {
-        const int groups = kPreWarps >> vw_log2;
-        for (int idx = threadIdx.x; idx < groups * NV * 32; idx += kPreThreads) {
-            const int grp = idx / (NV * 32), rest = idx - grp * NV * 32;
-            float *first = s_red + (grp * VW) * NV * 32 + rest;
-            float x = first[0];
-            for (int s = 1; s < VW; ++s) x += first[s * NV * 32];
-            first[0] = x;
+    for (int c = 0; c < kVGGrads; ++c) sg[c] = ws.vg_grads[((size_t)v * kVGGrads + c) * N + g];
+    float dpc[3] = {0.f, 0.f, 0.f};
+
+    // colour -> SH coefficients and the view direction; the forward's stored
+    // colour is max(0, raw), so a zero channel was clamped (no gradient)
+    float dx, dy, dz, rn;
+    view_dir(G, ps, dx, dy, dz, rn);
+    float Y[K];
+    sh_eval<DEG>(dx, dy, dz, Y);
+    const float4 rgb = ws.rec2[i];
+    const float dr0 = rgb.x > 0.f ? sg[6] : 0.f, dr1 = rgb.y > 0.f ? sg[7] : 0.f, dr2 = rgb.z > 0.f ? sg[8] : 0.f;
+    float wk[K];
+    const float *shg = gp.sh + g;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        part[(13 + k * 3) * kPreThreads] = dr0 * Y[k];
+        part[(14 + k * 3) * kPreThreads] = dr1 * Y[k];
+        part[(15 + k * 3) * kPreThreads] = dr2 * Y[k];
+        wk[k] = dr0 * __ldg(shg + (size_t)(k * 3) * N) + dr1 * __ldg(shg + (size_t)(k * 3 + 1) * N) +
+                dr2 * __ldg(shg + (size_t)(k * 3 + 2) * N);
+    }
+    float gdx, gdy, gdz;
+    sh_grad<DEG>(dx, dy, dz, wk, gdx, gdy, gdz);
+    const float radial = gdx * dx + gdy * dy + gdz * dz;
+    const float dv0 = (gdx - dx * radial) * rn, dv1 = (gdy - dy * radial) * rn, dv2 = (gdz - dz * radial) * rn;
+    dmu[0] += dv0;
+    dmu[1] += dv1;
+    dmu[2] += dv2;
+    // the camera centre moves by -W^T rho: dL/drho gets -W dL/dC with dL/dC = -dv
+    pose6[0] += ps.W[0][0] * dv0 + ps.W[0][1] * dv1 + ps.W[0][2] * dv2;
+    pose6[1] += ps.W[1][0] * dv0 + ps.W[1][1] * dv1 + ps.W[1][2] * dv2;
+    pose6[2] += ps.W[2][0] * dv0 + ps.W[2][1] * dv1 + ps.W[2][2] * dv2;
+
+    // the blend returns dL/d ln(sigma); the logit chain is applied once at the end
+    dlno = sg[5];
+
+    // pixel mean and depth: the blend returns the sums of dL/dp1 and dL/dp2
+    // (p = m d, d = pixel - mean), so dL/du = -m00 S1, dL/dv = -(m01 S1 + m11 S2)
+    const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
+    const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
+    const float dvv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
+    dpc[0] += du * vp.fx * rz;
+    dpc[1] += dvv * vp.fy * rz;
+    dpc[2] += -(du * vp.fx * x + dvv * vp.fy * y) * rz * rz + sg[9];
+
+    // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
+    const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;
+    const float dl00 = kSqrtHalfLog2e * sg[2], dl01 = kSqrtHalfLog2e * sg[3], dl11 = kSqrtHalfLog2e * sg[4];
+    const float rdc = 1.0f / sqrtf(det * C);
+    const float dA = -0.5f * C * idet * (dl00 * p.l00 + dl01 * p.l01);
+    const float dB = dl00 * p.l00 * B * idet + dl01 * (p.l01 * B * idet - rdc);
+    const float dC = dl00 * 0.5f * p.l00 * (iC - A * idet) - dl01 * 0.5f * p.l01 * (A * idet + iC) -
+                     dl11 * 0.5f * p.l11 * iC;
+    // Sigma' = P P^T + 0.3 I
+    float dP[2][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dP[0][j] = 2.f * dA * p.P[0][j] + dB * p.P[1][j];
+        dP[1][j] = dB * p.P[0][j] + 2.f * dC * p.P[1][j];
+    }
+    // P = T M
+    float dT[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dT[r][k] = dP[r][0] * G.M[k][0] + dP[r][1] * G.M[k][1] + dP[r][2] * G.M[k][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dM[k * 3 + j] += p.T[0][k] * dP[0][j] + p.T[1][k] * dP[1][j];
+    // T = J W  (J = [[J00, 0, J02], [0, J11, J12]])
+    const float dJ00 = dT[0][0] * ps.W[0][0] + dT[0][1] * ps.W[0][1] + dT[0][2] * ps.W[0][2];
+    const float dJ02 = dT[0][0] * ps.W[2][0] + dT[0][1] * ps.W[2][1] + dT[0][2] * ps.W[2][2];
+    const float dJ11 = dT[1][0] * ps.W[1][0] + dT[1][1] * ps.W[1][1] + dT[1][2] * ps.W[1][2];
+    const float dJ12 = dT[1][0] * ps.W[2][0] + dT[1][1] * ps.W[2][1] + dT[1][2] * ps.W[2][2];
+    float dW[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dW[0][j] = p.J00 * dT[0][j];
+        dW[1][j] = p.J11 * dT[1][j];
+        dW[2][j] = p.J02 * dT[0][j] + p.J12 * dT[1][j];
+    }
+    // J(p) with clamped x/z, y/z
+    const float rz2 = rz * rz;
+    dpc[2] += -(dJ00 * vp.fx + dJ11 * vp.fy) * rz2;
+    if (p.clx) {
+        dpc[2] += dJ02 * vp.fx * p.txz * rz2;
+    } else {
+        dpc[0] += -dJ02 * vp.fx * rz2;
+        dpc[2] += 2.f * dJ02 * vp.fx * x * rz2 * rz;
+    }
+    if (p.cly) {
+        dpc[2] += dJ12 * vp.fy * p.tyz * rz2;
+    } else {
+        dpc[1] += -dJ12 * vp.fy * rz2;
+        dpc[2] += 2.f * dJ12 * vp.fy * y * rz2 * rz;
+    }
+    // p = W mu + t
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dmu[j] += ps.W[0][j] * dpc[0] + ps.W[1][j] * dpc[1] + ps.W[2][j] * dpc[2];
+    // pose twist of T_cw <- Exp(rho, phi) T_cw
+    pose6[0] += dpc[0];
+    pose6[1] += dpc[1];
+    pose6[2] += dpc[2];
+    pose6[3] += y * dpc[2] - z * dpc[1];
+    pose6[4] += z * dpc[0] - x * dpc[2];
+    pose6[5] += x * dpc[1] - y * dpc[0];
+    float Am[3][3];  // dW W^T
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Am[r][k] = dW[r][0] * ps.W[k][0] + dW[r][1] * ps.W[k][1] + dW[r][2] * ps.W[k][2];
+    pose6[3] += Am[2][1] - Am[1][2];
+    pose6[4] += Am[0][2] - Am[2][0];
+    pose6[5] += Am[1][0] - Am[0][1];
+
+#pragma unroll
+    for (int k = 0; k < 3; ++k) part[k * kPreThreads] = dmu[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) part[(3 + k) * kPreThreads] = dM[k];
+    part[12 * kPreThreads] = dlno;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = pose6[c];
+}
+
+// Shared-memory bytes of preprocess_bwd_kernel<DEG, VW>; the per-Gaussian
+// accumulator is needed only when the views take more than one chunk.
+template <int DEG>
+static size_t bwd_smem_bytes(int VW, bool multi_chunk) {
+    const size_t NV = BwdAcc<DEG>::NV, GB = kPreThreads / VW;
+    return sizeof(float) * (NV * kPreThreads + 6 * kPreThreads + (multi_chunk ? NV * GB : 0) + 6 * (kPreThreads / 32)) +
+           sizeof(int) * 2 * kPreThreads;
+}
+
+// VW views per chunk, GB = kPreThreads / VW Gaussians per block: candidate
+// thread t is (view vbase + t / GB, Gaussian gbase + t % GB).
+template <int DEG, int VW>
+__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                        const GaussianPtrs gp, const Ws ws,
+                                                                        const GradPtrs out) {
+    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV;
+    constexpr int GB = kPreThreads / VW, WARPS = kPreThreads / 32;
+    const bool multi = vt.V > VW;
+    extern __shared__ float smem[];
+    float *s_part = smem;                              // [NV][kPreThreads]
+    float *s_pose = s_part + NV * kPreThreads;         // [6][kPreThreads]
+    float *s_wpose = s_pose + 6 * kPreThreads;         // [WARPS][6]
+    float *s_acc = s_wpose + 6 * WARPS;                // [NV][GB], multi-chunk only
+    int *s_item = reinterpret_cast<int *>(s_acc + (multi ? NV * GB : 0));   // [kPreThreads]
+    int *s_rank = s_item + kPreThreads;                // [kPreThreads]
+    __shared__ int s_wcnt[WARPS];
+    __shared__ Pose s_poses[GSR_MAX_VIEWS];
+    load_poses(vt, s_poses);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gbase = blockIdx.x * GB;
+    const size_t N = (size_t)gp.N;
+    if (multi)
+        for (int k = tid; k < NV * GB; k += kPreThreads) s_acc[k] = 0.f;
+
+    for (int vbase = 0; vbase < vt.V; vbase += VW) {
+        const int cw = tid / GB, cl = tid - cw * GB;
+        const int cv = vbase + cw, cg = gbase + cl;
+        const bool vis = cv < vt.V && cg < gp.N && ws.counts[(size_t)cv * N + cg] > 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, nvis = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const int c = s_wcnt[w];
+            before += w < warp ? c : 0;
+            nvis += c;
+        }
+        const int rank = vis ? before + __popc(bal & lanemask_lt()) : -1;
+        s_rank[tid] = rank;
+        if (vis) s_item[rank] = tid;
+        __syncthreads();
+        if (tid < nvis) {
+            const int c = s_item[tid];
+            const int v = vbase + c / GB, g = gbase + c % GB;
+            pair_backward<DEG>(gp, ws, vt.v[v], s_poses[v], v, g, s_part + tid, s_pose + tid);
         }
         __syncthreads();
+        // per-view pose partial of this block's Gaussians: each warp's 32
+        // candidates share one view; warp sums, then per view in warp order
+        {
+            float pv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float x = rank >= 0 ? s_pose[c * kPreThreads + rank] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                pv[c] = x;
+            }
+            if (lane < 6) {
+                float x = pv[0];
+#pragma unroll
+                for (int c = 1; c < 6; ++c) x = lane == c ? pv[c] : x;
+                s_wpose[warp * 6 + lane] = x;
+            }
+        }
+        if (multi) {   // per-Gaussian sums over this chunk's views, in view order
+            for (int idx = tid; idx < NV * GB; idx += kPreThreads) {
+                const int k = idx / GB, l = idx - k * GB;
+                float x = s_acc[idx];
+#pragma unroll
+                for (int w = 0; w < VW; ++w) {
+                    const int r = s_rank[w * GB + l];
+                    if (r >= 0) x += s_part[k * kPreThreads + r];
+                }
+                s_acc[idx] = x;
+            }
+        }
+        __syncthreads();
+        if (tid < VW * 6) {
+            const int w = tid / 6, comp = tid - w * 6, v = vbase + w;
+            if (v < vt.V) {
+                float x = 0.f;
+                for (int q = 0; q < GB / 32; ++q) x += s_wpose[(w * (GB / 32) + q) * 6 + comp];
+                ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + comp] = x;
+            }
+        }
+        if (multi || vbase + VW < vt.V) __syncthreads();
     }
-    if (!active) return;
-    const float *gsum = s_red + (group * VW) * NV * 32 + lane;   // element k at gsum[k * 32]
-    // every warp of the group writes its share of the SH gradient rows
-    {
-        const bool ac = out.accumulate != 0;
-        for (int k = slot; k < 3 * K; k += VW) {
-            float *ps2 = out.sh + (size_t)k * N + g;
-            const float x = gsum[(13 + k) * 32];
-            *ps2 = ac ? *ps2 + x : x;
+
+    // the sum over views of component k of Gaussian gbase + l
+    auto total = [&](int k, int l) -> float {
+        if (multi) return s_acc[k * GB + l];
+        const int r = s_rank[l];   // single chunk: view slot w is view w
+        float x = r >= 0 ? s_part[k * kPreThreads + r] : 0.f;
+        for (int w = 1; w < VW; ++w) {
+            const int r2 = s_rank[w * GB + l];
+            if (r2 >= 0) x += s_part[k * kPreThreads + r2];
+        }
+        return x;
+    };
+    // outputs: SH rows by all threads, the other parameters by one thread per Gaussian
+    const bool ac = out.accumulate != 0;
+    for (int idx = tid; idx < 3 * K * GB; idx += kPreThreads) {
+        const int k = idx / GB, l = idx - k * GB, g = gbase + l;
+        if (g < gp.N) {
+            float *o = out.sh + (size_t)k * N + g;
+            const float x = total(13 + k, l);
+            *o = ac ? *o + x : x;
         }
     }
-    if (slot != 0) return;
+    if (tid >= GB) return;
+    const int g = gbase + tid;
+    if (g >= gp.N) return;
+    GaussPre G;
+    gauss_pre(gp, g, G);
+    float acc[13];
 #pragma unroll
-    for (int k = 0; k < 13; ++k) acc[k] = gsum[k * 32];
+    for (int k = 0; k < 13; ++k) acc[k] = total(k, tid);
+    const float *dmu = acc, *dM = acc + 3;
 
     // M = R diag(s) -> log-scales and the rotation
     float dR[3][3], dls[3];
@@ -359,7 +432,6 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
     for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
     const float dlogit = acc[12] * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
 
-    const bool ac = out.accumulate != 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         float *pm = out.means + (size_t)j * N + g;
@@ -429,11 +501,11 @@ cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
     }
 }
 
-template <int DEG>
-static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
-                                  cudaStream_t st) {
-    const int l = views_log2(vt.V);
-    const size_t smem = sizeof(float) * kPreWarps * BwdAcc<DEG>::NV * 32;
+template <int DEG, int VW>
+static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp, Ws ws, const GradPtrs &out,
+                                     cudaStream_t st) {
+    const bool multi = vt.V > VW;
+    const size_t smem = bwd_smem_bytes<DEG>(VW, multi);
     // More than 48 KB of dynamic shared memory needs an opt-in, set once per
     // device (the first backward on a device, which should precede capture).
     static std::mutex mu;
@@ -444,30 +516,45 @@ static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, c
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 0 || dev >= 64 || !done[dev]) {
-            e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+            e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bwd_smem_bytes<DEG>(VW, true));
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) done[dev] = true;
         }
     }
-    preprocess_bwd_kernel<DEG><<<pre_blocks(gp.N, l), kPreThreads, smem, st>>>(vt, gp, ws, out, l);
+    constexpr int GB = kPreThreads / VW;
+    const int blocks = (gp.N + GB - 1) / GB;
+    ws.pose_blocks = (uint32_t)blocks;
+    preprocess_bwd_kernel<DEG, VW><<<blocks, kPreThreads, smem, st>>>(vt, gp, ws, out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
     return cudaGetLastError();
+}
+
+template <int DEG>
+static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
+                                  cudaStream_t st) {
+    switch (views_log2(vt.V)) {
+        case 0: return launch_pre_bwd_vw<DEG, 1>(vt, gp, ws, out, st);
+        case 1: return launch_pre_bwd_vw<DEG, 2>(vt, gp, ws, out, st);
+        case 2: return launch_pre_bwd_vw<DEG, 4>(vt, gp, ws, out, st);
+        default: return launch_pre_bwd_vw<DEG, 8>(vt, gp, ws, out, st);
+    }
 }
 
 cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    if (gp.N > 0) {
-        switch (gp.sh_degree) {
-            case 0: e = launch_pre_bwd<0>(vt, gp, ws, out, st); break;
-            case 1: e = launch_pre_bwd<1>(vt, gp, ws, out, st); break;
-            case 2: e = launch_pre_bwd<2>(vt, gp, ws, out, st); break;
-            default: e = launch_pre_bwd<3>(vt, gp, ws, out, st); break;
-        }
-        if (e != cudaSuccess) return e;
+    if (gp.N == 0) {   // no Gaussians: zero pose gradients (no partials to sum)
+        pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
+        return cudaGetLastError();
     }
-    pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
-    return cudaGetLastError();
+    switch (gp.sh_degree) {
+        case 0: return launch_pre_bwd<0>(vt, gp, ws, out, st);
+        case 1: return launch_pre_bwd<1>(vt, gp, ws, out, st);
+        case 2: return launch_pre_bwd<2>(vt, gp, ws, out, st);
+        default: return launch_pre_bwd<3>(vt, gp, ws, out, st);
+    }
 }
 
 }  // namespace gsr
