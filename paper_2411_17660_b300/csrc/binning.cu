@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Ws ws) {
 }
 
 // ------------------------------------------------------------------ duplicate
+// One thread per (view, Gaussian) pair emits its keys along the exact tile spans.
 __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ ViewTable vt, const Ws ws) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ws.VN) return;
@@ -328,14 +329,14 @@ cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_
     scan_reduce_kernel<<<ws.scan_blocks, kScanThreads, 0, st>>>(ws);
     scan_partials_kernel<<<1, 1024, 0, st>>>(ws);
     scan_down_kernel<<<ws.scan_blocks, kScanThreads, 0, st>>>(ws);
+    cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st);
+    if (e != cudaSuccess) return e;
     duplicate_kernel<<<(unsigned)((ws.VN + 255) / 256), 256, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     if (ws.VN == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st);
-    if (e != cudaSuccess) return e;
     sort_hist_kernel<<<sm_count * 4, 256, 0, st>>>(ws);
     for (int p = 0; p < ws.passes; ++p) onesweep_kernel<<<sm_count * 2, kSortThreads, 0, st>>>(ws, p);
     return cudaGetLastError();

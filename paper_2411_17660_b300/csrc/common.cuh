@@ -29,7 +29,7 @@ constexpr int kMaxPasses = 8;     // 8-bit radix digits of a 64-bit key
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 12;    // keys per thread per sort tile
-constexpr int kLookBatch = 8;     // predecessor flags read per look-back round
+constexpr int kLookBatch = 16;    // predecessor flags read per look-back round
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
