@@ -275,3 +275,53 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path):
     r = A.tune(params, sc.sh_degree, cams, vm, cache=cache, reps=2)
     assert r["tile"] in A.CANDIDATES and set(r["ms"]) == set(A.CANDIDATES)
     assert A.tune(params, sc.sh_degree, cams, vm, cache=cache) == r
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_parity_sh_degrees_1_and_2(deg):
+    """The degree-1 and degree-2 SH paths (bands cut from the degree-3 scene)."""
+    sc = REDUCED["window"]()
+    K = (deg + 1) ** 2
+    sc = scenes.dataclasses.replace(sc, sh_degree=deg, sh=np.ascontiguousarray(sc.sh[:3 * K]))
+    got, state = U.gpu_forward(sc)
+    ref = oracle.render(sc)
+    for v, (r, g) in enumerate(zip(ref, got)):
+        U.compare_images(r, g, f"deg {deg} view {v}")
+    gC, gD, gA = U.upstream(sc)
+    g = U.gpu_backward(sc, state, gC, gD, gA)
+    _, rg = oracle.render_backward(sc, gC, gD, gA)
+    U.compare_grads(rg, g, label=f"deg {deg}")
+
+
+def test_no_gaussians_and_nothing_visible():
+    """N = 0, and a scene entirely behind the camera: black images, T = 1,
+    zero gradients, zero pose gradients."""
+    base = REDUCED["small"]()
+    for sc in (base.subset(np.arange(0)), scenes.dataclasses.replace(base, means=base.means * np.array([[1], [1], [-1]], np.float32))):
+        got, state = U.gpu_forward(sc)
+        for g in got:
+            assert np.all(g["color"] == 0) and np.all(g["depth"] == 0) and np.all(g["alpha"] == 0)
+        gC, gD, gA = U.upstream(sc)
+        gr = U.gpu_backward(sc, state, gC, gD, gA)
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
+            assert np.all(gr[k] == 0), k
+
+
+def test_many_views_and_tiny_images():
+    """64 views (the maximum) of sizes down to 1x1, against the oracle."""
+    rng = np.random.default_rng(3)
+    sc = REDUCED["window"]()
+    cams = []
+    for v in range(64):
+        H, W = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        c = sc.cameras[v % sc.V]
+        cams.append(scenes.Camera(H, W, c.fx * W / 100, c.fy * W / 100, W / 2, H / 2, c.T_cw))
+    sc = sc.with_cameras(cams)
+    got, state = U.gpu_forward(sc)
+    ref = oracle.render(sc)
+    for v, (r, g) in enumerate(zip(ref, got)):
+        U.compare_images(r, g, f"view {v}")
+    gC, gD, gA = U.upstream(sc)
+    g = U.gpu_backward(sc, state, gC, gD, gA)
+    _, rg = oracle.render_backward(sc, gC, gD, gA)
+    U.compare_grads(rg, g, label="64 views")
