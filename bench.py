@@ -32,6 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Mpix/s & mapping it/s (8-view batch) vs per-view launches; % FP32/SFU peak"
+# Eq. "rnd_loss" weights of the paper's Replica setting (lambda1, lambda2)
+PAPER_LAMBDA1, PAPER_LAMBDA2 = 0.8, 0.2
+LOSS_NAMES = {"l1": "L1 colour/depth loss", "paper": "L1 + SSIM colour / L1 depth loss (0.8, 0.2)"}
 FWD_OPS_PER_PAIR = 17   # FP32-pipe instructions per composited (pixel, Gaussian) pair, blend forward
 BWD_OPS_PER_PAIR = 48   # the same for the blend backward (before the per-warp reduction)
 L2_FLUSH_BYTES = 256 << 20
@@ -46,6 +49,8 @@ def parse():
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--workload", default="window", choices=["small", "room", "window", "uneven", "outdoor"],
                    help="window (8 x 640x480, 100k Gaussians) is the metric's workload; the others are for reports")
+    p.add_argument("--loss", default="l1", choices=["l1", "paper"],
+                   help="l1: L1 colour + weighted L1 depth; paper: the mixed L1 + SSIM + depth loss (0.8, 0.2)")
     p.add_argument("--autotune", action="store_true", help="pick the tile size with the autotuner first")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -242,12 +247,13 @@ def reference_arm(args, ws, rank):
 class Window:
     """Device state of one mapping window (inputs, outputs, workspace)."""
 
-    def __init__(self, scene, rast, views=None, dev="cuda"):
+    def __init__(self, scene, rast, views=None, dev="cuda", loss="l1"):
         import torch
         from paper_2411_17660_b300 import render as R
         self.R, self.torch = R, torch
         idx = list(range(scene.V)) if views is None else views
         self.scene = scene
+        self.loss_kind = loss
         self.cams = [R.Intrinsics(scene.cameras[v].H, scene.cameras[v].W, scene.cameras[v].fx,
                                   scene.cameras[v].fy, scene.cameras[v].cx, scene.cameras[v].cy) for v in idx]
         self.params = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(dev)
@@ -274,8 +280,12 @@ class Window:
         R, sc = self.R, self.scene
         self.rast.forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
                               self.alpha)
-        R.l1_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, 1.0, sc.depth_weight,
-                  self.dC, self.dD, self.loss)
+        if self.loss_kind == "l1":
+            R.l1_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, 1.0,
+                      sc.depth_weight, self.dC, self.dD, self.loss)
+        else:
+            R.rgbd_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, PAPER_LAMBDA1,
+                        PAPER_LAMBDA2, self.dC, self.dD, self.loss)
         self.rast.backward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.dC, self.dD, None,
                                self.grads, self.d_pose, accumulate=accumulate)
 
@@ -339,12 +349,12 @@ def main():
     tile, tuned = args.tile, None
     if args.autotune:
         from paper_2411_17660_b300 import autotune as A
-        w0 = Window(scene, R.GaussianRasterizer(16))
+        w0 = Window(scene, R.GaussianRasterizer(16), loss=args.loss)
         tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
         tile = tuned["tile"]
         del w0
     rast = R.GaussianRasterizer(tile)
-    win = Window(scene, rast)
+    win = Window(scene, rast, loss=args.loss)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
     K, W = args.steps, args.warmup
@@ -382,11 +392,13 @@ def main():
     for k, name in enumerate(B.STAGES):
         a, b = B.STAGE_SPANS[k]
         stage_ms[name] = statistics.mean(ev_sets[i][a].elapsed_time(ev_sets[i][b]) for i in range(K))
+    # the loss front end runs between the forward's last event and the backward's first
+    stage_ms["loss"] = statistics.mean(ev_sets[i][5].elapsed_time(ev_sets[i][6]) for i in range(K))
 
     # the same window as 8 per-view launches
     per_view = None
     if not args.no_per_view:
-        wins = [Window(scene, rast, [v]) for v in range(scene.V)]
+        wins = [Window(scene, rast, [v], loss=args.loss) for v in range(scene.V)]
 
         def per_view_step():
             for i, w1 in enumerate(wins):
@@ -446,7 +458,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
                    "sh_degree": scene.sh_degree, "tile": tile, "autotune": tuned,
-                   "step": "forward + L1 colour/depth loss + backward (params + 8 poses)",
+                   "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
                    "l2": "flushed before every step (256 MB write), outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "mapping_it_per_s": 1000.0 / ms_step,

@@ -188,6 +188,18 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
 gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V,
                        float color_weight, float depth_weight, float *loss, gsr_stream stream);
 
+/* Mixed rendering loss of Eq. "rnd_loss" (Sec. 3.3), summed over views:
+ *   lambda1 [(1 - lambda2) mean|C - C*| + lambda2 (1 - SSIM(C, C*))]
+ *   + (1 - lambda1) mean|D - D*|,
+ * SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2,
+ * zero padding, averaged over the 3 channels and the pixels; the paper uses
+ * lambda2 = 0.2 and lambda1 = 0.9 (TUM-RGBD) or 0.8 (Replica).  Reads each
+ * view's rendered color/depth, writes dL/dC and dL/dD into targets[v]
+ * (d_depth may be NULL; without target_depth the depth term is 0).  loss:
+ * device float, overwritten.  Needs no workspace. */
+gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V, float lambda1,
+                         float lambda2, float *loss, gsr_stream stream);
+
 /* Stage events (a profiling aid).  events holds GSR_STAGE_EVENTS cudaEvent_t
  * handles created by the caller (copied at this call), or is NULL to stop.
  * While set, gsr_render records events[0] on its stream before its first

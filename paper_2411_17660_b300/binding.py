@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_l1_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
                                 ctypes.c_float, _p, _p]),
         "gsr_set_stage_events": (c_int, [_p, ctypes.POINTER(_p)]),
+        "gsr_rgbd_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
+                                  ctypes.c_float, _p, _p]),
         "gsr_render_noalloc": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, _p, _p]),
         "gsr_last_error": (ctypes.c_char_p, [_p]),
         "gsr_status_string": (ctypes.c_char_p, [c_int]),
@@ -170,6 +172,12 @@ class Context:
             return
         arr = (_p * STAGE_EVENTS)(*handles)
         self.check(self.lib.gsr_set_stage_events(self.h, arr), "gsr_set_stage_events")
+
+    def rgbd_loss(self, views, targets, lambda1: float, lambda2: float, loss_ptr: int, stream: int):
+        arr = (View * len(views))(*views)
+        tarr = (L1View * len(targets))(*targets)
+        self.check(self.lib.gsr_rgbd_loss(self.h, arr, tarr, len(views), lambda1, lambda2, loss_ptr, stream),
+                   "gsr_rgbd_loss")
 
     def l1_loss(self, views, targets, color_weight: float, depth_weight: float, loss_ptr: int, stream: int):
         arr = (View * len(views))(*views)

@@ -440,6 +440,24 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
     return GSR_OK;
 }
 
+gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V, float lambda1,
+                         float lambda2, float *loss, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, true);
+    if (s != GSR_OK) return s;
+    if (!targets || !loss) return fail(ctx, GSR_EINVAL, "targets and loss must be non-NULL");
+    if (!(lambda1 >= 0.f && lambda1 <= 1.f && lambda2 >= 0.f && lambda2 <= 1.f))
+        return fail(ctx, GSR_EINVAL, "lambda1 and lambda2 must lie in [0, 1]");
+    for (int v = 0; v < V; ++v)
+        if (!targets[v].target_color || !targets[v].d_color)
+            return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
+    ViewTable vt;
+    fill_views(vt, views, nullptr, V, ctx->tile);
+    cudaError_t e = launch_rgbd_loss(vt, targets, lambda1, lambda2, loss, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rgbd loss");
+    return GSR_OK;
+}
+
 gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events) {
     if (!ctx) return GSR_EINVAL;
     ctx->timing = events != nullptr;

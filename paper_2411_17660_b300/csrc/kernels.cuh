@@ -28,6 +28,8 @@ cudaError_t launch_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st)
 void set_ctx_error(gsr_ctx *ctx, const char *msg);
 
 // loss.cu
+cudaError_t launch_rgbd_loss(const ViewTable &vt, const gsr_l1_view *targets, float lambda1, float lambda2,
+                             float *loss, cudaStream_t st);
 cudaError_t launch_l1_loss(const ViewTable &vt, const gsr_l1_view *targets, float color_weight, float depth_weight,
                            float *loss, cudaStream_t st);
 

@@ -215,3 +215,19 @@ def l1_loss(rast: GaussianRasterizer, cams, viewmats, color, depth, target_color
                            d_color.data_ptr() + 12 * off[v],
                            0 if d_depth is None else d_depth.data_ptr() + 4 * off[v]))
     rast.ctx.l1_loss(views, t, color_weight, depth_weight, loss.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
+
+def rgbd_loss(rast: GaussianRasterizer, cams, viewmats, color, depth, target_color, target_depth,
+              lambda1: float, lambda2: float, d_color, d_depth, loss):
+    """Mixed L1 + SSIM colour and L1 depth loss of the paper (library kernel):
+    fills d_color, d_depth and the device scalar loss.  Flat buffers laid out
+    like the render outputs; lambda2 = 0.2 and lambda1 = 0.9 / 0.8 in the paper."""
+    views = view_structs(cams, viewmats, color, depth, None)
+    off = pixel_offsets(cams)
+    t = []
+    for v in range(len(cams)):
+        t.append(_b.L1View(target_color.data_ptr() + 12 * off[v],
+                           0 if target_depth is None else target_depth.data_ptr() + 4 * off[v],
+                           d_color.data_ptr() + 12 * off[v],
+                           0 if d_depth is None else d_depth.data_ptr() + 4 * off[v]))
+    rast.ctx.rgbd_loss(views, t, lambda1, lambda2, loss.data_ptr(), torch.cuda.current_stream().cuda_stream)
