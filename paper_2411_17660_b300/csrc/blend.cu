@@ -18,6 +18,15 @@
 // (two pixels per lane) and with a transposing warp butterfly before one set
 // of global atomics per (warp, Gaussian); when at most two lanes touch a
 // Gaussian they issue their atomics directly instead.
+//
+// In the backward, a lane's two pixels share their column, hence dx: their
+// per-pixel arithmetic runs on packed FP32 pairs (one fma.rn.f32x2 for both
+// pixels, the same rounding as two scalar ones, so that the decisions stay
+// bit-identical to the forward's scalar ones).  Its staged entries hold every
+// operand that both pixels use as a duplicated pair, so that one 128-bit
+// shared load yields two ready register pairs.  The forward stays scalar: it
+// skips a pixel row's work whenever no lane of the warp needs it, which
+// saves more than packing would.
 #include "kernels.cuh"
 
 namespace gsr {
@@ -44,6 +53,29 @@ __device__ __forceinline__ float pair_s(float dx, float dy, float m00, float m01
     p1 = __fmaf_rn(m00, dx, __fmul_rn(m01, dy));
     p2 = __fmul_rn(m11, dy);
     return __fmaf_rn(p1, p1, __fmul_rn(p2, p2));
+}
+
+// Backward: staged entry of a warp's slot k, five float4 of pairs and one
+// float2.
+//   e0 = (-ur, -ur, -vr, -vr)  mean relative to the warp's block origin
+//   e1 = (m00, m00, m01, m01)  Cholesky factor of 0.5 log2(e) Sigma'^-1
+//   e2 = (m11, m11, l, l)      l = log2(opacity)
+//   e3 = (r, r, g, g), e4 = (b, b, z, z)
+//   x  = (s_max, list index as bits)
+constexpr int kEntryQuads = 5;
+
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// s = 0.5 log2(e) d^2 of a lane's two pixels at offsets (dx, dy.x) and
+// (dx, dy.y) from the mean, with the Cholesky factor m of 0.5 log2(e)
+// Sigma'^-1.  Round-to-nearest throughout: the forward and the backward take
+// bit-identical decisions.
+__device__ __forceinline__ float2 pair_s2(float2 dx, float2 dy, float2 m00, float2 m01, float2 m11, float2 &p1,
+                                          float2 &p2) {
+    p1 = __ffma2_rn(m00, dx, __fmul2_rn(m01, dy));
+    p2 = __fmul2_rn(m11, dy);
+    return __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
 }
 
 // Whether min over the warp's block of pixel centres of s can reach s_max.
@@ -141,9 +173,10 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
 
 // Loads entry idx of the tile list (lane-parallel), tests it against the
 // warp's block and compacts the survivors into the warp's slots in list
-// order.  Returns the number of survivors.
+// order; Stage writes one survivor's slot.  Returns the number of survivors.
+template <typename Stage>
 __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, size_t vN, uint32_t idx, uint32_t end,
-                                           int X0, int Y0, float4 *sA, float4 *sB, float4 *sC) {
+                                           int X0, int Y0, Stage &&write) {
     bool keep = false;
     float4 r0, r1;
     float ur = 0.f, vr = 0.f;
@@ -158,14 +191,7 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
         keep = touches_block(ur, vr, r1.x, r1.y, r1.z, r1.w);
     }
     const unsigned ballot = __ballot_sync(kFull, keep);
-    if (keep) {
-        const int slot = __popc(ballot & lanemask_lt());
-        const float4 r2 = ws.rec2[gi];
-        const float log2o = ws.rec3[gi].x;
-        sA[slot] = make_float4(ur, vr, r1.x, r1.y);
-        sB[slot] = make_float4(r1.z, r1.w, log2o, r2.w);
-        sC[slot] = make_float4(r2.x, r2.y, r2.z, __uint_as_float(idx));
-    }
+    if (keep) write(__popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, idx);
     __syncwarp();
     return __popc(ballot);
 }
@@ -197,7 +223,12 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
 #pragma unroll
         for (int q = 0; q < kPPL; ++q) all_done &= done[q];
         if (__all_sync(kFull, all_done)) break;
-        const int n = stage_chunk(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0, sA[warp], sB[warp], sC[warp]);
+        const int n = stage_chunk(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
+                                  [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o, uint32_t idx) {
+                                      sA[warp][slot] = make_float4(ur, vr, r1.x, r1.y);
+                                      sB[warp][slot] = make_float4(r1.z, r1.w, log2o, r2.w);
+                                      sC[warp][slot] = make_float4(r2.x, r2.y, r2.z, __uint_as_float(idx));
+                                  });
         for (int j = 0; j < n; ++j) {
             const float4 a = sA[warp][j], b = sB[warp][j];
             const float dx = __fsub_rn(lxf, a.x);
@@ -249,7 +280,8 @@ template <int TS>
 __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     using S = BlendShape<TS>;
-    __shared__ float4 sA[S::WARPS][32], sB[S::WARPS][32], sC[S::WARPS][32];
+    __shared__ float4 sE[S::WARPS][kEntryQuads][32];
+    __shared__ float2 sX[S::WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
@@ -257,93 +289,106 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
     const size_t N = ws.N;
     const size_t vN = (size_t)wt.v * N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
+    const float2 lx2 = make_float2(lxf, lxf), ly2 = make_float2(lyf, lyf + (float)kRowStep);
+    const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
+    const float2 m2ln2 = make_float2(-2.f * kLn2, -2.f * kLn2);
 
-    // Q = gC . (colour behind) + gD (depth behind), normalised by the
-    // transmittance in front of the current entry
-    float T[kPPL], gC0[kPPL], gC1[kPPL], gC2[kPPL], gD[kPPL], gATf[kPPL], Q[kPPL];
+    // per pixel (.x, .y as in the forward): Q = gC . (colour behind) + gD
+    // (depth behind), normalised by the transmittance in front of the
+    // current entry
+    float Tq[kPPL], gq[5][kPPL];
     uint32_t last[kPPL], lmax = 0;
 #pragma unroll
     for (int q = 0; q < kPPL; ++q) {
-        T[q] = 1.f;
-        gC0[q] = gC1[q] = gC2[q] = gD[q] = gATf[q] = 0.f;
-        Q[q] = 0.f;
+        Tq[q] = 1.f;
         last[q] = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) gq[k][q] = 0.f;
         const int py = wt.py + q * kRowStep;
         if (wt.px < vp.W && py < vp.H) {
             const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
-            T[q] = ws.T_final[vp.pixel_offset + pix];
+            Tq[q] = ws.T_final[vp.pixel_offset + pix];
             last[q] = ws.last[vp.pixel_offset + pix];
             if (vp.d_color) {
-                gC0[q] = vp.d_color[pix];
-                gC1[q] = vp.d_color[HW + pix];
-                gC2[q] = vp.d_color[2 * HW + pix];
+                gq[0][q] = vp.d_color[pix];
+                gq[1][q] = vp.d_color[HW + pix];
+                gq[2][q] = vp.d_color[2 * HW + pix];
             }
-            if (vp.d_depth) gD[q] = vp.d_depth[pix];
-            if (vp.d_alpha) gATf[q] = vp.d_alpha[pix] * T[q];
+            if (vp.d_depth) gq[3][q] = vp.d_depth[pix];
+            if (vp.d_alpha) gq[4][q] = vp.d_alpha[pix] * Tq[q];
         }
         lmax = max(lmax, last[q]);
     }
+    float2 T = make_float2(Tq[0], Tq[1]), Q = make_float2(0.f, 0.f);
+    const float2 gR = make_float2(gq[0][0], gq[0][1]), gG = make_float2(gq[1][0], gq[1][1]);
+    const float2 gB = make_float2(gq[2][0], gq[2][1]), gZ = make_float2(gq[3][0], gq[3][1]);
+    const float2 gATf = make_float2(gq[4][0], gq[4][1]);
     const uint32_t wlast = __reduce_max_sync(kFull, lmax);
     float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads * N;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u ? end - 32u : wt.range.x;
-        const int n = stage_chunk(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0, sA[warp], sB[warp], sC[warp]);
+        const int n = stage_chunk(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0,
+                                  [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o, uint32_t idx) {
+                                      float4(&e)[kEntryQuads][32] = sE[warp];
+                                      e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
+                                      e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
+                                      e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
+                                      e[3][slot] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                                      e[4][slot] = make_float4(r2.z, r2.z, r2.w, r2.w);
+                                      sX[warp][slot] = make_float2(r1.w, __uint_as_float(idx));
+                                  });
         for (int j = n - 1; j >= 0; --j) {
-            const float4 a = sA[warp][j], b = sB[warp][j], c = sC[warp][j];
-            const uint32_t eidx = __float_as_uint(c.w);
-            const float dx = __fsub_rn(lxf, a.x);
-            float p1[kPPL], p2[kPPL], dy[kPPL], sv[kPPL];
-            bool contrib[kPPL], any = false;
-#pragma unroll
-            for (int q = 0; q < kPPL; ++q) {
-                dy[q] = __fsub_rn(lyf + (float)(q * kRowStep), a.y);
-                sv[q] = pair_s(dx, dy[q], a.z, a.w, b.x, p1[q], p2[q]);
-                contrib[q] = eidx < last[q] && sv[q] <= b.y;
-                any |= contrib[q];
-            }
-            const unsigned cmask = __ballot_sync(kFull, any);
+            const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
+            const float2 x = sX[warp][j];
+            const uint32_t eidx = __float_as_uint(x.y);
+            const float2 dx = __fadd2_rn(lx2, lo2(e0)), dy = __fadd2_rn(ly2, hi2(e0));
+            float2 p1, p2;
+            const float2 s = pair_s2(dx, dy, lo2(e1), hi2(e1), lo2(e2), p1, p2);
+            const bool c0 = eidx < last[0] && s.x <= x.x, c1 = eidx < last[1] && s.y <= x.x;
+            const unsigned cmask = __ballot_sync(kFull, c0 || c1);
             if (cmask == 0u) continue;
+            // Branch-free: a pixel without a contribution runs with alpha = 0,
+            // which leaves its T and Q unchanged and makes every gradient
+            // term zero.
+            const float2 arg = __ffma2_rn(s, neg2, hi2(e2));
+            const float2 raw = make_float2(c0 ? ex2_approx(arg.x) : 0.f, c1 ? ex2_approx(arg.y) : 0.f);
+            const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+            const float2 om = __ffma2_rn(al, neg2, one2);
+            const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+            const float2 Ti = __fmul2_rn(T, rom);
+            const float2 w = __fmul2_rn(al, Ti);
+            // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
+            // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
+            const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
+            const float2 gc = __ffma2_rn(gR, lo2(e3), __ffma2_rn(gG, hi2(e3), __ffma2_rn(gB, lo2(e4),
+                                                                                        __fmul2_rn(gZ, hi2(e4)))));
+            const float2 dgq = __ffma2_rn(Q, neg2, gc);
+            const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gATf, rom));
+            Q = __ffma2_rn(al, dgq, Q);
+            T = Ti;
+            // no gradient to position or opacity through the 0.99 clamp
+            float2 glo = __fmul2_rn(dA, raw);                       // dL/d ln(sigma)
+            glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
+            glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+            const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
+            const float2 dp1 = __fmul2_rn(p1, ds2), dp2 = __fmul2_rn(p2, ds2);
             float gv[kVGGrads];
-#pragma unroll
-            for (int k = 0; k < kVGGrads; ++k) gv[k] = 0.f;
-#pragma unroll
-            for (int q = 0; q < kPPL; ++q) {
-                // Branch-free: a pixel without a contribution runs with
-                // alpha = 0, which leaves its T and accumulated colour
-                // unchanged and makes every gradient term zero.
-                const float raw = contrib[q] ? ex2_approx(__fsub_rn(b.z, sv[q])) : 0.f;
-                const float alpha = fminf(kAlphaMax, raw);
-                const float rom = rcp_approx(1.f - alpha);
-                const float Ti = T[q] * rom;
-                const float w = alpha * Ti;
-                gv[6] = fmaf(gC0[q], w, gv[6]);
-                gv[7] = fmaf(gC1[q], w, gv[7]);
-                gv[8] = fmaf(gC2[q], w, gv[8]);
-                gv[9] = fmaf(gD[q], w, gv[9]);
-                // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
-                // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
-                const float gc = fmaf(gC0[q], c.x, fmaf(gC1[q], c.y, fmaf(gC2[q], c.z, gD[q] * b.w)));
-                const float dgq = gc - Q[q];
-                const float dA = fmaf(Ti, dgq, gATf[q] * rom);
-                Q[q] = fmaf(alpha, dgq, Q[q]);
-                T[q] = Ti;
-                // no gradient to position or opacity through the 0.99 clamp
-                const float glo = raw <= kAlphaMax ? dA * raw : 0.f;   // dL/d ln(sigma)
-                const float ds2 = (-2.f * kLn2) * glo;                  // 2 dL/ds
-                const float dp1 = p1[q] * ds2, dp2 = p2[q] * ds2;
-                gv[5] += glo;
-                gv[0] += dp1;                                          // du, dv follow from these and m
-                gv[1] += dp2;
-                gv[2] = fmaf(dp1, dx, gv[2]);
-                gv[3] = fmaf(dp1, dy[q], gv[3]);
-                gv[4] = fmaf(dp2, dy[q], gv[4]);
-            }
+            gv[0] = dp1.x + dp1.y;                                  // du, dv follow from these and m
+            gv[1] = dp2.x + dp2.y;
+            gv[2] = dx.x * gv[0];
+            gv[3] = fmaf(dp1.y, dy.y, dp1.x * dy.x);
+            gv[4] = fmaf(dp2.y, dy.y, dp2.x * dy.x);
+            gv[5] = glo.x + glo.y;
+            gv[6] = fmaf(gR.y, w.y, gR.x * w.x);
+            gv[7] = fmaf(gG.y, w.y, gG.x * w.x);
+            gv[8] = fmaf(gB.y, w.y, gB.x * w.x);
+            gv[9] = fmaf(gZ.y, w.y, gZ.x * w.x);
             const uint32_t g = vals[eidx];
             if (g >= N) continue;
             if (__popc(cmask) <= 2) {
                 // one or two lanes: their own atomics are cheaper than a reduction
-                if (any) {
+                if (c0 || c1) {
 #pragma unroll
                     for (int k = 0; k < kVGGrads; ++k) atomicAdd(grads + (size_t)k * N + g, gv[k]);
                 }
