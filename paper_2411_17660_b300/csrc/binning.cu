@@ -168,12 +168,49 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ws ws) {
     }
 }
 
+// One round of a digit's decoupled look-back over tiles hi-1, hi-2, ...,
+// hi-W (col: the digit's column of the [tile][digit] flags): adds the
+// published counts down to the first inclusive flag or to the first flag not
+// yet published, and returns the new hi.  Below tile 0 reads as an
+// inclusive zero.
+constexpr int kLookNear = 16;
+constexpr int kSortBlocksPerSM = 3;   // resident onesweep CTAs per SM (registers and shared memory allow 3)
+constexpr int kLookAll = 0, kLookFound = 1, kLookWaiting = 2;
+template <int W>
+__device__ __forceinline__ int lookback_round(const uint32_t *col, int hi, uint32_t &prefix, int &state) {
+    uint32_t f[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const int u = hi - 1 - q;
+        f[q] = u >= 0 ? ld_relaxed_gpu(col + (size_t)u * kRadix) : kFlagInc;
+    }
+    state = kLookAll;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        if (state != kLookAll) continue;
+        const uint32_t flag = f[q] & ~kCountMask;
+        if (flag == 0u) {
+            state = kLookWaiting;
+            continue;
+        }
+        prefix += f[q] & kCountMask;
+        --hi;
+        if (flag == kFlagInc) state = kLookFound;
+    }
+    return hi;
+}
+
 // One stable LSD pass over 8 bits: tiles of kSortTile keys are taken in order
 // from an atomic counter; each tile ranks its keys per digit (warp match +
-// per-warp counters), publishes its digit counts, resolves its global digit
-// offsets by a bounded decoupled look-back over earlier tiles, then scatters
-// through shared memory so that global writes are runs of equal digits.
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int pass) {
+// per-warp counters), publishes its digit counts, places its keys in shared
+// memory in digit order, resolves its global digit offsets by a bounded
+// decoupled look-back over earlier tiles, then writes them out, so that
+// global writes are runs of equal digits.  One thread per digit walks the
+// look-back; a round first reads the 16 nearest predecessors (while they are
+// still being ranked, polling them is cheap) and, once those are all
+// published, kLookBatch at a time, so that one round trip to L2 advances the
+// walk by up to kLookBatch tiles.
+__global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kernel(const Ws ws, int pass) {
     constexpr int WARPS = kSortThreads / 32;
     __shared__ uint32_t s_whist[WARPS][kRadix];
     __shared__ uint32_t s_hist_ex[kRadix];
@@ -192,8 +229,9 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int
     const uint32_t *vals_in = ws.vals[pass & 1];
     unsigned long long *keys_out = ws.keys[(pass + 1) & 1];
     uint32_t *vals_out = ws.vals[(pass + 1) & 1];
-    uint32_t *lb = ws.lookback + (size_t)(pass & 1) * ws.lb_tiles * kRadix;
-    uint32_t *lb_next = ws.lookback + (size_t)((pass + 1) & 1) * ws.lb_tiles * kRadix;
+    // this thread's digit column of the flags of this pass and of the next ([tile][digit])
+    uint32_t *col = ws.lookback + (size_t)(pass & 1) * ws.lb_tiles * kRadix + d_own;
+    uint32_t *col_next = ws.lookback + (size_t)((pass + 1) & 1) * ws.lb_tiles * kRadix + d_own;
 
     {   // global exclusive digit offsets of this pass
         uint32_t total;
@@ -206,18 +244,23 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int
         __syncthreads();
         const uint32_t t = s_tile;
         if (t >= ntiles) break;
-        // the next pass's look-back slot of this tile (its array is idle now)
-        lb_next[(size_t)t * kRadix + d_own] = 0u;
+        col_next[(size_t)t * kRadix] = 0u;   // the next pass's flag of this tile (its array is idle now)
 
         const uint32_t base = t * kSortTile + warp * (kSortItems * 32);
+        uint32_t rank[kSortItems];
         unsigned long long k[kSortItems];
-        uint32_t val[kSortItems], rank[kSortItems];
+        uint32_t val[kSortItems];
+        // all loads first: the warp barriers of the ranking below would
+        // otherwise serialise them
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const uint32_t idx = base + it * 32 + lane;
-            const bool valid = idx < n;
-            k[it] = valid ? keys_in[idx] : 0ull;
-            val[it] = valid ? vals_in[idx] : 0u;
+            k[it] = idx < n ? keys_in[idx] : 0ull;
+            val[it] = idx < n ? vals_in[idx] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const bool valid = base + it * 32 + lane < n;
             const uint32_t d = valid ? (uint32_t)((k[it] >> shift) & 0xff) : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
@@ -240,48 +283,14 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int
             s_whist[w][d_own] = cnt;
             cnt += c;
         }
-        uint32_t *my = lb + (size_t)t * kRadix + d_own;
         const bool stalled = t == 0 && pass == 0 && (ws.test_flags & GSR_TEST_STALL_SORT);
-        if (!stalled) st_relaxed_gpu(my, (t == 0 ? kFlagInc : kFlagAgg) | cnt);
+        if (!stalled) st_relaxed_gpu(col + (size_t)t * kRadix, (t == 0 ? kFlagInc : kFlagAgg) | cnt);
         uint32_t tile_total;
         const uint32_t tile_ex = block_exclusive_scan<uint32_t, kSortThreads>(cnt, s_scan, tile_total);
         s_tile_ex[d_own] = tile_ex;
-
-        // bounded decoupled look-back
-        // The flags of kLookBatch predecessors are loaded at once, so the
-        // walk costs one memory round trip per kLookBatch tiles.
-        uint32_t prefix = 0;
-        if (t > 0) {
-            int j = (int)t - 1;
-            uint32_t spins = 0;
-            bool found = false;
-            while (!found) {
-                uint32_t f[kLookBatch];
-#pragma unroll
-                for (int k = 0; k < kLookBatch; ++k)
-                    f[k] = j - k >= 0 ? ld_relaxed_gpu(lb + (size_t)(j - k) * kRadix + d_own) : kFlagInc;
-                int k = 0;
-#pragma unroll
-                for (int q = 0; q < kLookBatch; ++q) {
-                    if (found || k != q) continue;   // stop at the first inclusive or not-ready flag
-                    const uint32_t flag = f[q] & ~kCountMask;
-                    if (flag == 0u) continue;
-                    prefix += f[q] & kCountMask;
-                    if (flag == kFlagInc) found = true;
-                    ++k;
-                }
-                if (found) break;
-                j -= k;
-                if (k < kLookBatch && ++spins > ws.spin_limit) {  // waited on a flag that never came
-                    set_status(ws.hdr, GSR_ETIMEOUT);
-                    break;
-                }
-            }
-            st_relaxed_gpu(my, kFlagInc | ((prefix + cnt) & kCountMask));
-        }
-        s_glob[d_own] = s_hist_ex[d_own] + prefix - tile_ex;
         __syncthreads();
-
+        // the tile in digit order in shared memory (frees the registers
+        // before the look-back)
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const uint32_t idx = base + it * 32 + lane;
@@ -292,7 +301,31 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const Ws ws, int
                 s_vals[local] = val[it];
             }
         }
+
+        // bounded decoupled look-back: sums the counts of earlier tiles down
+        // to the first inclusive flag; a flag not yet published means
+        // another round trip
+        uint32_t prefix = 0;
+        if (t > 0) {
+            int hi = (int)t;   // tiles [0, hi) not yet summed
+            uint32_t spins = 0;
+            bool wide = false;
+            for (;;) {
+                int state;
+                hi = wide ? lookback_round<kLookBatch>(col, hi, prefix, state)
+                          : lookback_round<kLookNear>(col, hi, prefix, state);
+                if (state == kLookFound) break;
+                wide = state == kLookAll;
+                if (state == kLookWaiting && ++spins > ws.spin_limit) {  // waited on a flag that never came
+                    set_status(ws.hdr, GSR_ETIMEOUT);
+                    break;
+                }
+            }
+            st_relaxed_gpu(col + (size_t)t * kRadix, kFlagInc | ((prefix + cnt) & kCountMask));
+        }
+        s_glob[d_own] = s_hist_ex[d_own] + prefix - tile_ex;
         __syncthreads();
+
         const uint32_t tile_n = min((uint32_t)kSortTile, n - t * kSortTile);
         for (uint32_t j = threadIdx.x; j < tile_n; j += kSortThreads) {
             const unsigned long long key = s_keys[j];
@@ -338,7 +371,7 @@ cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     if (ws.VN == 0) return cudaSuccess;
     sort_hist_kernel<<<sm_count * 4, 256, 0, st>>>(ws);
-    for (int p = 0; p < ws.passes; ++p) onesweep_kernel<<<sm_count * 2, kSortThreads, 0, st>>>(ws, p);
+    for (int p = 0; p < ws.passes; ++p) onesweep_kernel<<<sm_count * kSortBlocksPerSM, kSortThreads, 0, st>>>(ws, p);
     return cudaGetLastError();
 }
 

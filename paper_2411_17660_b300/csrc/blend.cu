@@ -64,6 +64,11 @@ __device__ __forceinline__ float pair_s(float dx, float dy, float m00, float m01
 //   x  = (s_max, list index as bits)
 constexpr int kEntryQuads = 5;
 
+template <int R>
+struct RowTag {
+    static constexpr int value = R;
+};
+
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
@@ -346,44 +351,87 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
             float2 p1, p2;
             const float2 s = pair_s2(dx, dy, lo2(e1), hi2(e1), lo2(e2), p1, p2);
             const bool c0 = eidx < last[0] && s.x <= x.x, c1 = eidx < last[1] && s.y <= x.x;
-            const unsigned cmask = __ballot_sync(kFull, c0 || c1);
+            const unsigned m0 = __ballot_sync(kFull, c0), m1 = __ballot_sync(kFull, c1);
+            const unsigned cmask = m0 | m1;
             if (cmask == 0u) continue;
-            // Branch-free: a pixel without a contribution runs with alpha = 0,
-            // which leaves its T and Q unchanged and makes every gradient
-            // term zero.
-            const float2 arg = __ffma2_rn(s, neg2, hi2(e2));
-            const float2 raw = make_float2(c0 ? ex2_approx(arg.x) : 0.f, c1 ? ex2_approx(arg.y) : 0.f);
-            const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-            const float2 om = __ffma2_rn(al, neg2, one2);
-            const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-            const float2 Ti = __fmul2_rn(T, rom);
-            const float2 w = __fmul2_rn(al, Ti);
-            // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
-            // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
             const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
-            const float2 gc = __ffma2_rn(gR, lo2(e3), __ffma2_rn(gG, hi2(e3), __ffma2_rn(gB, lo2(e4),
-                                                                                        __fmul2_rn(gZ, hi2(e4)))));
-            const float2 dgq = __ffma2_rn(Q, neg2, gc);
-            const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gATf, rom));
-            Q = __ffma2_rn(al, dgq, Q);
-            T = Ti;
-            // no gradient to position or opacity through the 0.99 clamp
-            float2 glo = __fmul2_rn(dA, raw);                       // dL/d ln(sigma)
-            glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
-            glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
-            const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
-            const float2 dp1 = __fmul2_rn(p1, ds2), dp2 = __fmul2_rn(p2, ds2);
             float gv[kVGGrads];
-            gv[0] = dp1.x + dp1.y;                                  // du, dv follow from these and m
-            gv[1] = dp2.x + dp2.y;
-            gv[2] = dx.x * gv[0];
-            gv[3] = fmaf(dp1.y, dy.y, dp1.x * dy.x);
-            gv[4] = fmaf(dp2.y, dy.y, dp2.x * dy.x);
-            gv[5] = glo.x + glo.y;
-            gv[6] = fmaf(gR.y, w.y, gR.x * w.x);
-            gv[7] = fmaf(gG.y, w.y, gG.x * w.x);
-            gv[8] = fmaf(gB.y, w.y, gB.x * w.x);
-            gv[9] = fmaf(gZ.y, w.y, gZ.x * w.x);
+            if (m0 != 0u && m1 != 0u) {
+                // Both pixel rows, packed.  Branch-free: a pixel without a
+                // contribution runs with alpha = 0, which leaves its T and Q
+                // unchanged and makes every gradient term zero.
+                const float2 arg = __ffma2_rn(s, neg2, hi2(e2));
+                const float2 raw = make_float2(c0 ? ex2_approx(arg.x) : 0.f, c1 ? ex2_approx(arg.y) : 0.f);
+                const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                const float2 om = __ffma2_rn(al, neg2, one2);
+                const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                const float2 Ti = __fmul2_rn(T, rom);
+                const float2 w = __fmul2_rn(al, Ti);
+                // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
+                // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
+                const float2 gc = __ffma2_rn(gR, lo2(e3), __ffma2_rn(gG, hi2(e3), __ffma2_rn(gB, lo2(e4),
+                                                                                            __fmul2_rn(gZ, hi2(e4)))));
+                const float2 dgq = __ffma2_rn(Q, neg2, gc);
+                const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gATf, rom));
+                Q = __ffma2_rn(al, dgq, Q);
+                T = Ti;
+                // no gradient to position or opacity through the 0.99 clamp
+                float2 glo = __fmul2_rn(dA, raw);                       // dL/d ln(sigma)
+                glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
+                glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+                const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
+                const float2 dp1 = __fmul2_rn(p1, ds2), dp2 = __fmul2_rn(p2, ds2);
+                gv[0] = dp1.x + dp1.y;                                  // du, dv follow from these and m
+                gv[1] = dp2.x + dp2.y;
+                gv[2] = dx.x * gv[0];
+                gv[3] = fmaf(dp1.y, dy.y, dp1.x * dy.x);
+                gv[4] = fmaf(dp2.y, dy.y, dp2.x * dy.x);
+                gv[5] = glo.x + glo.y;
+                gv[6] = fmaf(gR.y, w.y, gR.x * w.x);
+                gv[7] = fmaf(gG.y, w.y, gG.x * w.x);
+                gv[8] = fmaf(gB.y, w.y, gB.x * w.x);
+                gv[9] = fmaf(gZ.y, w.y, gZ.x * w.x);
+            } else {
+                // Only one pixel row of the warp is reached: scalar work on it.
+                auto row = [&](auto tag) {
+                    constexpr int R = decltype(tag)::value;
+                    const float2 &cs = s;
+                    const bool c = R ? c1 : c0;
+                    const float sq = R ? cs.y : cs.x, dyq = R ? dy.y : dy.x;
+                    const float p1q = R ? p1.y : p1.x, p2q = R ? p2.y : p2.x;
+                    float &Tq = R ? T.y : T.x;
+                    float &Qq = R ? Q.y : Q.x;
+                    const float gRq = R ? gR.y : gR.x, gGq = R ? gG.y : gG.x, gBq = R ? gB.y : gB.x;
+                    const float gZq = R ? gZ.y : gZ.x, gAq = R ? gATf.y : gATf.x;
+                    const float raw = c ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
+                    const float al = fminf(kAlphaMax, raw);
+                    const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
+                    const float Ti = Tq * rom;
+                    const float w = al * Ti;
+                    const float gc = fmaf(gRq, e3.x, fmaf(gGq, e3.z, fmaf(gBq, e4.x, gZq * e4.z)));
+                    const float dgq = __fmaf_rn(Qq, -1.f, gc);
+                    const float dA = fmaf(Ti, dgq, gAq * rom);
+                    Qq = fmaf(al, dgq, Qq);
+                    Tq = Ti;
+                    const float glo = raw <= kAlphaMax ? dA * raw : 0.f;
+                    const float ds2 = (-2.f * kLn2) * glo;
+                    const float dp1 = p1q * ds2, dp2 = p2q * ds2;
+                    gv[0] = dp1;
+                    gv[1] = dp2;
+                    gv[2] = dx.x * dp1;
+                    gv[3] = dp1 * dyq;
+                    gv[4] = dp2 * dyq;
+                    gv[5] = glo;
+                    gv[6] = gRq * w;
+                    gv[7] = gGq * w;
+                    gv[8] = gBq * w;
+                    gv[9] = gZq * w;
+                };
+                if (m0 == 0u)
+                    row(RowTag<1>{});
+                else
+                    row(RowTag<0>{});
+            }
             const uint32_t g = vals[eidx];
             if (g >= N) continue;
             if (__popc(cmask) <= 2) {

@@ -29,7 +29,7 @@ constexpr int kMaxPasses = 8;     // 8-bit radix digits of a 64-bit key
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 12;    // keys per thread per sort tile
-constexpr int kLookBatch = 16;    // predecessor flags read per look-back round
+constexpr int kLookBatch = 32;    // predecessor flags read per wide look-back round
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -91,7 +91,7 @@ struct Ws {
     unsigned long long *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;          // [kMaxPasses][256]
-    uint32_t *lookback;      // [kMaxPasses][lb_tiles][256]
+    uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
     uint2 *ranges;           // [total_tiles]
     float *T_final;          // [total_pixels]
     uint32_t *last;          // [total_pixels] last contributor index + 1
