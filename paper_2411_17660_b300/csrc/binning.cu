@@ -115,13 +115,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Ws ws) {
 }
 
 // ------------------------------------------------------------------ duplicate
-// One thread per (view, Gaussian) pair emits its keys along the exact tile spans.
+// A block takes 256 consecutive (view, Gaussian) pairs, compacts those with
+// keys (most pairs have none) and has full warps emit them along the exact
+// tile spans.
 __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ ViewTable vt, const Ws ws) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ws.VN) return;
+    __shared__ int s_wcount[8];
+    __shared__ uint32_t s_pair[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t i0 = (size_t)blockIdx.x * 256 + threadIdx.x;
+    const bool has = i0 < ws.VN && ws.counts[i0] != 0u;
+    const unsigned ball = __ballot_sync(0xffffffffu, has);
+    if (lane == 0) s_wcount[warp] = __popc(ball);
+    __syncthreads();
+    int off = 0, n = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int c = s_wcount[w];
+        off += w < warp ? c : 0;
+        n += c;
+    }
+    if (has) s_pair[off + __popc(ball & lanemask_lt())] = threadIdx.x;
+    __syncthreads();
+    if ((int)threadIdx.x >= n) return;
+    const size_t i = (size_t)blockIdx.x * 256 + s_pair[threadIdx.x];
     const uint32_t cnt = ws.counts[i];
-    if (cnt == 0) return;
-    const uint32_t off = ws.offsets[i];
+    const uint32_t off_k = ws.offsets[i];
     const uint32_t v = (uint32_t)(i / ws.N), g = (uint32_t)(i - (size_t)v * ws.N);
     const ViewParams &vp = vt.v[v];
     const float4 r0 = ws.rec0[i], r1 = ws.rec1[i], r3 = ws.rec3[i];
@@ -129,18 +147,18 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     unsigned long long *keys = ws.keys[0];
     uint32_t *vals = ws.vals[0];
     const uint32_t cap = ws.cap;
-    uint32_t k = off;
-    const uint32_t n = visit_tile_spans(r0.x, r0.y, r3.y, r3.z, r3.w, r1.x, r1.w, vp.W, vp.H, vt.tile,
-                                        [&](int ty, int tx0, int tx1) {
-                                            const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
-                                            for (int tx = tx0; tx <= tx1; ++tx, ++k) {
-                                                if (k < cap) {
-                                                    keys[k] = ((unsigned long long)(row + tx) << 32) | zbits;
-                                                    vals[k] = g;
-                                                }
-                                            }
-                                        });
-    if (n != cnt) set_status(ws.hdr, GSR_EINTERNAL);
+    uint32_t k = off_k;
+    const uint32_t emitted = visit_tile_spans(r0.x, r0.y, r3.y, r3.z, r3.w, r1.x, r1.w, vp.W, vp.H, vt.tile,
+                                              [&](int ty, int tx0, int tx1) {
+                                                  const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
+                                                  for (int tx = tx0; tx <= tx1; ++tx, ++k) {
+                                                      if (k < cap) {
+                                                          keys[k] = ((unsigned long long)(row + tx) << 32) | zbits;
+                                                          vals[k] = g;
+                                                      }
+                                                  }
+                                              });
+    if (emitted != cnt) set_status(ws.hdr, GSR_EINTERNAL);
 }
 
 // ------------------------------------------------------------------ sort
@@ -157,9 +175,15 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ws ws) {
     if (tid < kMaxPasses) ws.hdr->sort_counter[tid] = 0u;
     __syncthreads();
     const unsigned long long *keys = ws.keys[0];
-    for (size_t i = tid; i < n; i += stride) {
-        const unsigned long long k = keys[i];
-        for (int p = 0; p < ws.passes; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
+    constexpr int U = 4;   // keys loaded ahead of their shared-memory atomics
+    for (size_t i = tid; i < n; i += U * stride) {
+        unsigned long long k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) k[u] = i + u * stride < n ? keys[i + u * stride] : 0ull;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i + u * stride < n)
+                for (int p = 0; p < ws.passes; ++p) atomicAdd(&s_hist[p][(k[u] >> (8 * p)) & 0xff], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ws.passes * kRadix; i += blockDim.x) {

@@ -2,11 +2,10 @@
 // (activation, camera transform, EWA projection, SH colour, exact tile count)
 // and its backward (projection/SH chain rule, per-view SE(3) pose reduction).
 //
-// Forward: a block has kPreWarps warps in groups of VW = min(V, kPreWarps) (a
-// power of two); each group owns 32 Gaussians (one per lane) and its warps
-// take the views round-robin.  The warps of a group read the same Gaussians,
-// so the parameters come from DRAM once and from L1 after that, while the
-// (view, Gaussian) work is spread over many warps.
+// Forward: a block owns 256 / VW Gaussians (VW = min(V, 8), a power of two)
+// and takes the views VW at a time; it projects every pair, compacts the
+// visible ones in shared memory and gives the expensive part (tile count, SH
+// colour, records) to full warps of visible pairs.
 // Backward: a block owns 32 Gaussians; it compacts the visible (view,
 // Gaussian) pairs so that its warps work on visible pairs only, and sums the
 // per-pair gradients over views in shared memory in a fixed order, so the
@@ -53,59 +52,139 @@ __device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, floa
 }
 
 // ------------------------------------------------------------------ forward
+// Compacted forward: a block owns kPreRounds * GB Gaussians (GB = 256 / VW,
+// VW = min(V, 8) a power of two) and takes 256 (view, Gaussian) pairs per
+// round: GB Gaussians in VW views.  Phase A projects every pair of a round
+// with full warps and appends the visible ones, in candidate order, to a
+// shared-memory queue with their projected state; once the queue may not
+// take another round, phase B counts the tiles and evaluates the SH colour
+// of the queued pairs, again with full warps, and writes their records.
+constexpr int kPreRounds = 3;
+constexpr int kPreQueue = kPreRounds * kPreThreads;
+
+struct PreQueue {
+    float uh[kPreQueue], vh[kPreQueue], ul[kPreQueue], vl[kPreQueue];
+    float m00[kPreQueue], m01[kPreQueue], m11[kPreQueue];
+    float sxx[kPreQueue], sxy[kPreQueue], syy[kPreQueue], zh[kPreQueue];
+    int v[kPreQueue], g[kPreQueue];
+};
+
+// Phase B for the queued pairs [0, n).
+template <int DEG>
+__device__ __forceinline__ void preprocess_fwd_flush(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
+                                                     const Pose *s_pose, const PreQueue &q, int n) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const size_t N = (size_t)gp.N;
+    for (int k = threadIdx.x; k < n; k += kPreThreads) {
+        const int pv = q.v[k], pg = q.g[k];
+        const ViewParams &vp = vt.v[pv];
+        const size_t i = (size_t)pv * N + pg;
+        const float puh = q.uh[k], pvh = q.vh[k], m00 = q.m00[k];
+        const float sxx = q.sxx[k], sxy = q.sxy[k], syy = q.syy[k];
+        // the same expressions as gauss_pre, so that the records match it
+        const float o = 1.0f / (1.0f + expf(-gp.opacity_logits[pg]));
+        const float log2o = log2f(o);
+        const float smax = fminf(kCutoffD2 * kHalfLog2e, log2o + kLog2_255);
+        const uint32_t count =
+            visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [](int, int, int) {});
+        ws.counts[i] = count;
+        if (count == 0u) continue;
+        const Pose &ps = s_pose[pv];
+        float dx = gp.means[pg] - ps.C[0], dy = gp.means[N + pg] - ps.C[1], dz = gp.means[2 * N + pg] - ps.C[2];
+        const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= rn;
+        dy *= rn;
+        dz *= rn;
+        float Y[K];
+        sh_eval<DEG>(dx, dy, dz, Y);
+        float rgb[3];
+        // one channel at a time keeps few coefficients live in registers
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const float *shc = gp.sh + (size_t)c * N + pg;
+            float acc = 0.5f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc = fmaf(__ldg(shc + (size_t)j * 3 * N), Y[j], acc);
+            rgb[c] = fmaxf(acc, 0.f);
+        }
+        ws.rec0[i] = make_float4(puh, pvh, q.ul[k], q.vl[k]);
+        ws.rec1[i] = make_float4(m00, q.m01[k], q.m11[k], smax);
+        ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
+        ws.rec3[i] = make_float4(log2o, sxx, sxy, syy);
+    }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                      const GaussianPtrs gp, const Ws ws,
                                                                      int vw_log2) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
+    __shared__ PreQueue q;
+    __shared__ int s_wcount[kPreWarps];
     load_poses(vt, s_pose);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int VW = 1 << vw_log2, slot = warp & (VW - 1);
-    const int g = (blockIdx.x * (kPreWarps >> vw_log2) + (warp >> vw_log2)) * 32 + lane;
-    if (g >= gp.N) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int VW = 1 << vw_log2, GB = kPreThreads >> vw_log2;
+    const int vv = tid / GB;
     const size_t N = (size_t)gp.N;
-    GaussPre G;
-    gauss_pre(gp, g, G);
-    for (int v = slot; v < vt.V; v += VW) {
-        const ViewParams &vp = vt.v[v];
-        const size_t i = (size_t)v * N + g;
-        uint32_t count = 0;
-        Proj p;
-        if (G.alive && project_view(G, s_pose[v], vp, p)) {
-            const float m00 = kSqrtHalfLog2e * p.l00, m01 = kSqrtHalfLog2e * p.l01, m11 = kSqrtHalfLog2e * p.l11;
-            float uh, ul, vh, vl;
-            project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
-            project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
-            if (isfinite(uh) && isfinite(vh))
-                count = visit_tile_spans(uh, vh, p.sxx, p.sxy, p.syy, m00, G.smax, vp.W, vp.H, vt.tile,
-                                         [](int, int, int) {});
-            if (count) {
-                float dx, dy, dz, rn;
-                view_dir(G, s_pose[v], dx, dy, dz, rn);
-                float Y[K];
-                sh_eval<DEG>(dx, dy, dz, Y);
-                float rgb0 = 0.f, rgb1 = 0.f, rgb2 = 0.f;
-                // one channel at a time keeps few coefficients live in registers
-#pragma unroll 1
-                for (int c = 0; c < 3; ++c) {
-                    const float *shc = gp.sh + (size_t)c * N + g;
-                    float acc = 0.5f;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) acc = fmaf(__ldg(shc + (size_t)k * 3 * N), Y[k], acc);
-                    acc = fmaxf(acc, 0.f);
-                    if (c == 0) rgb0 = acc;
-                    else if (c == 1) rgb1 = acc;
-                    else rgb2 = acc;
-                }
-                ws.rec0[i] = make_float4(uh, vh, ul, vl);
-                ws.rec1[i] = make_float4(m00, m01, m11, G.smax);
-                ws.rec2[i] = make_float4(rgb0, rgb1, rgb2, p.zh);
-                ws.rec3[i] = make_float4(G.log2o, p.sxx, p.sxy, p.syy);
+    int qn = 0;   // queued pairs (the same in every thread)
+    for (int r = 0; r < kPreRounds; ++r) {
+        const int g = (blockIdx.x * kPreRounds + r) * GB + tid % GB;
+        const bool real = g < gp.N;
+        GaussPre G;
+        if (real) gauss_pre(gp, g, G);
+        for (int v0 = 0; v0 < vt.V; v0 += VW) {
+            if (qn + kPreThreads > kPreQueue) {
+                __syncthreads();
+                preprocess_fwd_flush<DEG>(vt, gp, ws, s_pose, q, qn);
+                __syncthreads();
+                qn = 0;
             }
+            // phase A: projection and visibility of every pair of the round
+            const int v = v0 + vv;
+            bool vis = false;
+            float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+            Proj p;
+            if (real && v < vt.V) {
+                const ViewParams &vp = vt.v[v];
+                if (G.alive && project_view(G, s_pose[v], vp, p)) {
+                    project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
+                    project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
+                    vis = isfinite(uh) && isfinite(vh);
+                }
+                if (!vis) ws.counts[(size_t)v * N + g] = 0u;
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, vis);
+            __syncthreads();   // s_wcount of the previous round has been read
+            if (lane == 0) s_wcount[warp] = __popc(ball);
+            __syncthreads();
+            int off = 0, nvis = 0;
+#pragma unroll
+            for (int w = 0; w < kPreWarps; ++w) {
+                const int c = s_wcount[w];
+                off += w < warp ? c : 0;
+                nvis += c;
+            }
+            if (vis) {
+                const int k = qn + off + __popc(ball & lanemask_lt());
+                q.uh[k] = uh;
+                q.vh[k] = vh;
+                q.ul[k] = ul;
+                q.vl[k] = vl;
+                q.m00[k] = kSqrtHalfLog2e * p.l00;
+                q.m01[k] = kSqrtHalfLog2e * p.l01;
+                q.m11[k] = kSqrtHalfLog2e * p.l11;
+                q.sxx[k] = p.sxx;
+                q.sxy[k] = p.sxy;
+                q.syy[k] = p.syy;
+                q.zh[k] = p.zh;
+                q.v[k] = v;
+                q.g[k] = g;
+            }
+            qn += nvis;
         }
-        ws.counts[i] = count;
     }
+    __syncthreads();
+    preprocess_fwd_flush<DEG>(vt, gp, ws, s_pose, q, qn);
 }
 
 // ------------------------------------------------------------------ backward
@@ -480,7 +559,7 @@ static int views_log2(int V) {
 }
 
 static int pre_blocks(int N, int vw_log2) {
-    const int per_block = 32 * (kPreWarps >> vw_log2);
+    const int per_block = kPreRounds * (kPreThreads >> vw_log2);
     return (N + per_block - 1) / per_block;
 }
 
