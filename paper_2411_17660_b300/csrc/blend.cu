@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
     const float2 gB = make_float2(gq[2][0], gq[2][1]), gZ = make_float2(gq[3][0], gq[3][1]);
     const float2 gATf = make_float2(gq[4][0], gq[4][1]);
     const uint32_t wlast = __reduce_max_sync(kFull, lmax);
-    float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads * N;
+    float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads;   // + g V 10: (Gaussian, view) rows of 10
+    const size_t row = (size_t)ws.V * kVGGrads;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u ? end - 32u : wt.range.x;
@@ -438,13 +439,13 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
                 // one or two lanes: their own atomics are cheaper than a reduction
                 if (c0 || c1) {
 #pragma unroll
-                    for (int k = 0; k < kVGGrads; ++k) atomicAdd(grads + (size_t)k * N + g, gv[k]);
+                    for (int k = 0; k < kVGGrads; ++k) atomicAdd(grads + g * row + k, gv[k]);
                 }
             } else {
                 int comp;
                 bool valid;
                 const float sum = warp_sum10(gv, lane, comp, valid);
-                if (valid && (lane & 1) == 0) atomicAdd(grads + (size_t)comp * N + g, sum);
+                if (valid && (lane & 1) == 0) atomicAdd(grads + g * row + comp, sum);
             }
         }
         __syncwarp();

@@ -95,7 +95,7 @@ struct Ws {
     uint2 *ranges;           // [total_tiles]
     float *T_final;          // [total_pixels]
     uint32_t *last;          // [total_pixels] last contributor index + 1
-    float *vg_grads;         // [V][10][N]
+    float *vg_grads;         // [N][V][10] screen-space gradients of each (Gaussian, view)
     float *pose_partials;    // [V][pose_blocks][6]
     uint32_t N, V, VN;
     uint32_t cap, lb_tiles, scan_blocks, pose_blocks;

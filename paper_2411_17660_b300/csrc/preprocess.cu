@@ -188,21 +188,29 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __gri
 }
 
 // ------------------------------------------------------------------ backward
-// A block owns 256/VW Gaussians and takes the views VW at a time (VW a power
-// of two, as many as there are views, up to 8).  Of the 256 candidate
-// (view, Gaussian) pairs of a chunk, the visible ones are compacted with a
-// block-wide scan (in candidate order) so that warps work on visible pairs
-// only; each pair's partial gradients go to its shared-memory column, and are
-// then summed per Gaussian (in view order) and per view (in Gaussian order).
-// Deterministic.
+// A block owns GBT Gaussians and all V views (VW = V rounded up to a power
+// of two).  Its candidate (view, Gaussian) pairs are taken Gaussian-major,
+// 256 per round; the visible ones are appended, in candidate order, to a
+// shared-memory list, so that every Gaussian's visible views form one
+// contiguous run, in view order.  The list is then worked through 256 pairs
+// at a time with full warps: each pair's partial gradients go to its
+// shared-memory column; a Gaussian's run is summed in list order (a run cut
+// by the end of a chunk carries its partial sum into the next) and, once
+// complete, turned into the parameter gradients.  Per-view pose partials are
+// summed in list order.  Deterministic.
 template <int DEG>
 struct BwdAcc {
     static constexpr int K = (DEG + 1) * (DEG + 1);
     static constexpr int NV = 13 + 3 * K;   // dmu (3), dM (9), d ln(sigma) (1), dSH (3K)
+    static constexpr int NVP = NV | 1;      // odd row stride of the per-pair partials in shared memory
+    // shared-memory floats of the partials and of the run totals (one view
+    // needs neither: each pair is finished by its own thread)
+    __host__ __device__ static constexpr int parts(int VW) { return VW == 1 ? 0 : NVP * kPreThreads; }
+    __host__ __device__ static constexpr int tots(int VW) { return VW == 1 ? 0 : 13 * kPreThreads; }
 };
 
 // Backward of one visible (view, Gaussian) pair; writes its NV partials to
-// part[k * kPreThreads] and its pose twist to pose[k * kPreThreads].
+// part[k] and its pose twist to pose[c * kPreThreads].
 template <int DEG>
 __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &ws, const ViewParams &vp,
                                               const Pose &ps, int v, int g, float *part, float *pose) {
@@ -219,14 +227,18 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     float dlno = 0.f;
     if (!project_view(G, ps, vp, p)) {   // same decision as the forward; kept for safety
 #pragma unroll
-        for (int k = 0; k < BwdAcc<DEG>::NV; ++k) part[k * kPreThreads] = 0.f;
+        for (int k = 0; k < BwdAcc<DEG>::NV; ++k) part[k] = 0.f;
 #pragma unroll
         for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = 0.f;
         return;
     }
     float sg[kVGGrads];
 #pragma unroll
-    for (int c = 0; c < kVGGrads; ++c) sg[c] = ws.vg_grads[((size_t)v * kVGGrads + c) * N + g];
+    for (int c = 0; c < kVGGrads / 2; ++c) {   // one 40-byte row, 8-byte aligned
+        const float2 x = reinterpret_cast<const float2 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kVGGrads)[c];
+        sg[2 * c] = x.x;
+        sg[2 * c + 1] = x.y;
+    }
     float dpc[3] = {0.f, 0.f, 0.f};
 
     // colour -> SH coefficients and the view direction; the forward's stored
@@ -241,9 +253,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     const float *shg = gp.sh + g;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        part[(13 + k * 3) * kPreThreads] = dr0 * Y[k];
-        part[(14 + k * 3) * kPreThreads] = dr1 * Y[k];
-        part[(15 + k * 3) * kPreThreads] = dr2 * Y[k];
+        part[13 + k * 3] = dr0 * Y[k];
+        part[14 + k * 3] = dr1 * Y[k];
+        part[15 + k * 3] = dr2 * Y[k];
         wk[k] = dr0 * __ldg(shg + (size_t)(k * 3) * N) + dr1 * __ldg(shg + (size_t)(k * 3 + 1) * N) +
                 dr2 * __ldg(shg + (size_t)(k * 3 + 2) * N);
     }
@@ -343,145 +355,41 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     pose6[5] += Am[1][0] - Am[0][1];
 
 #pragma unroll
-    for (int k = 0; k < 3; ++k) part[k * kPreThreads] = dmu[k];
+    for (int k = 0; k < 3; ++k) part[k] = dmu[k];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) part[(3 + k) * kPreThreads] = dM[k];
-    part[12 * kPreThreads] = dlno;
+    for (int k = 0; k < 9; ++k) part[3 + k] = dM[k];
+    part[12] = dlno;
 #pragma unroll
     for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = pose6[c];
 }
 
-// Shared-memory bytes of preprocess_bwd_kernel<DEG, VW>; the per-Gaussian
-// accumulator is needed only when the views take more than one chunk.
-template <int DEG>
-static size_t bwd_smem_bytes(int VW, bool multi_chunk) {
-    const size_t NV = BwdAcc<DEG>::NV, GB = kPreThreads / VW;
-    return sizeof(float) * (NV * kPreThreads + 6 * kPreThreads + (multi_chunk ? NV * GB : 0) + 6 * (kPreThreads / 32)) +
-           sizeof(int) * 2 * kPreThreads;
+// Rounds of 256 candidates per block, and Gaussians per block.
+template <int VW>
+struct BwdShape {
+    static constexpr int GB = kPreThreads / VW;                   // Gaussians per round
+    static constexpr int R = VW <= 8 ? 3 : 3 * VW / 8;            // at least 96 Gaussians per block
+    static constexpr int GBT = R * GB;
+    static constexpr int LC = R * kPreThreads;                    // list capacity
+};
+
+// Shared-memory bytes of preprocess_bwd_kernel<DEG, VW>.
+template <int DEG, int VW>
+static size_t bwd_smem_bytes() {
+    using S = BwdShape<VW>;
+    constexpr size_t NV = BwdAcc<DEG>::NV;
+    return sizeof(unsigned long long) * S::GBT +
+           sizeof(float) * (BwdAcc<DEG>::parts(VW) + 6 * kPreThreads + BwdAcc<DEG>::tots(VW) + 2 * NV + 6 * VW) +
+           sizeof(int) * (S::LC + 2 * S::GBT);
 }
 
-// VW views per chunk, GB = kPreThreads / VW Gaussians per block: candidate
-// thread t is (view vbase + t / GB, Gaussian gbase + t % GB).
-template <int DEG, int VW>
-__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                        const GaussianPtrs gp, const Ws ws,
-                                                                        const GradPtrs out) {
-    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV;
-    constexpr int GB = kPreThreads / VW, WARPS = kPreThreads / 32;
-    const bool multi = vt.V > VW;
-    extern __shared__ float smem[];
-    float *s_part = smem;                              // [NV][kPreThreads]
-    float *s_pose = s_part + NV * kPreThreads;         // [6][kPreThreads]
-    float *s_wpose = s_pose + 6 * kPreThreads;         // [WARPS][6]
-    float *s_acc = s_wpose + 6 * WARPS;                // [NV][GB], multi-chunk only
-    int *s_item = reinterpret_cast<int *>(s_acc + (multi ? NV * GB : 0));   // [kPreThreads]
-    int *s_rank = s_item + kPreThreads;                // [kPreThreads]
-    __shared__ int s_wcnt[WARPS];
-    __shared__ Pose s_poses[GSR_MAX_VIEWS];
-    load_poses(vt, s_poses);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gbase = blockIdx.x * GB;
+// Parameter gradients of Gaussian g from its view-summed partials (acc:
+// dmu (3), dM (9), d ln(sigma) (1)).
+__device__ __forceinline__ void bwd_finish(const GaussianPtrs &gp, const GradPtrs &out, int g, const float *acc) {
     const size_t N = (size_t)gp.N;
-    if (multi)
-        for (int k = tid; k < NV * GB; k += kPreThreads) s_acc[k] = 0.f;
-
-    for (int vbase = 0; vbase < vt.V; vbase += VW) {
-        const int cw = tid / GB, cl = tid - cw * GB;
-        const int cv = vbase + cw, cg = gbase + cl;
-        const bool vis = cv < vt.V && cg < gp.N && ws.counts[(size_t)cv * N + cg] > 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, nvis = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-            const int c = s_wcnt[w];
-            before += w < warp ? c : 0;
-            nvis += c;
-        }
-        const int rank = vis ? before + __popc(bal & lanemask_lt()) : -1;
-        s_rank[tid] = rank;
-        if (vis) s_item[rank] = tid;
-        __syncthreads();
-        if (tid < nvis) {
-            const int c = s_item[tid];
-            const int v = vbase + c / GB, g = gbase + c % GB;
-            pair_backward<DEG>(gp, ws, vt.v[v], s_poses[v], v, g, s_part + tid, s_pose + tid);
-        }
-        __syncthreads();
-        // per-view pose partial of this block's Gaussians: each warp's 32
-        // candidates share one view; warp sums, then per view in warp order
-        {
-            float pv[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float x = rank >= 0 ? s_pose[c * kPreThreads + rank] : 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                pv[c] = x;
-            }
-            if (lane < 6) {
-                float x = pv[0];
-#pragma unroll
-                for (int c = 1; c < 6; ++c) x = lane == c ? pv[c] : x;
-                s_wpose[warp * 6 + lane] = x;
-            }
-        }
-        if (multi) {   // per-Gaussian sums over this chunk's views, in view order
-            for (int idx = tid; idx < NV * GB; idx += kPreThreads) {
-                const int k = idx / GB, l = idx - k * GB;
-                float x = s_acc[idx];
-#pragma unroll
-                for (int w = 0; w < VW; ++w) {
-                    const int r = s_rank[w * GB + l];
-                    if (r >= 0) x += s_part[k * kPreThreads + r];
-                }
-                s_acc[idx] = x;
-            }
-        }
-        __syncthreads();
-        if (tid < VW * 6) {
-            const int w = tid / 6, comp = tid - w * 6, v = vbase + w;
-            if (v < vt.V) {
-                float x = 0.f;
-                for (int q = 0; q < GB / 32; ++q) x += s_wpose[(w * (GB / 32) + q) * 6 + comp];
-                ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + comp] = x;
-            }
-        }
-        if (multi || vbase + VW < vt.V) __syncthreads();
-    }
-
-    // the sum over views of component k of Gaussian gbase + l
-    auto total = [&](int k, int l) -> float {
-        if (multi) return s_acc[k * GB + l];
-        const int r = s_rank[l];   // single chunk: view slot w is view w
-        float x = r >= 0 ? s_part[k * kPreThreads + r] : 0.f;
-        for (int w = 1; w < VW; ++w) {
-            const int r2 = s_rank[w * GB + l];
-            if (r2 >= 0) x += s_part[k * kPreThreads + r2];
-        }
-        return x;
-    };
-    // outputs: SH rows by all threads, the other parameters by one thread per Gaussian
     const bool ac = out.accumulate != 0;
-    for (int idx = tid; idx < 3 * K * GB; idx += kPreThreads) {
-        const int k = idx / GB, l = idx - k * GB, g = gbase + l;
-        if (g < gp.N) {
-            float *o = out.sh + (size_t)k * N + g;
-            const float x = total(13 + k, l);
-            *o = ac ? *o + x : x;
-        }
-    }
-    if (tid >= GB) return;
-    const int g = gbase + tid;
-    if (g >= gp.N) return;
     GaussPre G;
     gauss_pre(gp, g, G);
-    float acc[13];
-#pragma unroll
-    for (int k = 0; k < 13; ++k) acc[k] = total(k, tid);
     const float *dmu = acc, *dM = acc + 3;
-
     // M = R diag(s) -> log-scales and the rotation
     float dR[3][3], dls[3];
 #pragma unroll
@@ -510,7 +418,6 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
 #pragma unroll
     for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
     const float dlogit = acc[12] * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
-
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         float *pm = out.means + (size_t)j * N + g;
@@ -525,6 +432,218 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
     }
     float *po = out.opacity_logits + g;
     *po = ac ? *po + dlogit : dlogit;
+}
+
+template <int DEG, int VW>
+__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                        const GaussianPtrs gp, const Ws ws,
+                                                                        const GradPtrs out) {
+    using S = BwdShape<VW>;
+    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV, NVP = BwdAcc<DEG>::NVP;
+    constexpr int GB = S::GB, GBT = S::GBT, WARPS = kPreThreads / 32;
+    extern __shared__ __align__(16) unsigned long long smem_u64[];
+    unsigned long long *s_mask = smem_u64;             // [GBT] visible views of each Gaussian
+    float *s_part = reinterpret_cast<float *>(s_mask + GBT);   // [256][NVP] per-pair partials of a chunk
+    float *s_pose = s_part + BwdAcc<DEG>::parts(VW);   // [6][256] per-pair pose twists
+    float *s_tot = s_pose + 6 * kPreThreads;           // [256][13] totals of the runs that end in a chunk
+    float *s_carry = s_tot + BwdAcc<DEG>::tots(VW);    // [2][NV] partial sums of a run cut by a chunk's end
+    float *s_vpose = s_carry + 2 * NV;                 // [VW][6] pose partials per view
+    int *s_item = reinterpret_cast<int *>(s_vpose + 6 * VW);   // [LC] (Gaussian << 8 | view) per list position
+    int *s_first = s_item + S::LC;                     // [GBT] list position of each Gaussian's run
+    int *s_cnt = s_first + GBT;                        // [GBT] its length
+    __shared__ int s_wcnt[WARPS];
+    __shared__ unsigned s_wbal[WARPS];
+    __shared__ int s_end[kPreThreads];                 // chunk positions where a run ends
+    __shared__ Pose s_poses[GSR_MAX_VIEWS];
+    load_poses(vt, s_poses);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gbase = blockIdx.x * GBT;
+    const size_t N = (size_t)gp.N;
+    const bool ac = out.accumulate != 0;
+    for (int k = tid; k < 6 * VW; k += kPreThreads) s_vpose[k] = 0.f;
+
+    // The list of visible pairs, Gaussian-major: candidate t of round r is
+    // view t % VW of Gaussian r GB + t / VW.  A Gaussian's candidates are VW
+    // consecutive lanes of one warp (two whole warps when VW = 64).
+    int M = 0;
+    for (int r = 0; r < S::R; ++r) {
+        const int gl = r * GB + tid / VW, v = tid % VW, g = gbase + gl;
+        const bool vis = v < vt.V && g < gp.N && ws.counts[(size_t)v * N + g] > 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0) {
+            s_wcnt[warp] = __popc(bal);
+            s_wbal[warp] = bal;
+        }
+        __syncthreads();
+        int before = 0, nvis = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const int c = s_wcnt[w];
+            before += w < warp ? c : 0;
+            nvis += c;
+        }
+        if (vis) s_item[M + before + __popc(bal & lanemask_lt())] = (gl << 8) | v;
+        if constexpr (VW <= 32) {
+            const int lead = lane & ~(VW - 1);
+            if (lane == lead) {
+                const unsigned gbits = (bal >> lead) & (VW == 32 ? 0xffffffffu : ((1u << VW) - 1u));
+                s_first[gl] = M + before + __popc(bal & ((1u << lead) - 1u));
+                s_cnt[gl] = __popc(gbits);
+                s_mask[gl] = gbits;
+            }
+        } else if (lane == 0 && (warp & 1) == 0) {
+            s_first[gl] = M + before;
+            s_cnt[gl] = s_wcnt[warp] + s_wcnt[warp + 1];
+            s_mask[gl] = (unsigned long long)s_wbal[warp] | ((unsigned long long)s_wbal[warp + 1] << 32);
+        }
+        M += nvis;
+        __syncthreads();
+    }
+
+    for (int c0 = 0, chunk = 0; c0 < M; c0 += kPreThreads, ++chunk) {
+        const int n = min(kPreThreads, M - c0);
+        // carries alternate between two buffers: one chunk reads the previous
+        // chunk's while it writes its own
+        const float *carry_in = s_carry + ((chunk + 1) & 1) * NV;
+        float *carry_out = s_carry + (chunk & 1) * NV;
+        if constexpr (VW == 1) {
+            // one view: every run is one pair, finished by its own thread
+            if (tid < n) {
+                const int gl = s_item[c0 + tid] >> 8, g = gbase + gl;
+                float part[NV];
+                pair_backward<DEG>(gp, ws, vt.v[0], s_poses[0], 0, g, part, s_pose + tid);
+                for (int k = 13; k < NV; ++k) {
+                    float *o = out.sh + (size_t)(k - 13) * N + g;
+                    *o = ac ? *o + part[k] : part[k];
+                }
+                bwd_finish(gp, out, g, part);
+            }
+            __syncthreads();
+            if (warp == 0) {   // the view's pose partial, lanes striding the chunk, then a butterfly
+                float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int p = lane; p < n; p += 32)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) pv[c] += s_pose[c * kPreThreads + p];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) pv[c] += __shfl_xor_sync(0xffffffffu, pv[c], o);
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) s_vpose[c] += pv[c];
+            }
+            __syncthreads();
+            continue;
+        }
+        int item = 0;
+        bool end = false;
+        if (tid < n) {
+            item = s_item[c0 + tid];
+            const int v = item & 0xff, g = gbase + (item >> 8);
+            pair_backward<DEG>(gp, ws, vt.v[v], s_poses[v], v, g, s_part + tid * NVP, s_pose + tid);
+            end = tid + 1 == n || (s_item[c0 + tid + 1] >> 8) != (item >> 8);
+        }
+        // positions where a run ends in this chunk, in order
+        const unsigned bal = __ballot_sync(0xffffffffu, end);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, nruns = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const int c = s_wcnt[w];
+            before += w < warp ? c : 0;
+            nruns += c;
+        }
+        if (end) s_end[before + __popc(bal & lanemask_lt())] = tid;
+        __syncthreads();
+        // run sums over this chunk, plus the carry of a run begun earlier: an
+        // item is (run, component), components fastest, so that a warp reads
+        // consecutive words of a partials row
+        for (int idx = tid; idx < NV * nruns; idx += kPreThreads) {
+            const int j = idx / NV, k = idx - j * NV;
+            const int p = s_end[j], gl = s_item[c0 + p] >> 8;
+            const int first = s_first[gl];
+            float x = first < c0 ? carry_in[k] : 0.f;
+            for (int q = max(first, c0) - c0; q <= p; ++q) x += s_part[q * NVP + k];
+            if (c0 + p + 1 < first + s_cnt[gl]) {
+                carry_out[k] = x;   // continues in the next chunk
+            } else if (k < 13) {
+                s_tot[j * 13 + k] = x;
+            } else {
+                float *o = out.sh + (size_t)(k - 13) * N + gbase + gl;
+                *o = ac ? *o + x : x;
+            }
+        }
+        // pose partials per view, in list order
+        if (VW >= 16) {
+            // one thread per view walks the runs ending in this chunk and
+            // picks its view's entry from the Gaussian's mask
+            for (int v = tid; v < vt.V; v += kPreThreads) {
+                float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int j = 0; j < nruns; ++j) {
+                    const int gl = s_item[c0 + s_end[j]] >> 8;
+                    const unsigned long long m = s_mask[gl];
+                    if (!((m >> v) & 1ull)) continue;
+                    const int pos = s_first[gl] + __popcll(m & ((1ull << v) - 1ull)) - c0;
+                    if (pos < 0 || pos >= n) continue;   // in an earlier or a later chunk
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) pv[c] += s_pose[c * kPreThreads + pos];
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) s_vpose[v * 6 + c] += pv[c];
+            }
+        } else
+        // warp w takes views w, w + 8, ...: lanes stride the chunk, then a butterfly
+        for (int v = warp; v < vt.V; v += WARPS) {
+            float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int p = lane; p < n; p += 32) {
+                if ((s_item[c0 + p] & 0xff) != v) continue;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) pv[c] += s_pose[c * kPreThreads + p];
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) pv[c] += __shfl_xor_sync(0xffffffffu, pv[c], o);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) s_vpose[v * 6 + c] += pv[c];
+        }
+        __syncthreads();
+        // Gaussians whose runs ended in this chunk
+        for (int j = tid; j < nruns; j += kPreThreads) {
+            const int p = s_end[j], gl = s_item[c0 + p] >> 8;
+            if (c0 + p + 1 < s_first[gl] + s_cnt[gl]) continue;
+            float acc[13];
+#pragma unroll
+            for (int k = 0; k < 13; ++k) acc[k] = s_tot[j * 13 + k];
+            bwd_finish(gp, out, gbase + gl, acc);
+        }
+        __syncthreads();
+    }
+
+    // Gaussians visible in no view: zero gradients
+    if (!ac) {
+        for (int gl = tid; gl < GBT; gl += kPreThreads) {
+            const int g = gbase + gl;
+            if (g >= gp.N || s_cnt[gl] != 0) continue;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                out.means[(size_t)j * N + g] = 0.f;
+                out.log_scales[(size_t)j * N + g] = 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out.quats[(size_t)k * N + g] = 0.f;
+            out.opacity_logits[g] = 0.f;
+            for (int k = 0; k < 3 * K; ++k) out.sh[(size_t)k * N + g] = 0.f;
+        }
+    }
+    for (int i = tid; i < 6 * vt.V; i += kPreThreads) {
+        const int v = i / 6, c = i - v * 6;
+        ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + c] = s_vpose[v * 6 + c];
+    }
 }
 
 // Sum of the per-block pose partials of each view, in a fixed order.
@@ -583,8 +702,7 @@ cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
 template <int DEG, int VW>
 static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp, Ws ws, const GradPtrs &out,
                                      cudaStream_t st) {
-    const bool multi = vt.V > VW;
-    const size_t smem = bwd_smem_bytes<DEG>(VW, multi);
+    const size_t smem = bwd_smem_bytes<DEG, VW>();
     // More than 48 KB of dynamic shared memory needs an opt-in, set once per
     // device (the first backward on a device, which should precede capture).
     static std::mutex mu;
@@ -596,14 +714,13 @@ static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 0 || dev >= 64 || !done[dev]) {
             e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)bwd_smem_bytes<DEG>(VW, true));
+                                     (int)smem);
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) done[dev] = true;
         }
     }
-    constexpr int GB = kPreThreads / VW;
-    const int blocks = (gp.N + GB - 1) / GB;
-    ws.pose_blocks = (uint32_t)blocks;
+    const int blocks = (gp.N + BwdShape<VW>::GBT - 1) / BwdShape<VW>::GBT;
+    ws.pose_blocks = (uint32_t)blocks;   // at most (N + 31) / 32, the workspace's allotment
     preprocess_bwd_kernel<DEG, VW><<<blocks, kPreThreads, smem, st>>>(vt, gp, ws, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -614,12 +731,13 @@ static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp
 template <int DEG>
 static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st) {
-    switch (views_log2(vt.V)) {
-        case 0: return launch_pre_bwd_vw<DEG, 1>(vt, gp, ws, out, st);
-        case 1: return launch_pre_bwd_vw<DEG, 2>(vt, gp, ws, out, st);
-        case 2: return launch_pre_bwd_vw<DEG, 4>(vt, gp, ws, out, st);
-        default: return launch_pre_bwd_vw<DEG, 8>(vt, gp, ws, out, st);
-    }
+    if (vt.V <= 1) return launch_pre_bwd_vw<DEG, 1>(vt, gp, ws, out, st);
+    if (vt.V <= 2) return launch_pre_bwd_vw<DEG, 2>(vt, gp, ws, out, st);
+    if (vt.V <= 4) return launch_pre_bwd_vw<DEG, 4>(vt, gp, ws, out, st);
+    if (vt.V <= 8) return launch_pre_bwd_vw<DEG, 8>(vt, gp, ws, out, st);
+    if (vt.V <= 16) return launch_pre_bwd_vw<DEG, 16>(vt, gp, ws, out, st);
+    if (vt.V <= 32) return launch_pre_bwd_vw<DEG, 32>(vt, gp, ws, out, st);
+    return launch_pre_bwd_vw<DEG, 64>(vt, gp, ws, out, st);
 }
 
 cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
