@@ -338,7 +338,7 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, L.total_tiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
-    if ((e = launch_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
+    if ((e = launch_preprocess_fwd(vt, gp, w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
     ctx->mark(1, st);
     if ((e = launch_scan_duplicate(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "scan/duplicate");
     ctx->mark(2, st);

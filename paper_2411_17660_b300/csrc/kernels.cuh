@@ -11,7 +11,8 @@ struct GradPtrs {
 };
 
 // preprocess.cu
-cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st);
+cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,
+                                  cudaStream_t st);
 cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st);
 

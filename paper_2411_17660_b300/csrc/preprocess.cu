@@ -10,6 +10,7 @@
 // Gaussian) pairs so that its warps work on visible pairs only, and sums the
 // per-pair gradients over views in shared memory in a fixed order, so the
 // result does not depend on timing.
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -52,99 +53,87 @@ __device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, floa
 }
 
 // ------------------------------------------------------------------ forward
-// Compacted forward: a block owns kPreRounds * GB Gaussians (GB = 256 / VW,
-// VW = min(V, 8) a power of two) and takes 256 (view, Gaussian) pairs per
-// round: GB Gaussians in VW views.  Phase A projects every pair of a round
-// with full warps and appends the visible ones, in candidate order, to a
-// shared-memory queue with their projected state; once the queue may not
-// take another round, phase B counts the tiles and evaluates the SH colour
-// of the queued pairs, again with full warps, and writes their records.
-constexpr int kPreRounds = 3;
-constexpr int kPreQueue = kPreRounds * kPreThreads;
+// Warp-queue forward: persistent warps take batches of 32 Gaussians (one per
+// lane, parameters activated once per batch) and walk their views.  Phase A
+// projects the 32 pairs of one view; the visible ones are appended, with
+// their projected state, to the warp's shared-memory queue.  Whenever 32 are
+// queued, phase B gives them to the 32 lanes: tile count, SH colour and
+// records.  Warps never wait for each other, and the expensive part runs
+// with full warps however few pairs are visible.
+constexpr int kQueue = 64;   // a warp's queue: up to 31 waiting + 32 appended
 
-struct PreQueue {
-    float uh[kPreQueue], vh[kPreQueue], ul[kPreQueue], vl[kPreQueue];
-    float m00[kPreQueue], m01[kPreQueue], m11[kPreQueue];
-    float sxx[kPreQueue], sxy[kPreQueue], syy[kPreQueue], zh[kPreQueue];
-    int v[kPreQueue], g[kPreQueue];
+struct WarpQueue {
+    float uh[kQueue], vh[kQueue], ul[kQueue], vl[kQueue];
+    float m00[kQueue], m01[kQueue], m11[kQueue];
+    float sxx[kQueue], sxy[kQueue], syy[kQueue], zh[kQueue];
+    int v[kQueue], g[kQueue];
 };
 
-// Phase B for the queued pairs [0, n).
+// Phase B for queue entry k of one lane.
 template <int DEG>
-__device__ __forceinline__ void preprocess_fwd_flush(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
-                                                     const Pose *s_pose, const PreQueue &q, int n) {
+__device__ __forceinline__ void preprocess_fwd_pair(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
+                                                    const Pose *s_pose, const WarpQueue &q, int k) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const size_t N = (size_t)gp.N;
-    for (int k = threadIdx.x; k < n; k += kPreThreads) {
-        const int pv = q.v[k], pg = q.g[k];
-        const ViewParams &vp = vt.v[pv];
-        const size_t i = (size_t)pv * N + pg;
-        const float puh = q.uh[k], pvh = q.vh[k], m00 = q.m00[k];
-        const float sxx = q.sxx[k], sxy = q.sxy[k], syy = q.syy[k];
-        // the same expressions as gauss_pre, so that the records match it
-        const float o = 1.0f / (1.0f + expf(-gp.opacity_logits[pg]));
-        const float log2o = log2f(o);
-        const float smax = fminf(kCutoffD2 * kHalfLog2e, log2o + kLog2_255);
-        const uint32_t count =
-            visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [](int, int, int) {});
-        ws.counts[i] = count;
-        if (count == 0u) continue;
-        const Pose &ps = s_pose[pv];
-        float dx = gp.means[pg] - ps.C[0], dy = gp.means[N + pg] - ps.C[1], dz = gp.means[2 * N + pg] - ps.C[2];
-        const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= rn;
-        dy *= rn;
-        dz *= rn;
-        float Y[K];
-        sh_eval<DEG>(dx, dy, dz, Y);
-        float rgb[3];
-        // one channel at a time keeps few coefficients live in registers
+    const int pv = q.v[k], pg = q.g[k];
+    const ViewParams &vp = vt.v[pv];
+    const size_t i = (size_t)pv * N + pg;
+    const float puh = q.uh[k], pvh = q.vh[k], m00 = q.m00[k];
+    const float sxx = q.sxx[k], sxy = q.sxy[k], syy = q.syy[k];
+    // the same expressions as gauss_pre, so that the records match it
+    const float o = 1.0f / (1.0f + expf(-gp.opacity_logits[pg]));
+    const float log2o = log2f(o);
+    const float smax = fminf(kCutoffD2 * kHalfLog2e, log2o + kLog2_255);
+    const uint32_t count =
+        visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [](int, int, int) {});
+    ws.counts[i] = count;
+    if (count == 0u) return;
+    const Pose &ps = s_pose[pv];
+    float dx = gp.means[pg] - ps.C[0], dy = gp.means[N + pg] - ps.C[1], dz = gp.means[2 * N + pg] - ps.C[2];
+    const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= rn;
+    dy *= rn;
+    dz *= rn;
+    float Y[K];
+    sh_eval<DEG>(dx, dy, dz, Y);
+    float rgb[3];
+    // one channel at a time keeps few coefficients live in registers
 #pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-            const float *shc = gp.sh + (size_t)c * N + pg;
-            float acc = 0.5f;
+    for (int c = 0; c < 3; ++c) {
+        const float *shc = gp.sh + (size_t)c * N + pg;
+        float acc = 0.5f;
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc = fmaf(__ldg(shc + (size_t)j * 3 * N), Y[j], acc);
-            rgb[c] = fmaxf(acc, 0.f);
-        }
-        ws.rec0[i] = make_float4(puh, pvh, q.ul[k], q.vl[k]);
-        ws.rec1[i] = make_float4(m00, q.m01[k], q.m11[k], smax);
-        ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
-        ws.rec3[i] = make_float4(log2o, sxx, sxy, syy);
+        for (int j = 0; j < K; ++j) acc = fmaf(__ldg(shc + (size_t)j * 3 * N), Y[j], acc);
+        rgb[c] = fmaxf(acc, 0.f);
     }
+    ws.rec0[i] = make_float4(puh, pvh, q.ul[k], q.vl[k]);
+    ws.rec1[i] = make_float4(m00, q.m01[k], q.m11[k], smax);
+    ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
+    ws.rec3[i] = make_float4(log2o, sxx, sxy, syy);
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                     const GaussianPtrs gp, const Ws ws,
-                                                                     int vw_log2) {
+__global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                     const GaussianPtrs gp, const Ws ws) {
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
-    __shared__ PreQueue q;
-    __shared__ int s_wcount[kPreWarps];
+    __shared__ WarpQueue s_q[kPreWarps];
     load_poses(vt, s_pose);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-    const int VW = 1 << vw_log2, GB = kPreThreads >> vw_log2;
-    const int vv = tid / GB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpQueue &q = s_q[warp];
     const size_t N = (size_t)gp.N;
-    int qn = 0;   // queued pairs (the same in every thread)
-    for (int r = 0; r < kPreRounds; ++r) {
-        const int g = (blockIdx.x * kPreRounds + r) * GB + tid % GB;
+    const int nbatch = (gp.N + 31) / 32, nwarps = gridDim.x * kPreWarps;
+    int qn = 0;   // queued pairs (the same in every lane)
+    for (int b = blockIdx.x * kPreWarps + warp; b < nbatch; b += nwarps) {
+        const int g = b * 32 + lane;
         const bool real = g < gp.N;
         GaussPre G;
         if (real) gauss_pre(gp, g, G);
-        for (int v0 = 0; v0 < vt.V; v0 += VW) {
-            if (qn + kPreThreads > kPreQueue) {
-                __syncthreads();
-                preprocess_fwd_flush<DEG>(vt, gp, ws, s_pose, q, qn);
-                __syncthreads();
-                qn = 0;
-            }
-            // phase A: projection and visibility of every pair of the round
-            const int v = v0 + vv;
+        for (int v = 0; v < vt.V; ++v) {
+            // phase A: projection and visibility of (v, the 32 Gaussians)
             bool vis = false;
             float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
             Proj p;
-            if (real && v < vt.V) {
+            if (real) {
                 const ViewParams &vp = vt.v[v];
                 if (G.alive && project_view(G, s_pose[v], vp, p)) {
                     project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
@@ -154,18 +143,8 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __gri
                 if (!vis) ws.counts[(size_t)v * N + g] = 0u;
             }
             const unsigned ball = __ballot_sync(0xffffffffu, vis);
-            __syncthreads();   // s_wcount of the previous round has been read
-            if (lane == 0) s_wcount[warp] = __popc(ball);
-            __syncthreads();
-            int off = 0, nvis = 0;
-#pragma unroll
-            for (int w = 0; w < kPreWarps; ++w) {
-                const int c = s_wcount[w];
-                off += w < warp ? c : 0;
-                nvis += c;
-            }
             if (vis) {
-                const int k = qn + off + __popc(ball & lanemask_lt());
+                const int k = qn + __popc(ball & lanemask_lt());
                 q.uh[k] = uh;
                 q.vh[k] = vh;
                 q.ul[k] = ul;
@@ -180,11 +159,34 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(const __gri
                 q.v[k] = v;
                 q.g[k] = g;
             }
-            qn += nvis;
+            qn += __popc(ball);
+            if (qn >= 32) {   // phase B on the first 32, then move the rest to the front
+                __syncwarp();
+                preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane);
+                __syncwarp();
+                if (lane < qn - 32) {
+                    const int k = 32 + lane;
+                    q.uh[lane] = q.uh[k];
+                    q.vh[lane] = q.vh[k];
+                    q.ul[lane] = q.ul[k];
+                    q.vl[lane] = q.vl[k];
+                    q.m00[lane] = q.m00[k];
+                    q.m01[lane] = q.m01[k];
+                    q.m11[lane] = q.m11[k];
+                    q.sxx[lane] = q.sxx[k];
+                    q.sxy[lane] = q.sxy[k];
+                    q.syy[lane] = q.syy[k];
+                    q.zh[lane] = q.zh[k];
+                    q.v[lane] = q.v[k];
+                    q.g[lane] = q.g[k];
+                }
+                qn -= 32;
+                __syncwarp();
+            }
         }
     }
-    __syncthreads();
-    preprocess_fwd_flush<DEG>(vt, gp, ws, s_pose, q, qn);
+    __syncwarp();
+    if (lane < qn) preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane);
 }
 
 // ------------------------------------------------------------------ backward
@@ -669,33 +671,27 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------------ launchers
-// log2 of the warps that share one group of 32 Gaussians: as many as there
-// are views, up to the block's kPreWarps (a power of two).
-static int views_log2(int V) {
-    int l = 0;
-    while ((2 << l) <= V && (2 << l) <= kPreWarps) ++l;
-    return l;
-}
-
-static int pre_blocks(int N, int vw_log2) {
-    const int per_block = kPreRounds * (kPreThreads >> vw_log2);
-    return (N + per_block - 1) / per_block;
-}
+// Resident blocks per SM of the forward kernel (registers allow 3).
+constexpr int kPreFwdBlocksPerSM = 3;
 
 template <int DEG>
-static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st) {
-    const int l = views_log2(vt.V);
-    preprocess_fwd_kernel<DEG><<<pre_blocks(gp.N, l), kPreThreads, 0, st>>>(vt, gp, ws, l);
+static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,
+                                  cudaStream_t st) {
+    const long long batches = ((long long)gp.N + 31) / 32;
+    const long long need = (batches + kPreWarps - 1) / kPreWarps;
+    const unsigned blocks = (unsigned)std::min<long long>(need, (long long)sm_count * kPreFwdBlocksPerSM);
+    preprocess_fwd_kernel<DEG><<<blocks, kPreThreads, 0, st>>>(vt, gp, ws);
     return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st) {
+cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,
+                                  cudaStream_t st) {
     if (gp.N == 0) return cudaSuccess;
     switch (gp.sh_degree) {
-        case 0: return launch_pre_fwd<0>(vt, gp, ws, st);
-        case 1: return launch_pre_fwd<1>(vt, gp, ws, st);
-        case 2: return launch_pre_fwd<2>(vt, gp, ws, st);
-        default: return launch_pre_fwd<3>(vt, gp, ws, st);
+        case 0: return launch_pre_fwd<0>(vt, gp, ws, sm_count, st);
+        case 1: return launch_pre_fwd<1>(vt, gp, ws, sm_count, st);
+        case 2: return launch_pre_fwd<2>(vt, gp, ws, sm_count, st);
+        default: return launch_pre_fwd<3>(vt, gp, ws, sm_count, st);
     }
 }
 
