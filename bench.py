@@ -320,7 +320,9 @@ def traffic_for(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     source has not changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    src = os.path.join(ROOT, "paper_2411_17660_b300", "csrc", "blend.cu" if "blend" in kernel else "preprocess.cu")
+    name = "blend.cu" if "blend" in kernel else ("binning.cu" if kernel in ("sort", "duplicate") else "preprocess.cu")
+    src = os.path.join(ROOT, "paper_2411_17660_b300", "csrc", name)
+    kernel = "onesweep" if kernel == "sort" else kernel
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
