@@ -107,36 +107,45 @@ def _split(flat, counts, sizes, full, tail_shape):
     return out
 
 
+_NOUT = 9   # per pixel: r, g, b, depth, opacity, T_final, margin, median depth, median margin
+
+
+def _pixel_dict(o, n):
+    return dict(color=np.moveaxis(o[..., 0:3], -1, 0), depth=o[..., 3], alpha=o[..., 4], T=o[..., 5],
+                margin=o[..., 6], median_depth=o[..., 7], median_margin=o[..., 8], ncontrib=n)
+
+
 def render(scene, pixels: Optional[Sequence[np.ndarray]] = None, brute: bool = False,
            threads: int = 0, cameras=None):
     """Forward render.  pixels: per view arrays of linear indices y*W+x (None
     = all).  Returns per view dicts with color [3,...], depth, alpha, T,
-    ncontrib, margin (full images are [H, W])."""
+    ncontrib, margin, median_depth, median_margin (full images are [H, W])."""
     lib = _load()
     pk = _Packed(scene, cameras)
     off, flat, counts = _pixels(pk, pixels)
     P = int(sum(counts))
-    out = np.zeros((max(P, 1), 7), np.float64)
+    out = np.zeros((max(P, 1), _NOUT), np.float64)
     nc = np.zeros(max(P, 1), np.int32)
     lib.og_render(ctypes.byref(pk.g), pk.V, pk.cams,
                   None if off is None else _ptr(off), None if flat is None else _ptr(flat),
                   int(brute), int(threads), _ptr(out), _ptr(nc))
     full = pixels is None
     res = []
-    outs = _split(out[:P], counts, pk.sizes, full, (7,))
+    outs = _split(out[:P], counts, pk.sizes, full, (_NOUT,))
     ncs = _split(nc[:P], counts, pk.sizes, full, ())
     for o, n in zip(outs, ncs):
-        res.append(dict(color=np.moveaxis(o[..., 0:3], -1, 0), depth=o[..., 3], alpha=o[..., 4],
-                        T=o[..., 5], margin=o[..., 6], ncontrib=n))
+        res.append(_pixel_dict(o, n))
     return res
 
 
 def render_backward(scene, gC: List[np.ndarray], gD: List[np.ndarray], gA: List[np.ndarray],
                     pixels: Optional[Sequence[np.ndarray]] = None, brute: bool = False,
-                    threads: int = 0, want_screen: bool = False, cameras=None):
+                    threads: int = 0, want_screen: bool = False, cameras=None,
+                    gM: Optional[List[np.ndarray]] = None):
     """Forward + backward with upstream grads per view: gC [3, ...], gD, gA
-    shaped like the selected pixels ([3,H,W]/[H,W] for full images, [3,n]/[n]
-    for pixel lists).  Returns (per view forward dicts, grads dict)."""
+    (and optionally gM, dL/d median depth) shaped like the selected pixels
+    ([3,H,W]/[H,W] for full images, [3,n]/[n] for pixel lists).  Returns
+    (per view forward dicts, grads dict)."""
     lib = _load()
     pk = _Packed(scene, cameras)
     off, flat, counts = _pixels(pk, pixels)
@@ -145,23 +154,25 @@ def render_backward(scene, gC: List[np.ndarray], gD: List[np.ndarray], gA: List[
         [np.moveaxis(np.asarray(g, np.float64).reshape(3, -1), 0, -1) for g in gC]) if P else np.zeros((1, 3)))
     gDf = np.ascontiguousarray(np.concatenate([np.asarray(g, np.float64).reshape(-1) for g in gD]) if P else np.zeros(1))
     gAf = np.ascontiguousarray(np.concatenate([np.asarray(g, np.float64).reshape(-1) for g in gA]) if P else np.zeros(1))
+    gMf = None if gM is None else np.ascontiguousarray(
+        np.concatenate([np.asarray(g, np.float64).reshape(-1) for g in gM]) if P else np.zeros(1))
     N = scene.means.shape[1]
     K = (scene.sh_degree + 1) ** 2
-    out = np.zeros((max(P, 1), 7), np.float64)
+    out = np.zeros((max(P, 1), _NOUT), np.float64)
     nc = np.zeros(max(P, 1), np.int32)
     gm = np.zeros((3, N)); gls = np.zeros((3, N)); gq = np.zeros((4, N)); gl = np.zeros(N)
     gsh = np.zeros((3 * K, N)); pose = np.zeros((pk.V, 6))
     screen = np.zeros((pk.V, 10, N)) if want_screen else None
     lib.og_render_backward(ctypes.byref(pk.g), pk.V, pk.cams,
                            None if off is None else _ptr(off), None if flat is None else _ptr(flat),
-                           int(brute), int(threads), _ptr(gCf), _ptr(gDf), _ptr(gAf), _ptr(out), _ptr(nc),
+                           int(brute), int(threads), _ptr(gCf), _ptr(gDf), _ptr(gAf),
+                           None if gMf is None else _ptr(gMf), _ptr(out), _ptr(nc),
                            _ptr(gm), _ptr(gls), _ptr(gq), _ptr(gl), _ptr(gsh), _ptr(pose),
                            None if screen is None else _ptr(screen))
     full = pixels is None
     res = []
-    for o, n in zip(_split(out[:P], counts, pk.sizes, full, (7,)), _split(nc[:P], counts, pk.sizes, full, ())):
-        res.append(dict(color=np.moveaxis(o[..., 0:3], -1, 0), depth=o[..., 3], alpha=o[..., 4],
-                        T=o[..., 5], margin=o[..., 6], ncontrib=n))
+    for o, n in zip(_split(out[:P], counts, pk.sizes, full, (_NOUT,)), _split(nc[:P], counts, pk.sizes, full, ())):
+        res.append(_pixel_dict(o, n))
     grads = dict(means=gm, log_scales=gls, quats=gq, opacity_logits=gl, sh=gsh, pose=pose)
     if want_screen:
         grads["screen"] = screen

@@ -28,6 +28,11 @@
  *   - colour c = max(0, sum_k SH_k Y_k(dir) + 0.5), dir = (P - C)/|P - C|,
  *     C = -W^T t, real SH with the Condon-Shortley phase, order (l, m=-l..l);
  *   - depth D = sum_i w_i z_i (w_i = alpha_i T_i), opacity A = sum_i w_i;
+ *   - median depth (the paper renders "median depth" as MonoGS does): the z
+ *     of the last contributor whose transmittance in front of it, T_i, is
+ *     above 0.5 -- the Gaussian during which the accumulated opacity passes
+ *     0.5, or the last contributor if it never does; 0 without contributors.
+ *     Its gradient goes to that contributor's z only;
  *   - pose gradient: left perturbation T_cw <- Exp(xi) T_cw, xi = (rho, phi),
  *     taken at xi = 0;
  *   - gradients through the alpha clamp, the colour clamp and a clamped
@@ -414,7 +419,9 @@ static double fmin2(double a, double b) { return a < b ? a : b; }
 
 /* Composites one pixel from its candidate list.  Fills out[0..2] colour,
  * out[3] depth, out[4] opacity (sum of weights), out[5] final transmittance,
- * out[6] decision margin; returns the number of contributors written. */
+ * out[6] decision margin, out[7] median depth, out[8] the median's decision
+ * margin (min over contributors of |T_i / 0.5 - 1|); returns the number of
+ * contributors written. */
 typedef struct {
     cand_t *buf;
     contrib_t *con;
@@ -435,7 +442,7 @@ static void scratch_reserve(scratch_t *s, int n, int want_bwd) {
 }
 
 static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px, double py,
-                         scratch_t *s, int want_bwd, double out[7], int *ncontrib) {
+                         scratch_t *s, int want_bwd, double out[9], int *ncontrib) {
     int n = 0;
     const double keep_d2 = CUTOFF_D2 * (1 + 1e-3);
     for (int k = 0; k < ncand; ++k) {
@@ -455,7 +462,7 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
     cand_t *buf = s->buf;
     contrib_t *con = want_bwd ? s->con : NULL;
     if (n > 0) qsort(buf, n, sizeof(cand_t), cand_cmp);
-    double T = 1, C[3] = {0, 0, 0}, D = 0, A = 0, margin = 1e30;
+    double T = 1, C[3] = {0, 0, 0}, D = 0, A = 0, margin = 1e30, Zmed = 0, mmed = 1e30;
     int nc = 0;
     double prev_z = -1;
     for (int k = 0; k < n; ++k) {
@@ -475,6 +482,8 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         margin = fmin2(margin, fabs(Tn / T_STOP - 1));
         if (Tn < T_STOP) break;
         const double w = alpha * T;
+        mmed = fmin2(mmed, fabs(T / 0.5 - 1));
+        if (T > 0.5) Zmed = p->z;
         for (int c = 0; c < 3; ++c) C[c] += w * p->rgb[c];
         D += w * p->z;
         A += w;
@@ -491,14 +500,18 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         T = Tn;
     }
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2];
-    out[3] = D; out[4] = A; out[5] = T; out[6] = margin;
+    out[3] = D; out[4] = A; out[5] = T; out[6] = margin; out[7] = Zmed; out[8] = mmed;
     *ncontrib = nc;
     return nc;
 }
 
-/* Backward of one pixel: writes 10 screen-space grads per contributor. */
+/* Backward of one pixel: writes 10 screen-space grads per contributor.  gM
+ * (dL/d median depth) goes to the z of the contributor the median took. */
 static void pixel_backward(const og_proj *P, const contrib_t *con, int nc, double T_final,
-                           const double gC[3], double gD, double gA, double *sg /* [nc][10] */) {
+                           const double gC[3], double gD, double gA, double gM, double *sg /* [nc][10] */) {
+    int med = -1;
+    for (int i = 0; i < nc; ++i)
+        if (con[i].T > 0.5) med = i;
     double BC[3] = {0, 0, 0}, BD = 0;
     for (int i = nc - 1; i >= 0; --i) {
         const og_proj *p = &P[con[i].g];
@@ -506,7 +519,7 @@ static void pixel_backward(const og_proj *P, const contrib_t *con, int nc, doubl
         double *o = sg + 10 * i;
         for (int c = 0; c < 10; ++c) o[c] = 0;
         for (int c = 0; c < 3; ++c) o[6 + c] = gC[c] * a * Ti;
-        o[9] = gD * a * Ti;
+        o[9] = gD * a * Ti + (i == med ? gM : 0.0);
         double dA = Ti * ((p->rgb[0] - BC[0]) * gC[0] + (p->rgb[1] - BC[1]) * gC[1] +
                           (p->rgb[2] - BC[2]) * gC[2] + (p->z - BD) * gD) +
                     gA * T_final / (1 - a);
@@ -580,10 +593,10 @@ typedef struct {
     const int *all;        /* 0..N-1 for brute force */
     const int64_t *pix;    /* pixel linear indices (y*W + x) */
     int64_t p0, p1;        /* range of pixels for this worker */
-    double *out;           /* [npix][7] */
+    double *out;           /* [npix][9] */
     int32_t *ncontrib;
     /* backward */
-    const double *gC, *gD, *gA;
+    const double *gC, *gD, *gA, *gM;   /* gM may be NULL */
     double *sg;            /* growable [n][10] */
     int *sg_g;
     int64_t sg_n, sg_cap;
@@ -607,15 +620,15 @@ static void *worker(void *arg) {
             cand = w->all;
             ncand = w->N;
         }
-        double o[7];
+        double o[9];
         int nc = 0;
         pixel_forward(w->P, cand, ncand, (double)px, (double)py, &s, want_bwd, o, &nc);
-        if (w->out) memcpy(w->out + 7 * i, o, sizeof o);
+        if (w->out) memcpy(w->out + 9 * i, o, sizeof o);
         if (w->ncontrib) w->ncontrib[i] = nc;
         if (w->gC) {
             double *psg = s.psg;
             const contrib_t *con = s.con;
-            pixel_backward(w->P, con, nc, o[5], w->gC + 3 * i, w->gD[i], w->gA[i], psg);
+            pixel_backward(w->P, con, nc, o[5], w->gC + 3 * i, w->gD[i], w->gA[i], w->gM ? w->gM[i] : 0.0, psg);
             if (w->sg_n + nc > w->sg_cap) {
                 int64_t cap = w->sg_cap ? w->sg_cap : 1024;
                 while (cap < w->sg_n + nc) cap *= 2;
@@ -671,7 +684,8 @@ static void project_all(const og_gaussians *G, const og_camera *cam, og_proj *P,
  * into sgrad [10][N] (zeroed by the caller). */
 static int run_view(const og_gaussians *G, const og_camera *cam, const int64_t *pix, int64_t npix,
                     int brute, int nt, double *out, int32_t *ncontrib,
-                    const double *gC, const double *gD, const double *gA, double *sgrad, og_proj *P) {
+                    const double *gC, const double *gD, const double *gA, const double *gM, double *sgrad,
+                    og_proj *P) {
     const int N = G->N;
     project_all(G, cam, P, nt);
     buckets_t B = {0};
@@ -690,7 +704,7 @@ static int run_view(const og_gaussians *G, const og_camera *cam, const int64_t *
         w[k].P = P; w[k].N = N; w[k].cam = cam; w[k].B = brute ? NULL : &B; w[k].all = all;
         w[k].pix = pix; w[k].p0 = npix * k / nt; w[k].p1 = npix * (k + 1) / nt;
         w[k].out = out; w[k].ncontrib = ncontrib;
-        w[k].gC = gC; w[k].gD = gD; w[k].gA = gA;
+        w[k].gC = gC; w[k].gD = gD; w[k].gA = gA; w[k].gM = gM;
         pthread_create(&th[k], NULL, worker, &w[k]);
     }
     for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
@@ -725,8 +739,8 @@ static int64_t *full_pixels(const og_camera *cam, int64_t *npix) {
 
 /* Per-pixel forward over V views.  pix_off[V+1] and pix (concatenated
  * linear pixel indices y*W+x) select the pixels; pix == NULL renders every
- * pixel of every view in order.  out [P][7]: r, g, b, depth, opacity,
- * T_final, margin.  ncontrib [P]. */
+ * pixel of every view in order.  out [P][9]: r, g, b, depth, opacity,
+ * T_final, margin, median depth, median margin.  ncontrib [P]. */
 int og_render(const og_gaussians *G, int V, const og_camera *cams, const int64_t *pix_off,
               const int64_t *pix, int brute, int threads, double *out, int32_t *ncontrib) {
     const int nt = num_threads(threads);
@@ -743,7 +757,7 @@ int og_render(const og_gaussians *G, int V, const og_camera *cams, const int64_t
             own = full_pixels(&cams[v], &np);
             pv = own;
         }
-        run_view(G, &cams[v], pv, np, brute, nt, out + 7 * base, ncontrib + base, NULL, NULL, NULL, NULL, P);
+        run_view(G, &cams[v], pv, np, brute, nt, out + 9 * base, ncontrib + base, NULL, NULL, NULL, NULL, NULL, P);
         base += np;
         free(own);
     }
@@ -752,13 +766,13 @@ int og_render(const og_gaussians *G, int V, const og_camera *cams, const int64_t
 }
 
 /* Forward + backward.  gC [P][3], gD [P], gA [P] are dL/d(colour, depth,
- * opacity) at the selected pixels.  Gradients (zeroed here) come back for
+ * opacity) at the selected pixels, gM [P] dL/d(median depth) or NULL.  Gradients (zeroed here) come back for
  * means [3][N], log_scales [3][N], quats [4][N], opacity_logits [N],
  * sh [K*3][N], pose [V][6] (rho, phi) and, if screen != NULL, the summed
  * screen-space grads [V][10][N] (du, dv, dconic0..2, dopacity, drgb, dz). */
 int og_render_backward(const og_gaussians *G, int V, const og_camera *cams, const int64_t *pix_off,
                        const int64_t *pix, int brute, int threads, const double *gC, const double *gD,
-                       const double *gA, double *out, int32_t *ncontrib, double *gm, double *gls,
+                       const double *gA, const double *gM, double *out, int32_t *ncontrib, double *gm, double *gls,
                        double *gq, double *gl, double *gsh, double *pose, double *screen) {
     const int N = G->N;
     const int K = (G->sh_degree + 1) * (G->sh_degree + 1);
@@ -784,8 +798,8 @@ int og_render_backward(const og_gaussians *G, int V, const og_camera *cams, cons
             pv = own;
         }
         memset(sgrad, 0, sizeof(double) * 10 * (size_t)N);
-        run_view(G, &cams[v], pv, np, brute, nt, out + 7 * base, ncontrib + base, gC + 3 * base,
-                 gD + base, gA + base, sgrad, P);
+        run_view(G, &cams[v], pv, np, brute, nt, out + 9 * base, ncontrib + base, gC + 3 * base,
+                 gD + base, gA + base, gM ? gM + base : NULL, sgrad, P);
         for (int g = 0; g < N; ++g) {
             if (!P[g].valid) continue;
             double s[10];

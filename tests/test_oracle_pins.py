@@ -374,3 +374,95 @@ def test_pixel_subset_matches_full_image():
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
         np.testing.assert_allclose(g1[k], g2[k], rtol=1e-12, atol=1e-14)
     np.testing.assert_array_equal(o1[0]["color"], o2[0]["color"].reshape(3, -1)[:, pix])
+
+
+# ---------------------------------------------------------------- median depth
+
+def test_median_depth_worked_cases():
+    """Two Gaussians on the axis: the median is the front one's depth where it
+    alone takes the accumulated opacity past 0.5, else the one behind it."""
+    c = cam(9, 9, 50.0)
+    z1, z2 = 2.0, 3.0
+    sig = lambda l: 1 / (1 + np.exp(-l))
+    for l1, expect_front in ((3.0, True), (-1.0, False)):
+        sc = make_scene([[0.0, 0.0], [0.0, 0.0], [z2, z1]], np.log([[0.08, 0.04]] * 3),
+                        [[1.0, 1.0], [0, 0], [0, 0], [0, 0]], [1.2, l1],
+                        np.stack([dc_for_rgb([0.5] * 3), dc_for_rgb([0.5] * 3)], 1), 0, [c])
+        out = oracle.render(sc)[0]
+        for (x, y) in [(4, 4), (5, 5)]:
+            r2 = (x - 4.5) ** 2 + (y - 4.5) ** 2
+            a1 = float(_iso_alpha(sig(l1), 50.0, 0.04, z1, r2))
+            a2 = float(_iso_alpha(sig(1.2), 50.0, 0.08, z2, r2))
+            assert (1 - a1 < 0.5) == expect_front
+            want = z1 if (1 - a1 <= 0.5 or a2 == 0) else z2
+            assert out["median_depth"][y, x] == want
+    # no contributor: zero
+    sc = make_scene([[0.0], [0.0], [-3.0]], np.log([[0.05]] * 3), [[1.0], [0], [0], [0]], [1.0],
+                    dc_for_rgb([0.5] * 3)[:, None], 0, [c])
+    assert not oracle.render(sc)[0]["median_depth"].any()
+
+
+def test_median_depth_brute_force_from_projection():
+    """Per pixel, from the oracle's projected quantities alone: evaluate every
+    Gaussian's alpha with the skip/clamp/stop rules in (z, index) order and
+    take the z of the last contributor entered with transmittance above 0.5."""
+    rng = np.random.default_rng(21)
+    sc = _random_scene(rng, 12, 16, 20, 20.0, 0)
+    out = oracle.render(sc)[0]
+    P = oracle.project(sc, 0)
+    order = sorted(range(12), key=lambda g: (P["z"][g], g))
+    c = sc.cameras[0]
+    checked = 0
+    for y in range(c.H):
+        for x in range(c.W):
+            if out["median_margin"][y, x] < 1e-6:
+                continue
+            T, med = 1.0, 0.0
+            for g in order:
+                if not P["valid"][g]:
+                    continue
+                dx, dy = x - P["u"][g], y - P["v"][g]
+                d2 = P["conic0"][g] * dx * dx + 2 * P["conic1"][g] * dx * dy + P["conic2"][g] * dy * dy
+                if d2 > 9:
+                    continue
+                a = P["opacity"][g] * np.exp(-0.5 * d2)
+                if a < 1 / 255:
+                    continue
+                a = min(a, 0.99)
+                if T * (1 - a) < 1e-4:
+                    break
+                if T > 0.5:
+                    med = P["z"][g]
+                T *= 1 - a
+            assert out["median_depth"][y, x] == pytest.approx(med, abs=1e-12)
+            checked += 1
+    assert checked > 0.9 * c.H * c.W
+
+
+def test_median_depth_gradient_matches_central_fd():
+    rng = np.random.default_rng(5)
+    while True:
+        sc = _fd_scene(int(rng.integers(100, 10_000)), deg=0)
+        o = oracle.render(sc)[0]
+        if o["median_margin"].min() > 2e-3 and (o["median_depth"] > 0).mean() > 0.2:
+            break
+    c = sc.cameras[0]
+    wM = rng.uniform(-1, 1, (c.H, c.W))
+    zero = np.zeros((c.H, c.W))
+    _, g = oracle.render_backward(sc, [np.zeros((3, c.H, c.W))], [zero], [zero], gM=[wM])
+    h = 1e-6
+    fd = np.zeros_like(sc.means)
+    for i in range(sc.means.size):
+        flat = sc.means.reshape(-1)
+        keep = flat[i]
+        flat[i] = keep + h
+        lp = (wM * oracle.render(sc)[0]["median_depth"]).sum()
+        flat[i] = keep - h
+        lm = (wM * oracle.render(sc)[0]["median_depth"]).sum()
+        flat[i] = keep
+        fd.reshape(-1)[i] = (lp - lm) / (2 * h)
+    err = np.linalg.norm(g["means"] - fd) / max(np.linalg.norm(fd), 1e-30)
+    assert err < 1e-6
+    # nothing else moves the median: the other parameters get no gradient
+    for k in ("log_scales", "quats", "opacity_logits", "sh"):
+        assert not g[k].any(), k
