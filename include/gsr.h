@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 1
+#define GSR_ABI_VERSION 2
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -101,6 +101,10 @@ typedef struct {
     float *color;             /* device out [3][H][W] */
     float *depth;             /* device out [H][W] (may be NULL) */
     float *alpha;             /* device out [H][W] (may be NULL) */
+    float *median_depth;      /* device out [H][W] (may be NULL): the median depth of Sec. 3.3, read
+                                 as the z of the last contributor entered with transmittance above
+                                 0.5 (the Gaussian during which the accumulated opacity passes 0.5,
+                                 or the last contributor if it never does), 0 without contributors */
 } gsr_view;
 
 /* Upstream gradients of one keyframe (device; NULL means zero) and the
@@ -110,6 +114,8 @@ typedef struct {
     const float *d_color;     /* [3][H][W] or NULL */
     const float *d_depth;     /* [H][W] or NULL */
     const float *d_alpha;     /* [H][W] or NULL */
+    const float *d_median_depth; /* [H][W] or NULL; needs a forward that rendered median_depth
+                                    (of any view) on the same workspace, else GSR_ENOTREADY */
     float *d_pose;            /* out [6] or NULL */
 } gsr_view_grad;
 

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgsr.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
+ABI_VERSION = 2   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
@@ -40,11 +41,11 @@ class Gaussians(ctypes.Structure):
 class View(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("T_cw", _p), ("color", _p), ("depth", _p),
-                ("alpha", _p)]
+                ("alpha", _p), ("median_depth", _p)]
 
 
 class ViewGrad(ctypes.Structure):
-    _fields_ = [("d_color", _p), ("d_depth", _p), ("d_alpha", _p), ("d_pose", _p)]
+    _fields_ = [("d_color", _p), ("d_depth", _p), ("d_alpha", _p), ("d_median_depth", _p), ("d_pose", _p)]
 
 
 class Grads(ctypes.Structure):
@@ -109,6 +110,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    if lib.gsr_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{path} has ABI version {lib.gsr_abi_version()}, this binding expects {ABI_VERSION}; "
+                           "rebuild with `python -m paper_2411_17660_b300.build`")
     _lib = lib
     return lib
 

@@ -22,6 +22,7 @@ struct gsr_ctx {
         size_t bytes;
         int N, V, deg;
         std::vector<int> dims;
+        bool median;   // the forward recorded the median-depth contributors
     };
     std::vector<Rec> recs;  // recent forwards, for the backward's checks
     // caller-provided stage events (gsr_set_stage_events), 0..9
@@ -39,7 +40,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3;
-    size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, vg_grads, pose_partials;
+    size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
     size_t total;
     uint64_t VN;
     uint32_t cap, lb_tiles, scan_blocks, pose_blocks, total_pixels, total_tiles;
@@ -81,6 +82,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.ranges = take(8ull * L.total_tiles);
     L.T_final = take(4ull * L.total_pixels);
     L.last = take(4ull * L.total_pixels);
+    L.median = take(4ull * L.total_pixels);
     L.vg_grads = take(4ull * kVGGrads * L.VN);
     L.pose_partials = take(24ull * V * (L.pose_blocks ? L.pose_blocks : 1));
     L.keys0 = take(8 * cap);
@@ -130,6 +132,7 @@ Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) 
     w.ranges = reinterpret_cast<uint2 *>(b + L.ranges);
     w.T_final = reinterpret_cast<float *>(b + L.T_final);
     w.last = reinterpret_cast<uint32_t *>(b + L.last);
+    w.median = reinterpret_cast<uint32_t *>(b + L.median);
     w.vg_grads = reinterpret_cast<float *>(b + L.vg_grads);
     w.pose_partials = reinterpret_cast<float *>(b + L.pose_partials);
     w.N = (uint32_t)N;
@@ -215,6 +218,12 @@ GaussianPtrs gaussian_ptrs(const gsr_gaussians *gs) {
     return g;
 }
 
+bool want_median(const gsr_view *views, int V) {
+    for (int v = 0; v < V; ++v)
+        if (views[v].median_depth) return true;
+    return false;
+}
+
 void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile) {
     memset(&vt, 0, sizeof vt);
     vt.V = V;
@@ -233,10 +242,12 @@ void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads
         p.color = w.color;
         p.depth = w.depth;
         p.alpha = w.alpha;
+        p.median_depth = w.median_depth;
         if (grads) {
             p.d_color = grads[v].d_color;
             p.d_depth = grads[v].d_depth;
             p.d_alpha = grads[v].d_alpha;
+            p.d_median_depth = grads[v].d_median_depth;
             p.d_pose = grads[v].d_pose;
         }
         p.tiles_x = (w.W + tile - 1) / tile;
@@ -349,7 +360,7 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
 
-    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}};
+    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}, want_median(views, V)};
     for (int v = 0; v < V; ++v) {
         r.dims.push_back(views[v].H);
         r.dims.push_back(views[v].W);
@@ -381,6 +392,9 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     for (int v = 0; match && v < V; ++v)
         match = rec->dims[2 * v] == views[v].H && rec->dims[2 * v + 1] == views[v].W;
     if (!match) return fail(ctx, GSR_ENOTREADY, "no forward with these Gaussians and views on this workspace");
+    for (int v = 0; v < V; ++v)
+        if (grads[v].d_median_depth && !rec->median)
+            return fail(ctx, GSR_ENOTREADY, "view %d: a median-depth gradient needs a forward that rendered median depth", v);
     const uint32_t cap = capacity_for(gs->N, views, V, ctx->tile, ws_bytes);
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);

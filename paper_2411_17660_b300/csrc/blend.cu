@@ -201,7 +201,9 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
     return __popc(ballot);
 }
 
-template <int TS>
+// MED: also record, per pixel, the median-depth contributor (the last one
+// entered with transmittance above 0.5) and its depth.
+template <int TS, bool MED>
 __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     using S = BlendShape<TS>;
@@ -213,14 +215,14 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
-    float T[kPPL], C0[kPPL], C1[kPPL], C2[kPPL], D[kPPL];
-    uint32_t last[kPPL], ncon = 0;
+    float T[kPPL], C0[kPPL], C1[kPPL], C2[kPPL], D[kPPL], Zm[kPPL];
+    uint32_t last[kPPL], mi[kPPL], ncon = 0;
     bool done[kPPL];
 #pragma unroll
     for (int q = 0; q < kPPL; ++q) {
         T[q] = 1.f;
-        C0[q] = C1[q] = C2[q] = D[q] = 0.f;
-        last[q] = 0;
+        C0[q] = C1[q] = C2[q] = D[q] = Zm[q] = 0.f;
+        last[q] = mi[q] = 0;
         done[q] = !(wt.px < vp.W && wt.py + q * kRowStep < vp.H);
     }
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
@@ -254,6 +256,10 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
                         C1[q] = fmaf(w, c.y, C1[q]);
                         C2[q] = fmaf(w, c.z, C2[q]);
                         D[q] = fmaf(w, b.w, D[q]);
+                        if (MED && T[q] > 0.5f) {
+                            Zm[q] = b.w;
+                            mi[q] = __float_as_uint(c.w) + 1u;
+                        }
                         T[q] = Tn;
                         last[q] = __float_as_uint(c.w) + 1u;
                         ++ncon;
@@ -275,13 +281,18 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
             if (vp.alpha) vp.alpha[pix] = 1.f - T[q];
             ws.T_final[vp.pixel_offset + pix] = T[q];
             ws.last[vp.pixel_offset + pix] = last[q];
+            if (MED) {
+                if (vp.median_depth) vp.median_depth[pix] = Zm[q];
+                ws.median[vp.pixel_offset + pix] = mi[q];
+            }
         }
     }
     const uint32_t tot = __reduce_add_sync(kFull, ncon);
     if (lane == 0 && tot) atomicAdd(&ws.hdr->pairs_contrib, (unsigned long long)tot);
 }
 
-template <int TS>
+// MED: dL/d(median depth) goes to the z of each pixel's median contributor.
+template <int TS, bool MED>
 __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     using S = BlendShape<TS>;
@@ -301,12 +312,13 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
     // per pixel (.x, .y as in the forward): Q = gC . (colour behind) + gD
     // (depth behind), normalised by the transmittance in front of the
     // current entry
-    float Tq[kPPL], gq[5][kPPL];
-    uint32_t last[kPPL], lmax = 0;
+    float Tq[kPPL], gq[5][kPPL], gM[kPPL];
+    uint32_t last[kPPL], mi[kPPL], lmax = 0;
 #pragma unroll
     for (int q = 0; q < kPPL; ++q) {
         Tq[q] = 1.f;
-        last[q] = 0;
+        last[q] = mi[q] = 0;
+        gM[q] = 0.f;
 #pragma unroll
         for (int k = 0; k < 5; ++k) gq[k][q] = 0.f;
         const int py = wt.py + q * kRowStep;
@@ -321,6 +333,10 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
             }
             if (vp.d_depth) gq[3][q] = vp.d_depth[pix];
             if (vp.d_alpha) gq[4][q] = vp.d_alpha[pix] * Tq[q];
+            if (MED && vp.d_median_depth) {
+                gM[q] = vp.d_median_depth[pix];
+                mi[q] = ws.median[vp.pixel_offset + pix];
+            }
         }
         lmax = max(lmax, last[q]);
     }
@@ -392,6 +408,7 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
                 gv[7] = fmaf(gG.y, w.y, gG.x * w.x);
                 gv[8] = fmaf(gB.y, w.y, gB.x * w.x);
                 gv[9] = fmaf(gZ.y, w.y, gZ.x * w.x);
+                if (MED) gv[9] += (eidx + 1u == mi[0] ? gM[0] : 0.f) + (eidx + 1u == mi[1] ? gM[1] : 0.f);
             } else {
                 // Only one pixel row of the warp is reached: scalar work on it.
                 auto row = [&](auto tag) {
@@ -427,6 +444,7 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
                     gv[7] = gGq * w;
                     gv[8] = gBq * w;
                     gv[9] = gZq * w;
+                    if (MED && eidx + 1u == (R ? mi[1] : mi[0])) gv[9] += R ? gM[1] : gM[0];
                 };
                 if (m0 == 0u)
                     row(RowTag<1>{});
@@ -455,13 +473,23 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(cons
 
 template <int TS>
 cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
-    blend_fwd_kernel<TS><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+    bool med = false;
+    for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
+    if (med)
+        blend_fwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+    else
+        blend_fwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
 template <int TS>
 cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
-    blend_bwd_kernel<TS><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+    bool med = false;
+    for (int v = 0; v < vt.V; ++v) med |= vt.v[v].d_median_depth != nullptr;
+    if (med)
+        blend_bwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+    else
+        blend_bwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 

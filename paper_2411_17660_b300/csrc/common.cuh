@@ -42,8 +42,8 @@ struct ViewParams {
     int H, W;
     float fx, fy, cx, cy;
     const float *T_cw;
-    float *color, *depth, *alpha;
-    const float *d_color, *d_depth, *d_alpha;
+    float *color, *depth, *alpha, *median_depth;
+    const float *d_color, *d_depth, *d_alpha, *d_median_depth;
     float *d_pose;
     int tiles_x, tiles_y;
     uint32_t tile_offset;   // first global tile id of this view
@@ -95,6 +95,7 @@ struct Ws {
     uint2 *ranges;           // [total_tiles]
     float *T_final;          // [total_pixels]
     uint32_t *last;          // [total_pixels] last contributor index + 1
+    uint32_t *median;        // [total_pixels] median-depth contributor index + 1 (0: none)
     float *vg_grads;         // [N][V][10] screen-space gradients of each (Gaussian, view)
     float *pose_partials;    // [V][pose_blocks][6]
     uint32_t N, V, VN;

@@ -66,9 +66,10 @@ def pixel_offsets(cams: Sequence[Intrinsics]) -> List[int]:
     return off
 
 
-def view_structs(cams, viewmats: torch.Tensor, color=None, depth=None, alpha=None) -> List[_b.View]:
-    """C view structs; color/depth/alpha are flat buffers of all views
-    (colour [3*P_v] per view, laid out view after view)."""
+def view_structs(cams, viewmats: torch.Tensor, color=None, depth=None, alpha=None,
+                 median_depth=None) -> List[_b.View]:
+    """C view structs; color/depth/alpha/median_depth are flat buffers of all
+    views (colour [3*P_v] per view, laid out view after view)."""
     if viewmats.dtype != torch.float32 or not viewmats.is_cuda or not viewmats.is_contiguous() or \
             tuple(viewmats.shape) != (len(cams), 3, 4):
         raise ValueError("viewmats must be a contiguous float32 CUDA tensor [V, 3, 4]")
@@ -80,7 +81,8 @@ def view_structs(cams, viewmats: torch.Tensor, color=None, depth=None, alpha=Non
             int(c.H), int(c.W), float(c.fx), float(c.fy), float(c.cx), float(c.cy), base + 48 * v,
             0 if color is None else color.data_ptr() + 4 * 3 * off[v],
             0 if depth is None else depth.data_ptr() + 4 * off[v],
-            0 if alpha is None else alpha.data_ptr() + 4 * off[v]))
+            0 if alpha is None else alpha.data_ptr() + 4 * off[v],
+            0 if median_depth is None else median_depth.data_ptr() + 4 * off[v]))
     return out
 
 
@@ -104,7 +106,7 @@ class GaussianRasterizer:
 
     # ------------------------------------------------------------ workspace
     def workspace_bytes(self, N: int, cams, key_capacity: int = 0) -> int:
-        dummy = [_b.View(c.H, c.W, c.fx, c.fy, c.cx, c.cy, 1, 1, 0, 0) for c in cams]
+        dummy = [_b.View(c.H, c.W, c.fx, c.fy, c.cx, c.cy, 1, 1, 0, 0, 0) for c in cams]
         return self.ctx.workspace_size(N, dummy, key_capacity)
 
     def alloc_workspace(self, N: int, cams, key_capacity: int = 0, device=None) -> torch.Tensor:
@@ -116,14 +118,16 @@ class GaussianRasterizer:
 
     # ------------------------------------------------------------ raw calls
     def forward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
-                    color: torch.Tensor, depth: Optional[torch.Tensor], alpha: Optional[torch.Tensor]):
+                    color: torch.Tensor, depth: Optional[torch.Tensor], alpha: Optional[torch.Tensor],
+                    median_depth: Optional[torch.Tensor] = None):
         g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
-        views = view_structs(cams, viewmats, color, depth, alpha)
+        views = view_structs(cams, viewmats, color, depth, alpha, median_depth)
         st = self.ctx.render(g, views, ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
         self.ctx.check(st, "gsr_render")
 
     def backward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
-                     d_color, d_depth, d_alpha, grads: dict, d_pose: Optional[torch.Tensor], accumulate=False):
+                     d_color, d_depth, d_alpha, grads: dict, d_pose: Optional[torch.Tensor], accumulate=False,
+                     d_median_depth: Optional[torch.Tensor] = None):
         g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
         views = view_structs(cams, viewmats)
         off = pixel_offsets(cams)
@@ -133,6 +137,7 @@ class GaussianRasterizer:
                 0 if d_color is None else d_color.data_ptr() + 4 * 3 * off[v],
                 0 if d_depth is None else d_depth.data_ptr() + 4 * off[v],
                 0 if d_alpha is None else d_alpha.data_ptr() + 4 * off[v],
+                0 if d_median_depth is None else d_median_depth.data_ptr() + 4 * off[v],
                 0 if d_pose is None else d_pose.data_ptr() + 4 * 6 * v))
         out = _b.Grads(*[grads[k].data_ptr() for k in PARAM_NAMES], int(accumulate))
         st = self.ctx.render_backward(g, views, vg, out, ws.data_ptr(), ws.numel(),

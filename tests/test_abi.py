@@ -32,7 +32,7 @@ def test_struct_layouts_match_binding(lib):
     for i, s in enumerate(B.ABI_STRUCTS):
         assert lib.gsr_abi_sizeof(i) == ctypes.sizeof(s), s.__name__
     assert lib.gsr_abi_sizeof(99) == 0
-    assert lib.gsr_abi_version() == 1
+    assert lib.gsr_abi_version() == B.ABI_VERSION
 
 
 def test_status_strings(lib):

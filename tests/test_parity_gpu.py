@@ -325,3 +325,64 @@ def test_many_views_and_tiny_images():
     g = U.gpu_backward(sc, state, gC, gD, gA)
     _, rg = oracle.render_backward(sc, gC, gD, gA)
     U.compare_grads(rg, g, label="64 views")
+
+
+# ------------------------------------------------------------------ median depth
+
+def _gpu_median(sc, tile=16):
+    rast = R.GaussianRasterizer(tile)
+    params, cams, vm = U.to_device(sc)
+    _, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+    P = R.pixel_offsets(cams)[-1]
+    color = torch.empty(3 * P, device="cuda")
+    depth, alpha, med = (torch.empty(P, device="cuda") for _ in range(3))
+    rast.forward_raw(params, sc.sh_degree, cams, vm, ws, color, depth, alpha, med)
+    torch.cuda.synchronize()
+    return rast, params, cams, vm, ws, color, depth, alpha, med
+
+
+@pytest.mark.parametrize("name", ["window", "uneven", "small"])
+def test_median_depth_forward_and_backward(name):
+    sc = REDUCED[name]()
+    rast, params, cams, vm, ws, color, depth, alpha, med = _gpu_median(sc)
+    # rendering the median changes nothing else
+    base, _ = U.gpu_forward(sc)
+    for v, (b, c, d) in enumerate(zip(base, R.split_views(color, cams, 3), R.split_views(depth, cams))):
+        assert np.array_equal(b["color"], c.cpu().numpy().astype(np.float64)), v
+        assert np.array_equal(b["depth"], d.cpu().numpy().astype(np.float64)), v
+    ref = oracle.render(sc)
+    flips = total = 0
+    for v, (r, m) in enumerate(zip(ref, R.split_views(med, cams))):
+        got = m.cpu().numpy().astype(np.float64)
+        err = np.abs(got - r["median_depth"]) / np.maximum(np.abs(r["median_depth"]), 1e-3)
+        flip = (r["median_margin"] < U.MARGIN) | (r["margin"] < U.MARGIN)
+        bad = err > U.DEPTH_TOL
+        assert not (bad & ~flip).any(), f"view {v}: {int((bad & ~flip).sum())} median pixels off"
+        flips += int((bad & flip).sum())
+        total += bad.size
+    assert flips <= U.FLIP_SHARE * total
+    # backward: dL/d median depth (with the other upstream gradients)
+    gC, gD, gA = U.upstream(sc)
+    rng = np.random.default_rng(9)
+    gM = [rng.uniform(-1, 1, (c.H, c.W)) for c in sc.cameras]
+    flat = lambda arrs: torch.from_numpy(np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in arrs])).cuda()
+    grads = {k: torch.empty_like(x) for k, x in params.items()}
+    d_pose = torch.empty(len(cams), 6, device="cuda")
+    rast.backward_raw(params, sc.sh_degree, cams, vm, ws, flat(gC), flat(gD), flat(gA), grads, d_pose,
+                      d_median_depth=flat(gM))
+    torch.cuda.synchronize()
+    got = {k: x.cpu().numpy().astype(np.float64) for k, x in grads.items()}
+    got["pose"] = d_pose.cpu().numpy().astype(np.float64)
+    _, rg = oracle.render_backward(sc, gC, gD, gA, gM=gM)
+    U.compare_grads(rg, got, label=f"{name} median")
+
+
+def test_median_gradient_needs_a_median_forward():
+    sc = REDUCED["small"]()
+    got, state = U.gpu_forward(sc)   # forward without median depth
+    rast, params, cams, vm, ws, color, depth, alpha = state
+    P = R.pixel_offsets(cams)[-1]
+    grads = {k: torch.empty_like(x) for k, x in params.items()}
+    with pytest.raises(B.GsrError, match="median"):
+        rast.backward_raw(params, sc.sh_degree, cams, vm, ws, None, None, None, grads, None,
+                          d_median_depth=torch.zeros(P, device="cuda"))
