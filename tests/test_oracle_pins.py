@@ -466,3 +466,59 @@ def test_median_depth_gradient_matches_central_fd():
     # nothing else moves the median: the other parameters get no gradient
     for k in ("log_scales", "quats", "opacity_logits", "sh"):
         assert not g[k].any(), k
+
+
+# ---------------------------------------------------------------- densification statistics
+
+def test_densify_stats_single_gaussian_closed_form():
+    """One isotropic Gaussian on the axis: visible in the view, radius
+    3 sqrt((f s/z)^2 + 0.3), and |dL/du| of L = sum_p w_p C_r(p) from the
+    closed-form footprint: dC_r/du = c alpha (x - u)/var."""
+    c = cam(40, 48, 80.0)
+    z, s, logit = 3.0, 0.06, 0.8
+    rgb = np.array([0.7, 0.2, 0.4])
+    sc = make_scene([[0.0], [0.0], [z]], np.full((3, 1), np.log(s)), [[1.0], [0.0], [0.0], [0.0]],
+                    [logit], dc_for_rgb(rgb)[:, None], 0, [c])
+    rng = np.random.default_rng(2)
+    wr = rng.uniform(-1, 1, (c.H, c.W))
+    gC = np.stack([wr, np.zeros_like(wr), np.zeros_like(wr)])
+    zero = np.zeros((c.H, c.W))
+    _, g = oracle.render_backward(sc, [gC], [zero], [zero], want_screen=True)
+    st = oracle.densify_stats(sc, g["screen"])
+    var = (80.0 * s / z) ** 2 + 0.3
+    yy, xx = np.mgrid[0:c.H, 0:c.W]
+    r2 = (xx - 24.0) ** 2 + (yy - 20.0) ** 2
+    a = _iso_alpha(1 / (1 + np.exp(-logit)), 80.0, s, z, r2)
+    dudx = (wr * rgb[0] * a * (xx - 24.0) / var).sum()
+    dvdy = (wr * rgb[0] * a * (yy - 20.0) / var).sum()
+    assert st["count"][0] == 1
+    assert st["radius"][0] == pytest.approx(3 * np.sqrt(var), rel=1e-12)
+    assert st["grad"][0] == pytest.approx(np.hypot(dudx, dvdy), rel=1e-10)
+
+
+def test_densify_stats_visibility_and_sums_over_views():
+    """Visible views are counted once each, the gradient norms add up, the
+    radius is the largest; a Gaussian behind every camera has no statistics."""
+    rng = np.random.default_rng(8)
+    sc = _random_scene(rng, 10, 18, 22, 22.0, 0)
+    c0 = sc.cameras[0]
+    far = scenes.Camera(c0.H, c0.W, c0.fx, c0.fy, c0.cx, c0.cy,
+                        np.hstack([np.eye(3), [[0.0], [0.0], [0.7]]]))
+    sc = sc.with_cameras([c0, far])
+    gC, gD, gA = (rng.uniform(-1, 1, (3, c0.H, c0.W)), rng.uniform(-1, 1, (c0.H, c0.W)),
+                  rng.uniform(-1, 1, (c0.H, c0.W)))
+    _, g = oracle.render_backward(sc, [gC, gC], [gD, gD], [gA, gA], want_screen=True)
+    st = oracle.densify_stats(sc, g["screen"])
+    per = [oracle.densify_stats(sc.with_cameras([cc]), g["screen"][v:v + 1]) for v, cc in enumerate(sc.cameras)]
+    np.testing.assert_allclose(st["grad"], per[0]["grad"] + per[1]["grad"], rtol=1e-12)
+    np.testing.assert_array_equal(st["count"], per[0]["count"] + per[1]["count"])
+    np.testing.assert_allclose(st["radius"], np.maximum(per[0]["radius"], per[1]["radius"]), rtol=1e-12)
+    # a Gaussian with a screen gradient is visible in that view
+    for v in range(2):
+        moved = np.hypot(g["screen"][v][0], g["screen"][v][1]) > 0
+        assert (per[v]["count"][moved] == 1).all()
+    # behind the camera: nothing
+    sc2 = make_scene([[0.0], [0.0], [-2.0]], np.full((3, 1), -3.0), [[1.0], [0], [0], [0]], [1.0],
+                     dc_for_rgb([0.5] * 3)[:, None], 0, [c0])
+    st2 = oracle.densify_stats(sc2, np.zeros((1, 10, 1)))
+    assert st2["count"][0] == 0 and st2["grad"][0] == 0 and st2["radius"][0] == 0
