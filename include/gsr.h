@@ -129,6 +129,16 @@ typedef struct {
     float *opacity_logits;
     float *sh;
     int accumulate;
+    /* Densification statistics of the batch (adaptive density control of
+     * 3DGS, used by the paper's mapper), [N] each, all NULL or all set.  A
+     * Gaussian is visible in a view when it is not culled and its cutoff
+     * ellipse (d^2 <= min(9, 2 ln(255 sigma))) contains a pixel centre
+     * (decided with the tile coverage's conservative inflation of at most
+     * 0.2 % + 0.02 in d^2).  With accumulate != 0, grad and count add and
+     * radius takes the maximum, so the arrays can gather several batches. */
+    float *densify_grad;      /* sum over visible views of |(dL/du, dL/dv)|, pixels */
+    float *densify_count;     /* number of visible views */
+    float *densify_radius;    /* max over visible views of 3 sqrt(lambda_max(Sigma')), pixels */
 } gsr_grads;
 
 /* Device-side state of the last call on a workspace (gsr_read_info). */

@@ -210,6 +210,25 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
+def _quad_min_over_box(a, b, d, u, v, x0, x1, y0, y1):
+    """min over the box [x0, x1] x [y0, y1] of the convex quadratic
+    q(x, y) = a dx^2 + 2 b dx dy + d dy^2, (dx, dy) = (x - u, y - v): zero
+    when the centre is inside, else the smallest of the four edges' 1-D
+    minima (clamped stationary points)."""
+    if x0 <= u <= x1 and y0 <= v <= y1:
+        return 0.0
+    best = np.inf
+    for x in (x0, x1):          # vertical edges: minimise over y
+        dx = x - u
+        dy = min(max(-b * dx / d, y0 - v), y1 - v)
+        best = min(best, a * dx * dx + 2 * b * dx * dy + d * dy * dy)
+    for y in (y0, y1):          # horizontal edges: minimise over x
+        dy = y - v
+        dx = min(max(-b * dy / a, x0 - u), x1 - u)
+        best = min(best, a * dx * dx + 2 * b * dx * dy + d * dy * dy)
+    return best
+
+
 def densify_stats(scene, screen, cameras=None):
     """Densification statistics of one batch of views (the adaptive density
     control of 3DGS that the paper's mapper uses, Sec. 3.3): per Gaussian,
@@ -217,10 +236,10 @@ def densify_stats(scene, screen, cameras=None):
       count  = number of such views,
       radius = max over them of 3 sqrt(lambda_max(Sigma')) (pixels),
     with "visible" = not culled and its cutoff ellipse, d^2 <= min(9,
-    2 ln(255 sigma)), contains at least one pixel centre of the view.
-    screen: grads["screen"] of render_backward(..., want_screen=True).
-    Also returns margin: per Gaussian the smallest relative distance
-    |d^2/d2max - 1| of the pixel centre that decides a view's visibility."""
+    2 ln(255 sigma)), meets the rectangle [0, W-1] x [0, H-1] spanned by the
+    pixel centres.  screen: grads["screen"] of render_backward(...,
+    want_screen=True).  Also returns margin, per Gaussian the smallest
+    |min d^2 / d2max - 1| of its views' visibility decisions."""
     cams = scene.cameras if cameras is None else cameras
     N = scene.means.shape[1]
     grad, count, radius = np.zeros(N), np.zeros(N), np.zeros(N)
@@ -233,22 +252,14 @@ def densify_stats(scene, screen, cameras=None):
             d2max = min(9.0, 2.0 * np.log(255.0 * P["opacity"][g]))
             if not d2max >= 0:
                 continue
-            c0, c1, c2 = P["cov0"][g], P["cov1"][g], P["cov2"][g]
-            a, b, d = P["conic0"][g], P["conic1"][g], P["conic2"][g]
-            ex, ey = np.sqrt(1.01 * d2max * c0) + 1, np.sqrt(1.01 * d2max * c2) + 1
-            x0, x1 = max(0, int(np.ceil(P["u"][g] - ex))), min(c.W - 1, int(np.floor(P["u"][g] + ex)))
-            y0, y1 = max(0, int(np.ceil(P["v"][g] - ey))), min(c.H - 1, int(np.floor(P["v"][g] + ey)))
-            if x0 > x1 or y0 > y1:
-                continue
-            ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-            dx, dy = xs - P["u"][g], ys - P["v"][g]
-            q = a * dx * dx + 2 * b * dx * dy + d * dy * dy
-            qmin = q.min()
+            qmin = _quad_min_over_box(P["conic0"][g], P["conic1"][g], P["conic2"][g], P["u"][g], P["v"][g],
+                                      0.0, c.W - 1.0, 0.0, c.H - 1.0)
             margin[g] = min(margin[g], abs(qmin / max(d2max, 1e-300) - 1))
             if qmin > d2max:
                 continue
             grad[g] += np.hypot(screen[v][0][g], screen[v][1][g])
             count[g] += 1
+            c0, c1, c2 = P["cov0"][g], P["cov1"][g], P["cov2"][g]
             mid = 0.5 * (c0 + c2)
             lam = mid + np.sqrt(max(mid * mid - (c0 * c2 - c1 * c1), 0.0))
             radius[g] = max(radius[g], 3.0 * np.sqrt(lam))

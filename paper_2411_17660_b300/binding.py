@@ -50,7 +50,7 @@ class ViewGrad(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [("means", _p), ("log_scales", _p), ("quats", _p), ("opacity_logits", _p), ("sh", _p),
-                ("accumulate", ctypes.c_int)]
+                ("accumulate", ctypes.c_int), ("densify_grad", _p), ("densify_count", _p), ("densify_radius", _p)]
 
 
 class Info(ctypes.Structure):

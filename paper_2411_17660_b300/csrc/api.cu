@@ -39,7 +39,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3;
+    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, radius;
     size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
     size_t total;
     uint64_t VN;
@@ -78,6 +78,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.rec1 = take(16 * L.VN);
     L.rec2 = take(16 * L.VN);
     L.rec3 = take(16 * L.VN);
+    L.radius = take(4 * L.VN);
     L.hist = take(4ull * kMaxPasses * kRadix);
     L.ranges = take(8ull * L.total_tiles);
     L.T_final = take(4ull * L.total_pixels);
@@ -123,6 +124,7 @@ Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) 
     w.rec1 = reinterpret_cast<float4 *>(b + L.rec1);
     w.rec2 = reinterpret_cast<float4 *>(b + L.rec2);
     w.rec3 = reinterpret_cast<float4 *>(b + L.rec3);
+    w.radius = reinterpret_cast<float *>(b + L.radius);
     w.keys[0] = reinterpret_cast<unsigned long long *>(b + L.keys0);
     w.keys[1] = reinterpret_cast<unsigned long long *>(b + L.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(b + L.vals0);
@@ -385,6 +387,8 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     if (!grads) return fail(ctx, GSR_EINVAL, "grads is NULL");
     if (!out || (gs->N > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh)))
         return fail(ctx, GSR_EINVAL, "an output gradient pointer is NULL");
+    if (!out->densify_grad != !out->densify_count || !out->densify_grad != !out->densify_radius)
+        return fail(ctx, GSR_EINVAL, "densify_grad, densify_count and densify_radius must be all NULL or all set");
     const gsr_ctx::Rec *rec = nullptr;
     for (const auto &r : ctx->recs)
         if (r.ws == ws_ptr) rec = &r;
@@ -409,6 +413,9 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     gout.opacity_logits = out->opacity_logits;
     gout.sh = out->sh;
     gout.accumulate = out->accumulate;
+    gout.densify_grad = out->densify_grad;
+    gout.densify_count = out->densify_count;
+    gout.densify_radius = out->densify_radius;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     ctx->mark(6, st);

@@ -88,6 +88,7 @@ struct Ws {
     float4 *rec1;            // [V*N] (m00, m01, m11, s_max)
     float4 *rec2;            // [V*N] (r, g, b, z)
     float4 *rec3;            // [V*N] (log2 opacity, Sxx, Sxy, Syy)
+    float *radius;           // [V*N] 3 sqrt(lambda_max(Sigma')) if the pair is visible for densification, else 0
     unsigned long long *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;          // [kMaxPasses][256]

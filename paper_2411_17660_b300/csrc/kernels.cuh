@@ -8,6 +8,7 @@ namespace gsr {
 struct GradPtrs {
     float *means, *log_scales, *quats, *opacity_logits, *sh;
     int accumulate;
+    float *densify_grad, *densify_count, *densify_radius;   // all NULL or all set
 };
 
 // preprocess.cu

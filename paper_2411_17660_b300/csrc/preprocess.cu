@@ -135,12 +135,26 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
             Proj p;
             if (real) {
                 const ViewParams &vp = vt.v[v];
+                float rad = 0.f;
                 if (G.alive && project_view(G, s_pose[v], vp, p)) {
                     project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
                     project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
                     vis = isfinite(uh) && isfinite(vh);
+                    // densification visibility: the cutoff ellipse meets the
+                    // rectangle of pixel centres
+                    if (vis) {
+                        const float u = uh + ul, w = vh + vl;
+                        const float smin = quad_min_over_box(-u, (float)(vp.W - 1) - u, -w, (float)(vp.H - 1) - w,
+                                                             kSqrtHalfLog2e * p.l00, kSqrtHalfLog2e * p.l01,
+                                                             kSqrtHalfLog2e * p.l11);
+                        if (smin <= G.smax) {
+                            const float mid = 0.5f * (p.sxx + p.syy);
+                            rad = 3.f * sqrtf(mid + sqrtf(fmaxf(mid * mid - p.det, 0.f)));
+                        }
+                    }
                 }
                 if (!vis) ws.counts[(size_t)v * N + g] = 0u;
+                ws.radius[(size_t)v * N + g] = rad;
             }
             const unsigned ball = __ballot_sync(0xffffffffu, vis);
             if (vis) {
@@ -204,7 +218,8 @@ template <int DEG>
 struct BwdAcc {
     static constexpr int K = (DEG + 1) * (DEG + 1);
     static constexpr int NV = 13 + 3 * K;   // dmu (3), dM (9), d ln(sigma) (1), dSH (3K)
-    static constexpr int NVP = NV | 1;      // odd row stride of the per-pair partials in shared memory
+    static constexpr int NS = NV + 1;       // + densification: |(dL/du, dL/dv)|
+    static constexpr int NVP = NS | 1;      // odd row stride of the per-pair partials in shared memory
     // shared-memory floats of the partials and of the run totals (one view
     // needs neither: each pair is finished by its own thread)
     __host__ __device__ static constexpr int parts(int VW) { return VW == 1 ? 0 : NVP * kPreThreads; }
@@ -212,7 +227,8 @@ struct BwdAcc {
 };
 
 // Backward of one visible (view, Gaussian) pair; writes its NV partials to
-// part[k] and its pose twist to pose[c * kPreThreads].
+// part[k], its screen-gradient norm |(dL/du, dL/dv)| (densification) to
+// part[NV], and its pose twist to pose[c * kPreThreads].
 template <int DEG>
 __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &ws, const ViewParams &vp,
                                               const Pose &ps, int v, int g, float *part, float *pose) {
@@ -229,7 +245,7 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     float dlno = 0.f;
     if (!project_view(G, ps, vp, p)) {   // same decision as the forward; kept for safety
 #pragma unroll
-        for (int k = 0; k < BwdAcc<DEG>::NV; ++k) part[k] = 0.f;
+        for (int k = 0; k < BwdAcc<DEG>::NS; ++k) part[k] = 0.f;
 #pragma unroll
         for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = 0.f;
         return;
@@ -361,6 +377,7 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
 #pragma unroll
     for (int k = 0; k < 9; ++k) part[3 + k] = dM[k];
     part[12] = dlno;
+    part[BwdAcc<DEG>::NV] = sqrtf(du * du + dvv * dvv);   // densification
 #pragma unroll
     for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = pose6[c];
 }
@@ -378,10 +395,19 @@ struct BwdShape {
 template <int DEG, int VW>
 static size_t bwd_smem_bytes() {
     using S = BwdShape<VW>;
-    constexpr size_t NV = BwdAcc<DEG>::NV;
+    constexpr size_t NS = BwdAcc<DEG>::NS;
     return sizeof(unsigned long long) * S::GBT +
-           sizeof(float) * (BwdAcc<DEG>::parts(VW) + 6 * kPreThreads + BwdAcc<DEG>::tots(VW) + 2 * NV + 6 * VW) +
-           sizeof(int) * (S::LC + 2 * S::GBT);
+           sizeof(float) * (BwdAcc<DEG>::parts(VW) + 6 * kPreThreads + BwdAcc<DEG>::tots(VW) + 2 * NS + 6 * VW) +
+           sizeof(int) * (S::LC + 5 * S::GBT);
+}
+
+// Densification statistics of Gaussian g: overwritten, or gathered with
+// the earlier ones when accumulating (sums for grad and count, max radius).
+__device__ __forceinline__ void densify_write(const GradPtrs &out, int g, float grad, float count, float radius) {
+    const bool ac = out.accumulate != 0;
+    out.densify_grad[g] = ac ? out.densify_grad[g] + grad : grad;
+    out.densify_count[g] = ac ? out.densify_count[g] + count : count;
+    out.densify_radius[g] = ac ? fmaxf(out.densify_radius[g], radius) : radius;
 }
 
 // Parameter gradients of Gaussian g from its view-summed partials (acc:
@@ -441,18 +467,21 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
                                                                         const GaussianPtrs gp, const Ws ws,
                                                                         const GradPtrs out) {
     using S = BwdShape<VW>;
-    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV, NVP = BwdAcc<DEG>::NVP;
+    constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV, NS = BwdAcc<DEG>::NS, NVP = BwdAcc<DEG>::NVP;
     constexpr int GB = S::GB, GBT = S::GBT, WARPS = kPreThreads / 32;
     extern __shared__ __align__(16) unsigned long long smem_u64[];
     unsigned long long *s_mask = smem_u64;             // [GBT] visible views of each Gaussian
     float *s_part = reinterpret_cast<float *>(s_mask + GBT);   // [256][NVP] per-pair partials of a chunk
     float *s_pose = s_part + BwdAcc<DEG>::parts(VW);   // [6][256] per-pair pose twists
     float *s_tot = s_pose + 6 * kPreThreads;           // [256][13] totals of the runs that end in a chunk
-    float *s_carry = s_tot + BwdAcc<DEG>::tots(VW);    // [2][NV] partial sums of a run cut by a chunk's end
-    float *s_vpose = s_carry + 2 * NV;                 // [VW][6] pose partials per view
+    float *s_carry = s_tot + BwdAcc<DEG>::tots(VW);    // [2][NS] partial sums of a run cut by a chunk's end
+    float *s_vpose = s_carry + 2 * NS;                 // [VW][6] pose partials per view
     int *s_item = reinterpret_cast<int *>(s_vpose + 6 * VW);   // [LC] (Gaussian << 8 | view) per list position
     int *s_first = s_item + S::LC;                     // [GBT] list position of each Gaussian's run
     int *s_cnt = s_first + GBT;                        // [GBT] its length
+    float *s_dgrad = reinterpret_cast<float *>(s_cnt + GBT);   // [GBT] densification: summed gradient norms
+    int *s_dcount = reinterpret_cast<int *>(s_dgrad + GBT);    // [GBT] visible views
+    int *s_drad = s_dcount + GBT;                      // [GBT] max screen radius (bits of a float >= 0)
     __shared__ int s_wcnt[WARPS];
     __shared__ unsigned s_wbal[WARPS];
     __shared__ int s_end[kPreThreads];                 // chunk positions where a run ends
@@ -461,8 +490,14 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gbase = blockIdx.x * GBT;
     const size_t N = (size_t)gp.N;
-    const bool ac = out.accumulate != 0;
+    const bool ac = out.accumulate != 0, dens = out.densify_grad != nullptr;
     for (int k = tid; k < 6 * VW; k += kPreThreads) s_vpose[k] = 0.f;
+    for (int k = tid; k < GBT; k += kPreThreads) {
+        s_dgrad[k] = 0.f;
+        s_dcount[k] = 0;
+        s_drad[k] = 0;
+    }
+    __syncthreads();
 
     // The list of visible pairs, Gaussian-major: candidate t of round r is
     // view t % VW of Gaussian r GB + t / VW.  A Gaussian's candidates are VW
@@ -485,6 +520,13 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
             nvis += c;
         }
         if (vis) s_item[M + before + __popc(bal & lanemask_lt())] = (gl << 8) | v;
+        if (dens && v < vt.V && g < gp.N) {   // densification visibility, from the forward
+            const float rad = ws.radius[(size_t)v * N + g];
+            if (rad > 0.f) {
+                atomicAdd(&s_dcount[gl], 1);
+                atomicMax(&s_drad[gl], __float_as_int(rad));
+            }
+        }
         if constexpr (VW <= 32) {
             const int lead = lane & ~(VW - 1);
             if (lane == lead) {
@@ -506,19 +548,20 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
         const int n = min(kPreThreads, M - c0);
         // carries alternate between two buffers: one chunk reads the previous
         // chunk's while it writes its own
-        const float *carry_in = s_carry + ((chunk + 1) & 1) * NV;
-        float *carry_out = s_carry + (chunk & 1) * NV;
+        const float *carry_in = s_carry + ((chunk + 1) & 1) * NS;
+        float *carry_out = s_carry + (chunk & 1) * NS;
         if constexpr (VW == 1) {
             // one view: every run is one pair, finished by its own thread
             if (tid < n) {
                 const int gl = s_item[c0 + tid] >> 8, g = gbase + gl;
-                float part[NV];
+                float part[NS];
                 pair_backward<DEG>(gp, ws, vt.v[0], s_poses[0], 0, g, part, s_pose + tid);
                 for (int k = 13; k < NV; ++k) {
                     float *o = out.sh + (size_t)(k - 13) * N + g;
                     *o = ac ? *o + part[k] : part[k];
                 }
                 bwd_finish(gp, out, g, part);
+                s_dgrad[gl] = part[NV];
             }
             __syncthreads();
             if (warp == 0) {   // the view's pose partial, lanes striding the chunk, then a butterfly
@@ -562,8 +605,9 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
         // run sums over this chunk, plus the carry of a run begun earlier: an
         // item is (run, component), components fastest, so that a warp reads
         // consecutive words of a partials row
-        for (int idx = tid; idx < NV * nruns; idx += kPreThreads) {
-            const int j = idx / NV, k = idx - j * NV;
+        const int nk = dens ? NS : NV;   // components summed per run
+        for (int idx = tid; idx < nk * nruns; idx += kPreThreads) {
+            const int j = idx / nk, k = idx - j * nk;
             const int p = s_end[j], gl = s_item[c0 + p] >> 8;
             const int first = s_first[gl];
             float x = first < c0 ? carry_in[k] : 0.f;
@@ -572,6 +616,8 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
                 carry_out[k] = x;   // continues in the next chunk
             } else if (k < 13) {
                 s_tot[j * 13 + k] = x;
+            } else if (k == NV) {
+                s_dgrad[gl] = x;
             } else {
                 float *o = out.sh + (size_t)(k - 13) * N + gbase + gl;
                 *o = ac ? *o + x : x;
@@ -646,6 +692,10 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
         const int v = i / 6, c = i - v * 6;
         ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + c] = s_vpose[v * 6 + c];
     }
+    if (dens)
+        for (int gl = tid; gl < GBT; gl += kPreThreads)
+            if (gbase + gl < gp.N)
+                densify_write(out, gbase + gl, s_dgrad[gl], (float)s_dcount[gl], __int_as_float(s_drad[gl]));
 }
 
 // Sum of the per-block pose partials of each view, in a fixed order.

@@ -127,4 +127,27 @@ __device__ __forceinline__ bool project_view(const GaussPre &G, const Pose &ps, 
     return isfinite(p.l00) && isfinite(p.l01);
 }
 
+// Minimum over the box dx in [dx0, dx1], dy in [dy0, dy1] of the quadratic
+// s = (m00 dx + m01 dy)^2 + (m11 dy)^2 (m00, m11 > 0): for fixed dy the first
+// term's minimum over dx is max(0, m00 dx0 + m01 dy, -(m00 dx1 + m01 dy))^2,
+// a convex function of dy whose minimum lies at an end of [dy0, dy1] or at
+// the stationary point of one of its three pieces.
+__device__ __forceinline__ float quad_min_over_box(float dx0, float dx1, float dy0, float dy1, float m00, float m01,
+                                                   float m11) {
+    const float a0 = m00 * dx0, a1 = m00 * dx1;
+    const float inv_den = 1.0f / (m01 * m01 + m11 * m11);
+    auto f = [&](float dy) {
+        const float t = m01 * dy;
+        const float p = fmaxf(0.f, fmaxf(a0 + t, -(a1 + t)));
+        const float q = m11 * dy;
+        return p * p + q * q;
+    };
+    auto cl = [&](float y) { return fminf(fmaxf(y, dy0), dy1); };
+    float smin = fminf(f(dy0), f(dy1));
+    smin = fminf(smin, f(cl(0.f)));
+    smin = fminf(smin, f(cl(-m01 * a0 * inv_den)));
+    smin = fminf(smin, f(cl(-m01 * a1 * inv_den)));
+    return smin;
+}
+
 }  // namespace gsr

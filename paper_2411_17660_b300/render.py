@@ -127,7 +127,10 @@ class GaussianRasterizer:
 
     def backward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
                      d_color, d_depth, d_alpha, grads: dict, d_pose: Optional[torch.Tensor], accumulate=False,
-                     d_median_depth: Optional[torch.Tensor] = None):
+                     d_median_depth: Optional[torch.Tensor] = None, densify: Optional[dict] = None):
+        """densify: optional dict of [N] float32 tensors grad, count, radius that
+        receive the densification statistics of the batch (accumulated like
+        the gradients when accumulate is set)."""
         g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
         views = view_structs(cams, viewmats)
         off = pixel_offsets(cams)
@@ -139,7 +142,8 @@ class GaussianRasterizer:
                 0 if d_alpha is None else d_alpha.data_ptr() + 4 * off[v],
                 0 if d_median_depth is None else d_median_depth.data_ptr() + 4 * off[v],
                 0 if d_pose is None else d_pose.data_ptr() + 4 * 6 * v))
-        out = _b.Grads(*[grads[k].data_ptr() for k in PARAM_NAMES], int(accumulate))
+        dens = [0, 0, 0] if densify is None else [densify[k].data_ptr() for k in ("grad", "count", "radius")]
+        out = _b.Grads(*[grads[k].data_ptr() for k in PARAM_NAMES], int(accumulate), *dens)
         st = self.ctx.render_backward(g, views, vg, out, ws.data_ptr(), ws.numel(),
                                       torch.cuda.current_stream().cuda_stream)
         self.ctx.check(st, "gsr_render_backward")

@@ -84,6 +84,6 @@ def test_argument_errors_return_einval_without_device(lib):
     assert c.render(g0, [_view()], 0x1000, 1 << 30, 0) == B.EINVAL
     assert "NULL" in lib.gsr_last_error(c.h).decode()
     # backward without a forward on that workspace
-    out = B.Grads(0x100, 0x100, 0x100, 0x100, 0x100, 0)
+    out = B.Grads(0x100, 0x100, 0x100, 0x100, 0x100, 0, 0, 0, 0)
     vg = [B.ViewGrad(0, 0, 0, 0)]
     assert c.render_backward(g, [_view()], vg, out, 0x1000, 1 << 30, 0) == B.ENOTREADY

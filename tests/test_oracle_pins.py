@@ -522,3 +522,20 @@ def test_densify_stats_visibility_and_sums_over_views():
                      dc_for_rgb([0.5] * 3)[:, None], 0, [c0])
     st2 = oracle.densify_stats(sc2, np.zeros((1, 10, 1)))
     assert st2["count"][0] == 0 and st2["grad"][0] == 0 and st2["radius"][0] == 0
+
+
+def test_densify_box_visibility_brute_force():
+    """The box minimum of the quadratic equals a dense grid search (to the
+    grid's resolution), inside and outside the box."""
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        A = rng.normal(size=(2, 2))
+        S = A @ A.T + 0.1 * np.eye(2)
+        a, b, d = np.linalg.inv(S)[0, 0], np.linalg.inv(S)[0, 1], np.linalg.inv(S)[1, 1]
+        u, v = rng.uniform(-6, 16, 2)
+        q = oracle._quad_min_over_box(a, b, d, u, v, 0.0, 9.0, 0.0, 7.0)
+        xs, ys = np.meshgrid(np.linspace(0, 9, 901), np.linspace(0, 7, 701))
+        dx, dy = xs - u, ys - v
+        grid = (a * dx * dx + 2 * b * dx * dy + d * dy * dy).min()
+        assert q <= grid + 1e-12
+        assert q == pytest.approx(grid, rel=2e-3, abs=2e-4)

@@ -386,3 +386,37 @@ def test_median_gradient_needs_a_median_forward():
     with pytest.raises(B.GsrError, match="median"):
         rast.backward_raw(params, sc.sh_degree, cams, vm, ws, None, None, None, grads, None,
                           d_median_depth=torch.zeros(P, device="cuda"))
+
+
+# ------------------------------------------------------------------ densification statistics
+
+@pytest.mark.parametrize("name", ["window", "uneven", "room"])
+def test_densify_stats_against_oracle(name):
+    sc = REDUCED[name]()
+    _, state = U.gpu_forward(sc)
+    rast, params, cams, vm, ws, color, depth, alpha = state
+    gC, gD, gA = U.upstream(sc)
+    flat = lambda arrs: torch.from_numpy(np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in arrs])).cuda()
+    N = sc.N
+    grads = {k: torch.empty_like(x) for k, x in params.items()}
+    dens = {k: torch.full((N,), np.nan, device="cuda") for k in ("grad", "count", "radius")}
+    args = (params, sc.sh_degree, cams, vm, ws, flat(gC), flat(gD), flat(gA), grads, None)
+    rast.backward_raw(*args, densify=dens)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in dens.items()}
+    _, rg = oracle.render_backward(sc, gC, gD, gA, want_screen=True)
+    ref = oracle.densify_stats(sc, rg["screen"])
+    sure = ref["margin"] > U.MARGIN * 10
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(got["count"][sure], ref["count"][sure])
+    assert U.rel_l2(got["grad"], ref["grad"]) < U.GRAD_TOL
+    m = sure & (ref["count"] > 0)
+    np.testing.assert_allclose(got["radius"][m], ref["radius"][m], rtol=1e-4)
+    assert not got["radius"][sure & (ref["count"] == 0)].any()
+    # accumulate: grad and count add up, the radius keeps its maximum
+    rast.backward_raw(*args, accumulate=True, densify=dens)
+    torch.cuda.synchronize()
+    acc = {k: v.cpu().numpy().astype(np.float64) for k, v in dens.items()}
+    np.testing.assert_allclose(acc["grad"], 2 * got["grad"], rtol=1e-6, atol=1e-12)
+    np.testing.assert_array_equal(acc["count"], 2 * got["count"])
+    np.testing.assert_array_equal(acc["radius"], got["radius"])
