@@ -216,6 +216,49 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
 gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V, float lambda1,
                          float lambda2, float *loss, gsr_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* 2-D surfels (the "2D Gaussian Splatting" primitives the paper compares
+ * its 3-D Gaussians with, Sec. 3.3 last paragraph, Supp. "2D Gaussian
+ * Splatting"): each Gaussian is a flat disk with tangents t_u, t_v (first
+ * two columns of R(q)) scaled by exp(log_scales[0..1]) (log_scales[2] is
+ * unused and gets zero gradient) and normal t_w.  A pixel meets the disk
+ * where its two homogeneous planes h_x = M_0 - x M_2, h_y = M_1 - y M_2 cross
+ * (M = K [s_u W t_u | s_v W t_v | W mu + t]): (u, v, 1) ~ h_x x h_y;
+ * rho = min(u^2 + v^2, 2 |pixel - projected centre|^2) (screen-space
+ * low-pass), alpha = min(0.99, sigma exp(-rho/2)) with the 3-D path's cutoff
+ * (rho <= 9), skip (1/255) and stop (1e-4) rules; sorted by the depth of
+ * the centre.  Culled: centre depth <= 0.2 or the cutoff disk reaching
+ * depth 0.2.  Extra outputs: the normal map sum w n (n = W t_w turned
+ * towards the camera, camera frame) and the depth distortion
+ * sum_{i>j} w_i w_j (z_i - z_j)^2 with z the depth of the ray-disk
+ * intersection (the colour/depth/alpha outputs of gsr_view use the same
+ * weights and z). */
+typedef struct {
+    float *normal;            /* device out [3][H][W] or NULL */
+    float *distortion;        /* device out [H][W] or NULL */
+} gsr_surfel_out;
+
+typedef struct {
+    const float *d_normal;    /* [3][H][W] or NULL */
+    const float *d_distortion; /* [H][W] or NULL */
+} gsr_surfel_grad;
+
+/* Forward render of surfels, batched like gsr_render; views[v].median_depth
+ * must be NULL; extra[v] holds view v's normal and distortion outputs
+ * (extra may be NULL: neither is written).  Same workspace rules. */
+gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                              const gsr_surfel_out *extra, int V, void *ws, size_t ws_bytes, gsr_stream stream);
+
+/* Backward of the last gsr_render_surfels on ws: grads[v] (d_median_depth
+ * must be NULL) and extra[v] (may be NULL) give the upstream gradients;
+ * parameter and pose gradients as for gsr_render_backward (densification
+ * statistics are not produced for surfels: their pointers must be NULL).
+ * Returns GSR_ENOTREADY unless ws holds a surfel forward of the same
+ * Gaussians and views. */
+gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                                       const gsr_view_grad *grads, const gsr_surfel_grad *extra, int V,
+                                       const gsr_grads *out, void *ws, size_t ws_bytes, gsr_stream stream);
+
 /* Stage events (a profiling aid).  events holds GSR_STAGE_EVENTS cudaEvent_t
  * handles created by the caller (copied at this call), or is NULL to stop.
  * While set, gsr_render records events[0] on its stream before its first
@@ -262,7 +305,7 @@ int gsr_abi_version(void);
 
 /* sizeof of the ABI structs, for binding checks: 0 gsr_config, 1
  * gsr_gaussians, 2 gsr_view, 3 gsr_view_grad, 4 gsr_grads, 5 gsr_info,
- * 6 gsr_l1_view; 0 for other values. */
+ * 6 gsr_l1_view, 7 gsr_surfel_out, 8 gsr_surfel_grad; 0 for other values. */
 size_t gsr_abi_sizeof(int which);
 
 #ifdef __cplusplus

@@ -22,8 +22,14 @@ losses without restating them):
     Gaussians are sorted by the depth p_z of their centre (then index);
   * culled: p_z <= 0.2, or the cutoff disk u^2 + v^2 <= 9 reaching the near
     plane (p_z - 3 sqrt(a_z^2 + b_z^2) <= 0.2), or 255 sigma < 1;
+  * per pixel the oracle also reports a margin: the smallest relative
+    distance of a threshold decision (as for 3-D Gaussians) or 0.1 sin(theta)
+    of a contributor's ray-disk intersection (the 2x2 solve's conditioning);
   * outputs: colour, depth D = sum w z (z = a_z u + b_z v + p_z, the depth
-    of the ray-disk intersection), opacity A = sum w, normal map
+    of the ray-disk intersection, where rho3 <= rho2; the centre's depth p_z
+    where the low-pass term decides alpha, so that a grazing or missed disk
+    never reports the depth of a far or backward intersection), opacity
+    A = sum w, normal map
     N = sum w n (n = W t_w turned to face the camera, camera frame) and the
     depth distortion sum_{i > j} w_i w_j (z_i - z_j)^2.
 """
@@ -133,7 +139,10 @@ def _composite(S, xs, ys):
     rho3 = torch.where(torch.isfinite(rho3), rho3, torch.full_like(rho3, math.inf))
     rho = torch.minimum(rho3, rho2)
     a_raw = sigma[None] * torch.exp(-0.5 * rho)
-    zint = a[None, :, 2] * u + b[None, :, 2] * v + pc[None, :, 2]
+    # depth of the contributor: the ray-disk intersection where the disk term
+    # decides alpha, the centre's depth where the screen-space low-pass does
+    zint = torch.where(rho3 <= rho2, a[None, :, 2] * u + b[None, :, 2] * v + pc[None, :, 2],
+                       pc[None, :, 2].expand_as(rho2))
     with torch.no_grad():
         keep = valid[None] & (rho <= CUTOFF) & (a_raw >= ALPHA_MIN)
         al = torch.where(keep, torch.clamp(a_raw, max=ALPHA_MAX), torch.zeros_like(a_raw))
@@ -144,6 +153,12 @@ def _composite(S, xs, ys):
         m = torch.minimum(torch.where(valid[None], (rho / CUTOFF - 1).abs(), big),
                           torch.where(valid[None] & (rho <= CUTOFF), (a_raw / ALPHA_MIN - 1).abs(), big))
         m = torch.minimum(m, torch.where(keep, ((Tb * (1 - al)) / T_STOP - 1).abs(), big))
+        # conditioning of the ray-disk intersection: FP32 loses about eps / sin(theta) of
+        # (u, v), sin(theta) = |q2| / (|h_x| |h_y|); below 1e-3 the pixel counts as a margin pixel
+        sin_t = q[..., 2].abs() / (hx.norm(dim=-1) * hy.norm(dim=-1))
+        m = torch.minimum(m, torch.where(keep & (rho3 <= rho2), 0.1 * sin_t, big))
+        # the depth switches between the intersection and the centre at rho3 = rho2
+        m = torch.minimum(m, torch.where(keep, (rho3 / rho2 - 1).abs(), big))
         margin = m.min(1).values if m.shape[1] else torch.full_like(xs, math.inf)
     alpha = torch.where(live, torch.clamp(a_raw, max=ALPHA_MAX), torch.zeros_like(a_raw))
     Tb = torch.cumprod(torch.cat([torch.ones_like(alpha[:, :1]), 1 - alpha[:, :-1]], 1), 1)

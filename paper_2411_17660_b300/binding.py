@@ -62,7 +62,15 @@ class L1View(ctypes.Structure):
     _fields_ = [("target_color", _p), ("target_depth", _p), ("d_color", _p), ("d_depth", _p)]
 
 
-ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View]
+class SurfelOut(ctypes.Structure):
+    _fields_ = [("normal", _p), ("distortion", _p)]
+
+
+class SurfelGrad(ctypes.Structure):
+    _fields_ = [("d_normal", _p), ("d_distortion", _p)]
+
+
+ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View, SurfelOut, SurfelGrad]
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -101,6 +109,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_rgbd_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
                                   ctypes.c_float, _p, _p]),
         "gsr_render_noalloc": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, _p, _p]),
+        "gsr_render_surfels": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
+                                       ctypes.POINTER(SurfelOut), c_int, _p, c_size, _p]),
+        "gsr_render_surfels_backward": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
+                                                ctypes.POINTER(ViewGrad), ctypes.POINTER(SurfelGrad), c_int,
+                                                ctypes.POINTER(Grads), _p, c_size, _p]),
         "gsr_last_error": (ctypes.c_char_p, [_p]),
         "gsr_status_string": (ctypes.c_char_p, [c_int]),
         "gsr_abi_version": (c_int, []),
@@ -157,6 +170,19 @@ class Context:
         garr = (ViewGrad * len(vgrads))(*vgrads)
         return self.lib.gsr_render_backward(self.h, ctypes.byref(g), arr, garr, len(views), ctypes.byref(out),
                                             ws_ptr, ws_bytes, stream)
+
+    def render_surfels(self, g: Gaussians, views, extra, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        arr = (View * len(views))(*views)
+        ex = None if extra is None else (SurfelOut * len(extra))(*extra)
+        return self.lib.gsr_render_surfels(self.h, ctypes.byref(g), arr, ex, len(views), ws_ptr, ws_bytes, stream)
+
+    def render_surfels_backward(self, g: Gaussians, views, vgrads, extra, out: Grads, ws_ptr: int, ws_bytes: int,
+                                stream: int) -> int:
+        arr = (View * len(views))(*views)
+        garr = (ViewGrad * len(vgrads))(*vgrads)
+        ex = None if extra is None else (SurfelGrad * len(extra))(*extra)
+        return self.lib.gsr_render_surfels_backward(self.h, ctypes.byref(g), arr, garr, ex, len(views),
+                                                    ctypes.byref(out), ws_ptr, ws_bytes, stream)
 
     def render_noalloc(self, g: Gaussians, views, status_ptr: int, stream: int) -> int:
         """Forward render into the library's static scratch (no allocation);

@@ -23,6 +23,7 @@ struct gsr_ctx {
         int N, V, deg;
         std::vector<int> dims;
         bool median;   // the forward recorded the median-depth contributors
+        bool surfels;  // the forward rendered surfels
     };
     std::vector<Rec> recs;  // recent forwards, for the backward's checks
     // caller-provided stage events (gsr_set_stage_events), 0..9
@@ -39,7 +40,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, radius;
+    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, rec4, rec5, radius, aux;
     size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
     size_t total;
     uint64_t VN;
@@ -78,13 +79,16 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.rec1 = take(16 * L.VN);
     L.rec2 = take(16 * L.VN);
     L.rec3 = take(16 * L.VN);
+    L.rec4 = take(16 * L.VN);
+    L.rec5 = take(16 * L.VN);
     L.radius = take(4 * L.VN);
+    L.aux = take(8ull * L.total_pixels);
     L.hist = take(4ull * kMaxPasses * kRadix);
     L.ranges = take(8ull * L.total_tiles);
     L.T_final = take(4ull * L.total_pixels);
     L.last = take(4ull * L.total_pixels);
     L.median = take(4ull * L.total_pixels);
-    L.vg_grads = take(4ull * kVGGrads * L.VN);
+    L.vg_grads = take(4ull * kVGGradsMax * L.VN);
     L.pose_partials = take(24ull * V * (L.pose_blocks ? L.pose_blocks : 1));
     L.keys0 = take(8 * cap);
     L.keys1 = take(8 * cap);
@@ -125,6 +129,11 @@ Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) 
     w.rec2 = reinterpret_cast<float4 *>(b + L.rec2);
     w.rec3 = reinterpret_cast<float4 *>(b + L.rec3);
     w.radius = reinterpret_cast<float *>(b + L.radius);
+    w.rec4 = reinterpret_cast<float4 *>(b + L.rec4);
+    w.rec5 = reinterpret_cast<float4 *>(b + L.rec5);
+    w.aux = reinterpret_cast<float *>(b + L.aux);
+    w.surfels = 0;
+    w.vg_stride = kVGGrads;
     w.keys[0] = reinterpret_cast<unsigned long long *>(b + L.keys0);
     w.keys[1] = reinterpret_cast<unsigned long long *>(b + L.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(b + L.vals0);
@@ -245,6 +254,8 @@ void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads
         p.depth = w.depth;
         p.alpha = w.alpha;
         p.median_depth = w.median_depth;
+        p.normal = p.distortion = nullptr;
+        p.d_normal = p.d_distortion = nullptr;
         if (grads) {
             p.d_color = grads[v].d_color;
             p.d_depth = grads[v].d_depth;
@@ -261,6 +272,35 @@ void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads
     }
     vt.total_tiles = toff;
     vt.total_pixels = poff;
+}
+
+// The backward checks that its workspace holds a forward of the same
+// Gaussians and views (and of the same kind).
+void remember_forward(gsr_ctx *ctx, const void *ws_ptr, size_t ws_bytes, const gsr_gaussians *gs,
+                      const gsr_view *views, int V, bool median, bool surfels) {
+    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}, median, surfels};
+    for (int v = 0; v < V; ++v) {
+        r.dims.push_back(views[v].H);
+        r.dims.push_back(views[v].W);
+    }
+    for (auto it = ctx->recs.begin(); it != ctx->recs.end(); ++it)
+        if (it->ws == ws_ptr) {
+            ctx->recs.erase(it);
+            break;
+        }
+    ctx->recs.push_back(r);
+    if (ctx->recs.size() > 64) ctx->recs.erase(ctx->recs.begin());
+}
+
+const gsr_ctx::Rec *find_forward(gsr_ctx *ctx, const void *ws_ptr, size_t ws_bytes, const gsr_gaussians *gs,
+                                 const gsr_view *views, int V) {
+    const gsr_ctx::Rec *rec = nullptr;
+    for (const auto &r : ctx->recs)
+        if (r.ws == ws_ptr) rec = &r;
+    bool match = rec && rec->bytes == ws_bytes && rec->N == gs->N && rec->V == V && rec->deg == gs->sh_degree;
+    for (int v = 0; match && v < V; ++v)
+        match = rec->dims[2 * v] == views[v].H && rec->dims[2 * v + 1] == views[v].W;
+    return match ? rec : nullptr;
 }
 
 int sm_count(gsr_ctx *ctx) {
@@ -362,18 +402,7 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
 
-    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}, want_median(views, V)};
-    for (int v = 0; v < V; ++v) {
-        r.dims.push_back(views[v].H);
-        r.dims.push_back(views[v].W);
-    }
-    for (auto it = ctx->recs.begin(); it != ctx->recs.end(); ++it)
-        if (it->ws == ws_ptr) {
-            ctx->recs.erase(it);
-            break;
-        }
-    ctx->recs.push_back(r);
-    if (ctx->recs.size() > 64) ctx->recs.erase(ctx->recs.begin());
+    remember_forward(ctx, ws_ptr, ws_bytes, gs, views, V, want_median(views, V), false);
     return GSR_OK;
 }
 
@@ -389,13 +418,9 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
         return fail(ctx, GSR_EINVAL, "an output gradient pointer is NULL");
     if (!out->densify_grad != !out->densify_count || !out->densify_grad != !out->densify_radius)
         return fail(ctx, GSR_EINVAL, "densify_grad, densify_count and densify_radius must be all NULL or all set");
-    const gsr_ctx::Rec *rec = nullptr;
-    for (const auto &r : ctx->recs)
-        if (r.ws == ws_ptr) rec = &r;
-    bool match = rec && rec->bytes == ws_bytes && rec->N == gs->N && rec->V == V && rec->deg == gs->sh_degree;
-    for (int v = 0; match && v < V; ++v)
-        match = rec->dims[2 * v] == views[v].H && rec->dims[2 * v + 1] == views[v].W;
-    if (!match) return fail(ctx, GSR_ENOTREADY, "no forward with these Gaussians and views on this workspace");
+    const gsr_ctx::Rec *rec = find_forward(ctx, ws_ptr, ws_bytes, gs, views, V);
+    if (!rec || rec->surfels)
+        return fail(ctx, GSR_ENOTREADY, "no forward with these Gaussians and views on this workspace");
     for (int v = 0; v < V; ++v)
         if (grads[v].d_median_depth && !rec->median)
             return fail(ctx, GSR_ENOTREADY, "view %d: a median-depth gradient needs a forward that rendered median depth", v);
@@ -425,6 +450,103 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     if ((e = launch_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
     ctx->mark(8, st);
     if ((e = launch_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess backward");
+    ctx->mark(9, st);
+    return GSR_OK;
+}
+
+gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                              const gsr_surfel_out *extra, int V, void *ws_ptr, size_t ws_bytes, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, true);
+    if (s != GSR_OK) return s;
+    if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
+    if (want_median(views, V)) return fail(ctx, GSR_EINVAL, "surfels render no median depth");
+    if (!ws_ptr || (reinterpret_cast<uintptr_t>(ws_ptr) & 255))
+        return fail(ctx, GSR_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    const uint32_t cap = capacity_for(gs->N, views, V, ctx->tile, ws_bytes);
+    if (cap == 0) return fail(ctx, GSR_EINVAL, "workspace of %zu bytes holds no tile keys", ws_bytes);
+    Layout L;
+    make_layout(gs->N, views, V, ctx->tile, cap, L);
+    ViewTable vt;
+    fill_views(vt, views, nullptr, V, ctx->tile);
+    if (extra)
+        for (int v = 0; v < V; ++v) {
+            vt.v[v].normal = extra[v].normal;
+            vt.v[v].distortion = extra[v].distortion;
+        }
+    Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    w.surfels = 1;
+    w.vg_stride = kVGGradsMax;
+    const GaussianPtrs gp = gaussian_ptrs(gs);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    ctx->mark(0, st);
+    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, L.total_tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
+    if ((e = launch_surfel_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
+    ctx->mark(1, st);
+    if ((e = launch_scan_duplicate(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "scan/duplicate");
+    ctx->mark(2, st);
+    if ((e = launch_sort(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
+    ctx->mark(3, st);
+    if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
+    ctx->mark(4, st);
+    if ((e = launch_surfel_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
+    ctx->mark(5, st);
+    remember_forward(ctx, ws_ptr, ws_bytes, gs, views, V, false, true);
+    return GSR_OK;
+}
+
+gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,
+                                       const gsr_view_grad *grads, const gsr_surfel_grad *extra, int V,
+                                       const gsr_grads *out, void *ws_ptr, size_t ws_bytes, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    gsr_status s = check_views(ctx, views, V, false);
+    if (s != GSR_OK) return s;
+    if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
+    if (!grads) return fail(ctx, GSR_EINVAL, "grads is NULL");
+    if (!out || (gs->N > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh)))
+        return fail(ctx, GSR_EINVAL, "an output gradient pointer is NULL");
+    if (out->densify_grad || out->densify_count || out->densify_radius)
+        return fail(ctx, GSR_EINVAL, "surfels produce no densification statistics");
+    for (int v = 0; v < V; ++v)
+        if (grads[v].d_median_depth) return fail(ctx, GSR_EINVAL, "surfels render no median depth");
+    const gsr_ctx::Rec *rec = find_forward(ctx, ws_ptr, ws_bytes, gs, views, V);
+    if (!rec || !rec->surfels)
+        return fail(ctx, GSR_ENOTREADY, "no surfel forward with these Gaussians and views on this workspace");
+    const uint32_t cap = capacity_for(gs->N, views, V, ctx->tile, ws_bytes);
+    Layout L;
+    make_layout(gs->N, views, V, ctx->tile, cap, L);
+    ViewTable vt;
+    fill_views(vt, views, grads, V, ctx->tile);
+    if (extra)
+        for (int v = 0; v < V; ++v) {
+            vt.v[v].d_normal = extra[v].d_normal;
+            vt.v[v].d_distortion = extra[v].d_distortion;
+        }
+    Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    w.surfels = 1;
+    w.vg_stride = kVGGradsMax;
+    const GaussianPtrs gp = gaussian_ptrs(gs);
+    GradPtrs gout;
+    gout.means = out->means;
+    gout.log_scales = out->log_scales;
+    gout.quats = out->quats;
+    gout.opacity_logits = out->opacity_logits;
+    gout.sh = out->sh;
+    gout.accumulate = out->accumulate;
+    gout.densify_grad = gout.densify_count = gout.densify_radius = nullptr;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    ctx->mark(6, st);
+    cudaError_t e = cudaMemsetAsync(w.vg_grads, 0, sizeof(float) * kVGGradsMax * L.VN, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear");
+    ctx->mark(7, st);
+    if ((e = launch_surfel_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
+    ctx->mark(8, st);
+    if ((e = launch_surfel_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "preprocess backward");
     ctx->mark(9, st);
     return GSR_OK;
 }
@@ -512,6 +634,8 @@ size_t gsr_abi_sizeof(int which) {
         case 4: return sizeof(gsr_grads);
         case 5: return sizeof(gsr_info);
         case 6: return sizeof(gsr_l1_view);
+        case 7: return sizeof(gsr_surfel_out);
+        case 8: return sizeof(gsr_surfel_grad);
     }
     return 0;
 }

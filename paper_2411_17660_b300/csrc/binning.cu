@@ -148,6 +148,23 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     uint32_t *vals = ws.vals[0];
     const uint32_t cap = ws.cap;
     uint32_t k = off_k;
+    if (ws.surfels) {   // surfels: every tile of the pixel bounds
+        const float4 r = ws.rec5[i];
+        const int TS = vt.tile;
+        const int px0 = (int)fmaxf(ceilf(r.x), 0.f), px1 = (int)fminf(floorf(r.z), (float)(vp.W - 1));
+        const int py0 = (int)fmaxf(ceilf(r.y), 0.f), py1 = (int)fminf(floorf(r.w), (float)(vp.H - 1));
+        uint32_t emitted = 0;
+        for (int ty = py0 / TS; ty <= py1 / TS; ++ty) {
+            const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
+            for (int tx = px0 / TS; tx <= px1 / TS; ++tx, ++k, ++emitted)
+                if (k < cap) {
+                    keys[k] = ((unsigned long long)(row + tx) << 32) | zbits;
+                    vals[k] = g;
+                }
+        }
+        if (emitted != cnt) set_status(ws.hdr, GSR_EINTERNAL);
+        return;
+    }
     const uint32_t emitted = visit_tile_spans(r0.x, r0.y, r3.y, r3.z, r3.w, r1.x, r1.w, vp.W, vp.H, vt.tile,
                                               [&](int ty, int tx0, int tx1) {
                                                   const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;

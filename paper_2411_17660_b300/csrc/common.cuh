@@ -34,6 +34,7 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kVGGradsMax = 16;   // surfels: a, b (6), p_z, u_c, v_c, ln sigma, rgb, normal
 constexpr int kVGGrads = 10;      // per (view, Gaussian) screen-space grads
 constexpr uint32_t kDefaultSpin = 1u << 24;
 
@@ -44,6 +45,8 @@ struct ViewParams {
     const float *T_cw;
     float *color, *depth, *alpha, *median_depth;
     const float *d_color, *d_depth, *d_alpha, *d_median_depth;
+    float *normal, *distortion;               // surfels only
+    const float *d_normal, *d_distortion;     // surfels only
     float *d_pose;
     int tiles_x, tiles_y;
     uint32_t tile_offset;   // first global tile id of this view
@@ -89,6 +92,11 @@ struct Ws {
     float4 *rec2;            // [V*N] (r, g, b, z)
     float4 *rec3;            // [V*N] (log2 opacity, Sxx, Sxy, Syy)
     float *radius;           // [V*N] 3 sqrt(lambda_max(Sigma')) if the pair is visible for densification, else 0
+    float4 *rec4;            // [V*N] surfels: (n_x, n_y, n_z, 0) normal towards the camera
+    float4 *rec5;            // [V*N] surfels: (x_lo, y_lo, x_hi, y_hi) pixel bounds of the cutoff region
+    float *aux;              // surfels: [2][total_pixels] sum w z, sum w z^2 of the forward
+    int surfels;             // 1: records, tile coverage and gradient rows are the surfel ones
+    uint32_t vg_stride;      // floats per (Gaussian, view) gradient row: 10, or 16 for surfels
     unsigned long long *keys[2];
     uint32_t *vals[2];
     uint32_t *hist;          // [kMaxPasses][256]

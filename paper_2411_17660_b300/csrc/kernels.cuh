@@ -17,6 +17,15 @@ cudaError_t launch_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
 cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st);
 
+cudaError_t launch_pose_reduce(const ViewTable &vt, const Ws &ws, int accumulate, cudaStream_t st);
+
+// surfel.cu
+cudaError_t launch_surfel_preprocess_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, cudaStream_t st);
+cudaError_t launch_surfel_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
+                                         const GradPtrs &out, cudaStream_t st);
+cudaError_t launch_surfel_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
+cudaError_t launch_surfel_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
+
 // binning.cu
 cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_t st);
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st);

@@ -23,35 +23,6 @@ namespace gsr {
 constexpr int kPreWarps = 8;
 constexpr int kPreThreads = 32 * kPreWarps;
 
-__device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
-    for (int i = threadIdx.x; i < vt.V * 12; i += blockDim.x) {
-        const int v = i / 12, k = i % 12;
-        const float x = vt.v[v].T_cw[k];
-        if (k % 4 == 3)
-            s_pose[v].t[k / 4] = x;
-        else
-            s_pose[v].W[k / 4][k % 4] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < (unsigned)vt.V) {
-        Pose &p = s_pose[threadIdx.x];
-        for (int j = 0; j < 3; ++j) p.C[j] = -(p.W[0][j] * p.t[0] + p.W[1][j] * p.t[1] + p.W[2][j] * p.t[2]);
-    }
-    __syncthreads();
-}
-
-// Unit view direction from the camera centre to the mean and its length.
-__device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, float &dx, float &dy, float &dz,
-                                         float &rn) {
-    dx = G.mx - ps.C[0];
-    dy = G.my - ps.C[1];
-    dz = G.mz - ps.C[2];
-    rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= rn;
-    dy *= rn;
-    dz *= rn;
-}
-
 // ------------------------------------------------------------------ forward
 // Warp-queue forward: persistent warps take batches of 32 Gaussians (one per
 // lane, parameters activated once per batch) and walk their views.  Phase A
@@ -430,21 +401,8 @@ __device__ __forceinline__ void bwd_finish(const GaussianPtrs &gp, const GradPtr
         }
         dls[j] = ds * G.s[j];
     }
-    const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
-    // dR/dq for the unit quaternion (w, x, y, z)
-    float dq[4];
-    dq[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
-    dq[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
-                   w * dR[2][1] - 2.f * x * dR[2][2]);
-    dq[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
-                   z * dR[2][1] - 2.f * y * dR[2][2]);
-    dq[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
-                   y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
-    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
-    const float qu[4] = {w, x, y, z};
     float dqr[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
+    rot_grad_to_quat(G, dR, dqr);
     const float dlogit = acc[12] * (1.f - G.o);   // d ln(sigmoid(l)) / dl = 1 - sigma
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -721,6 +679,11 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------------ launchers
+cudaError_t launch_pose_reduce(const ViewTable &vt, const Ws &ws, int accumulate, cudaStream_t st) {
+    pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, accumulate);
+    return cudaGetLastError();
+}
+
 // Resident blocks per SM of the forward kernel (registers allow 3).
 constexpr int kPreFwdBlocksPerSM = 3;
 
@@ -770,8 +733,7 @@ static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp
     preprocess_bwd_kernel<DEG, VW><<<blocks, kPreThreads, smem, st>>>(vt, gp, ws, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
-    return cudaGetLastError();
+    return launch_pose_reduce(vt, ws, out.accumulate, st);
 }
 
 template <int DEG>
@@ -788,10 +750,7 @@ static cudaError_t launch_pre_bwd(const ViewTable &vt, const GaussianPtrs &gp, c
 
 cudaError_t launch_preprocess_bwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, const GradPtrs &out,
                                   cudaStream_t st) {
-    if (gp.N == 0) {   // no Gaussians: zero pose gradients (no partials to sum)
-        pose_reduce_kernel<<<vt.V, 256, 0, st>>>(vt, ws, out.accumulate);
-        return cudaGetLastError();
-    }
+    if (gp.N == 0) return launch_pose_reduce(vt, ws, out.accumulate, st);   // zero pose gradients
     switch (gp.sh_degree) {
         case 0: return launch_pre_bwd<0>(vt, gp, ws, out, st);
         case 1: return launch_pre_bwd<1>(vt, gp, ws, out, st);

@@ -70,6 +70,55 @@ struct Pose {
     float C[3];
 };
 
+// dL/dq of the raw quaternion from dL/dR of R(q / |q|).
+__device__ __forceinline__ void rot_grad_to_quat(const GaussPre &G, const float (&dR)[3][3], float (&dqr)[4]) {
+    const float w = G.qw, x = G.qx, y = G.qy, z = G.qz;
+    // dR/dq for the unit quaternion (w, x, y, z)
+    float dq[4];
+    dq[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    dq[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
+                   w * dR[2][1] - 2.f * x * dR[2][2]);
+    dq[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
+                   z * dR[2][1] - 2.f * y * dR[2][2]);
+    dq[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                   y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    const float qu[4] = {w, x, y, z};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dqr[k] = (dq[k] - qu[k] * qd) * G.qinv;
+}
+
+__device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
+    for (int i = threadIdx.x; i < vt.V * 12; i += blockDim.x) {
+        const int v = i / 12, k = i % 12;
+        const float x = vt.v[v].T_cw[k];
+        if (k % 4 == 3)
+            s_pose[v].t[k / 4] = x;
+        else
+            s_pose[v].W[k / 4][k % 4] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)vt.V) {
+        Pose &p = s_pose[threadIdx.x];
+        for (int j = 0; j < 3; ++j) p.C[j] = -(p.W[0][j] * p.t[0] + p.W[1][j] * p.t[1] + p.W[2][j] * p.t[2]);
+    }
+    __syncthreads();
+}
+
+// Unit view direction from the camera centre to the mean and its length.
+__device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, float &dx, float &dy, float &dz,
+                                         float &rn) {
+    dx = G.mx - ps.C[0];
+    dy = G.my - ps.C[1];
+    dz = G.mz - ps.C[2];
+    rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= rn;
+    dy *= rn;
+    dz *= rn;
+}
+
+
+
 struct Proj {
     float xh, yh, zh, xl, yl, zl;  // camera-frame mean, hi + lo
     bool clx, cly;

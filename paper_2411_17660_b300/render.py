@@ -148,6 +148,35 @@ class GaussianRasterizer:
                                       torch.cuda.current_stream().cuda_stream)
         self.ctx.check(st, "gsr_render_backward")
 
+    # ------------------------------------------------------------ surfels (2DGS)
+    def surfels_forward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
+                            color: torch.Tensor, depth=None, alpha=None, normal=None, distortion=None):
+        """Surfel render into flat buffers (normal: [3 * P_v] per view like colour)."""
+        g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
+        views = view_structs(cams, viewmats, color, depth, alpha)
+        off = pixel_offsets(cams)
+        extra = [_b.SurfelOut(0 if normal is None else normal.data_ptr() + 4 * 3 * off[v],
+                              0 if distortion is None else distortion.data_ptr() + 4 * off[v])
+                 for v in range(len(cams))]
+        st = self.ctx.render_surfels(g, views, extra, ws.data_ptr(), ws.numel(),
+                                     torch.cuda.current_stream().cuda_stream)
+        self.ctx.check(st, "gsr_render_surfels")
+
+    def surfels_backward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
+                             d_color, d_depth, d_alpha, d_normal, d_distortion, grads: dict,
+                             d_pose: Optional[torch.Tensor], accumulate=False):
+        g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
+        views = view_structs(cams, viewmats)
+        off = pixel_offsets(cams)
+        ptr = lambda t, v, ch: 0 if t is None else t.data_ptr() + 4 * ch * off[v]
+        vg = [_b.ViewGrad(ptr(d_color, v, 3), ptr(d_depth, v, 1), ptr(d_alpha, v, 1), 0,
+                          0 if d_pose is None else d_pose.data_ptr() + 4 * 6 * v) for v in range(len(cams))]
+        extra = [_b.SurfelGrad(ptr(d_normal, v, 3), ptr(d_distortion, v, 1)) for v in range(len(cams))]
+        out = _b.Grads(*[grads[k].data_ptr() for k in PARAM_NAMES], int(accumulate), 0, 0, 0)
+        st = self.ctx.render_surfels_backward(g, views, vg, extra, out, ws.data_ptr(), ws.numel(),
+                                              torch.cuda.current_stream().cuda_stream)
+        self.ctx.check(st, "gsr_render_surfels_backward")
+
     # ------------------------------------------------------------ convenience
     def render_forward(self, params, sh_degree: int, cams, viewmats: torch.Tensor,
                        ws: Optional[torch.Tensor] = None, grow: bool = True):
