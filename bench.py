@@ -39,6 +39,8 @@ PAPER_LAMBDA1, PAPER_LAMBDA2 = 0.8, 0.2
 LOSS_NAMES = {"l1": "L1 colour/depth loss", "paper": "L1 + SSIM colour / L1 depth loss (0.8, 0.2)"}
 FWD_OPS_PER_PAIR = 17   # FP32-pipe instructions per composited (pixel, Gaussian) pair, blend forward
 BWD_OPS_PER_PAIR = 48   # the same for the blend backward (before the per-warp reduction)
+SURFEL_FWD_OPS_PER_PAIR = 47   # surfels: ray-disk intersection + compositing with normal and distortion
+SURFEL_BWD_OPS_PER_PAIR = 85   # surfels: recomputed intersection + its backward
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -53,6 +55,10 @@ def parse():
                    help="window (8 x 640x480, 100k Gaussians) is the metric's workload; the others are for reports")
     p.add_argument("--loss", default="l1", choices=["l1", "paper"],
                    help="l1: L1 colour + weighted L1 depth; paper: the mixed L1 + SSIM + depth loss (0.8, 0.2)")
+    p.add_argument("--primitive", default="gaussians", choices=["gaussians", "surfels"],
+                   help="surfels: the 2-D surfel renderer (with normal and distortion outputs and gradients)")
+    p.add_argument("--median", action="store_true", help="also render median depth and feed it a gradient")
+    p.add_argument("--densify", action="store_true", help="also gather densification statistics in the backward")
     p.add_argument("--autotune", action="store_true", help="pick the tile size with the autotuner first")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -249,13 +255,16 @@ def reference_arm(args, ws, rank):
 class Window:
     """Device state of one mapping window (inputs, outputs, workspace)."""
 
-    def __init__(self, scene, rast, views=None, dev="cuda", loss="l1"):
+    def __init__(self, scene, rast, views=None, dev="cuda", loss="l1", primitive="gaussians", median=False,
+                 densify=False):
         import torch
         from paper_2411_17660_b300 import render as R
         self.R, self.torch = R, torch
         idx = list(range(scene.V)) if views is None else views
         self.scene = scene
         self.loss_kind = loss
+        self.surfels = primitive == "surfels"
+        self.median, self.densify = median, densify
         self.cams = [R.Intrinsics(scene.cameras[v].H, scene.cameras[v].W, scene.cameras[v].fx,
                                   scene.cameras[v].fy, scene.cameras[v].cx, scene.cameras[v].cy) for v in idx]
         self.params = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(dev)
@@ -273,23 +282,51 @@ class Window:
         self.loss = torch.empty(1, device=dev)
         self.grads = {k: torch.empty_like(v) for k, v in self.params.items()}
         self.d_pose = torch.empty(len(self.cams), 6, device=dev)
+        # extra outputs and their (fixed) upstream gradients
+        self.med = torch.empty(self.P, device=dev) if median else None
+        self.dM = torch.full((self.P,), 1e-3, device=dev) if median else None
+        self.normal = torch.empty(3 * self.P, device=dev) if self.surfels else None
+        self.dist = torch.empty(self.P, device=dev) if self.surfels else None
+        self.dN = torch.full((3 * self.P,), 1e-3, device=dev) if self.surfels else None
+        self.dL = torch.full((self.P,), 1e-3, device=dev) if self.surfels else None
+        self.dens = {k: torch.empty(scene.N, device=dev) for k in ("grad", "count", "radius")} if densify else None
         _, _, _, self.ws = rast.render_forward(self.params, scene.sh_degree, self.cams, self.vm)
         info = rast.info(self.ws)
+        keys = info.keys
+        if self.surfels:   # the surfels' tile bounds give their own key count
+            cap = int(keys * 2) + 8192
+            for _ in range(6):
+                self.ws = rast.alloc_workspace(scene.N, self.cams, cap, dev)
+                rast.surfels_forward_raw(self.params, scene.sh_degree, self.cams, self.vm, self.ws, self.color)
+                info = rast.info(self.ws)
+                if info.status == 0:
+                    break
+                cap = int(info.keys * 1.25) + 8192
+            keys = info.keys
         # headroom so that the timed steps never re-grow
-        self.ws = rast.alloc_workspace(scene.N, self.cams, int(info.keys * 1.1) + 8192, dev)
+        self.ws = rast.alloc_workspace(scene.N, self.cams, int(keys * 1.1) + 8192, dev)
 
     def step(self, accumulate=False):
         R, sc = self.R, self.scene
-        self.rast.forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
-                              self.alpha)
+        if self.surfels:
+            self.rast.surfels_forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color,
+                                          self.depth, self.alpha, self.normal, self.dist)
+        else:
+            self.rast.forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
+                                  self.alpha, self.med)
         if self.loss_kind == "l1":
             R.l1_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, 1.0,
                       sc.depth_weight, self.dC, self.dD, self.loss)
         else:
             R.rgbd_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, PAPER_LAMBDA1,
                         PAPER_LAMBDA2, self.dC, self.dD, self.loss)
-        self.rast.backward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.dC, self.dD, None,
-                               self.grads, self.d_pose, accumulate=accumulate)
+        if self.surfels:
+            self.rast.surfels_backward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.dC, self.dD,
+                                           None, self.dN, self.dL, self.grads, self.d_pose, accumulate=accumulate)
+        else:
+            self.rast.backward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.dC, self.dD, None,
+                                   self.grads, self.d_pose, accumulate=accumulate, d_median_depth=self.dM,
+                                   densify=self.dens)
 
 
 def launches_per_step(rast, win):
@@ -353,12 +390,13 @@ def main():
     tile, tuned = args.tile, None
     if args.autotune:
         from paper_2411_17660_b300 import autotune as A
-        w0 = Window(scene, R.GaussianRasterizer(16), loss=args.loss)
+        w0 = Window(scene, R.GaussianRasterizer(16), loss=args.loss, primitive=args.primitive)
         tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
         tile = tuned["tile"]
         del w0
     rast = R.GaussianRasterizer(tile)
-    win = Window(scene, rast, loss=args.loss)
+    opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify)
+    win = Window(scene, rast, **opts)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
     K, W = args.steps, args.warmup
@@ -401,7 +439,7 @@ def main():
     # the same window as 8 per-view launches
     per_view = None
     if not args.no_per_view:
-        wins = [Window(scene, rast, [v], loss=args.loss) for v in range(scene.V)]
+        wins = [Window(scene, rast, [v], **opts) for v in range(scene.V)]
 
         def per_view_step():
             for i, w1 in enumerate(wins):
@@ -444,10 +482,13 @@ def main():
     pairs = info.pairs_contributing
     dominant = max(("blend_fwd", "blend_bwd", "sort", "preprocess", "preprocess_bwd"), key=lambda s: stage_ms[s])
     ops = {"blend_fwd": FWD_OPS_PER_PAIR, "blend_bwd": BWD_OPS_PER_PAIR}
+    if args.primitive == "surfels":
+        ops = {"blend_fwd": SURFEL_FWD_OPS_PER_PAIR, "blend_bwd": SURFEL_BWD_OPS_PER_PAIR}
     if dominant in ops:
         achieved = pairs * ops[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
         roof = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved / alu_peak, "traffic": traffic_for(dominant),
+                "frac": achieved / alu_peak,
+                "traffic": traffic_for(dominant) if args.primitive == "gaussians" else None,
                 "peak_note": f"FP32 lanes: {n_sm} SMs x 128 x {peaks['sm_max_mhz']:.0f} MHz (max clock)",
                 "work": f"{pairs} composited pairs x {ops[dominant]} FP32 ops"}
     else:
@@ -466,6 +507,9 @@ def main():
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
                    "sh_degree": scene.sh_degree, "tile": tile, "autotune": tuned,
                    "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
+                   "primitive": args.primitive,
+                   "extras": [k for k, on in (("median depth", args.median), ("densification statistics", args.densify),
+                                              ("normal + distortion", args.primitive == "surfels")) if on],
                    "l2": "flushed before every step (256 MB write), outside the timed events",
                    "launch": "one CUDA graph per step, replayed" if graph_ms is not None else "eager launches",
                    "parallelism": "replicas" if world > 1 else "single"},
