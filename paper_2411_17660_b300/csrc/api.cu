@@ -443,10 +443,11 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     gout.densify_radius = out->densify_radius;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
+    // the per-pair gradient rows were cleared by the forward (and by the last
+    // backward after reading them), so nothing is cleared here
     ctx->mark(6, st);
-    cudaError_t e = cudaMemsetAsync(w.vg_grads, 0, sizeof(float) * kVGGrads * L.VN, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear");
     ctx->mark(7, st);
+    cudaError_t e;
     if ((e = launch_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
     ctx->mark(8, st);
     if ((e = launch_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess backward");
@@ -539,10 +540,9 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
     gout.densify_grad = gout.densify_count = gout.densify_radius = nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-    ctx->mark(6, st);
-    cudaError_t e = cudaMemsetAsync(w.vg_grads, 0, sizeof(float) * kVGGradsMax * L.VN, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear");
+    ctx->mark(6, st);   // gradient rows are cleared by the forward and after use
     ctx->mark(7, st);
+    cudaError_t e;
     if ((e = launch_surfel_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
     ctx->mark(8, st);
     if ((e = launch_surfel_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess)

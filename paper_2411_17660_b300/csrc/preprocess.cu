@@ -81,6 +81,10 @@ __device__ __forceinline__ void preprocess_fwd_pair(const ViewTable &vt, const G
     ws.rec1[i] = make_float4(m00, q.m01[k], q.m11[k], smax);
     ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
     ws.rec3[i] = make_float4(log2o, sxx, sxy, syy);
+    // the backward's blend accumulates this pair's screen gradients with atomics
+    float2 *row = reinterpret_cast<float2 *>(ws.vg_grads + ((size_t)pg * ws.V + pv) * kVGGrads);
+#pragma unroll
+    for (int k = 0; k < kVGGrads / 2; ++k) row[k] = make_float2(0.f, 0.f);
 }
 
 template <int DEG>
@@ -223,8 +227,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     }
     float sg[kVGGrads];
 #pragma unroll
+    float2 *row = reinterpret_cast<float2 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kVGGrads);
     for (int c = 0; c < kVGGrads / 2; ++c) {   // one 40-byte row, 8-byte aligned
-        const float2 x = reinterpret_cast<const float2 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kVGGrads)[c];
+        const float2 x = row[c];
         sg[2 * c] = x.x;
         sg[2 * c + 1] = x.y;
     }
@@ -349,6 +354,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     for (int k = 0; k < 9; ++k) part[3 + k] = dM[k];
     part[12] = dlno;
     part[BwdAcc<DEG>::NV] = sqrtf(du * du + dvv * dvv);   // densification
+    // the row is cleared for the next backward, after every load of this pair
+#pragma unroll
+    for (int c = 0; c < kVGGrads / 2; ++c) __stcs(row + c, make_float2(0.f, 0.f));
 #pragma unroll
     for (int c = 0; c < 6; ++c) pose[c * kPreThreads] = pose6[c];
 }

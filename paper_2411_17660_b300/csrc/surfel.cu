@@ -122,6 +122,9 @@ __global__ void __launch_bounds__(128) surfel_pre_fwd_kernel(const __grid_consta
                     ws.rec3[i] = make_float4(G.log2o, G.smax, b[1], b[2]);
                     ws.rec4[i] = make_float4(n[0], n[1], n[2], 0.f);
                     ws.rec5[i] = rect;
+                    float4 *row = reinterpret_cast<float4 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kSG);
+#pragma unroll
+                    for (int k = 0; k < kSG / 4; ++k) row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
         }
@@ -520,11 +523,11 @@ __global__ void __launch_bounds__(kPB) surfel_pre_bwd_kernel(const __grid_consta
         const Pose &ps = s_pose[v];
         float pose6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (real && ws.counts[(size_t)v * N + g] > 0) {
-            const float *sgp = ws.vg_grads + ((size_t)g * ws.V + v) * kSG;
+            float4 *sgp = reinterpret_cast<float4 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kSG);
             float sg[kSG];
 #pragma unroll
             for (int k = 0; k < kSG / 4; ++k) {
-                const float4 x4 = reinterpret_cast<const float4 *>(sgp)[k];
+                const float4 x4 = sgp[k];
                 sg[4 * k] = x4.x;
                 sg[4 * k + 1] = x4.y;
                 sg[4 * k + 2] = x4.z;
@@ -613,6 +616,9 @@ __global__ void __launch_bounds__(kPB) surfel_pre_bwd_kernel(const __grid_consta
                         Wt[2][2] * dn[0] - Wt[2][0] * dn[2];
             pose6[5] += p[0] * dp[1] - p[1] * dp[0] + a[0] * da[1] - a[1] * da[0] + b[0] * db[1] - b[1] * db[0] +
                         Wt[2][0] * dn[1] - Wt[2][1] * dn[0];
+            // the row is cleared for the next backward, after every load of this pair
+#pragma unroll
+            for (int k = 0; k < kSG / 4; ++k) __stcs(sgp + k, make_float4(0.f, 0.f, 0.f, 0.f));
         }
         // this block's pose partial of view v, summed in a fixed order
 #pragma unroll
