@@ -3,7 +3,9 @@
 // back-to-front backward.
 //
 // One CTA per screen tile (all views concatenated), one warp per 8x8 block
-// of pixels, two pixels per lane.  Each warp walks its tile's depth-sorted
+// of pixels in the forward (two pixels per lane) and per 8x16 block in the
+// backward (four pixels per lane, where the tile is that tall: the warp's
+// per-Gaussian reduction then serves twice the pixels).  Each warp walks its tile's depth-sorted
 // list in chunks of 32 entries: the 32 lanes load one entry each, keep only
 // the Gaussians whose cutoff ellipse reaches the warp's 8x8 block (an exact
 // convex minimum of d^2 over the block), compact the survivors into the
@@ -19,10 +21,10 @@
 // of global atomics per (warp, Gaussian); when at most two lanes touch a
 // Gaussian they issue their atomics directly instead.
 //
-// In the backward, a lane's two pixels share their column, hence dx: their
-// per-pixel arithmetic runs on packed FP32 pairs (one fma.rn.f32x2 for both
-// pixels, the same rounding as two scalar ones, so that the decisions stay
-// bit-identical to the forward's scalar ones).  Its staged entries hold every
+// In the backward, a lane's pixels share their column, hence dx: the
+// per-pixel arithmetic of two of them runs on packed FP32 pairs (one
+// fma.rn.f32x2 for both pixels, the same rounding as two scalar ones, so that
+// the decisions stay bit-identical to the forward's scalar ones).  Its staged entries hold every
 // operand that both pixels use as a duplicated pair, so that one 128-bit
 // shared load yields two ready register pairs.  The forward stays scalar: it
 // skips a pixel row's work whenever no lane of the warp needs it, which
@@ -33,15 +35,17 @@ namespace gsr {
 
 namespace {
 
-// A warp covers an 8x8 block of pixels: lane (x, y), y < 4, owns pixel rows
-// y and y + 4 of column x.
-constexpr int kSubW = 8, kSubH = 8, kPPL = 2, kRowStep = 4;
+// A warp covers a block of 8 columns and BH rows: lane (x, y), y < 4, owns
+// the pixel rows y + 4 r of column x.  The forward's blocks are 8x8 (rows y
+// and y + 4); the backward's are 8x16 where the tile allows.
+constexpr int kSubW = 8, kSubH = 8, kRowStep = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
-template <int TS>
+template <int TS, int BH = kSubH>
 struct BlendShape {
+    static_assert(TS % kSubW == 0 && TS % BH == 0, "a tile holds whole warp blocks");
     static constexpr int WX = TS / kSubW;
-    static constexpr int WY = TS / kSubH;
+    static constexpr int WY = TS / BH;
     static constexpr int WARPS = WX * WY;
     static constexpr int THREADS = WARPS * 32;
 };
@@ -83,14 +87,32 @@ __device__ __forceinline__ float2 pair_s2(float2 dx, float2 dy, float2 m00, floa
     return __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
 }
 
+// Backward block height: 16 rows (two packed row pairs per lane) when the
+// tile is at least that tall.
+template <int TS>
+struct BwdBlock {
+    static constexpr int H = TS >= 16 ? 16 : kSubH;
+    // resident blocks per SM asked of the compiler: 24 warps, 80 registers
+    // (measured faster than the uncapped 115 with their lower occupancy)
+    static constexpr int MIN_BLOCKS = 768 / BlendShape<TS, H>::THREADS;
+};
+
+// Forward block height: 8 rows (16 measured slower: the forward has no
+// per-Gaussian reduction to share, and its taller blocks cull less).
+template <int TS>
+struct FwdBlock {
+    static constexpr int H = kSubH;
+};
+
 // Whether min over the warp's block of pixel centres of s can reach s_max.
 // s(dx, dy) = (m00 dx + m01 dy)^2 + (m11 dy)^2; for fixed dy the first term's
 // minimum over dx in [dx0, dx1] is max(0, m00 dx0 + m01 dy, -(m00 dx1 + m01 dy))^2,
 // a convex function of dy whose minimum over [dy0, dy1] lies at an end or at
 // one of three stationary points, all clamped into the interval.
+template <int BH>
 __device__ __forceinline__ bool touches_block(float ur, float vr, float m00, float m01, float m11, float smax) {
     const float dx0 = -ur, dx1 = (float)(kSubW - 1) - ur;
-    const float dy0 = -vr, dy1 = (float)(kSubH - 1) - vr;
+    const float dy0 = -vr, dy1 = (float)(BH - 1) - vr;
     const float a0 = m00 * dx0, a1 = m00 * dx1;
     const float inv_den = 1.0f / (m01 * m01 + m11 * m11);
     auto f = [&](float dy) {
@@ -158,9 +180,9 @@ struct WarpTile {
     uint2 range;
 };
 
-template <int TS>
+template <int TS, int BH = kSubH>
 __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws) {
-    using S = BlendShape<TS>;
+    using S = BlendShape<TS, BH>;
     WarpTile w;
     const uint32_t tile = blockIdx.x;
     w.v = view_of_tile(vt, tile);
@@ -169,7 +191,7 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     const int tx = (int)(lt % (uint32_t)vp.tiles_x), ty = (int)(lt / (uint32_t)vp.tiles_x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     w.X0 = tx * TS + (warp % S::WX) * kSubW;
-    w.Y0 = ty * TS + (warp / S::WX) * kSubH;
+    w.Y0 = ty * TS + (warp / S::WX) * BH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
     w.range = ws.ranges[tile];
@@ -177,9 +199,10 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
 }
 
 // Loads entry idx of the tile list (lane-parallel), tests it against the
-// warp's block and compacts the survivors into the warp's slots in list
-// order; Stage writes one survivor's slot.  Returns the number of survivors.
-template <typename Stage>
+// warp's block of BH rows and compacts the survivors into the warp's slots in
+// list order; Stage writes one survivor's slot.  Returns the number of
+// survivors.
+template <int BH, typename Stage>
 __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, size_t vN, uint32_t idx, uint32_t end,
                                            int X0, int Y0, Stage &&write) {
     bool keep = false;
@@ -193,10 +216,10 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
         r1 = ws.rec1[gi];
         ur = __fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z);
         vr = __fadd_rn(__fsub_rn(r0.y, (float)Y0), r0.w);
-        keep = touches_block(ur, vr, r1.x, r1.y, r1.z, r1.w);
+        keep = touches_block<BH>(ur, vr, r1.x, r1.y, r1.z, r1.w);
     }
     const unsigned ballot = __ballot_sync(kFull, keep);
-    if (keep) write(__popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, idx);
+    if (keep) write(__popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, idx, g);
     __syncwarp();
     return __popc(ballot);
 }
@@ -204,22 +227,23 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 // MED: also record, per pixel, the median-depth contributor (the last one
 // entered with transmittance above 0.5) and its depth.
 template <int TS, bool MED>
-__global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
+__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
-    using S = BlendShape<TS>;
+    constexpr int BH = FwdBlock<TS>::H, NR = BH / kRowStep;
+    using S = BlendShape<TS, BH>;
     __shared__ float4 sA[S::WARPS][32], sB[S::WARPS][32], sC[S::WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpTile wt = warp_tile<TS>(vt, ws);
+    const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.vals[ws.passes & 1];
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
-    float T[kPPL], C0[kPPL], C1[kPPL], C2[kPPL], D[kPPL], Zm[kPPL];
-    uint32_t last[kPPL], mi[kPPL], ncon = 0;
-    bool done[kPPL];
+    float T[NR], C0[NR], C1[NR], C2[NR], D[NR], Zm[NR];
+    uint32_t last[NR], mi[NR], ncon = 0;
+    bool done[NR];
 #pragma unroll
-    for (int q = 0; q < kPPL; ++q) {
+    for (int q = 0; q < NR; ++q) {
         T[q] = 1.f;
         C0[q] = C1[q] = C2[q] = D[q] = Zm[q] = 0.f;
         last[q] = mi[q] = 0;
@@ -228,10 +252,11 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
         bool all_done = true;
 #pragma unroll
-        for (int q = 0; q < kPPL; ++q) all_done &= done[q];
+        for (int q = 0; q < NR; ++q) all_done &= done[q];
         if (__all_sync(kFull, all_done)) break;
-        const int n = stage_chunk(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
-                                  [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o, uint32_t idx) {
+        const int n = stage_chunk<BH>(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
+                                         [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
+                                             uint32_t idx, uint32_t) {
                                       sA[warp][slot] = make_float4(ur, vr, r1.x, r1.y);
                                       sB[warp][slot] = make_float4(r1.z, r1.w, log2o, r2.w);
                                       sC[warp][slot] = make_float4(r2.x, r2.y, r2.z, __uint_as_float(idx));
@@ -240,7 +265,7 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
             const float4 a = sA[warp][j], b = sB[warp][j];
             const float dx = __fsub_rn(lxf, a.x);
 #pragma unroll
-            for (int q = 0; q < kPPL; ++q) {
+            for (int q = 0; q < NR; ++q) {
                 if (done[q]) continue;
                 float p1, p2;
                 const float s = pair_s(dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.z, a.w, b.x, p1, p2);
@@ -270,7 +295,7 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
         __syncwarp();
     }
 #pragma unroll
-    for (int q = 0; q < kPPL; ++q) {
+    for (int q = 0; q < NR; ++q) {
         const int py = wt.py + q * kRowStep;
         if (wt.px < vp.W && py < vp.H) {
             const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
@@ -291,179 +316,236 @@ __global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_fwd_kernel(cons
     if (lane == 0 && tot) atomicAdd(&ws.hdr->pairs_contrib, (unsigned long long)tot);
 }
 
+// A lane's gradient sums over its pixels, kept as pairs (A[2] is not used: the
+// dx term follows from A[0]).  SET starts them with pair p's terms, otherwise
+// they are added.
+template <bool SET>
+__device__ __forceinline__ void pair_sums(float2 (&A)[kVGGrads], float2 dp1, float2 dp2, float2 glo, float2 w,
+                                          float2 dy, float2 gR, float2 gG, float2 gB, float2 gZ) {
+    if (SET) {
+        A[0] = dp1;
+        A[1] = dp2;
+        A[3] = __fmul2_rn(dp1, dy);
+        A[4] = __fmul2_rn(dp2, dy);
+        A[5] = glo;
+        A[6] = __fmul2_rn(gR, w);
+        A[7] = __fmul2_rn(gG, w);
+        A[8] = __fmul2_rn(gB, w);
+        A[9] = __fmul2_rn(gZ, w);
+    } else {
+        A[0] = __fadd2_rn(A[0], dp1);
+        A[1] = __fadd2_rn(A[1], dp2);
+        A[3] = __ffma2_rn(dp1, dy, A[3]);
+        A[4] = __ffma2_rn(dp2, dy, A[4]);
+        A[5] = __fadd2_rn(A[5], glo);
+        A[6] = __ffma2_rn(gR, w, A[6]);
+        A[7] = __ffma2_rn(gG, w, A[7]);
+        A[8] = __ffma2_rn(gB, w, A[8]);
+        A[9] = __ffma2_rn(gZ, w, A[9]);
+    }
+}
+
 // MED: dL/d(median depth) goes to the z of each pixel's median contributor.
+// A lane owns NR = BH / 4 pixel rows of its column; rows 2p and 2p + 1 (y + 8p
+// and y + 8p + 4) form pair p, whose arithmetic runs on packed FP32 pairs.
 template <int TS, bool MED>
-__global__ void __launch_bounds__(BlendShape<TS>::THREADS) blend_bwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                           const Ws ws) {
-    using S = BlendShape<TS>;
+__global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdBlock<TS>::MIN_BLOCKS)
+    blend_bwd_kernel(const __grid_constant__ ViewTable vt, const Ws ws) {
+    constexpr int BH = BwdBlock<TS>::H;
+    constexpr int NR = BH / kRowStep, NP = NR / 2;
+    using S = BlendShape<TS, BH>;
     __shared__ float4 sE[S::WARPS][kEntryQuads][32];
-    __shared__ float2 sX[S::WARPS][32];
+    __shared__ float4 sX[S::WARPS][32];  // (s_max, list index, Gaussian index, -)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpTile wt = warp_tile<TS>(vt, ws);
+    const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.vals[ws.passes & 1];
-    const size_t N = ws.N;
-    const size_t vN = (size_t)wt.v * N;
+    const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
-    const float2 lx2 = make_float2(lxf, lxf), ly2 = make_float2(lyf, lyf + (float)kRowStep);
+    const float2 lx2 = make_float2(lxf, lxf);
     const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
     const float2 m2ln2 = make_float2(-2.f * kLn2, -2.f * kLn2);
 
-    // per pixel (.x, .y as in the forward): Q = gC . (colour behind) + gD
-    // (depth behind), normalised by the transmittance in front of the
+    // per pixel (pair p: .x row 2p, .y row 2p + 1): Q = gC . (colour behind)
+    // + gD (depth behind), normalised by the transmittance in front of the
     // current entry
-    float Tq[kPPL], gq[5][kPPL], gM[kPPL];
-    uint32_t last[kPPL], mi[kPPL], lmax = 0;
+    float2 T[NP], Q[NP], gR[NP], gG[NP], gB[NP], gZ[NP], gA[NP];
+    uint32_t last[NR], mi[NR], lmax = 0;
+    float gM[NR];
 #pragma unroll
-    for (int q = 0; q < kPPL; ++q) {
-        Tq[q] = 1.f;
-        last[q] = mi[q] = 0;
-        gM[q] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) gq[k][q] = 0.f;
-        const int py = wt.py + q * kRowStep;
+    for (int r = 0; r < NR; ++r) {
+        float t = 1.f, g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        last[r] = mi[r] = 0;
+        gM[r] = 0.f;
+        const int py = wt.py + r * kRowStep;
         if (wt.px < vp.W && py < vp.H) {
             const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
-            Tq[q] = ws.T_final[vp.pixel_offset + pix];
-            last[q] = ws.last[vp.pixel_offset + pix];
+            t = ws.T_final[vp.pixel_offset + pix];
+            last[r] = ws.last[vp.pixel_offset + pix];
             if (vp.d_color) {
-                gq[0][q] = vp.d_color[pix];
-                gq[1][q] = vp.d_color[HW + pix];
-                gq[2][q] = vp.d_color[2 * HW + pix];
+                g[0] = vp.d_color[pix];
+                g[1] = vp.d_color[HW + pix];
+                g[2] = vp.d_color[2 * HW + pix];
             }
-            if (vp.d_depth) gq[3][q] = vp.d_depth[pix];
-            if (vp.d_alpha) gq[4][q] = vp.d_alpha[pix] * Tq[q];
+            if (vp.d_depth) g[3] = vp.d_depth[pix];
+            if (vp.d_alpha) g[4] = vp.d_alpha[pix] * t;
             if (MED && vp.d_median_depth) {
-                gM[q] = vp.d_median_depth[pix];
-                mi[q] = ws.median[vp.pixel_offset + pix];
+                gM[r] = vp.d_median_depth[pix];
+                mi[r] = ws.median[vp.pixel_offset + pix];
             }
         }
-        lmax = max(lmax, last[q]);
+        lmax = max(lmax, last[r]);
+        const int p = r / 2;
+        if (r & 1) {
+            T[p].y = t, gR[p].y = g[0], gG[p].y = g[1], gB[p].y = g[2], gZ[p].y = g[3], gA[p].y = g[4];
+        } else {
+            T[p].x = t, gR[p].x = g[0], gG[p].x = g[1], gB[p].x = g[2], gZ[p].x = g[3], gA[p].x = g[4];
+        }
+        Q[p] = make_float2(0.f, 0.f);
     }
-    float2 T = make_float2(Tq[0], Tq[1]), Q = make_float2(0.f, 0.f);
-    const float2 gR = make_float2(gq[0][0], gq[0][1]), gG = make_float2(gq[1][0], gq[1][1]);
-    const float2 gB = make_float2(gq[2][0], gq[2][1]), gZ = make_float2(gq[3][0], gq[3][1]);
-    const float2 gATf = make_float2(gq[4][0], gq[4][1]);
     const uint32_t wlast = __reduce_max_sync(kFull, lmax);
     float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads;   // + g V 10: (Gaussian, view) rows of 10
     const size_t row = (size_t)ws.V * kVGGrads;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u ? end - 32u : wt.range.x;
-        const int n = stage_chunk(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0,
-                                  [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o, uint32_t idx) {
-                                      float4(&e)[kEntryQuads][32] = sE[warp];
-                                      e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
-                                      e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
-                                      e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
-                                      e[3][slot] = make_float4(r2.x, r2.x, r2.y, r2.y);
-                                      e[4][slot] = make_float4(r2.z, r2.z, r2.w, r2.w);
-                                      sX[warp][slot] = make_float2(r1.w, __uint_as_float(idx));
-                                  });
+        const int n = stage_chunk<BH>(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0,
+                                      [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
+                                          uint32_t idx, uint32_t g) {
+                                          float4(&e)[kEntryQuads][32] = sE[warp];
+                                          e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
+                                          e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
+                                          e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
+                                          e[3][slot] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                                          e[4][slot] = make_float4(r2.z, r2.z, r2.w, r2.w);
+                                          sX[warp][slot] = make_float4(r1.w, __uint_as_float(idx),
+                                                                       __uint_as_float(g), 0.f);
+                                      });
         for (int j = n - 1; j >= 0; --j) {
             const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
-            const float2 x = sX[warp][j];
+            const float4 x = sX[warp][j];
             const uint32_t eidx = __float_as_uint(x.y);
-            const float2 dx = __fadd2_rn(lx2, lo2(e0)), dy = __fadd2_rn(ly2, hi2(e0));
-            float2 p1, p2;
-            const float2 s = pair_s2(dx, dy, lo2(e1), hi2(e1), lo2(e2), p1, p2);
-            const bool c0 = eidx < last[0] && s.x <= x.x, c1 = eidx < last[1] && s.y <= x.x;
-            const unsigned m0 = __ballot_sync(kFull, c0), m1 = __ballot_sync(kFull, c1);
-            const unsigned cmask = m0 | m1;
+            const float2 dx = __fadd2_rn(lx2, lo2(e0));
+            float2 dy[NP], s[NP], p1[NP], p2[NP];
+            bool c[NR];
+            unsigned m[NR], cmask = 0u;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float2 ly = make_float2(lyf + (float)(2 * p * kRowStep), lyf + (float)((2 * p + 1) * kRowStep));
+                dy[p] = __fadd2_rn(ly, hi2(e0));
+                s[p] = pair_s2(dx, dy[p], lo2(e1), hi2(e1), lo2(e2), p1[p], p2[p]);
+                c[2 * p] = eidx < last[2 * p] && s[p].x <= x.x;
+                c[2 * p + 1] = eidx < last[2 * p + 1] && s[p].y <= x.x;
+                m[2 * p] = __ballot_sync(kFull, c[2 * p]);
+                m[2 * p + 1] = __ballot_sync(kFull, c[2 * p + 1]);
+                cmask |= m[2 * p] | m[2 * p + 1];
+            }
             if (cmask == 0u) continue;
             const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
-            float gv[kVGGrads];
-            if (m0 != 0u && m1 != 0u) {
-                // Both pixel rows, packed.  Branch-free: a pixel without a
-                // contribution runs with alpha = 0, which leaves its T and Q
-                // unchanged and makes every gradient term zero.
-                const float2 arg = __ffma2_rn(s, neg2, hi2(e2));
-                const float2 raw = make_float2(c0 ? ex2_approx(arg.x) : 0.f, c1 ? ex2_approx(arg.y) : 0.f);
-                const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-                const float2 om = __ffma2_rn(al, neg2, one2);
-                const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-                const float2 Ti = __fmul2_rn(T, rom);
-                const float2 w = __fmul2_rn(al, Ti);
-                // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
-                // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
-                const float2 gc = __ffma2_rn(gR, lo2(e3), __ffma2_rn(gG, hi2(e3), __ffma2_rn(gB, lo2(e4),
-                                                                                            __fmul2_rn(gZ, hi2(e4)))));
-                const float2 dgq = __ffma2_rn(Q, neg2, gc);
-                const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gATf, rom));
-                Q = __ffma2_rn(al, dgq, Q);
-                T = Ti;
-                // no gradient to position or opacity through the 0.99 clamp
-                float2 glo = __fmul2_rn(dA, raw);                       // dL/d ln(sigma)
-                glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
-                glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
-                const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
-                const float2 dp1 = __fmul2_rn(p1, ds2), dp2 = __fmul2_rn(p2, ds2);
-                gv[0] = dp1.x + dp1.y;                                  // du, dv follow from these and m
-                gv[1] = dp2.x + dp2.y;
-                gv[2] = dx.x * gv[0];
-                gv[3] = fmaf(dp1.y, dy.y, dp1.x * dy.x);
-                gv[4] = fmaf(dp2.y, dy.y, dp2.x * dy.x);
-                gv[5] = glo.x + glo.y;
-                gv[6] = fmaf(gR.y, w.y, gR.x * w.x);
-                gv[7] = fmaf(gG.y, w.y, gG.x * w.x);
-                gv[8] = fmaf(gB.y, w.y, gB.x * w.x);
-                gv[9] = fmaf(gZ.y, w.y, gZ.x * w.x);
-                if (MED) gv[9] += (eidx + 1u == mi[0] ? gM[0] : 0.f) + (eidx + 1u == mi[1] ? gM[1] : 0.f);
-            } else {
-                // Only one pixel row of the warp is reached: scalar work on it.
-                auto row = [&](auto tag) {
-                    constexpr int R = decltype(tag)::value;
-                    const float2 &cs = s;
-                    const bool c = R ? c1 : c0;
-                    const float sq = R ? cs.y : cs.x, dyq = R ? dy.y : dy.x;
-                    const float p1q = R ? p1.y : p1.x, p2q = R ? p2.y : p2.x;
-                    float &Tq = R ? T.y : T.x;
-                    float &Qq = R ? Q.y : Q.x;
-                    const float gRq = R ? gR.y : gR.x, gGq = R ? gG.y : gG.x, gBq = R ? gB.y : gB.x;
-                    const float gZq = R ? gZ.y : gZ.x, gAq = R ? gATf.y : gATf.x;
-                    const float raw = c ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
-                    const float al = fminf(kAlphaMax, raw);
-                    const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
-                    const float Ti = Tq * rom;
-                    const float w = al * Ti;
-                    const float gc = fmaf(gRq, e3.x, fmaf(gGq, e3.z, fmaf(gBq, e4.x, gZq * e4.z)));
-                    const float dgq = __fmaf_rn(Qq, -1.f, gc);
-                    const float dA = fmaf(Ti, dgq, gAq * rom);
-                    Qq = fmaf(al, dgq, Qq);
-                    Tq = Ti;
-                    const float glo = raw <= kAlphaMax ? dA * raw : 0.f;
-                    const float ds2 = (-2.f * kLn2) * glo;
-                    const float dp1 = p1q * ds2, dp2 = p2q * ds2;
-                    gv[0] = dp1;
-                    gv[1] = dp2;
-                    gv[2] = dx.x * dp1;
-                    gv[3] = dp1 * dyq;
-                    gv[4] = dp2 * dyq;
-                    gv[5] = glo;
-                    gv[6] = gRq * w;
-                    gv[7] = gGq * w;
-                    gv[8] = gBq * w;
-                    gv[9] = gZq * w;
-                    if (MED && eidx + 1u == (R ? mi[1] : mi[0])) gv[9] += R ? gM[1] : gM[0];
-                };
-                if (m0 == 0u)
-                    row(RowTag<1>{});
+            float2 A[kVGGrads];
+            // pair 0 sets the sums (to zero when it is not reached), later pairs add
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const unsigned ma = m[2 * p], mb = m[2 * p + 1];
+                if ((ma | mb) == 0u) {
+                    if (p == 0) {
+#pragma unroll
+                        for (int k = 0; k < kVGGrads; ++k) A[k] = make_float2(0.f, 0.f);
+                    }
+                    continue;
+                }
+                float2 dp1, dp2, glo, w;
+                if (ma != 0u && mb != 0u) {
+                    // Both rows of the pair, packed.  Branch-free: a pixel
+                    // without a contribution runs with alpha = 0, which leaves
+                    // its T and Q unchanged and makes every gradient term zero.
+                    const float2 arg = __ffma2_rn(s[p], neg2, hi2(e2));
+                    const float2 raw = make_float2(c[2 * p] ? ex2_approx(arg.x) : 0.f,
+                                                   c[2 * p + 1] ? ex2_approx(arg.y) : 0.f);
+                    const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                    const float2 om = __ffma2_rn(al, neg2, one2);
+                    const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                    const float2 Ti = __fmul2_rn(T[p], rom);
+                    w = __fmul2_rn(al, Ti);
+                    // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
+                    // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
+                    const float2 gc = __ffma2_rn(gR[p], lo2(e3),
+                                                 __ffma2_rn(gG[p], hi2(e3),
+                                                            __ffma2_rn(gB[p], lo2(e4), __fmul2_rn(gZ[p], hi2(e4)))));
+                    const float2 dgq = __ffma2_rn(Q[p], neg2, gc);
+                    const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gA[p], rom));
+                    Q[p] = __ffma2_rn(al, dgq, Q[p]);
+                    T[p] = Ti;
+                    // no gradient to position or opacity through the 0.99 clamp
+                    glo = __fmul2_rn(dA, raw);                              // dL/d ln(sigma)
+                    glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
+                    glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+                    const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
+                    dp1 = __fmul2_rn(p1[p], ds2);
+                    dp2 = __fmul2_rn(p2[p], ds2);
+                } else {
+                    // Only one row of the pair is reached in the warp: scalar
+                    // work on it, its results in its own half of the pairs.
+                    auto one_row = [&](auto tag) {
+                        constexpr int R = decltype(tag)::value;
+                        const bool cq = c[2 * p + R];
+                        const float sq = R ? s[p].y : s[p].x;
+                        const float p1q = R ? p1[p].y : p1[p].x, p2q = R ? p2[p].y : p2[p].x;
+                        float &Tq = R ? T[p].y : T[p].x;
+                        float &Qq = R ? Q[p].y : Q[p].x;
+                        const float gRq = R ? gR[p].y : gR[p].x, gGq = R ? gG[p].y : gG[p].x;
+                        const float gBq = R ? gB[p].y : gB[p].x, gZq = R ? gZ[p].y : gZ[p].x;
+                        const float gAq = R ? gA[p].y : gA[p].x;
+                        const float raw = cq ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
+                        const float al = fminf(kAlphaMax, raw);
+                        const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
+                        const float Ti = Tq * rom;
+                        const float wq = al * Ti;
+                        const float gc = fmaf(gRq, e3.x, fmaf(gGq, e3.z, fmaf(gBq, e4.x, gZq * e4.z)));
+                        const float dgq = __fmaf_rn(Qq, -1.f, gc);
+                        const float dA = fmaf(Ti, dgq, gAq * rom);
+                        Qq = fmaf(al, dgq, Qq);
+                        Tq = Ti;
+                        const float gl = raw <= kAlphaMax ? dA * raw : 0.f;
+                        const float ds2 = (-2.f * kLn2) * gl;
+                        auto put = [](float v) { return R ? make_float2(0.f, v) : make_float2(v, 0.f); };
+                        dp1 = put(p1q * ds2);
+                        dp2 = put(p2q * ds2);
+                        glo = put(gl);
+                        w = put(wq);
+                    };
+                    if (ma == 0u)
+                        one_row(RowTag<1>{});
+                    else
+                        one_row(RowTag<0>{});
+                }
+                if (p == 0)
+                    pair_sums<true>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
                 else
-                    row(RowTag<0>{});
+                    pair_sums<false>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
             }
-            const uint32_t g = vals[eidx];
-            if (g >= N) continue;
+            float gv[kVGGrads];
+            gv[0] = A[0].x + A[0].y;                                    // du, dv follow from these and m
+            gv[1] = A[1].x + A[1].y;
+            gv[2] = dx.x * gv[0];
+#pragma unroll
+            for (int k = 3; k < kVGGrads; ++k) gv[k] = A[k].x + A[k].y;
+            if (MED) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) gv[9] += eidx + 1u == mi[r] ? gM[r] : 0.f;
+            }
+            float *gp = grads + (size_t)__float_as_uint(x.z) * row;
             if (__popc(cmask) <= 2) {
                 // one or two lanes: their own atomics are cheaper than a reduction
-                if (c0 || c1) {
+                if ((cmask >> lane) & 1u) {
 #pragma unroll
-                    for (int k = 0; k < kVGGrads; ++k) atomicAdd(grads + g * row + k, gv[k]);
+                    for (int k = 0; k < kVGGrads; ++k) atomicAdd(gp + k, gv[k]);
                 }
             } else {
                 int comp;
                 bool valid;
                 const float sum = warp_sum10(gv, lane, comp, valid);
-                if (valid && (lane & 1) == 0) atomicAdd(grads + g * row + comp, sum);
+                if (valid && (lane & 1) == 0) atomicAdd(gp + comp, sum);
             }
         }
         __syncwarp();
@@ -476,9 +558,9 @@ cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
     if (med)
-        blend_fwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS, FwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS, FwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
@@ -487,9 +569,9 @@ cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].d_median_depth != nullptr;
     if (med)
-        blend_bwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS, BwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
     else
-        blend_bwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS>::THREADS, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS, BwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 

@@ -226,8 +226,8 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
         return;
     }
     float sg[kVGGrads];
-#pragma unroll
     float2 *row = reinterpret_cast<float2 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kVGGrads);
+#pragma unroll
     for (int c = 0; c < kVGGrads / 2; ++c) {   // one 40-byte row, 8-byte aligned
         const float2 x = row[c];
         sg[2 * c] = x.x;
