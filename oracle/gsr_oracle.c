@@ -469,7 +469,9 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         const og_proj *p = &P[buf[k].g];
         const double d2 = buf[k].d2;
         margin = fmin2(margin, fabs(d2 - CUTOFF_D2) / CUTOFF_D2);
-        if (prev_z > 0) margin = fmin2(margin, fabs(p->z - prev_z) / p->z);
+        /* an exact tie is ordered by the index on either side, whatever the
+         * precision; only distinct close depths can swap under rounding */
+        if (prev_z > 0 && p->z != prev_z) margin = fmin2(margin, fabs(p->z - prev_z) / p->z);
         prev_z = p->z;
         if (d2 > CUTOFF_D2) continue;
         const double Gexp = exp(-0.5 * d2);
