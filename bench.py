@@ -59,7 +59,9 @@ def parse():
                    help="surfels: the 2-D surfel renderer (with normal and distortion outputs and gradients)")
     p.add_argument("--median", action="store_true", help="also render median depth and feed it a gradient")
     p.add_argument("--densify", action="store_true", help="also gather densification statistics in the backward")
-    p.add_argument("--autotune", action="store_true", help="pick the tile size with the autotuner first")
+    p.add_argument("--binning", default="tile", choices=["tile", "radix"],
+                   help="tile binning strategy: per-tile counting sort (default) or onesweep radix sort")
+    p.add_argument("--autotune", action="store_true", help="pick the tile size and binning with the autotuner first")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -340,8 +342,12 @@ def launches_per_step(rast, win):
     tbits = 1
     while (1 << tbits) < tiles:
         tbits += 1
-    passes = (32 + tbits + 7) // 8
-    return 9 + passes + 1 + 3
+    # init, preprocess, 3 scan kernels, duplicate, histogram, the radix
+    # passes, ranges, blend, loss, blend backward, preprocess backward, pose
+    # sums; per-tile binning sorts the tile bits only and adds 2 tile sorts
+    if rast.binning == "tile":
+        return 13 + (tbits + 7) // 8 + 2
+    return 13 + (32 + tbits + 7) // 8
 
 
 def time_steps(torch, fn, K, flush, events_per_step=None):
@@ -395,11 +401,11 @@ def main():
     tile, tuned = args.tile, None
     if args.autotune:
         from paper_2411_17660_b300 import autotune as A
-        w0 = Window(scene, R.GaussianRasterizer(16), loss=args.loss, primitive=args.primitive)
+        w0 = Window(scene, R.GaussianRasterizer(16, binning=args.binning), loss=args.loss, primitive=args.primitive)
         tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
-        tile = tuned["tile"]
+        tile, args.binning = tuned["tile"], tuned["binning"]
         del w0
-    rast = R.GaussianRasterizer(tile)
+    rast = R.GaussianRasterizer(tile, binning=args.binning)
     opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify)
     win = Window(scene, rast, **opts)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -510,7 +516,7 @@ def main():
         "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
-                   "sh_degree": scene.sh_degree, "tile": tile, "autotune": tuned,
+                   "sh_degree": scene.sh_degree, "tile": tile, "binning": args.binning, "autotune": tuned,
                    "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
                    "primitive": args.primitive,
                    "extras": [k for k, on in (("median depth", args.median), ("densification statistics", args.densify),

@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 2
+#define GSR_ABI_VERSION 3
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -73,13 +73,26 @@ typedef struct {
     int tile;              /* screen tile edge in pixels: 8, 16 or 32 (0 = 16) */
     uint32_t spin_limit;   /* iterations before a bounded device wait gives up (0 = default) */
     int flags;             /* 0, or GSR_TEST_STALL_SORT (test hook, see below) */
+    int binning;           /* GSR_BIN_TILE (0, default) or GSR_BIN_RADIX */
 } gsr_config;
 
 /* Test hook for the bounded-wait path: the first tile of the first radix-sort
  * pass never publishes its digit counts, so the next tile's look-back wait
  * runs out after spin_limit iterations and the call reports GSR_ETIMEOUT
- * (outputs undefined).  Never set outside tests. */
+ * (outputs undefined).  Only GSR_BIN_RADIX has an inter-block wait.  Never set
+ * outside tests. */
 #define GSR_TEST_STALL_SORT 1
+
+/* Tile binning strategies; both give the same list order (by tile, then
+ * depth, then Gaussian index) and so bit-identical results.
+ * GSR_BIN_TILE: a counting sort on the tile (the preprocess counts each
+ *   tile's keys, a scan gives each tile its place, the duplication fills it
+ *   with atomics) and a sort of each tile's (depth, index) words in shared
+ *   memory; no kernel waits on another block.
+ * GSR_BIN_RADIX: one stable onesweep LSD radix sort of all (tile, depth)
+ *   keys, 8 bits per pass, with a bounded decoupled look-back. */
+#define GSR_BIN_TILE 0
+#define GSR_BIN_RADIX 1
 
 /* The Gaussian map (Sec. 3.3: position P, rotation r, scale s, density
  * sigma, SH coefficients).  Device pointers, float32, planar. */

@@ -1,12 +1,15 @@
-"""Tile-size autotuner for the batched rasteriser.
+"""Autotuner of the batched rasteriser's tile size and binning strategy.
 
 The screen tile (8, 16 or 32 pixels) sets how many (Gaussian, tile) keys the
-sort handles and how many warps share a tile's depth-sorted list; which is
-fastest depends on the scene (Gaussian footprints) and the views.  The tuner
-times one forward + backward per candidate on the caller's own inputs (CUDA
-events on the current stream, after warm-up) and keeps the fastest, cached
-per (GPU, N, SH degree, view sizes).  The images do not depend on the tile
-size, so the choice changes only speed.
+sort handles and how many warps share a tile's depth-sorted list; the binning
+strategy ("tile": radix passes over the tile bits and a sort inside each
+tile; "radix": radix passes over tile and depth bits) trades fewer global
+passes against per-tile sorts that grow with the keys per tile.  Which pair
+is fastest depends on the scene (Gaussian footprints) and the views.  The
+tuner times one forward + backward per candidate on the caller's own inputs
+(CUDA events on the current stream, after warm-up) and keeps the fastest,
+cached per (GPU, N, SH degree, view sizes).  The images do not depend on
+either choice, so it changes only speed.
 
 The per-warp entry batch of the blend kernels is the warp width (32 entries
 per chunk, one per lane) and is not a tuning parameter.
@@ -17,7 +20,15 @@ import json
 import os
 from typing import Callable, Dict, Iterable, Optional, Sequence
 
-CANDIDATES = (8, 16, 32)
+TILES = (8, 16, 32)
+BINNINGS = ("tile", "radix")
+CANDIDATES = tuple(f"{t}/{b}" for t in TILES for b in BINNINGS)   # "tile size/binning"
+
+
+def parse(candidate: str):
+    """("16/tile") -> (16, "tile")."""
+    t, b = candidate.split("/")
+    return int(t), b
 
 
 def signature(gpu: str, N: int, sh_degree: int, cams: Sequence) -> str:
@@ -25,12 +36,12 @@ def signature(gpu: str, N: int, sh_degree: int, cams: Sequence) -> str:
     return f"{gpu}|N={N}|deg={sh_degree}|views={views}"
 
 
-def choose(time_ms: Callable[[int], float], candidates: Iterable[int] = CANDIDATES) -> Dict[str, object]:
-    """Times every candidate once with time_ms(tile) and returns the fastest
-    (ties go to the earlier candidate) with all timings."""
-    times = {int(t): float(time_ms(int(t))) for t in candidates}
-    best = min(times, key=lambda t: (times[t], list(times).index(t)))
-    return {"tile": best, "ms": times}
+def choose(time_ms: Callable[[object], float], candidates: Iterable = CANDIDATES) -> Dict[str, object]:
+    """Times every candidate once with time_ms(candidate) and returns the
+    fastest (ties go to the earlier candidate) with all timings."""
+    times = {c: float(time_ms(c)) for c in candidates}
+    best = min(times, key=lambda c: (times[c], list(times).index(c)))
+    return {"best": best, "ms": times}
 
 
 class TileCache:
@@ -56,9 +67,10 @@ class TileCache:
 
 
 def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = None, reps: int = 3,
-         warmup: int = 2, candidates: Iterable[int] = CANDIDATES) -> Dict[str, object]:
+         warmup: int = 2, candidates: Iterable[str] = CANDIDATES) -> Dict[str, object]:
     """Times forward + backward (upstream gradient of ones on the colour) for
-    each tile size on these inputs and returns {"tile": best, "ms": {...}}."""
+    each "tile size/binning" candidate on these inputs and returns
+    {"tile": size, "binning": strategy, "ms": {candidate: ms}}."""
     import torch
 
     from . import render as R
@@ -72,8 +84,9 @@ def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = No
     grads = {k: torch.empty_like(v) for k, v in params.items()}
     d_pose = torch.empty(len(cams), 6, device=params["means"].device)
 
-    def time_ms(tile: int) -> float:
-        rast = R.GaussianRasterizer(tile)
+    def time_ms(candidate: str) -> float:
+        tile, binning = parse(candidate)
+        rast = R.GaussianRasterizer(tile, binning=binning)
         color, depth, alpha, ws = rast.render_forward(params, sh_degree, cams, viewmats)
         ws = rast.alloc_workspace(int(params["means"].shape[1]), cams, int(rast.info(ws).keys * 1.1) + 8192)
 
@@ -93,7 +106,9 @@ def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = No
             best = min(best, start.elapsed_time(end))
         return best
 
-    result = choose(time_ms, candidates)
+    chosen = choose(time_ms, candidates)
+    tile, binning = parse(chosen["best"])
+    result = {"tile": tile, "binning": binning, "ms": chosen["ms"]}
     if cache is not None:
         cache.put(key, result)
     return result

@@ -16,11 +16,12 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgsr.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
-ABI_VERSION = 2   # GSR_ABI_VERSION these structs follow
+ABI_VERSION = 3   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
 TEST_STALL_SORT = 1
+BIN_TILE, BIN_RADIX = 0, 1
 STAGE_EVENTS = 10
 # stage k lasts from event STAGE_SPANS[k][0] to STAGE_SPANS[k][1]
 STAGES = ("preprocess", "scan_duplicate", "sort", "ranges", "blend_fwd", "clear", "blend_bwd", "preprocess_bwd")
@@ -30,7 +31,8 @@ _p = ctypes.c_void_p
 
 
 class Config(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("flags", ctypes.c_int)]
+    _fields_ = [("tile", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("flags", ctypes.c_int),
+                ("binning", ctypes.c_int)]
 
 
 class Gaussians(ctypes.Structure):
@@ -133,9 +135,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 class Context:
     """Owns one gsr_ctx (host memory only)."""
 
-    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0):
+    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: int = BIN_TILE):
         self.lib = load()
-        cfg = Config(tile, spin_limit, flags)
+        cfg = Config(tile, spin_limit, flags, binning)
         h = _p()
         st = self.lib.gsr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:

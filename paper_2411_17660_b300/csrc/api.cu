@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/gsr.h: argument checks, the workspace
 // layout, and the launch sequence of the forward and backward passes.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -15,6 +16,7 @@ struct gsr_ctx {
     int tile = 16;
     uint32_t spin = gsr::kDefaultSpin;
     int flags = 0;
+    int binning = GSR_BIN_TILE;
     int sm_count = 0;
     std::string err;
     struct Rec {
@@ -45,7 +47,7 @@ struct Layout {
     size_t total;
     uint64_t VN;
     uint32_t cap, lb_tiles, scan_blocks, pose_blocks, total_pixels, total_tiles;
-    int passes;
+    int tbits;   // bits of a global tile id
 };
 
 void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layout &L) {
@@ -59,7 +61,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.total_tiles = (uint32_t)tiles;
     int tbits = 1;
     while ((1ull << tbits) < tiles) ++tbits;
-    L.passes = (32 + tbits + 7) / 8;
+    L.tbits = tbits;
     L.cap = (uint32_t)cap;
     L.lb_tiles = (uint32_t)((cap + kSortTile - 1) / kSortTile);
     L.scan_blocks = (uint32_t)((L.VN + kScanChunk - 1) / kScanChunk);
@@ -117,7 +119,7 @@ uint32_t capacity_for(int N, const gsr_view *views, int V, int tile, size_t byte
     return (uint32_t)cap;
 }
 
-Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) {
+Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     char *b = static_cast<char *>(base);
     Ws w;
     w.hdr = reinterpret_cast<WsHeader *>(b + L.hdr);
@@ -138,6 +140,11 @@ Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) 
     w.keys[1] = reinterpret_cast<unsigned long long *>(b + L.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(b + L.vals0);
     w.vals[1] = reinterpret_cast<uint32_t *>(b + L.vals1);
+    // radix: 8-bit passes over (tile, depth bits); per-tile: over the tile id
+    // only, then each tile's words are sorted in shared memory
+    w.bin_tile = ctx.binning == GSR_BIN_TILE;
+    w.passes = w.bin_tile ? (L.tbits + 7) / 8 : (32 + L.tbits + 7) / 8;
+    w.sorted = w.vals[w.bin_tile ? (w.passes + 1) & 1 : w.passes & 1];
     w.hist = reinterpret_cast<uint32_t *>(b + L.hist);
     w.lookback = reinterpret_cast<uint32_t *>(b + L.lookback);
     w.ranges = reinterpret_cast<uint2 *>(b + L.ranges);
@@ -155,9 +162,8 @@ Ws make_ws(void *base, const Layout &L, int N, int V, uint32_t spin, int flags) 
     w.pose_blocks = L.pose_blocks;
     w.total_pixels = L.total_pixels;
     w.total_tiles = L.total_tiles;
-    w.passes = L.passes;
-    w.spin_limit = spin;
-    w.test_flags = flags;
+    w.spin_limit = ctx.spin;
+    w.test_flags = ctx.flags;
     return w;
 }
 
@@ -169,6 +175,10 @@ __global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles) {
         h->key_capacity = cap;
         h->tiles = tiles;
     }
+}
+
+void launch_init(const Ws &w, uint32_t cap, cudaStream_t st) {
+    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, w.total_tiles);
 }
 
 gsr_status fail(gsr_ctx *ctx, gsr_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -329,13 +339,15 @@ extern "C" {
 gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     if (!out) return GSR_EINVAL;
     *out = nullptr;
-    int tile = 16, flags = 0;
+    int tile = 16, flags = 0, binning = GSR_BIN_TILE;
     uint32_t spin = kDefaultSpin;
     if (cfg) {
         if (cfg->tile != 0) tile = cfg->tile;
         if (cfg->spin_limit != 0) spin = cfg->spin_limit;
         if (cfg->flags & ~GSR_TEST_STALL_SORT) return GSR_EINVAL;
         flags = cfg->flags;
+        if (cfg->binning != GSR_BIN_TILE && cfg->binning != GSR_BIN_RADIX) return GSR_EINVAL;
+        binning = cfg->binning;
     }
     if (tile != 8 && tile != 16 && tile != 32) return GSR_EINVAL;
     gsr_ctx *c = new (std::nothrow) gsr_ctx;
@@ -343,6 +355,7 @@ gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     c->tile = tile;
     c->spin = spin;
     c->flags = flags;
+    c->binning = binning;
     *out = c;
     return GSR_OK;
 }
@@ -383,12 +396,12 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
     fill_views(vt, views, nullptr, V, ctx->tile);
-    const Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    const Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     ctx->mark(0, st);
-    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, L.total_tiles);
+    launch_init(w, cap, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_preprocess_fwd(vt, gp, w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
@@ -429,7 +442,7 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
     fill_views(vt, views, grads, V, ctx->tile);
-    const Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    const Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     GradPtrs gout;
     gout.means = out->means;
@@ -475,14 +488,14 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
             vt.v[v].normal = extra[v].normal;
             vt.v[v].distortion = extra[v].distortion;
         }
-    Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     w.surfels = 1;
     w.vg_stride = kVGGradsMax;
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     ctx->mark(0, st);
-    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, L.total_tiles);
+    launch_init(w, cap, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_surfel_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
@@ -526,7 +539,7 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
             vt.v[v].d_normal = extra[v].d_normal;
             vt.v[v].d_distortion = extra[v].d_distortion;
         }
-    Ws w = make_ws(ws_ptr, L, gs->N, V, ctx->spin, ctx->flags);
+    Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     w.surfels = 1;
     w.vg_stride = kVGGradsMax;
     const GaussianPtrs gp = gaussian_ptrs(gs);

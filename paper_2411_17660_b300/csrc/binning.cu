@@ -1,10 +1,26 @@
-// binning.cu -- tile binning of the projected Gaussians: exclusive scan of the
-// per-(view, Gaussian) tile counts, key duplication (key = global tile id in
-// the high 32 bits, FP32 depth bits in the low 32), a hand-written onesweep
-// LSD radix sort of the (key, Gaussian id) pairs, and the [start, end) range
-// of every tile in the sorted list.  All sizes the host cannot know (the key
-// count) are read on the device, so the sequence needs no host sync and can
-// be captured in a CUDA graph.
+// binning.cu -- tile binning of the projected Gaussians: every (view,
+// Gaussian) pair becomes one key per screen tile it touches, the keys are put
+// in (global tile, FP32 depth, Gaussian id) order, and every tile gets its
+// [start, end) range of the sorted list.  An exclusive scan of the per-pair
+// tile counts places each pair's keys; then one of two strategies, with the
+// same result:
+//
+// radix: keys (tile << 32 | depth bits) with the Gaussian id as value, one
+//   stable hand-written onesweep LSD radix sort over all used bits (8 per
+//   pass; equal depths keep the pair order, i.e. the id order), and a boundary
+//   pass for the ranges.
+// per-tile (default): u32 tile keys with (depth bits << 32 | id) words as
+//   values; the onesweep sort runs over the tile bits only (2 passes for up to
+//   65,536 tiles instead of 6), the boundary pass gives the ranges, and each
+//   tile's words -- unique, since a Gaussian meets a tile once -- are sorted
+//   in registers (a warp) or shared memory (a block), which orders them by
+//   depth and then id.
+//
+// All sizes the host cannot know (the key count) are read on the device, so
+// either sequence needs no host sync and can be captured in a CUDA graph.
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.cuh"
 #include "spans.cuh"
 
@@ -17,6 +33,8 @@ constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 
 __device__ __forceinline__ uint32_t key_count(const Ws &ws) { return min(ws.hdr->keys, ws.cap); }
+
+constexpr unsigned long long kNoKey = ~0ull;   // padding, after every real (depth, id) word
 
 // Block-wide exclusive scan of one value per thread (blockDim.x = 32 * W).
 template <typename T, int THREADS>
@@ -139,6 +157,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     if ((int)threadIdx.x >= n) return;
     const size_t i = (size_t)blockIdx.x * 256 + s_pair[threadIdx.x];
     const uint32_t cnt = ws.counts[i];
+    const bool by_tile = ws.bin_tile != 0;
     const uint32_t off_k = ws.offsets[i];
     const uint32_t v = (uint32_t)(i / ws.N), g = (uint32_t)(i - (size_t)v * ws.N);
     const ViewParams &vp = vt.v[v];
@@ -148,6 +167,19 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     uint32_t *vals = ws.vals[0];
     const uint32_t cap = ws.cap;
     uint32_t k = off_k;
+    // the pair's next key: tile t
+    auto emit = [&](uint32_t t) {
+        if (k < cap) {
+            if (by_tile) {
+                vals[k] = t;
+                keys[k] = (zbits << 32) | g;
+            } else {
+                keys[k] = ((unsigned long long)t << 32) | zbits;
+                vals[k] = g;
+            }
+        }
+        ++k;
+    };
     if (ws.surfels) {   // surfels: every tile of the pixel bounds
         const float4 r = ws.rec5[i];
         const int TS = vt.tile;
@@ -156,11 +188,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
         uint32_t emitted = 0;
         for (int ty = py0 / TS; ty <= py1 / TS; ++ty) {
             const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
-            for (int tx = px0 / TS; tx <= px1 / TS; ++tx, ++k, ++emitted)
-                if (k < cap) {
-                    keys[k] = ((unsigned long long)(row + tx) << 32) | zbits;
-                    vals[k] = g;
-                }
+            for (int tx = px0 / TS; tx <= px1 / TS; ++tx, ++emitted) emit(row + tx);
         }
         if (emitted != cnt) set_status(ws.hdr, GSR_EINTERNAL);
         return;
@@ -168,20 +196,35 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     const uint32_t emitted = visit_tile_spans(r0.x, r0.y, r3.y, r3.z, r3.w, r1.x, r1.w, vp.W, vp.H, vt.tile,
                                               [&](int ty, int tx0, int tx1) {
                                                   const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
-                                                  for (int tx = tx0; tx <= tx1; ++tx, ++k) {
-                                                      if (k < cap) {
-                                                          keys[k] = ((unsigned long long)(row + tx) << 32) | zbits;
-                                                          vals[k] = g;
-                                                      }
-                                                  }
+                                                  for (int tx = tx0; tx <= tx1; ++tx) emit(row + tx);
                                               });
     if (emitted != cnt) set_status(ws.hdr, GSR_EINTERNAL);
 }
 
 // ------------------------------------------------------------------ sort
+// Keys and values of the two strategies (radix: u64 (tile, depth) keys, u32
+// ids; per-tile: u32 tile keys, u64 (depth, id) words), double-buffered.
+template <typename K, typename V>
+struct SortBufs {
+    K *k[2];
+    V *v[2];
+};
+
+template <typename K, typename V>
+SortBufs<K, V> sort_bufs(const Ws &ws);
+template <>
+SortBufs<unsigned long long, uint32_t> sort_bufs(const Ws &ws) {
+    return {{ws.keys[0], ws.keys[1]}, {ws.vals[0], ws.vals[1]}};
+}
+template <>
+SortBufs<uint32_t, unsigned long long> sort_bufs(const Ws &ws) {
+    return {{ws.vals[0], ws.vals[1]}, {ws.keys[0], ws.keys[1]}};
+}
+
 // One read of the keys gives the digit histogram of every pass; it also
 // clears the look-back flags of the first pass and the tile counters.
-__global__ void __launch_bounds__(256) sort_hist_kernel(const Ws ws) {
+template <typename K>
+__global__ void __launch_bounds__(256) sort_hist_kernel(const Ws ws, const K *keys) {
     __shared__ uint32_t s_hist[kMaxPasses][kRadix];
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     const uint32_t n = key_count(ws);
@@ -191,16 +234,15 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ws ws) {
     for (size_t i = tid; i < (size_t)ntiles * kRadix; i += stride) ws.lookback[i] = 0u;
     if (tid < kMaxPasses) ws.hdr->sort_counter[tid] = 0u;
     __syncthreads();
-    const unsigned long long *keys = ws.keys[0];
     constexpr int U = 4;   // keys loaded ahead of their shared-memory atomics
     for (size_t i = tid; i < n; i += U * stride) {
-        unsigned long long k[U];
+        K k[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) k[u] = i + u * stride < n ? keys[i + u * stride] : 0ull;
+        for (int u = 0; u < U; ++u) k[u] = i + u * stride < n ? keys[i + u * stride] : K(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (i + u * stride < n)
-                for (int p = 0; p < ws.passes; ++p) atomicAdd(&s_hist[p][(k[u] >> (8 * p)) & 0xff], 1u);
+                for (int p = 0; p < ws.passes; ++p) atomicAdd(&s_hist[p][(uint32_t)(k[u] >> (8 * p)) & 0xff], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ws.passes * kRadix; i += blockDim.x) {
@@ -251,7 +293,9 @@ __device__ __forceinline__ int lookback_round(const uint32_t *col, int hi, uint3
 // still being ranked, polling them is cheap) and, once those are all
 // published, kLookBatch at a time, so that one round trip to L2 advances the
 // walk by up to kLookBatch tiles.
-__global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kernel(const Ws ws, int pass) {
+template <typename K, typename V>
+__global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kernel(const Ws ws, int pass,
+                                                                              const SortBufs<K, V> b) {
     constexpr int WARPS = kSortThreads / 32;
     __shared__ uint32_t s_whist[WARPS][kRadix];
     __shared__ uint32_t s_hist_ex[kRadix];
@@ -259,17 +303,17 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kerne
     __shared__ uint32_t s_glob[kRadix];
     __shared__ uint32_t s_scan[WARPS];
     __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ K s_keys[kSortTile];
+    __shared__ V s_vals[kSortTile];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, d_own = threadIdx.x;
     const uint32_t n = key_count(ws);
     const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
     const int shift = 8 * pass;
-    const unsigned long long *keys_in = ws.keys[pass & 1];
-    const uint32_t *vals_in = ws.vals[pass & 1];
-    unsigned long long *keys_out = ws.keys[(pass + 1) & 1];
-    uint32_t *vals_out = ws.vals[(pass + 1) & 1];
+    const K *keys_in = b.k[pass & 1];
+    const V *vals_in = b.v[pass & 1];
+    K *keys_out = b.k[(pass + 1) & 1];
+    V *vals_out = b.v[(pass + 1) & 1];
     // this thread's digit column of the flags of this pass and of the next ([tile][digit])
     uint32_t *col = ws.lookback + (size_t)(pass & 1) * ws.lb_tiles * kRadix + d_own;
     uint32_t *col_next = ws.lookback + (size_t)((pass + 1) & 1) * ws.lb_tiles * kRadix + d_own;
@@ -289,15 +333,15 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kerne
 
         const uint32_t base = t * kSortTile + warp * (kSortItems * 32);
         uint32_t rank[kSortItems];
-        unsigned long long k[kSortItems];
-        uint32_t val[kSortItems];
+        K k[kSortItems];
+        V val[kSortItems];
         // all loads first: the warp barriers of the ranking below would
         // otherwise serialise them
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const uint32_t idx = base + it * 32 + lane;
-            k[it] = idx < n ? keys_in[idx] : 0ull;
-            val[it] = idx < n ? vals_in[idx] : 0u;
+            k[it] = idx < n ? keys_in[idx] : K(0);
+            val[it] = idx < n ? vals_in[idx] : V(0);
         }
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
@@ -369,7 +413,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kerne
 
         const uint32_t tile_n = min((uint32_t)kSortTile, n - t * kSortTile);
         for (uint32_t j = threadIdx.x; j < tile_n; j += kSortThreads) {
-            const unsigned long long key = s_keys[j];
+            const K key = s_keys[j];
             const uint32_t d = (uint32_t)((key >> shift) & 0xff);
             const uint32_t o = s_glob[d] + j;
             if (o < n) {
@@ -382,18 +426,237 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kerne
 }
 
 // ------------------------------------------------------------------ ranges
-__global__ void __launch_bounds__(256) ranges_kernel(const Ws ws, const unsigned long long *keys) {
+__device__ __forceinline__ uint32_t tile_of(unsigned long long key) { return (uint32_t)(key >> 32); }
+__device__ __forceinline__ uint32_t tile_of(uint32_t key) { return key; }
+
+template <typename K>
+__global__ void __launch_bounds__(256) ranges_kernel(const Ws ws, const K *keys) {
     const uint32_t n = key_count(ws);
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t tile = (uint32_t)(keys[i] >> 32);
+        const uint32_t tile = tile_of(keys[i]);
         if (tile >= ws.total_tiles) {  // only after a reported device error
             set_status(ws.hdr, GSR_EINTERNAL);
             continue;
         }
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != tile) ws.ranges[tile].x = (uint32_t)i;
-        if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != tile) ws.ranges[tile].y = (uint32_t)(i + 1);
+        if (i == 0 || tile_of(keys[i - 1]) != tile) ws.ranges[tile].x = (uint32_t)i;
+        if (i + 1 == n || tile_of(keys[i + 1]) != tile) ws.ranges[tile].y = (uint32_t)(i + 1);
     }
+}
+
+// ------------------------------------------------------------------ per-tile: sort within each tile
+// After the tile-key passes, tile t's (depth bits << 32 | id) words sit in
+// words[start, end) in pair order; ascending words are the list order.  Up to
+// kWarpSortMax words a warp sorts them in registers (a bitonic network over
+// 32 E words, word e * 32 + lane in lane's x[e]); up to kBlockSortMid the
+// block of the tile's warp sorts them in shared memory; beyond, a block with
+// kBlockSortCap words of shared memory sorts them, as runs merged pairwise
+// through the free word buffer when there are more.  The ids go to ws.sorted.
+constexpr int kWarpSortMax = 256;
+constexpr int kBlockSortMid = 2048;
+constexpr int kTilesPerSortBlock = 8;   // one warp each
+constexpr int kBlockSortCap = 16384;
+constexpr int kBigSortThreads = 1024;
+constexpr int kMergeItems = 16;         // outputs per thread per merge-path step
+
+__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long x, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E], int lane) {
+    constexpr int M = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= M; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const bool up = ((e * 32 + lane) & k) == 0;   // this pair sorts ascending
+                if (j >= 32) {   // partner word in the same lane
+                    const int f = e ^ (j >> 5);
+                    if (f > e) {
+                        const unsigned long long a = x[e], b = x[f];
+                        const bool sw = (a > b) == up;
+                        x[e] = sw ? b : a;
+                        x[f] = sw ? a : b;
+                    }
+                } else {         // partner word in lane ^ j
+                    const unsigned long long y = shfl_xor64(x[e], j);
+                    x[e] = ((lane & j) == 0) == up ? min(x[e], y) : max(x[e], y);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_tile(const unsigned long long *in, uint32_t *out, uint32_t n, int lane) {
+    unsigned long long x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)(e * 32 + lane);
+        x[e] = i < n ? in[i] : kNoKey;
+    }
+    warp_bitonic<E>(x, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)(e * 32 + lane);
+        if (i < n) out[i] = (uint32_t)x[e];
+    }
+}
+
+// Bitonic sort of s[0, M), M a power of two, by a whole block of THREADS.
+template <int THREADS>
+__device__ __forceinline__ void block_bitonic(unsigned long long *s, uint32_t M) {
+    for (uint32_t k = 2; k <= M; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t c = threadIdx.x; c < M / 2; c += THREADS) {
+                const uint32_t i = ((c & ~(j - 1)) << 1) | (c & (j - 1)), l = i | j;
+                const unsigned long long a = s[i], b = s[l];
+                if ((a > b) == ((i & k) == 0)) {
+                    s[i] = b;
+                    s[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pow2_at_least(uint32_t n) { return n <= 1 ? 1u : 1u << (32 - __clz(n - 1)); }
+
+// Sorts the m words of src (m <= the shared-memory room) with the whole block
+// and writes them to dst (words) or, if ids is set, their ids to ids.
+template <int THREADS>
+__device__ __forceinline__ void block_sort_run(const unsigned long long *src, uint32_t m, unsigned long long *s,
+                                               unsigned long long *dst, uint32_t *ids) {
+    const uint32_t M = pow2_at_least(m);
+    for (uint32_t i = threadIdx.x; i < M; i += THREADS) s[i] = i < m ? src[i] : kNoKey;
+    __syncthreads();
+    block_bitonic<THREADS>(s, M);
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
+        if (ids)
+            ids[i] = (uint32_t)s[i];
+        else
+            dst[i] = s[i];
+    }
+    __syncthreads();
+}
+
+// Tiles of up to kBlockSortMid keys: warp w of block b takes tile
+// 8 b + w if it holds at most kWarpSortMax keys; then the block sorts, one
+// after another, those of its 8 tiles that hold more (and at most
+// kBlockSortMid).
+__global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(const Ws ws) {
+    constexpr int THREADS = 32 * kTilesPerSortBlock;
+    __shared__ unsigned long long s_sort[kBlockSortMid];
+    const int lane = threadIdx.x & 31;
+    const uint32_t t0 = blockIdx.x * kTilesPerSortBlock;
+    const unsigned long long *words = ws.keys[ws.passes & 1];
+    uint32_t *ids = ws.sorted;
+    {
+        const uint32_t t = t0 + (threadIdx.x >> 5);
+        if (t < ws.total_tiles) {
+            const uint2 r = ws.ranges[t];
+            const uint32_t n = r.y - r.x;
+            if (n == 1) {
+                if (lane == 0) ids[r.x] = (uint32_t)words[r.x];
+            } else if (n == 0) {
+            } else if (n <= 32) {
+                warp_sort_tile<1>(words + r.x, ids + r.x, n, lane);
+            } else if (n <= 64) {
+                warp_sort_tile<2>(words + r.x, ids + r.x, n, lane);
+            } else if (n <= 128) {
+                warp_sort_tile<4>(words + r.x, ids + r.x, n, lane);
+            } else if (n <= kWarpSortMax) {
+                warp_sort_tile<8>(words + r.x, ids + r.x, n, lane);
+            }
+        }
+    }
+    for (int w = 0; w < kTilesPerSortBlock; ++w) {
+        const uint32_t t = t0 + w;
+        if (t >= ws.total_tiles) break;
+        const uint2 r = ws.ranges[t];
+        const uint32_t n = r.y - r.x;
+        if (n > (uint32_t)kWarpSortMax && n <= (uint32_t)kBlockSortMid)
+            block_sort_run<THREADS>(words + r.x, n, s_sort, nullptr, ids + r.x);
+    }
+}
+
+// Merge of the sorted runs A[0, na) and B[0, nb) (distinct words) into C:
+// each thread finds where its kMergeItems outputs start on the merge path by
+// a binary search, then merges them sequentially.
+__device__ __forceinline__ void block_merge(const unsigned long long *A, uint32_t na, const unsigned long long *B,
+                                            uint32_t nb, unsigned long long *C) {
+    const uint32_t n = na + nb;
+    for (uint32_t d0 = threadIdx.x * kMergeItems; d0 < n; d0 += kBigSortThreads * kMergeItems) {
+        uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = min(d0, na);
+        while (lo < hi) {   // the number of A's words among the first d0 outputs
+            const uint32_t m = (lo + hi) >> 1;
+            if (A[m] < B[d0 - m - 1])
+                lo = m + 1;
+            else
+                hi = m;
+        }
+        uint32_t ia = lo, ib = d0 - lo;
+        const uint32_t d1 = min(d0 + kMergeItems, n);
+        for (uint32_t d = d0; d < d1; ++d) {
+            const bool from_a = ib >= nb || (ia < na && A[ia] < B[ib]);
+            C[d] = from_a ? A[ia++] : B[ib++];
+        }
+    }
+}
+
+// Tiles of more than kBlockSortMid keys, a block each in turn.
+__global__ void __launch_bounds__(kBigSortThreads) tile_sort_big_kernel(const Ws ws) {
+    extern __shared__ unsigned long long s_sort[];   // kBlockSortCap words
+    uint32_t *ids = ws.sorted;
+    for (uint32_t t = blockIdx.x; t < ws.total_tiles; t += gridDim.x) {
+        const uint2 r = ws.ranges[t];
+        const uint32_t n = r.y - r.x;
+        if (n <= (uint32_t)kBlockSortMid) continue;
+        unsigned long long *a = ws.keys[ws.passes & 1] + r.x, *b = ws.keys[(ws.passes + 1) & 1] + r.x;
+        if (n <= (uint32_t)kBlockSortCap) {
+            block_sort_run<kBigSortThreads>(a, n, s_sort, nullptr, ids + r.x);
+            continue;
+        }
+        for (uint32_t c0 = 0; c0 < n; c0 += kBlockSortCap)
+            block_sort_run<kBigSortThreads>(a + c0, min(n - c0, (uint32_t)kBlockSortCap), s_sort, a + c0, nullptr);
+        for (uint32_t w = kBlockSortCap; w < n; w <<= 1) {
+            for (uint32_t lo = 0; lo < n; lo += 2 * w) {
+                const uint32_t mid = min(lo + w, n), hi = min(lo + 2 * w, n);
+                block_merge(a + lo, mid - lo, a + mid, hi - mid, b + lo);
+            }
+            __syncthreads();
+            unsigned long long *x = a;
+            a = b;
+            b = x;
+        }
+        for (uint32_t i = threadIdx.x; i < n; i += kBigSortThreads) ids[r.x + i] = (uint32_t)a[i];
+        __syncthreads();
+    }
+}
+
+template <typename K, typename V>
+cudaError_t launch_radix(const Ws &ws, int sm_count, cudaStream_t st) {
+    const SortBufs<K, V> b = sort_bufs<K, V>(ws);
+    sort_hist_kernel<K><<<sm_count * 4, 256, 0, st>>>(ws, b.k[0]);
+    for (int p = 0; p < ws.passes; ++p)
+        onesweep_kernel<K, V><<<sm_count * kSortBlocksPerSM, kSortThreads, 0, st>>>(ws, p, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges_of(const Ws &ws, int sm_count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * ws.total_tiles, st);
+    if (e != cudaSuccess || ws.VN == 0) return e;
+    if (ws.bin_tile)
+        ranges_kernel<uint32_t><<<sm_count * 4, 256, 0, st>>>(ws, ws.vals[ws.passes & 1]);
+    else
+        ranges_kernel<unsigned long long><<<sm_count * 4, 256, 0, st>>>(ws, ws.keys[ws.passes & 1]);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -409,18 +672,36 @@ cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_
     return cudaGetLastError();
 }
 
+// Per-tile binning also makes the ranges and sorts within the tiles here.
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
-    if (ws.VN == 0) return cudaSuccess;
-    sort_hist_kernel<<<sm_count * 4, 256, 0, st>>>(ws);
-    for (int p = 0; p < ws.passes; ++p) onesweep_kernel<<<sm_count * kSortBlocksPerSM, kSortThreads, 0, st>>>(ws, p);
+    if (!ws.bin_tile) return ws.VN == 0 ? cudaSuccess : launch_radix<unsigned long long, uint32_t>(ws, sm_count, st);
+    cudaError_t e = ws.VN == 0 ? cudaSuccess : launch_radix<uint32_t, unsigned long long>(ws, sm_count, st);
+    if (e == cudaSuccess) e = launch_ranges_of(ws, sm_count, st);   // clears the ranges even with no pairs
+    if (e != cudaSuccess || ws.VN == 0 || ws.total_tiles == 0) return e;
+    tile_sort_kernel<<<(ws.total_tiles + kTilesPerSortBlock - 1) / kTilesPerSortBlock, 32 * kTilesPerSortBlock, 0,
+                       st>>>(ws);
+    // more than 48 KB of dynamic shared memory needs an opt-in, once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64 || !done[dev]) {
+            e = cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kBlockSortCap * sizeof(unsigned long long)));
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) done[dev] = true;
+        }
+    }
+    const unsigned blocks = std::min<unsigned>(ws.total_tiles, (unsigned)sm_count);
+    tile_sort_big_kernel<<<blocks, kBigSortThreads, kBlockSortCap * sizeof(unsigned long long), st>>>(ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const Ws &ws, int sm_count, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * ws.total_tiles, st);
-    if (e != cudaSuccess || ws.VN == 0) return e;
-    ranges_kernel<<<sm_count * 4, 256, 0, st>>>(ws, ws.keys[ws.passes & 1]);
-    return cudaGetLastError();
+    if (ws.bin_tile) return cudaSuccess;   // made by launch_sort
+    return launch_ranges_of(ws, sm_count, st);
 }
 
 }  // namespace gsr

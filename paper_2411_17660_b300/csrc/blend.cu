@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
-    const uint32_t *vals = ws.vals[ws.passes & 1];
+    const uint32_t *vals = ws.sorted;
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
-    const uint32_t *vals = ws.vals[ws.passes & 1];
+    const uint32_t *vals = ws.sorted;
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
     const float2 lx2 = make_float2(lxf, lxf);

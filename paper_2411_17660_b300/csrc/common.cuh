@@ -97,11 +97,17 @@ struct Ws {
     float *aux;              // surfels: [2][total_pixels] sum w z, sum w z^2 of the forward
     int surfels;             // 1: records, tile coverage and gradient rows are the surfel ones
     uint32_t vg_stride;      // floats per (Gaussian, view) gradient row: 10, or 16 for surfels
+    // Binning buffers, double-buffered by pass parity.  Radix: keys =
+    // (tile << 32 | depth bits), vals = Gaussian id.  Per-tile: the u32 tile
+    // keys live in vals[] and the (depth bits << 32 | Gaussian id) words in
+    // keys[] (tile_keys / tile_words below).
     unsigned long long *keys[2];
     uint32_t *vals[2];
+    uint32_t *sorted;        // [keys] Gaussian ids in (tile, depth, id) order
+    int bin_tile;
     uint32_t *hist;          // [kMaxPasses][256]
     uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
-    uint2 *ranges;           // [total_tiles]
+    uint2 *ranges;           // [total_tiles] [start, end) in the sorted list
     float *T_final;          // [total_pixels]
     uint32_t *last;          // [total_pixels] last contributor index + 1
     uint32_t *median;        // [total_pixels] median-depth contributor index + 1 (0: none)

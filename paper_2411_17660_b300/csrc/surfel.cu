@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS) surfel_blend_fwd_kernel(co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Tile wt = tile_of<TS>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
-    const uint32_t *vals = ws.vals[ws.passes & 1];
+    const uint32_t *vals = ws.sorted;
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
 
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS, Shape<TS>::BWD_BLOCKS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Tile wt = tile_of<TS>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
-    const uint32_t *vals = ws.vals[ws.passes & 1];
+    const uint32_t *vals = ws.sorted;
     const size_t N = ws.N, vN = (size_t)wt.v * N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
     const float ox = (float)wt.X0 - vp.cx, oy = (float)wt.Y0 - vp.cy;

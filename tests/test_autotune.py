@@ -4,11 +4,16 @@ from paper_2411_17660_b300.render import Intrinsics
 
 
 def test_choose_picks_fastest_and_breaks_ties_in_order():
-    times = {8: 3.0, 16: 1.5, 32: 2.0}
-    r = A.choose(lambda t: times[t])
-    assert r["tile"] == 16 and r["ms"] == times
-    r = A.choose(lambda t: 1.0)
-    assert r["tile"] == 8
+    times = {"8/tile": 3.0, "8/radix": 2.5, "16/tile": 1.5, "16/radix": 1.7, "32/tile": 2.0, "32/radix": 1.6}
+    r = A.choose(lambda c: times[c])
+    assert r["best"] == "16/tile" and r["ms"] == times
+    r = A.choose(lambda c: 1.0)
+    assert r["best"] == A.CANDIDATES[0]
+
+
+def test_candidates_cover_every_tile_size_and_binning():
+    assert {A.parse(c) for c in A.CANDIDATES} == {(t, b) for t in A.TILES for b in A.BINNINGS}
+    assert A.parse("32/radix") == (32, "radix")
 
 
 def test_signature_distinguishes_views_and_sizes():

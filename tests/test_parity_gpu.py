@@ -113,15 +113,15 @@ def test_capacity_overflow_is_reported_then_grown():
 
 
 def test_bounded_lookback_gives_up_with_status():
-    """Test hook: the first sort tile never publishes its digit counts, so the
+    """Test hook (radix binning): the first sort tile never publishes its digit counts, so the
     next tile's bounded wait must run out and report GSR_ETIMEOUT; the
     context and the device stay usable."""
     sc = REDUCED["uneven"]()
     params, cams, vm = U.to_device(sc)
-    ok = R.GaussianRasterizer(16)
+    ok = R.GaussianRasterizer(16, binning="radix")
     _, _, _, ws = ok.render_forward(params, sc.sh_degree, cams, vm)
     assert ok.info(ws).keys > 2 * 3072, "needs at least two sort tiles"
-    stall = R.GaussianRasterizer(16, spin_limit=2000, flags=B.TEST_STALL_SORT)
+    stall = R.GaussianRasterizer(16, spin_limit=2000, flags=B.TEST_STALL_SORT, binning="radix")
     P = sum(c.H * c.W for c in cams)
     color = torch.empty(3 * P, device="cuda")
     stall.forward_raw(params, sc.sh_degree, cams, vm, ws, color, None, None)
@@ -273,7 +273,7 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path):
     params, cams, vm = U.to_device(sc)
     cache = A.TileCache(str(tmp_path / "tiles.json"))
     r = A.tune(params, sc.sh_degree, cams, vm, cache=cache, reps=2)
-    assert r["tile"] in A.CANDIDATES and set(r["ms"]) == set(A.CANDIDATES)
+    assert r["tile"] in A.TILES and r["binning"] in A.BINNINGS and set(r["ms"]) == set(A.CANDIDATES)
     assert A.tune(params, sc.sh_degree, cams, vm, cache=cache) == r
 
 

@@ -27,8 +27,8 @@ def surfel_scene(name="window"):
     return scenes.config_uneven(N=1200, V=3, res_scale=0.08)
 
 
-def gpu_surfels(sc, tile=16):
-    rast = R.GaussianRasterizer(tile)
+def gpu_surfels(sc, tile=16, binning="tile"):
+    rast = R.GaussianRasterizer(tile, binning=binning)
     params, cams, vm = U.to_device(sc)
     P = R.pixel_offsets(cams)[-1]
     ws = rast.alloc_workspace(sc.N, cams, 1 << 20)
