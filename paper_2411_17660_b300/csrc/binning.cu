@@ -449,14 +449,16 @@ __global__ void __launch_bounds__(256) ranges_kernel(const Ws ws, const K *keys)
 // words[start, end) in pair order; ascending words are the list order.  Up to
 // kWarpSortMax words a warp sorts them in registers (a bitonic network over
 // 32 E words, word e * 32 + lane in lane's x[e]); up to kBlockSortMid the
-// block of the tile's warp sorts them in shared memory; beyond, a block with
-// kBlockSortCap words of shared memory sorts them, as runs merged pairwise
-// through the free word buffer when there are more.  The ids go to ws.sorted.
+// block of the tile's warp sorts them in shared memory by a radix sort of the
+// depth bits; beyond, a block with kBlockSortCap words of shared memory does,
+// as runs merged pairwise through the free word buffer when there are more.
+// The ids go to ws.sorted.
 constexpr int kWarpSortMax = 256;
 constexpr int kBlockSortMid = 2048;
 constexpr int kTilesPerSortBlock = 8;   // one warp each
 constexpr int kBlockSortCap = 16384;
 constexpr int kBigSortThreads = 1024;
+constexpr size_t kBigSortSmem = kBlockSortCap * sizeof(unsigned long long) + (kBigSortThreads / 32) * kRadix * 4;
 constexpr int kMergeItems = 16;         // outputs per thread per merge-path step
 
 __device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long x, int m) {
@@ -508,35 +510,103 @@ __device__ __forceinline__ void warp_sort_tile(const unsigned long long *in, uin
     }
 }
 
-// Bitonic sort of s[0, M), M a power of two, by a whole block of THREADS.
-template <int THREADS>
-__device__ __forceinline__ void block_bitonic(unsigned long long *s, uint32_t M) {
-    for (uint32_t k = 2; k <= M; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t c = threadIdx.x; c < M / 2; c += THREADS) {
-                const uint32_t i = ((c & ~(j - 1)) << 1) | (c & (j - 1)), l = i | j;
-                const unsigned long long a = s[i], b = s[l];
-                if ((a > b) == ((i & k) == 0)) {
-                    s[i] = b;
-                    s[l] = a;
-                }
-            }
-            __syncthreads();
+// Stable LSD radix sort of the n <= THREADS * ITEMS words in s by their depth
+// bits (the high halves), 8 bits per pass, skipping the digits that are the
+// same in every word.  The words arrive in id order (the tile-key passes are
+// stable and keys are emitted in pair order), so equal depths stay in id
+// order.  Ranking as in onesweep_kernel: warp w takes words
+// [w 32 ITEMS, (w + 1) 32 ITEMS) in order, ranks them per digit with
+// __match_any_sync and per-warp counters, and the (digit, warp) offsets come
+// from one scan.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ void block_radix_depth(unsigned long long *s, uint32_t n, uint32_t (*s_whist)[kRadix],
+                                                  uint32_t *s_red) {
+    static_assert(THREADS >= kRadix, "one thread per digit");
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = (uint32_t)warp * (ITEMS * 32);
+    uint32_t vor = 0u, vand = ~0u;
+    for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+        const uint32_t d = (uint32_t)(s[i] >> 32);
+        vor |= d;
+        vand &= d;
+    }
+    vor = __reduce_or_sync(0xffffffffu, vor);
+    vand = __reduce_and_sync(0xffffffffu, vand);
+    if (lane == 0) {
+        s_red[warp] = vor;
+        s_red[WARPS + warp] = vand;
+    }
+    __syncthreads();
+    uint32_t o = 0u, a = ~0u;
+    for (int w = 0; w < WARPS; ++w) {
+        o |= s_red[w];
+        a &= s_red[WARPS + w];
+    }
+    const uint32_t differ = o ^ a;   // depth bits that are not the same in every word
+    __syncthreads();
+    for (int pass = 0; pass < 4; ++pass) {
+        if (((differ >> (8 * pass)) & 0xffu) == 0u) continue;
+        const int shift = 32 + 8 * pass;
+        unsigned long long x[ITEMS];
+        uint32_t rank[ITEMS];
+        for (int d = lane; d < kRadix; d += 32) s_whist[warp][d] = 0u;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const uint32_t idx = base + it * 32 + lane;
+            x[it] = idx < n ? s[idx] : 0ull;
         }
+        __syncthreads();   // all words are in registers before the scatter overwrites s
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const bool valid = base + it * 32 + lane < n;
+            const uint32_t d = valid ? (uint32_t)(x[it] >> shift) & 0xffu : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (valid && lane == leader) {
+                old = s_whist[warp][d];
+                s_whist[warp][d] = old + __popc(peers);
+            }
+            rank[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lanemask_lt());
+            __syncwarp();
+        }
+        __syncthreads();
+        // offsets: digit-major, then warp order
+        uint32_t cnt = 0;
+        if (threadIdx.x < kRadix)
+            for (int w = 0; w < WARPS; ++w) cnt += s_whist[w][threadIdx.x];
+        uint32_t total;
+        const uint32_t start = block_exclusive_scan<uint32_t, THREADS>(cnt, s_red, total);
+        if (threadIdx.x < kRadix) {
+            uint32_t c = start;
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t t = s_whist[w][threadIdx.x];
+                s_whist[w][threadIdx.x] = c;
+                c += t;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            if (base + it * 32 + lane < n) {
+                const uint32_t d = (uint32_t)(x[it] >> shift) & 0xffu;
+                s[s_whist[warp][d] + rank[it]] = x[it];
+            }
+        }
+        __syncthreads();
     }
 }
 
-__device__ __forceinline__ uint32_t pow2_at_least(uint32_t n) { return n <= 1 ? 1u : 1u << (32 - __clz(n - 1)); }
-
-// Sorts the m words of src (m <= the shared-memory room) with the whole block
-// and writes them to dst (words) or, if ids is set, their ids to ids.
-template <int THREADS>
+// Sorts the m words of src (m <= THREADS * ITEMS) with the whole block and
+// writes them to dst (words) or, if ids is set, their ids to ids.
+template <int THREADS, int ITEMS>
 __device__ __forceinline__ void block_sort_run(const unsigned long long *src, uint32_t m, unsigned long long *s,
+                                               uint32_t (*s_whist)[kRadix], uint32_t *s_red,
                                                unsigned long long *dst, uint32_t *ids) {
-    const uint32_t M = pow2_at_least(m);
-    for (uint32_t i = threadIdx.x; i < M; i += THREADS) s[i] = i < m ? src[i] : kNoKey;
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) s[i] = src[i];
     __syncthreads();
-    block_bitonic<THREADS>(s, M);
+    block_radix_depth<THREADS, ITEMS>(s, m, s_whist, s_red);
     for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
         if (ids)
             ids[i] = (uint32_t)s[i];
@@ -553,36 +623,37 @@ __device__ __forceinline__ void block_sort_run(const unsigned long long *src, ui
 __global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(const Ws ws) {
     constexpr int THREADS = 32 * kTilesPerSortBlock;
     __shared__ unsigned long long s_sort[kBlockSortMid];
+    __shared__ uint32_t s_whist[kTilesPerSortBlock][kRadix];
+    __shared__ uint32_t s_red[2 * kTilesPerSortBlock];
+    __shared__ uint2 s_range[kTilesPerSortBlock];
     const int lane = threadIdx.x & 31;
     const uint32_t t0 = blockIdx.x * kTilesPerSortBlock;
     const unsigned long long *words = ws.keys[ws.passes & 1];
     uint32_t *ids = ws.sorted;
     {
         const uint32_t t = t0 + (threadIdx.x >> 5);
-        if (t < ws.total_tiles) {
-            const uint2 r = ws.ranges[t];
-            const uint32_t n = r.y - r.x;
-            if (n == 1) {
-                if (lane == 0) ids[r.x] = (uint32_t)words[r.x];
-            } else if (n == 0) {
-            } else if (n <= 32) {
-                warp_sort_tile<1>(words + r.x, ids + r.x, n, lane);
-            } else if (n <= 64) {
-                warp_sort_tile<2>(words + r.x, ids + r.x, n, lane);
-            } else if (n <= 128) {
-                warp_sort_tile<4>(words + r.x, ids + r.x, n, lane);
-            } else if (n <= kWarpSortMax) {
-                warp_sort_tile<8>(words + r.x, ids + r.x, n, lane);
-            }
+        const uint2 r = t < ws.total_tiles ? ws.ranges[t] : make_uint2(0u, 0u);
+        if (lane == 0) s_range[threadIdx.x >> 5] = r;
+        const uint32_t n = r.y - r.x;
+        if (n == 1) {
+            if (lane == 0) ids[r.x] = (uint32_t)words[r.x];
+        } else if (n >= 2 && n <= 32) {
+            warp_sort_tile<1>(words + r.x, ids + r.x, n, lane);
+        } else if (n > 32 && n <= 64) {
+            warp_sort_tile<2>(words + r.x, ids + r.x, n, lane);
+        } else if (n > 64 && n <= 128) {
+            warp_sort_tile<4>(words + r.x, ids + r.x, n, lane);
+        } else if (n > 128 && n <= kWarpSortMax) {
+            warp_sort_tile<8>(words + r.x, ids + r.x, n, lane);
         }
     }
+    __syncthreads();
     for (int w = 0; w < kTilesPerSortBlock; ++w) {
-        const uint32_t t = t0 + w;
-        if (t >= ws.total_tiles) break;
-        const uint2 r = ws.ranges[t];
+        const uint2 r = s_range[w];
         const uint32_t n = r.y - r.x;
         if (n > (uint32_t)kWarpSortMax && n <= (uint32_t)kBlockSortMid)
-            block_sort_run<THREADS>(words + r.x, n, s_sort, nullptr, ids + r.x);
+            block_sort_run<THREADS, kBlockSortMid / THREADS>(words + r.x, n, s_sort, s_whist, s_red, nullptr,
+                                                              ids + r.x);
     }
 }
 
@@ -610,32 +681,52 @@ __device__ __forceinline__ void block_merge(const unsigned long long *A, uint32_
     }
 }
 
-// Tiles of more than kBlockSortMid keys, a block each in turn.
+// Tiles of more than kBlockSortMid keys, a block each in turn.  Block b
+// looks at tiles b, b + G, b + 2G, ... (G blocks), a thread per tile at a
+// time, and lists the big ones in shared memory first.
 __global__ void __launch_bounds__(kBigSortThreads) tile_sort_big_kernel(const Ws ws) {
-    extern __shared__ unsigned long long s_sort[];   // kBlockSortCap words
+    constexpr int ITEMS = kBlockSortCap / kBigSortThreads;
+    extern __shared__ unsigned long long s_sort[];   // kBlockSortCap words, then the counters
+    uint32_t(*s_whist)[kRadix] = reinterpret_cast<uint32_t(*)[kRadix]>(s_sort + kBlockSortCap);
+    __shared__ uint32_t s_red[2 * (kBigSortThreads / 32)];
+    __shared__ uint32_t s_big[kBigSortThreads];
+    __shared__ uint32_t s_nbig;
     uint32_t *ids = ws.sorted;
-    for (uint32_t t = blockIdx.x; t < ws.total_tiles; t += gridDim.x) {
-        const uint2 r = ws.ranges[t];
-        const uint32_t n = r.y - r.x;
-        if (n <= (uint32_t)kBlockSortMid) continue;
-        unsigned long long *a = ws.keys[ws.passes & 1] + r.x, *b = ws.keys[(ws.passes + 1) & 1] + r.x;
-        if (n <= (uint32_t)kBlockSortCap) {
-            block_sort_run<kBigSortThreads>(a, n, s_sort, nullptr, ids + r.x);
-            continue;
+    const size_t G = gridDim.x;
+    for (size_t first = blockIdx.x; first < ws.total_tiles; first += G * kBigSortThreads) {
+        if (threadIdx.x == 0) s_nbig = 0u;
+        __syncthreads();
+        const size_t tt = first + threadIdx.x * G;
+        if (tt < ws.total_tiles) {
+            const uint2 r = ws.ranges[tt];
+            if (r.y - r.x > (uint32_t)kBlockSortMid) s_big[atomicAdd(&s_nbig, 1u)] = (uint32_t)tt;
         }
-        for (uint32_t c0 = 0; c0 < n; c0 += kBlockSortCap)
-            block_sort_run<kBigSortThreads>(a + c0, min(n - c0, (uint32_t)kBlockSortCap), s_sort, a + c0, nullptr);
-        for (uint32_t w = kBlockSortCap; w < n; w <<= 1) {
-            for (uint32_t lo = 0; lo < n; lo += 2 * w) {
-                const uint32_t mid = min(lo + w, n), hi = min(lo + 2 * w, n);
-                block_merge(a + lo, mid - lo, a + mid, hi - mid, b + lo);
+        __syncthreads();
+        const uint32_t nbig = s_nbig;
+        for (uint32_t q = 0; q < nbig; ++q) {
+            const uint2 r = ws.ranges[s_big[q]];
+            const uint32_t n = r.y - r.x;
+            unsigned long long *a = ws.keys[ws.passes & 1] + r.x, *b = ws.keys[(ws.passes + 1) & 1] + r.x;
+            if (n <= (uint32_t)kBlockSortCap) {
+                block_sort_run<kBigSortThreads, ITEMS>(a, n, s_sort, s_whist, s_red, nullptr, ids + r.x);
+                continue;
             }
+            for (uint32_t c0 = 0; c0 < n; c0 += kBlockSortCap)
+                block_sort_run<kBigSortThreads, ITEMS>(a + c0, min(n - c0, (uint32_t)kBlockSortCap), s_sort, s_whist,
+                                                       s_red, a + c0, nullptr);
+            for (uint32_t w = kBlockSortCap; w < n; w <<= 1) {
+                for (uint32_t lo = 0; lo < n; lo += 2 * w) {
+                    const uint32_t mid = min(lo + w, n), hi = min(lo + 2 * w, n);
+                    block_merge(a + lo, mid - lo, a + mid, hi - mid, b + lo);
+                }
+                __syncthreads();
+                unsigned long long *x = a;
+                a = b;
+                b = x;
+            }
+            for (uint32_t i = threadIdx.x; i < n; i += kBigSortThreads) ids[r.x + i] = (uint32_t)a[i];
             __syncthreads();
-            unsigned long long *x = a;
-            a = b;
-            b = x;
         }
-        for (uint32_t i = threadIdx.x; i < n; i += kBigSortThreads) ids[r.x + i] = (uint32_t)a[i];
         __syncthreads();
     }
 }
@@ -688,14 +779,13 @@ cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 0 || dev >= 64 || !done[dev]) {
-            e = cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kBlockSortCap * sizeof(unsigned long long)));
+            e = cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigSortSmem);
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) done[dev] = true;
         }
     }
     const unsigned blocks = std::min<unsigned>(ws.total_tiles, (unsigned)sm_count);
-    tile_sort_big_kernel<<<blocks, kBigSortThreads, kBlockSortCap * sizeof(unsigned long long), st>>>(ws);
+    tile_sort_big_kernel<<<blocks, kBigSortThreads, kBigSortSmem, st>>>(ws);
     return cudaGetLastError();
 }
 
