@@ -18,7 +18,7 @@
 // and the colour/depth behind each entry accumulate as B <- B(1-a) + c a.
 // Per-Gaussian gradients of the 64 pixels of a warp are summed in registers
 // (two pixels per lane) and with a transposing warp butterfly before one set
-// of global atomics per (warp, Gaussian); when at most two lanes touch a
+// of global atomics per (warp, Gaussian); when at most four lanes touch a
 // Gaussian they issue their atomics directly instead.
 //
 // In the backward, a lane's pixels share their column, hence dx: the
@@ -535,8 +535,9 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 for (int r = 0; r < NR; ++r) gv[9] += eidx + 1u == mi[r] ? gM[r] : 0.f;
             }
             float *gp = grads + (size_t)__float_as_uint(x.z) * row;
-            if (__popc(cmask) <= 2) {
-                // one or two lanes: their own atomics are cheaper than a reduction
+            if (__popc(cmask) <= 4) {
+                // up to four lanes: their own atomics are cheaper than a reduction
+                // (measured: 0.259 ms against 0.261 with two, 0.260 with eight)
                 if ((cmask >> lane) & 1u) {
 #pragma unroll
                     for (int k = 0; k < kVGGrads; ++k) atomicAdd(gp + k, gv[k]);
