@@ -16,8 +16,8 @@
 // The backward recomputes the blend state from the stored final
 // transmittance and last contributor: walking back, T_i = T_{i+1}/(1-alpha_i)
 // and the colour/depth behind each entry accumulate as B <- B(1-a) + c a.
-// Per-Gaussian gradients of the 64 pixels of a warp are summed in registers
-// (two pixels per lane) and with a transposing warp butterfly before one set
+// Per-Gaussian gradients of the pixels of a warp are summed in registers
+// (four pixels per lane) and with a transposing warp butterfly before one set
 // of global atomics per (warp, Gaussian); when at most four lanes touch a
 // Gaussian they issue their atomics directly instead.
 //
