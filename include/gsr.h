@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 3
+#define GSR_ABI_VERSION 4
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -307,6 +307,71 @@ gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events);
 gsr_status gsr_render_noalloc(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
                               int32_t *status, gsr_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Density control of the map between optimisation steps (Sec. 3.3, last
+ * paragraph; Supp. "Monte Carlo Markov Chain Gaussian Splatting"): the 3DGS
+ * adaptive density control driven by the statistics of gsr_grads.densify_*,
+ * and the MCMC strategy's relocation and position noise.  Every random draw
+ * is an input, so the results are deterministic.  All pointers are device
+ * pointers; parameter arrays are planar like gsr_gaussians. */
+
+/* Thresholds of the adaptive density control. */
+typedef struct {
+    float grad_threshold;      /* densify when densify_grad >= grad_threshold * densify_count (count > 0) */
+    float split_scale;         /* a densifying Gaussian whose largest scale exceeds this is split, else cloned */
+    float min_opacity;         /* prune below this opacity, > 0 and < 1 */
+    float max_screen_radius;   /* prune above this densify_radius (pixels); 0 = no such test */
+    float max_world_scale;     /* prune above this largest scale; 0 = no such test */
+} gsr_adc_params;
+
+/* Writable Gaussian arrays with room for N Gaussians (planar with stride N;
+ * sh has 3 (deg+1)^2 rows for the degree of the input). */
+typedef struct {
+    int N;
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+} gsr_gaussians_out;
+
+/* Scratch bytes the density calls need for N Gaussians (caller-allocated,
+ * 256-byte aligned, passed as ws). */
+gsr_status gsr_density_workspace_size(gsr_ctx *ctx, int N, size_t *bytes);
+
+/* Adaptive density control.  In the input's order, Gaussian g becomes:
+ * nothing if pruned (opacity < min_opacity, or densify_radius above
+ * max_screen_radius, or largest scale above max_world_scale); two children
+ * if it densifies and its largest scale exceeds split_scale, at
+ * mean + R diag(scale) eps_c (eps_c = split_normals rows [3c, 3c+3), c = 0,
+ * 1, each [N]) with log-scales - ln 1.6 and everything else copied; itself
+ * and an exact copy if it densifies otherwise; else itself.  grad, count,
+ * radius: [N] as gathered by gsr_render_backward.  *out_count (device int)
+ * receives the number of output Gaussians, which may exceed out->N: only the
+ * first out->N are written.  out must not overlap the input. */
+gsr_status gsr_densify_adc(gsr_ctx *ctx, const gsr_gaussians *gs, const float *grad, const float *count,
+                           const float *radius, const float *split_normals, const gsr_adc_params *params,
+                           const gsr_gaussians_out *out, int *out_count, void *ws, size_t ws_bytes,
+                           gsr_stream stream);
+
+/* MCMC relocation.  Gaussians of opacity <= min_opacity are dead; dead slot
+ * g takes a live source drawn with probability proportional to opacity by
+ * the uniform 32-bit draws[g] (integer weights floor(sigmoid(logit) 2^24),
+ * the first source whose inclusive weight sum exceeds floor(draws[g] W /
+ * 2^32)).  A source drawn n times and its n copies get opacity
+ * o' = 1 - (1 - o)^(1/k) and scales times
+ * o / sum_{i=1..k} sum_{j<i} C(i-1, j) (-1)^j o'^(j+1) / sqrt(j+1),
+ * k = min(n + 1, 51), o' within [min_opacity, 1 - 2^-23].  out (room for at
+ * least gs->N, not overlapping the input) receives all N Gaussians;
+ * *relocated (device int) the number of dead slots filled (0 when no
+ * Gaussian is live). */
+gsr_status gsr_mcmc_relocate(gsr_ctx *ctx, const gsr_gaussians *gs, const uint32_t *draws, float min_opacity,
+                             const gsr_gaussians_out *out, int *relocated, void *ws, size_t ws_bytes,
+                             gsr_stream stream);
+
+/* MCMC position noise: means_out = mean + scale sigmoid(-100 (o - 0.005))
+ * Sigma eta, Sigma = R diag(scale^2) R^T the Gaussian's covariance, eta
+ * [3][N] standard-normal draws, scale = lr_noise (1e4 in the paper) times
+ * the position learning rate.  means_out ([3][N]) may be gs->means. */
+gsr_status gsr_mcmc_noise(gsr_ctx *ctx, const gsr_gaussians *gs, const float *eta, float scale,
+                          float *means_out, gsr_stream stream);
+
 /* Message of the last synchronous error on ctx (host string owned by ctx). */
 const char *gsr_last_error(const gsr_ctx *ctx);
 
@@ -318,7 +383,8 @@ int gsr_abi_version(void);
 
 /* sizeof of the ABI structs, for binding checks: 0 gsr_config, 1
  * gsr_gaussians, 2 gsr_view, 3 gsr_view_grad, 4 gsr_grads, 5 gsr_info,
- * 6 gsr_l1_view, 7 gsr_surfel_out, 8 gsr_surfel_grad; 0 for other values. */
+ * 6 gsr_l1_view, 7 gsr_surfel_out, 8 gsr_surfel_grad, 9 gsr_adc_params,
+ * 10 gsr_gaussians_out; 0 for other values. */
 size_t gsr_abi_sizeof(int which);
 
 #ifdef __cplusplus

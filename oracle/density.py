@@ -35,7 +35,9 @@ MCMC relocation (3DGS-MCMC), Gaussians "dead" at opacity <= min_opacity:
   multiplied by
       c = o / sum_{i=1..k} sum_{j=0..i-1} C(i-1, j) (-1)^j o'^(j+1) / sqrt(j+1),
   which keeps the integral of the composited opacity profile; o' is clamped
-  to [min_opacity, 1 - 2^-23] so that the logit stays finite.  With no live
+  to [min_opacity, 1 - 2^-23] so that the logit stays finite, and k is capped
+  at MAX_COPIES = 51 in both formulas (the published rule's table size; the
+  alternating binomial sum loses all precision far beyond it).  With no live
   Gaussian nothing moves.
 
 MCMC noise (3DGS-MCMC):
@@ -55,6 +57,7 @@ SPLIT_FACTOR = 1.6
 NOISE_K = 100.0
 NOISE_T = 0.005
 WEIGHT_BITS = 24
+MAX_COPIES = 51
 _F = np.float32
 
 
@@ -247,7 +250,7 @@ def mcmc_relocate(g: Gaussians, r, min_opacity: float) -> Tuple[Gaussians, np.nd
     new = g.as64()
     o = sigmoid(new.opacity_logits)
     for s in np.nonzero(drawn)[0]:
-        k = int(drawn[s]) + 1
+        k = min(int(drawn[s]) + 1, MAX_COPIES)
         o_new = float(relocation_opacity(o[s], k))
         o_new = min(max(o_new, min_opacity), 1.0 - 2.0 ** -23)
         c = relocation_scale_factor(o[s], o_new, k)

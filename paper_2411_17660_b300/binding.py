@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgsr.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
-ABI_VERSION = 3   # GSR_ABI_VERSION these structs follow
+ABI_VERSION = 4   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
@@ -72,7 +72,18 @@ class SurfelGrad(ctypes.Structure):
     _fields_ = [("d_normal", _p), ("d_distortion", _p)]
 
 
-ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View, SurfelOut, SurfelGrad]
+class AdcParams(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("split_scale", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("max_screen_radius", ctypes.c_float), ("max_world_scale", ctypes.c_float)]
+
+
+class GaussiansOut(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("means", _p), ("log_scales", _p), ("quats", _p), ("opacity_logits", _p),
+                ("sh", _p)]
+
+
+ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View, SurfelOut, SurfelGrad, AdcParams,
+               GaussiansOut]
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -116,6 +127,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_render_surfels_backward": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
                                                 ctypes.POINTER(ViewGrad), ctypes.POINTER(SurfelGrad), c_int,
                                                 ctypes.POINTER(Grads), _p, c_size, _p]),
+        "gsr_density_workspace_size": (c_int, [_p, c_int, ctypes.POINTER(c_size)]),
+        "gsr_densify_adc": (c_int, [_p, ctypes.POINTER(Gaussians), _p, _p, _p, _p, ctypes.POINTER(AdcParams),
+                                    ctypes.POINTER(GaussiansOut), _p, _p, c_size, _p]),
+        "gsr_mcmc_relocate": (c_int, [_p, ctypes.POINTER(Gaussians), _p, ctypes.c_float,
+                                      ctypes.POINTER(GaussiansOut), _p, _p, c_size, _p]),
+        "gsr_mcmc_noise": (c_int, [_p, ctypes.POINTER(Gaussians), _p, ctypes.c_float, _p, _p]),
         "gsr_last_error": (ctypes.c_char_p, [_p]),
         "gsr_status_string": (ctypes.c_char_p, [c_int]),
         "gsr_abi_version": (c_int, []),
@@ -210,6 +227,24 @@ class Context:
         tarr = (L1View * len(targets))(*targets)
         self.check(self.lib.gsr_rgbd_loss(self.h, arr, tarr, len(views), lambda1, lambda2, loss_ptr, stream),
                    "gsr_rgbd_loss")
+
+    def density_workspace_size(self, N: int) -> int:
+        b = ctypes.c_size_t()
+        self.check(self.lib.gsr_density_workspace_size(self.h, N, ctypes.byref(b)), "gsr_density_workspace_size")
+        return b.value
+
+    def densify_adc(self, g: Gaussians, grad: int, count: int, radius: int, normals: int, params: AdcParams,
+                    out: GaussiansOut, out_count: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        return self.lib.gsr_densify_adc(self.h, ctypes.byref(g), grad, count, radius, normals, ctypes.byref(params),
+                                        ctypes.byref(out), out_count, ws_ptr, ws_bytes, stream)
+
+    def mcmc_relocate(self, g: Gaussians, draws: int, min_opacity: float, out: GaussiansOut, relocated: int,
+                      ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        return self.lib.gsr_mcmc_relocate(self.h, ctypes.byref(g), draws, min_opacity, ctypes.byref(out), relocated,
+                                          ws_ptr, ws_bytes, stream)
+
+    def mcmc_noise(self, g: Gaussians, eta: int, scale: float, means_out: int, stream: int) -> int:
+        return self.lib.gsr_mcmc_noise(self.h, ctypes.byref(g), eta, scale, means_out, stream)
 
     def l1_loss(self, views, targets, color_weight: float, depth_weight: float, loss_ptr: int, stream: int):
         arr = (View * len(views))(*views)

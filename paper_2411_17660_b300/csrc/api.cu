@@ -638,6 +638,83 @@ const char *gsr_status_string(gsr_status s) {
 
 int gsr_abi_version(void) { return GSR_ABI_VERSION; }
 
+gsr_status gsr_density_workspace_size(gsr_ctx *ctx, int N, size_t *bytes) {
+    if (!ctx || !bytes) return fail(ctx, GSR_EINVAL, "ctx and bytes must be non-NULL");
+    if (N < 0) return fail(ctx, GSR_EINVAL, "N=%d is negative", N);
+    *bytes = density_workspace_bytes(N);
+    return GSR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared checks of the density calls: Gaussians, the output arrays and the workspace.
+gsr_status check_density(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_gaussians_out *out, int min_room,
+                         const void *ws, size_t ws_bytes) {
+    gsr_status s = check_gaussians(ctx, gs, 1);
+    if (s != GSR_OK) return s;
+    if (out) {
+        if (out->N < min_room) return fail(ctx, GSR_EINVAL, "out has room for %d Gaussians, needs %d", out->N, min_room);
+        if (out->N > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
+            return fail(ctx, GSR_EINVAL, "an output array is NULL");
+        if (out->means == gs->means || out->log_scales == gs->log_scales || out->quats == gs->quats ||
+            out->opacity_logits == gs->opacity_logits || out->sh == gs->sh)
+            return fail(ctx, GSR_EINVAL, "out must not be the input arrays");
+    }
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < density_workspace_bytes(gs->N))
+        return fail(ctx, GSR_EINVAL, "workspace must be 256-byte aligned and hold gsr_density_workspace_size bytes");
+    return GSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gsr_status gsr_densify_adc(gsr_ctx *ctx, const gsr_gaussians *gs, const float *grad, const float *count,
+                           const float *radius, const float *split_normals, const gsr_adc_params *params,
+                           const gsr_gaussians_out *out, int *out_count, void *ws, size_t ws_bytes,
+                           gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    if (!gs || !params || !out || !out_count) return fail(ctx, GSR_EINVAL, "gs, params, out and out_count must be non-NULL");
+    gsr_status s = check_density(ctx, gs, out, 0, ws, ws_bytes);
+    if (s != GSR_OK) return s;
+    if (gs->N > 0 && (!grad || !count || !split_normals || (params->max_screen_radius > 0.f && !radius)))
+        return fail(ctx, GSR_EINVAL, "grad, count, split_normals (and radius with max_screen_radius) must be non-NULL");
+    if (!(params->min_opacity > 0.f && params->min_opacity < 1.f) || !(params->split_scale > 0.f) ||
+        !(params->max_screen_radius >= 0.f) || !(params->max_world_scale >= 0.f) || !(params->grad_threshold >= 0.f))
+        return fail(ctx, GSR_EINVAL, "adc thresholds out of range");
+    cudaError_t e = launch_densify_adc(gaussian_ptrs(gs), grad, count, radius, split_normals, *params, *out, out_count,
+                                       ws, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "densify");
+}
+
+gsr_status gsr_mcmc_relocate(gsr_ctx *ctx, const gsr_gaussians *gs, const uint32_t *draws, float min_opacity,
+                             const gsr_gaussians_out *out, int *relocated, void *ws, size_t ws_bytes,
+                             gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    if (!gs || !out || !relocated) return fail(ctx, GSR_EINVAL, "gs, out and relocated must be non-NULL");
+    gsr_status s = check_density(ctx, gs, out, gs->N, ws, ws_bytes);
+    if (s != GSR_OK) return s;
+    if (gs->N > 0 && !draws) return fail(ctx, GSR_EINVAL, "draws must be non-NULL");
+    if (!(min_opacity > 0.f && min_opacity < 1.f)) return fail(ctx, GSR_EINVAL, "min_opacity must lie in (0, 1)");
+    cudaError_t e = launch_mcmc_relocate(gaussian_ptrs(gs), draws, min_opacity, *out, relocated, ws,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "relocate");
+}
+
+gsr_status gsr_mcmc_noise(gsr_ctx *ctx, const gsr_gaussians *gs, const float *eta, float scale, float *means_out,
+                          gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    if (!gs) return fail(ctx, GSR_EINVAL, "gs must be non-NULL");
+    gsr_status s = check_gaussians(ctx, gs, 1);
+    if (s != GSR_OK) return s;
+    if (gs->N > 0 && (!eta || !means_out)) return fail(ctx, GSR_EINVAL, "eta and means_out must be non-NULL");
+    if (!std::isfinite(scale)) return fail(ctx, GSR_EINVAL, "scale must be finite");
+    cudaError_t e = launch_mcmc_noise(gaussian_ptrs(gs), eta, scale, means_out, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "noise");
+}
+
 size_t gsr_abi_sizeof(int which) {
     switch (which) {
         case 0: return sizeof(gsr_config);
@@ -649,6 +726,8 @@ size_t gsr_abi_sizeof(int which) {
         case 6: return sizeof(gsr_l1_view);
         case 7: return sizeof(gsr_surfel_out);
         case 8: return sizeof(gsr_surfel_grad);
+        case 9: return sizeof(gsr_adc_params);
+        case 10: return sizeof(gsr_gaussians_out);
     }
     return 0;
 }

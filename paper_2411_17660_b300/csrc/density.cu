@@ -1,0 +1,413 @@
+// density.cu -- density control of the Gaussian map between optimisation
+// steps (Sec. 3.3, last paragraph; Supp. "Monte Carlo Markov Chain Gaussian
+// Splatting"): the 3DGS adaptive density control (clone, split, prune from
+// the densification statistics the backward gathers) and the MCMC strategy's
+// relocation of low-opacity Gaussians and its position noise.
+//
+// Every decision that selects or counts Gaussians is exact: thresholds are
+// compared in FP64 (FP32 inputs, exact products) or, for the MCMC draws, on
+// integer weights made from an FP32 sigmoid built only from correctly rounded
+// operations (exp by Cody-Waite reduction and a degree-7 Taylor polynomial),
+// so the result does not depend on the compiler or the GPU.  Output order is
+// the input order (device-wide scans), so the results are deterministic.
+#include <cmath>
+
+#include "kernels.cuh"
+#include "project.cuh"
+
+namespace gsr {
+
+namespace {
+
+constexpr int kDThreads = 256;
+constexpr int kDItems = 16;
+constexpr int kDChunk = kDThreads * kDItems;   // values per scan block
+constexpr int kMaxCopies = 51;
+constexpr float kSplitLog = 0.47000362924573558f;   // ln 1.6
+constexpr float kNoiseK = 100.f, kNoiseT = 0.005f;
+
+// ---------------------------------------------------------------- device-wide scan of u64 values
+// Block b scans values [b kDChunk, (b + 1) kDChunk), kDItems consecutive ones
+// per thread; the block totals are scanned by one block; a last pass adds
+// each block's offset.
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x, unsigned long long *s_warp,
+                                                            unsigned long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int W = THREADS / 32;
+        unsigned long long w = lane < W ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < W) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long before = warp > 0 ? s_warp[warp - 1] : 0ull;
+    total = s_warp[THREADS / 32 - 1];
+    __syncthreads();
+    return before + incl - x;
+}
+
+// vals[i] := exclusive (or inclusive) prefix of vals within its block; block
+// totals to partials.
+__global__ void __launch_bounds__(kDThreads) scan_local_kernel(unsigned long long *vals, size_t n,
+                                                               unsigned long long *partials, int inclusive) {
+    __shared__ unsigned long long s_warp[kDThreads / 32];
+    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)threadIdx.x * kDItems;
+    unsigned long long v[kDItems], run = 0;
+#pragma unroll
+    for (int k = 0; k < kDItems; ++k) {
+        v[k] = base + k < n ? vals[base + k] : 0ull;
+        run += v[k];
+    }
+    unsigned long long total;
+    unsigned long long ex = block_scan_ex<kDThreads>(run, s_warp, total);
+#pragma unroll
+    for (int k = 0; k < kDItems; ++k) {
+        ex += inclusive ? v[k] : 0ull;
+        if (base + k < n) vals[base + k] = ex;
+        ex += inclusive ? 0ull : v[k];
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+// partials := exclusive prefix of the block totals; *total := their sum.
+__global__ void __launch_bounds__(1024) scan_partials_kernel(unsigned long long *partials, uint32_t blocks,
+                                                             unsigned long long *total) {
+    __shared__ unsigned long long s_warp[32];
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < blocks; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const unsigned long long x = i < blocks ? partials[i] : 0ull;
+        unsigned long long t;
+        const unsigned long long ex = block_scan_ex<1024>(x, s_warp, t);
+        if (i < blocks) partials[i] = carry + ex;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kDThreads) scan_add_kernel(unsigned long long *vals, size_t n,
+                                                             const unsigned long long *partials) {
+    const size_t i = (size_t)blockIdx.x * kDThreads + threadIdx.x;
+    if (i < n) vals[i] += partials[i / kDChunk];
+}
+
+// ---------------------------------------------------------------- shared per-Gaussian helpers
+struct DensityPtrs {
+    GaussianPtrs in;
+    int C;   // SH rows
+    float *om, *ols, *oq, *oo, *osh;   // outputs, planar with capacity cap
+    uint32_t cap;
+};
+
+// Copies Gaussian g of the input to output slot k.
+__device__ __forceinline__ void copy_gaussian(const DensityPtrs &d, int g, uint32_t k) {
+    const size_t N = (size_t)d.in.N, cap = d.cap;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        d.om[j * cap + k] = d.in.means[j * N + g];
+        d.ols[j * cap + k] = d.in.log_scales[j * N + g];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d.oq[j * cap + k] = d.in.quats[j * N + g];
+    d.oo[k] = d.in.opacity_logits[g];
+    for (int j = 0; j < d.C; ++j) d.osh[j * cap + k] = d.in.sh[j * N + g];
+}
+
+// ---------------------------------------------------------------- adaptive density control
+struct AdcParams {
+    float grad_threshold, max_screen_radius;
+    double log_split, logit_min, log_world;   // ln(split_scale), logit(min_opacity), ln(max_world_scale) or +inf
+    int screen_on;
+};
+
+// 0: pruned, 1: kept, 2: kept and cloned, 3: split into two
+__device__ __forceinline__ int adc_decide(const GaussianPtrs &gp, const float *grad, const float *count,
+                                          const float *radius, const AdcParams &p, int g) {
+    const size_t N = (size_t)gp.N;
+    const float ls = fmaxf(gp.log_scales[g], fmaxf(gp.log_scales[N + g], gp.log_scales[2 * N + g]));
+    const float cnt = count[g];
+    const bool dense = cnt > 0.f && (double)grad[g] >= (double)p.grad_threshold * (double)cnt;
+    const bool big = (double)ls > p.log_split;
+    bool pruned = (double)gp.opacity_logits[g] < p.logit_min || (double)ls > p.log_world;
+    if (p.screen_on) pruned |= radius[g] > p.max_screen_radius;
+    return pruned ? 0 : (dense ? (big ? 3 : 2) : 1);
+}
+
+__global__ void __launch_bounds__(kDThreads) adc_count_kernel(const GaussianPtrs gp, const float *grad,
+                                                              const float *count, const float *radius,
+                                                              const AdcParams p, unsigned long long *outs) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= gp.N) return;
+    const int c = adc_decide(gp, grad, count, radius, p, g);
+    outs[g] = c == 0 ? 0ull : (c == 1 ? 1ull : 2ull);
+}
+
+__global__ void __launch_bounds__(kDThreads) adc_write_kernel(const DensityPtrs d, const float *grad,
+                                                              const float *count, const float *radius,
+                                                              const AdcParams p, const float *normals,
+                                                              const unsigned long long *at,
+                                                              const unsigned long long *total, int *out_count) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g == 0) *out_count = *total > 0x7fffffffull ? 0x7fffffff : (int)*total;
+    if (g >= d.in.N) return;
+    const int c = adc_decide(d.in, grad, count, radius, p, g);
+    if (c == 0) return;
+    const unsigned long long k0 = at[g];
+    if (c != 3) {
+        for (int r = 0; r < (c == 2 ? 2 : 1); ++r)
+            if (k0 + r < d.cap) copy_gaussian(d, g, (uint32_t)(k0 + r));
+        return;
+    }
+    GaussPre G;
+    gauss_pre(d.in, g, G);
+    const size_t N = (size_t)d.in.N, cap = d.cap;
+    for (int r = 0; r < 2; ++r) {
+        if (k0 + r >= d.cap) break;
+        const uint32_t k = (uint32_t)(k0 + r);
+        copy_gaussian(d, g, k);
+        const float e0 = normals[(size_t)(r * 3 + 0) * N + g], e1 = normals[(size_t)(r * 3 + 1) * N + g];
+        const float e2 = normals[(size_t)(r * 3 + 2) * N + g];
+        const float mu[3] = {G.mx, G.my, G.mz};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            d.om[j * cap + k] = mu[j] + (G.M[j][0] * e0 + G.M[j][1] * e1 + G.M[j][2] * e2);
+            d.ols[j * cap + k] = d.in.log_scales[j * N + g] - kSplitLog;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- MCMC relocation
+// FP32 exp and sigmoid from correctly rounded operations only (no fused
+// multiply-add, no approximate instructions): x = n ln2 + f with ln 2 split
+// into an exactly representable high part and a low part, e^f by its
+// degree-7 Taylor polynomial, then 2^n by exponent scaling.
+__device__ __forceinline__ float exp_rn(float x) {
+    // FP32 constants, written with the digits that round to them exactly
+    const float ln2_hi = 0.693145751953125f, ln2_lo = 1.428606765330187e-06f;
+    const float log2e = 1.4426950216293335f;
+    x = fminf(fmaxf(x, -87.f), 88.f);
+    const float n = rintf(__fmul_rn(x, log2e));
+    const float f = __fsub_rn(__fsub_rn(x, __fmul_rn(n, ln2_hi)), __fmul_rn(n, ln2_lo));
+    const float c[8] = {1.f, 1.f, 0.5f, 0.16666667f, 0.041666668f, 0.008333334f, 0.0013888889f, 0.0001984127f};
+    float p = c[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, f), c[k]);
+    return ldexpf(p, (int)n);
+}
+
+__device__ __forceinline__ float sigmoid_rn(float l) { return __fdiv_rn(1.f, __fadd_rn(1.f, exp_rn(-l))); }
+
+// weights (then, after the scan, their inclusive prefix) and the dead flags
+__global__ void __launch_bounds__(kDThreads) mcmc_weight_kernel(const GaussianPtrs gp, float min_opacity,
+                                                                unsigned long long *w, uint32_t *dead) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= gp.N) return;
+    const float o = sigmoid_rn(gp.opacity_logits[g]);
+    const bool d = o <= min_opacity;
+    dead[g] = d ? 1u : 0u;
+    w[g] = d ? 0ull : (unsigned long long)(o * 16777216.f);   // exact scaling; truncation = floor
+}
+
+// Each dead slot draws its source: the first Gaussian whose inclusive weight
+// sum exceeds floor(r W / 2^32).  src[g] = source, or 0xffffffff.
+__global__ void __launch_bounds__(kDThreads) mcmc_draw_kernel(int N, const uint32_t *draws,
+                                                              const unsigned long long *cum,
+                                                              const unsigned long long *W_total,
+                                                              const uint32_t *dead, uint32_t *src, uint32_t *drawn,
+                                                              int *relocated) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= N) return;
+    const unsigned long long W = *W_total;
+    uint32_t s = 0xffffffffu;
+    if (dead[g] && W > 0) {
+        const unsigned long long r = draws[g];
+        const unsigned long long lo = r * W, hi = __umul64hi(r, W);
+        const unsigned long long t = (hi << 32) | (lo >> 32);   // floor(r W / 2^32), r W < 2^77
+        int a = 0, b = N;   // first index with cum > t: in [a, b)
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (cum[m] > t)
+                b = m;
+            else
+                a = m + 1;
+        }
+        s = (uint32_t)a;
+        atomicAdd(&drawn[s], 1u);
+        atomicAdd(relocated, 1);
+    }
+    src[g] = s;
+}
+
+// Opacity logit and log-scale shift of a source drawn n times.
+__device__ __forceinline__ void relocation_rule(float logit, uint32_t n, float min_opacity, float &new_logit,
+                                                float &dls) {
+    const int k = min((int)n + 1, kMaxCopies);
+    const double o = 1.0 / (1.0 + exp(-(double)logit));
+    double on = 1.0 - pow(1.0 - o, 1.0 / (double)k);
+    on = fmin(fmax(on, (double)min_opacity), 1.0 - 1.0 / 8388608.0);
+    double den = 0.0;
+    for (int i = 1; i <= k; ++i) {
+        double binom = 1.0, pw = on;   // C(i-1, j), on^(j+1)
+        for (int j = 0; j < i; ++j) {
+            den += ((j & 1) ? -1.0 : 1.0) * binom * pw / sqrt((double)(j + 1));
+            binom = binom * (double)(i - 1 - j) / (double)(j + 1);
+            pw *= on;
+        }
+    }
+    new_logit = (float)log(on / (1.0 - on));
+    dls = (float)log(o / den);
+}
+
+__global__ void __launch_bounds__(kDThreads) mcmc_write_kernel(const DensityPtrs d, float min_opacity,
+                                                               const uint32_t *src, const uint32_t *drawn) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= d.in.N) return;
+    const uint32_t s = src[g] != 0xffffffffu ? src[g] : (uint32_t)g;
+    copy_gaussian(d, (int)s, (uint32_t)g);
+    const uint32_t n = drawn[s];
+    if (n == 0) return;
+    float new_logit, dls;
+    relocation_rule(d.in.opacity_logits[s], n, min_opacity, new_logit, dls);
+    const size_t N = (size_t)d.in.N, cap = d.cap;
+    d.oo[g] = new_logit;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d.ols[j * cap + g] = d.in.log_scales[j * N + s] + dls;
+}
+
+// ---------------------------------------------------------------- MCMC noise
+__global__ void __launch_bounds__(kDThreads) mcmc_noise_kernel(const GaussianPtrs gp, const float *eta, float scale,
+                                                               float *means_out) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= gp.N) return;
+    GaussPre G;
+    gauss_pre(gp, g, G);
+    const size_t N = (size_t)gp.N;
+    const float o = 1.f / (1.f + expf(-gp.opacity_logits[g]));
+    const float gate = 1.f / (1.f + expf(kNoiseK * (o - kNoiseT)));
+    const float e[3] = {eta[g], eta[N + g], eta[2 * N + g]};
+    // Sigma eta = M (M^T eta), M = R diag(s)
+    float t[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t[j] = G.M[0][j] * e[0] + G.M[1][j] * e[1] + G.M[2][j] * e[2];
+    const float mu[3] = {G.mx, G.my, G.mz};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        means_out[j * N + g] = mu[j] + scale * gate * (G.M[j][0] * t[0] + G.M[j][1] * t[1] + G.M[j][2] * t[2]);
+}
+
+unsigned blocks_of(size_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+cudaError_t scan(unsigned long long *vals, size_t n, unsigned long long *partials, unsigned long long *total,
+                 bool inclusive, cudaStream_t st) {
+    const unsigned nb = blocks_of(n, kDChunk);
+    scan_local_kernel<<<nb, kDThreads, 0, st>>>(vals, n, partials, inclusive ? 1 : 0);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(partials, nb, total);
+    scan_add_kernel<<<blocks_of(n, kDThreads), kDThreads, 0, st>>>(vals, n, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t density_workspace_bytes(int N) {
+    const size_t n = (size_t)(N > 0 ? N : 1), nb = (n + kDChunk - 1) / kDChunk;
+    auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return a(8 * n) + a(4 * n) + a(4 * n) + a(4 * n) + a(8 * nb) + a(64);
+}
+
+namespace {
+struct DensityWs {
+    unsigned long long *vals;
+    uint32_t *dead, *src, *drawn;
+    unsigned long long *partials, *total;
+};
+
+DensityWs density_ws(void *base, int N) {
+    const size_t n = (size_t)(N > 0 ? N : 1), nb = (n + kDChunk - 1) / kDChunk;
+    auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(base);
+    DensityWs w;
+    w.vals = reinterpret_cast<unsigned long long *>(p);
+    p += a(8 * n);
+    w.dead = reinterpret_cast<uint32_t *>(p);
+    p += a(4 * n);
+    w.src = reinterpret_cast<uint32_t *>(p);
+    p += a(4 * n);
+    w.drawn = reinterpret_cast<uint32_t *>(p);
+    p += a(4 * n);
+    w.partials = reinterpret_cast<unsigned long long *>(p);
+    p += a(8 * nb);
+    w.total = reinterpret_cast<unsigned long long *>(p);
+    return w;
+}
+
+DensityPtrs density_ptrs(const GaussianPtrs &gp, const gsr_gaussians_out &out) {
+    DensityPtrs d;
+    d.in = gp;
+    d.C = 3 * (gp.sh_degree + 1) * (gp.sh_degree + 1);
+    d.om = out.means;
+    d.ols = out.log_scales;
+    d.oq = out.quats;
+    d.oo = out.opacity_logits;
+    d.osh = out.sh;
+    d.cap = (uint32_t)out.N;
+    return d;
+}
+}  // namespace
+
+cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const float *count, const float *radius,
+                               const float *normals, const gsr_adc_params &prm, const gsr_gaussians_out &out,
+                               int *out_count, void *ws, cudaStream_t st) {
+    const DensityWs w = density_ws(ws, gp.N);
+    AdcParams p;
+    p.grad_threshold = prm.grad_threshold;
+    p.max_screen_radius = prm.max_screen_radius;
+    p.screen_on = prm.max_screen_radius > 0.f;
+    p.log_split = std::log((double)prm.split_scale);
+    const double m = (double)prm.min_opacity;
+    p.logit_min = std::log(m / (1.0 - m));
+    p.log_world = prm.max_world_scale > 0.f ? std::log((double)prm.max_world_scale) : HUGE_VAL;
+    if (gp.N == 0) return cudaMemsetAsync(out_count, 0, sizeof(int), st);
+    const unsigned nb = blocks_of((size_t)gp.N, kDThreads);
+    adc_count_kernel<<<nb, kDThreads, 0, st>>>(gp, grad, count, radius, p, w.vals);
+    cudaError_t e = scan(w.vals, (size_t)gp.N, w.partials, w.total, false, st);
+    if (e != cudaSuccess) return e;
+    adc_write_kernel<<<nb, kDThreads, 0, st>>>(density_ptrs(gp, out), grad, count, radius, p, normals, w.vals,
+                                               w.total, out_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_relocate(const GaussianPtrs &gp, const uint32_t *draws, float min_opacity,
+                                 const gsr_gaussians_out &out, int *relocated, void *ws, cudaStream_t st) {
+    const DensityWs w = density_ws(ws, gp.N);
+    cudaError_t e = cudaMemsetAsync(relocated, 0, sizeof(int), st);
+    if (e != cudaSuccess || gp.N == 0) return e;
+    if ((e = cudaMemsetAsync(w.drawn, 0, 4 * (size_t)gp.N, st)) != cudaSuccess) return e;
+    const unsigned nb = blocks_of((size_t)gp.N, kDThreads);
+    mcmc_weight_kernel<<<nb, kDThreads, 0, st>>>(gp, min_opacity, w.vals, w.dead);
+    if ((e = scan(w.vals, (size_t)gp.N, w.partials, w.total, true, st)) != cudaSuccess) return e;
+    mcmc_draw_kernel<<<nb, kDThreads, 0, st>>>(gp.N, draws, w.vals, w.total, w.dead, w.src, w.drawn, relocated);
+    mcmc_write_kernel<<<nb, kDThreads, 0, st>>>(density_ptrs(gp, out), min_opacity, w.src, w.drawn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_noise(const GaussianPtrs &gp, const float *eta, float scale, float *means_out,
+                              cudaStream_t st) {
+    if (gp.N == 0) return cudaSuccess;
+    mcmc_noise_kernel<<<blocks_of((size_t)gp.N, kDThreads), kDThreads, 0, st>>>(gp, eta, scale, means_out);
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -31,6 +31,16 @@ cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st);
 cudaError_t launch_ranges(const Ws &ws, int sm_count, cudaStream_t st);
 
+// density.cu
+size_t density_workspace_bytes(int N);
+cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const float *count, const float *radius,
+                               const float *normals, const gsr_adc_params &prm, const gsr_gaussians_out &out,
+                               int *out_count, void *ws, cudaStream_t st);
+cudaError_t launch_mcmc_relocate(const GaussianPtrs &gp, const uint32_t *draws, float min_opacity,
+                                 const gsr_gaussians_out &out, int *relocated, void *ws, cudaStream_t st);
+cudaError_t launch_mcmc_noise(const GaussianPtrs &gp, const float *eta, float scale, float *means_out,
+                              cudaStream_t st);
+
 // blend.cu
 cudaError_t launch_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
 cudaError_t launch_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st);
