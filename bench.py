@@ -59,6 +59,8 @@ def parse():
                    help="surfels: the 2-D surfel renderer (with normal and distortion outputs and gradients)")
     p.add_argument("--median", action="store_true", help="also render median depth and feed it a gradient")
     p.add_argument("--densify", action="store_true", help="also gather densification statistics in the backward")
+    p.add_argument("--density-ops", action="store_true",
+                   help="also time the density-control calls (ADC, MCMC relocation and noise) at 2M Gaussians")
     p.add_argument("--binning", default="tile", choices=["tile", "radix"],
                    help="tile binning strategy: per-tile counting sort (default) or onesweep radix sort")
     p.add_argument("--autotune", action="store_true", help="pick the tile size and binning with the autotuner first")
@@ -540,6 +542,8 @@ def main():
         "wall_s": wall,
         "peaks_source": peaks["source"],
     }
+    if args.density_ops:
+        line["density_ops"] = measure_density(torch, win, K, W, flush, peaks["hbm_gbs"])
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds)
     if rank == 0:
@@ -547,6 +551,50 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_density(torch, win, K, W, flush, hbm_gbs, N_target=2_000_000):
+    """Times the density-control calls on the workload's Gaussians tiled (and
+    jittered) to 2M, the outdoor map size, with seeded statistics and draws.
+    Roofline: algorithmic HBM bytes (parameters and statistics read once,
+    outputs written once) over the measured time."""
+    from paper_2411_17660_b300.density import DensityControl
+    reps = max(1, N_target // win.scene.N)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    p = {k: (v.repeat(1, reps) if v.dim() == 2 else v.repeat(reps)).contiguous() for k, v in win.params.items()}
+    N = int(p["means"].shape[1])
+    p["means"] += 0.01 * torch.randn(p["means"].shape, device="cuda", generator=gen)
+    deg = win.scene.sh_degree
+    count = torch.randint(0, 9, (N,), device="cuda", generator=gen).float()
+    grad = count * torch.empty(N, device="cuda").exponential_(1.0 / 2e-4, generator=gen)
+    radius = 40.0 * torch.rand(N, device="cuda", generator=gen)
+    normals = torch.randn((2, 3, N), device="cuda", generator=gen)
+    draws = torch.randint(-(1 << 31), (1 << 31) - 1, (N,), device="cuda", dtype=torch.int32, generator=gen)
+    eta = torch.randn((3, N), device="cuda", generator=gen)
+    dc = DensityControl(win.rast)
+    adc = dict(grad_threshold=2e-4, split_scale=0.02, min_opacity=0.005, max_screen_radius=30.0, max_world_scale=0.1)
+    out, n_out = dc.densify_adc(p, deg, grad, count, radius, normals, sync=False, **adc)
+    n_out = int(n_out.item())
+    dead = int((torch.sigmoid(p["opacity_logits"]) <= 0.005).sum().item())
+    noisy = torch.empty_like(p["means"])
+    param_b = 4 * sum(v.shape[0] if v.dim() == 2 else 1 for v in p.values())   # bytes of one Gaussian
+    ops = {
+        "adc": (lambda: dc.densify_adc(p, deg, grad, count, radius, normals, sync=False, **adc),
+                N * (param_b + 12) + n_out * param_b),
+        "mcmc_relocate": (lambda: dc.mcmc_relocate(p, deg, draws, 0.005), N * (2 * param_b + 4)),
+        "mcmc_noise": (lambda: dc.mcmc_noise(p, deg, eta, 1e4 * 1.6e-4, means_out=noisy), N * 68),
+    }
+    res = {"gaussians": N, "sh_degree": deg, "outputs_adc": n_out, "dead": dead,
+           "note": "window Gaussians tiled to 2M; algorithmic bytes: parameters and statistics read once, "
+                   "outputs written once; L2 flushed before each call"}
+    for name, (fn, nbytes) in ops.items():
+        for _ in range(max(W, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ms = statistics.mean(time_steps(torch, fn, K, flush))
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "algorithmic_MB": nbytes / 1e6, "achieved_GBs": gbs, "frac_of_hbm": gbs / hbm_gbs}
+    return res
 
 
 def measure_e2e(torch, R, scene, win, K, W, flush):

@@ -112,18 +112,34 @@ struct DensityPtrs {
     uint32_t cap;
 };
 
-// Copies Gaussian g of the input to output slot k.
-__device__ __forceinline__ void copy_gaussian(const DensityPtrs &d, int g, uint32_t k) {
-    const size_t N = (size_t)d.in.N, cap = d.cap;
+// rows values of column g of a planar source to columns k .. k + copies - 1
+// (those below cap) of a planar destination, loaded kCopyBatch at a time
+// ahead of their stores (one load in flight per thread otherwise: the stores
+// may alias the source)
+constexpr int kCopyBatch = 16;
+__device__ __forceinline__ void copy_rows(const float *src, size_t sstride, float *dst, size_t dstride, int rows,
+                                          size_t g, size_t k, int copies, size_t cap) {
+    for (int j0 = 0; j0 < rows; j0 += kCopyBatch) {
+        float v[kCopyBatch];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        d.om[j * cap + k] = d.in.means[j * N + g];
-        d.ols[j * cap + k] = d.in.log_scales[j * N + g];
+        for (int c = 0; c < kCopyBatch; ++c) v[c] = j0 + c < rows ? __ldg(src + (j0 + c) * sstride + g) : 0.f;
+        for (int r = 0; r < copies; ++r) {
+            if (k + r >= cap) break;
+#pragma unroll
+            for (int c = 0; c < kCopyBatch; ++c)
+                if (j0 + c < rows) dst[(j0 + c) * dstride + k + r] = v[c];
+        }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) d.oq[j * cap + k] = d.in.quats[j * N + g];
-    d.oo[k] = d.in.opacity_logits[g];
-    for (int j = 0; j < d.C; ++j) d.osh[j * cap + k] = d.in.sh[j * N + g];
+}
+
+// Copies Gaussian g of the input to output slots k .. k + copies - 1 (those below the capacity).
+__device__ __forceinline__ void copy_gaussian(const DensityPtrs &d, int g, uint32_t k, int copies = 1) {
+    const size_t N = (size_t)d.in.N, cap = d.cap;
+    copy_rows(d.in.means, N, d.om, cap, 3, (size_t)g, k, copies, cap);
+    copy_rows(d.in.log_scales, N, d.ols, cap, 3, (size_t)g, k, copies, cap);
+    copy_rows(d.in.quats, N, d.oq, cap, 4, (size_t)g, k, copies, cap);
+    copy_rows(d.in.opacity_logits, N, d.oo, cap, 1, (size_t)g, k, copies, cap);
+    copy_rows(d.in.sh, N, d.osh, cap, d.C, (size_t)g, k, copies, cap);
 }
 
 // ---------------------------------------------------------------- adaptive density control
@@ -155,29 +171,34 @@ __global__ void __launch_bounds__(kDThreads) adc_count_kernel(const GaussianPtrs
     outs[g] = c == 0 ? 0ull : (c == 1 ? 1ull : 2ull);
 }
 
+// Every kept Gaussian to its output slots (a split one to both children's).
 __global__ void __launch_bounds__(kDThreads) adc_write_kernel(const DensityPtrs d, const float *grad,
                                                               const float *count, const float *radius,
-                                                              const AdcParams p, const float *normals,
-                                                              const unsigned long long *at,
+                                                              const AdcParams p, const unsigned long long *at,
                                                               const unsigned long long *total, int *out_count) {
     const int g = blockIdx.x * kDThreads + threadIdx.x;
     if (g == 0) *out_count = *total > 0x7fffffffull ? 0x7fffffff : (int)*total;
     if (g >= d.in.N) return;
     const int c = adc_decide(d.in, grad, count, radius, p, g);
-    if (c == 0) return;
     const unsigned long long k0 = at[g];
-    if (c != 3) {
-        for (int r = 0; r < (c == 2 ? 2 : 1); ++r)
-            if (k0 + r < d.cap) copy_gaussian(d, g, (uint32_t)(k0 + r));
-        return;
-    }
+    if (c != 0 && k0 < d.cap) copy_gaussian(d, g, (uint32_t)k0, c == 1 ? 1 : 2);
+}
+
+// The children of the split Gaussians (already copied there): means
+// mu + R diag(s) eps_c and log-scales - ln 1.6.
+__global__ void __launch_bounds__(kDThreads) adc_split_kernel(const DensityPtrs d, const float *grad,
+                                                              const float *count, const float *radius,
+                                                              const AdcParams p, const float *normals,
+                                                              const unsigned long long *at) {
+    const int g = blockIdx.x * kDThreads + threadIdx.x;
+    if (g >= d.in.N || adc_decide(d.in, grad, count, radius, p, g) != 3) return;
+    const unsigned long long k0 = at[g];
     GaussPre G;
     gauss_pre(d.in, g, G);
     const size_t N = (size_t)d.in.N, cap = d.cap;
     for (int r = 0; r < 2; ++r) {
         if (k0 + r >= d.cap) break;
         const uint32_t k = (uint32_t)(k0 + r);
-        copy_gaussian(d, g, k);
         const float e0 = normals[(size_t)(r * 3 + 0) * N + g], e1 = normals[(size_t)(r * 3 + 1) * N + g];
         const float e2 = normals[(size_t)(r * 3 + 2) * N + g];
         const float mu[3] = {G.mx, G.my, G.mz};
@@ -384,8 +405,9 @@ cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const 
     adc_count_kernel<<<nb, kDThreads, 0, st>>>(gp, grad, count, radius, p, w.vals);
     cudaError_t e = scan(w.vals, (size_t)gp.N, w.partials, w.total, false, st);
     if (e != cudaSuccess) return e;
-    adc_write_kernel<<<nb, kDThreads, 0, st>>>(density_ptrs(gp, out), grad, count, radius, p, normals, w.vals,
-                                               w.total, out_count);
+    const DensityPtrs d = density_ptrs(gp, out);
+    adc_write_kernel<<<nb, kDThreads, 0, st>>>(d, grad, count, radius, p, w.vals, w.total, out_count);
+    adc_split_kernel<<<nb, kDThreads, 0, st>>>(d, grad, count, radius, p, normals, w.vals);
     return cudaGetLastError();
 }
 
