@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) surfel_pre_fwd_kernel(const __grid_consta
 // ------------------------------------------------------------------ blend
 // Staged entry of a warp's slot: e0 = (ax', bx', ay', by'), e1 = (a_z, b_z, p_z,
 // log2 sigma), e2 = (du, dv, s_max, list index), e3 = (r, g, b, n_x),
-// e4 = (n_y, n_z, -, -).
+// e4 = (n_y, n_z, Gaussian id, -).
 constexpr int kQuads = 5;
 
 struct Hit {
@@ -183,7 +183,7 @@ __device__ __forceinline__ int stage_surfels(const Ws &ws, const uint32_t *vals,
                r.w >= (float)Y0;
     }
     const unsigned ballot = __ballot_sync(kFull, keep);
-    if (keep) write(__popc(ballot & lanemask_lt()), gi, idx);
+    if (keep) write(__popc(ballot & lanemask_lt()), gi, idx, g);
     __syncwarp();
     return __popc(ballot);
 }
@@ -211,7 +211,7 @@ __device__ __forceinline__ Tile tile_of(const ViewTable &vt, const Ws &ws) {
 }
 
 __device__ __forceinline__ void stage_entry(float4 (*sE)[32], const Ws &ws, const ViewParams &vp, int X0, int Y0,
-                                            int slot, size_t gi, uint32_t idx) {
+                                            int slot, size_t gi, uint32_t idx, uint32_t g) {
     const float4 r0 = ws.rec0[gi], r1 = ws.rec1[gi], r2 = ws.rec2[gi], r3 = ws.rec3[gi], r4 = ws.rec4[gi];
     const float ox = (float)X0 - vp.cx, oy = (float)Y0 - vp.cy;
     // (a_x, a_y, a_z, b_x) = r1, (b_y, b_z) = r3.zw
@@ -221,7 +221,7 @@ __device__ __forceinline__ void stage_entry(float4 (*sE)[32], const Ws &ws, cons
     sE[2][slot] = make_float4(__fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z), __fadd_rn(__fsub_rn(r0.y, (float)Y0), r0.w),
                               r3.y, __uint_as_float(idx));
     sE[3][slot] = make_float4(r2.x, r2.y, r2.z, r4.x);
-    sE[4][slot] = make_float4(r4.y, r4.z, 0.f, 0.f);
+    sE[4][slot] = make_float4(r4.y, r4.z, __uint_as_float(g), 0.f);
 }
 
 template <int TS>
@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS) surfel_blend_fwd_kernel(co
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
         if (__all_sync(kFull, done[0] && done[1])) break;
         const int n = stage_surfels(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
-                                    [&](int slot, size_t gi, uint32_t idx) {
-                                        stage_entry(sE[warp], ws, vp, wt.X0, wt.Y0, slot, gi, idx);
+                                    [&](int slot, size_t gi, uint32_t idx, uint32_t g) {
+                                        stage_entry(sE[warp], ws, vp, wt.X0, wt.Y0, slot, gi, idx, g);
                                     });
         for (int j = 0; j < n; ++j) {
             const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS, Shape<TS>::BWD_BLOCKS)
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u ? end - 32u : wt.range.x;
         const int n = stage_surfels(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0,
-                                    [&](int slot, size_t gi, uint32_t idx) {
-                                        stage_entry(sE[warp], ws, vp, wt.X0, wt.Y0, slot, gi, idx);
+                                    [&](int slot, size_t gi, uint32_t idx, uint32_t g) {
+                                        stage_entry(sE[warp], ws, vp, wt.X0, wt.Y0, slot, gi, idx, g);
                                     });
         for (int j = n - 1; j >= 0; --j) {
             const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
@@ -490,10 +490,17 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS, Shape<TS>::BWD_BLOCKS)
             gv[5] = acc[5] - ox * acc[1] - oy * acc[3];              // b_z
 #pragma unroll
             for (int k = 6; k < kSG; ++k) gv[k] = acc[k];            // p_z, u_c, v_c, ln sigma, rgb, n
-            const uint32_t g = vals[eidx];
-            if (g >= N) continue;
-            const float sum = warp_sum16(gv, lane);
-            if ((lane & 1) == 0) atomicAdd(grads + g * row + (lane >> 1), sum);
+            float *gp = grads + (size_t)__float_as_uint(e4.z) * row;   // staged ids are < N
+            if (__popc(cmask) <= 4) {
+                // up to four lanes: their own atomics are cheaper than a reduction
+                if (any) {
+#pragma unroll
+                    for (int k = 0; k < kSG; ++k) atomicAdd(gp + k, gv[k]);
+                }
+            } else {
+                const float sum = warp_sum16(gv, lane);
+                if ((lane & 1) == 0) atomicAdd(gp + (lane >> 1), sum);
+            }
         }
         __syncwarp();
         end = begin;
