@@ -12,7 +12,8 @@ import re
 from typing import Optional
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libgsr.so")
+# GSR_LIBRARY selects another build of the library, e.g. libgsr_checked.so
+LIB_PATH = os.environ.get("GSR_LIBRARY") or os.path.join(_PKG, "_build", "libgsr.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64

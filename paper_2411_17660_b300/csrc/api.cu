@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 
 struct gsr_ctx {
@@ -40,6 +42,23 @@ namespace gsr {
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// NVTX ranges around a call and each of its stages, for timeline tools and
+// ncu's --nvtx filters; a stage's range ends where the next one begins, and
+// all close on every return.  Without an attached tool the calls do nothing.
+struct CallTrace {
+    bool stage_open = false;
+    explicit CallTrace(const char *call) { nvtxRangePushA(call); }
+    void stage(const char *name) {
+        if (stage_open) nvtxRangePop();
+        nvtxRangePushA(name);
+        stage_open = true;
+    }
+    ~CallTrace() {
+        if (stage_open) nvtxRangePop();
+        nvtxRangePop();
+    }
+};
 
 struct Layout {
     size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, rec4, rec5, radius, aux;
@@ -400,18 +419,24 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
+    CallTrace tr("gsr_render");
     ctx->mark(0, st);
+    tr.stage("preprocess");
     launch_init(w, cap, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_preprocess_fwd(vt, gp, w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
     ctx->mark(1, st);
+    tr.stage("scan+duplicate");
     if ((e = launch_scan_duplicate(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "scan/duplicate");
     ctx->mark(2, st);
+    tr.stage("sort");
     if ((e = launch_sort(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->mark(3, st);
+    tr.stage("ranges");
     if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
     ctx->mark(4, st);
+    tr.stage("blend");
     if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
 
@@ -458,11 +483,14 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
 
     // the per-pair gradient rows were cleared by the forward (and by the last
     // backward after reading them), so nothing is cleared here
+    CallTrace tr("gsr_render_backward");
     ctx->mark(6, st);
     ctx->mark(7, st);
+    tr.stage("blend backward");
     cudaError_t e;
     if ((e = launch_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
     ctx->mark(8, st);
+    tr.stage("preprocess backward");
     if ((e = launch_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess backward");
     ctx->mark(9, st);
     return GSR_OK;
@@ -494,18 +522,24 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
+    CallTrace tr("gsr_render_surfels");
     ctx->mark(0, st);
+    tr.stage("preprocess");
     launch_init(w, cap, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_surfel_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
     ctx->mark(1, st);
+    tr.stage("scan+duplicate");
     if ((e = launch_scan_duplicate(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "scan/duplicate");
     ctx->mark(2, st);
+    tr.stage("sort");
     if ((e = launch_sort(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->mark(3, st);
+    tr.stage("ranges");
     if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
     ctx->mark(4, st);
+    tr.stage("blend");
     if ((e = launch_surfel_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
     remember_forward(ctx, ws_ptr, ws_bytes, gs, views, V, false, true);
@@ -553,11 +587,14 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
     gout.densify_grad = gout.densify_count = gout.densify_radius = nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
+    CallTrace tr("gsr_render_surfels_backward");
     ctx->mark(6, st);   // gradient rows are cleared by the forward and after use
     ctx->mark(7, st);
+    tr.stage("blend backward");
     cudaError_t e;
     if ((e = launch_surfel_blend_bwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend backward");
     ctx->mark(8, st);
+    tr.stage("preprocess backward");
     if ((e = launch_surfel_preprocess_bwd(vt, gp, w, gout, st)) != cudaSuccess)
         return cuda_fail(ctx, e, "preprocess backward");
     ctx->mark(9, st);
@@ -591,6 +628,7 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
     fill_views(vt, views, nullptr, V, ctx->tile);
+    CallTrace tr("gsr_l1_loss");
     cudaError_t e = launch_l1_loss(vt, targets, color_weight, depth_weight, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "l1 loss");
     return GSR_OK;
@@ -609,6 +647,7 @@ gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view 
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
     fill_views(vt, views, nullptr, V, ctx->tile);
+    CallTrace tr("gsr_rgbd_loss");
     cudaError_t e = launch_rgbd_loss(vt, targets, lambda1, lambda2, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rgbd loss");
     return GSR_OK;
@@ -684,6 +723,7 @@ gsr_status gsr_densify_adc(gsr_ctx *ctx, const gsr_gaussians *gs, const float *g
     if (!(params->min_opacity > 0.f && params->min_opacity < 1.f) || !(params->split_scale > 0.f) ||
         !(params->max_screen_radius >= 0.f) || !(params->max_world_scale >= 0.f) || !(params->grad_threshold >= 0.f))
         return fail(ctx, GSR_EINVAL, "adc thresholds out of range");
+    CallTrace tr("gsr_densify_adc");
     cudaError_t e = launch_densify_adc(gaussian_ptrs(gs), grad, count, radius, split_normals, *params, *out, out_count,
                                        ws, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "densify");
@@ -698,6 +738,7 @@ gsr_status gsr_mcmc_relocate(gsr_ctx *ctx, const gsr_gaussians *gs, const uint32
     if (s != GSR_OK) return s;
     if (gs->N > 0 && !draws) return fail(ctx, GSR_EINVAL, "draws must be non-NULL");
     if (!(min_opacity > 0.f && min_opacity < 1.f)) return fail(ctx, GSR_EINVAL, "min_opacity must lie in (0, 1)");
+    CallTrace tr("gsr_mcmc_relocate");
     cudaError_t e = launch_mcmc_relocate(gaussian_ptrs(gs), draws, min_opacity, *out, relocated, ws,
                                          reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "relocate");
@@ -711,6 +752,7 @@ gsr_status gsr_mcmc_noise(gsr_ctx *ctx, const gsr_gaussians *gs, const float *et
     if (s != GSR_OK) return s;
     if (gs->N > 0 && (!eta || !means_out)) return fail(ctx, GSR_EINVAL, "eta and means_out must be non-NULL");
     if (!std::isfinite(scale)) return fail(ctx, GSR_EINVAL, "scale must be finite");
+    CallTrace tr("gsr_mcmc_noise");
     cudaError_t e = launch_mcmc_noise(gaussian_ptrs(gs), eta, scale, means_out, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "noise");
 }

@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) onesweep_kerne
             const K key = s_keys[j];
             const uint32_t d = (uint32_t)((key >> shift) & 0xff);
             const uint32_t o = s_glob[d] + j;
-            if (o < n) {
+            if (GSR_CHECK(ws.hdr, o < n)) {
                 keys_out[o] = key;
                 vals_out[o] = s_vals[j];
             }
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(cons
     uint32_t *ids = ws.sorted;
     {
         const uint32_t t = t0 + (threadIdx.x >> 5);
-        const uint2 r = t < ws.total_tiles ? ws.ranges[t] : make_uint2(0u, 0u);
+        const uint2 r = t < ws.total_tiles ? checked_range(ws.ranges, t, ws.hdr, ws.cap) : make_uint2(0u, 0u);
         if (lane == 0) s_range[threadIdx.x >> 5] = r;
         const uint32_t n = r.y - r.x;
         if (n == 1) {
@@ -698,13 +698,13 @@ __global__ void __launch_bounds__(kBigSortThreads) tile_sort_big_kernel(const Ws
         __syncthreads();
         const size_t tt = first + threadIdx.x * G;
         if (tt < ws.total_tiles) {
-            const uint2 r = ws.ranges[tt];
+            const uint2 r = checked_range(ws.ranges, (uint32_t)tt, ws.hdr, ws.cap);
             if (r.y - r.x > (uint32_t)kBlockSortMid) s_big[atomicAdd(&s_nbig, 1u)] = (uint32_t)tt;
         }
         __syncthreads();
         const uint32_t nbig = s_nbig;
         for (uint32_t q = 0; q < nbig; ++q) {
-            const uint2 r = ws.ranges[s_big[q]];
+            const uint2 r = checked_range(ws.ranges, s_big[q], ws.hdr, ws.cap);
             const uint32_t n = r.y - r.x;
             unsigned long long *a = ws.keys[ws.passes & 1] + r.x, *b = ws.keys[(ws.passes + 1) & 1] + r.x;
             if (n <= (uint32_t)kBlockSortCap) {

@@ -194,7 +194,7 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     w.Y0 = ty * TS + (warp / S::WX) * BH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
-    w.range = ws.ranges[tile];
+    w.range = checked_range(ws.ranges, tile, ws.hdr, ws.cap);
     return w;
 }
 
@@ -210,7 +210,8 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
     float ur = 0.f, vr = 0.f;
     size_t gi = 0;
     const uint32_t g = idx < end ? vals[idx] : 0xffffffffu;
-    if (g < ws.N) {  // g >= N only after a reported device error
+    if (idx < end) (void)GSR_CHECK(ws.hdr, g < ws.N);   // a listed id >= N: only after another error
+    if (g < ws.N) {
         gi = vN + g;
         r0 = ws.rec0[gi];
         r1 = ws.rec1[gi];

@@ -125,6 +125,25 @@ __device__ __forceinline__ void set_status(WsHeader *h, int code) {
     atomicCAS(reinterpret_cast<int *>(&h->status), 0, code);
 }
 
+// Checked builds (-DGSR_CHECKED; `python -m paper_2411_17660_b300.build
+// --checked` makes libgsr_checked.so) verify the data-dependent indices of the
+// kernels: a failed check records GSR_EINTERNAL in the status word and the
+// caller skips the access, instead of trapping.  Release builds compile the
+// checks out (the expression is then true).
+#ifdef GSR_CHECKED
+#define GSR_CHECK(hdr, ok) ((ok) || (set_status((hdr), GSR_EINTERNAL), false))
+#else
+#define GSR_CHECK(hdr, ok) true
+#endif
+
+// A tile's [start, end) range, checked against the sorted key count (empty
+// when the check fails).
+__device__ __forceinline__ uint2 checked_range(const uint2 *ranges, uint32_t tile, WsHeader *hdr, uint32_t cap) {
+    uint2 r = ranges[tile];
+    if (!GSR_CHECK(hdr, r.x <= r.y && r.y <= min(hdr->keys, cap))) r = make_uint2(0u, 0u);
+    return r;
+}
+
 // ---------------------------------------------------------------- numerics
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProd) written with
 // round-to-nearest intrinsics so that no contraction or reassociation can

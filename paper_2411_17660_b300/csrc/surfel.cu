@@ -176,6 +176,7 @@ __device__ __forceinline__ int stage_surfels(const Ws &ws, const uint32_t *vals,
     bool keep = false;
     size_t gi = 0;
     const uint32_t g = idx < end ? vals[idx] : 0xffffffffu;
+    if (idx < end) (void)GSR_CHECK(ws.hdr, g < ws.N);
     if (g < ws.N) {
         gi = vN + g;
         const float4 r = ws.rec5[gi];
@@ -206,7 +207,7 @@ __device__ __forceinline__ Tile tile_of(const ViewTable &vt, const Ws &ws) {
     w.Y0 = ty * TS + (warp / Shape<TS>::WX) * kSubH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
-    w.range = ws.ranges[tile];
+    w.range = checked_range(ws.ranges, tile, ws.hdr, ws.cap);
     return w;
 }
 
