@@ -195,7 +195,7 @@ def crop_pixels(scene, w, h):
 def oracle_step(scene, pix, gC, gD):
     import oracle
     gA = [np.zeros(len(p)) for p in pix]
-    oracle.render_backward(scene, gC, gD, gA, pixels=pix)
+    return oracle.render_backward(scene, gC, gD, gA, pixels=pix)[0]
 
 
 def oracle_sample(scene, seconds):
@@ -209,12 +209,12 @@ def oracle_sample(scene, seconds):
         gC = [rng.uniform(-1, 1, (3, len(p))) for p in pix]
         gD = [rng.uniform(-0.1, 0.1, len(p)) for p in pix]
         t0 = time.perf_counter()
-        oracle_step(scene, pix, gC, gD)
-        return time.perf_counter() - t0, pix, gC, gD
+        res = oracle_step(scene, pix, gC, gD)
+        return time.perf_counter() - t0, pix, gC, gD, res
 
     w, h = 32, 24
-    t, _, _, _ = run(w, h)
-    t0, _, _, _ = run(2, 2)                 # projection + binning cost, no pixels
+    t = run(w, h)[0]
+    t0 = run(2, 2)[0]                       # projection + binning cost, no pixels
     per_px = max(t - t0, 1e-9) / (w * h * scene.V)
     target_px = max((seconds - t0) / per_px / scene.V, 64)
     side = int(np.sqrt(target_px * 4 / 3))
@@ -223,13 +223,34 @@ def oracle_sample(scene, seconds):
     return w, h, run
 
 
-def cpu_baseline(scene, seconds):
+def cpu_baseline(scene, seconds, images=None):
+    """The oracle's fwd+bwd on a crop; with images (per view (colour [3, H W],
+    depth [H W]) of the timed GPU steps) also the parity of those pixels."""
     w, h, run = oracle_sample(scene, seconds)
-    t, pix, _, _ = run(w, h)
+    t, pix, _, _, res = run(w, h)
     npx = sum(len(p) for p in pix)
-    return {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"fwd+bwd of a centred {w}x{h} crop (or less) of each of the {scene.V} views "
-                      f"({npx} px, all {scene.N} Gaussians projected), {t:.1f} s, FP64"}
+    out = {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"fwd+bwd of a centred {w}x{h} crop (or less) of each of the {scene.V} views "
+                     f"({npx} px, all {scene.N} Gaussians projected), {t:.1f} s, FP64"}
+    if images is not None:
+        worst_c = worst_d = all_c = all_d = 0.0
+        near = over = 0
+        for (col, dep), p, r in zip(images, pix, res):
+            ok = r["margin"] >= 1e-4          # pixels away from every FP32-vs-FP64 threshold decision
+            near += int((~ok).sum())
+            dc = np.abs(col[:, p] - r["color"]).max(axis=0)
+            dd = np.abs(dep[p] - r["depth"]) / np.maximum(np.abs(r["depth"]), 1e-3)
+            worst_c = max(worst_c, float(dc[ok].max(initial=0.0)))
+            worst_d = max(worst_d, float(dd[ok].max(initial=0.0)))
+            all_c = max(all_c, float(dc.max(initial=0.0)))
+            all_d = max(all_d, float(dd.max(initial=0.0)))
+            over += int(((dc > 1e-4) | (dd > 1e-4)).sum())
+        out["parity"] = {"pixels": npx, "near_threshold_pixels": near, "max_abs_color": worst_c,
+                         "max_rel_depth": worst_d, "max_abs_color_all_pixels": all_c,
+                         "max_rel_depth_all_pixels": all_d, "pixels_over_tolerance": over,
+                         "tolerance": {"color": 1e-4, "depth": 1e-4},
+                         "within": worst_c <= 1e-4 and worst_d <= 1e-4}
+    return out
 
 
 def reference_arm(args, ws, rank):
@@ -243,7 +264,7 @@ def reference_arm(args, ws, rank):
     times = []
     npx = 0
     for _ in range(args.steps):
-        t, pix, _, _ = run(w, h)
+        t, pix = run(w, h)[:2]
         times.append(t)
         npx = sum(len(p) for p in pix)
     ms = 1000 * statistics.mean(times)
@@ -545,7 +566,13 @@ def main():
     if args.density_ops:
         line["density_ops"] = measure_density(torch, win, K, W, flush, peaks["hbm_gbs"])
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds)
+        imgs = None
+        if args.primitive == "gaussians":   # the oracle renders Gaussians
+            cols = R.split_views(win.color, win.cams, 3)
+            deps = R.split_views(win.depth, win.cams)
+            imgs = [(c.reshape(3, -1).cpu().numpy().astype(np.float64), d.reshape(-1).cpu().numpy().astype(np.float64))
+                    for c, d in zip(cols, deps)]
+        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, imgs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
