@@ -444,86 +444,103 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             if (cmask == 0u) continue;
             const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
             float2 A[kVGGrads];
-            // pair 0 sets the sums (to zero when it is not reached), later pairs add
+            // Both rows of pair p, packed.  Branch-free: a pixel without a
+            // contribution runs with alpha = 0, which leaves its T and Q
+            // unchanged and makes every gradient term zero.
+            auto packed = [&](int p, float2 &dp1, float2 &dp2, float2 &glo, float2 &w) {
+                const float2 arg = __ffma2_rn(s[p], neg2, hi2(e2));
+                const float2 raw = make_float2(c[2 * p] ? ex2_approx(arg.x) : 0.f,
+                                               c[2 * p + 1] ? ex2_approx(arg.y) : 0.f);
+                const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                const float2 om = __ffma2_rn(al, neg2, one2);
+                const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                const float2 Ti = __fmul2_rn(T[p], rom);
+                w = __fmul2_rn(al, Ti);
+                // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
+                // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
+                const float2 gc = __ffma2_rn(gR[p], lo2(e3),
+                                             __ffma2_rn(gG[p], hi2(e3),
+                                                        __ffma2_rn(gB[p], lo2(e4), __fmul2_rn(gZ[p], hi2(e4)))));
+                const float2 dgq = __ffma2_rn(Q[p], neg2, gc);
+                const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gA[p], rom));
+                Q[p] = __ffma2_rn(al, dgq, Q[p]);
+                T[p] = Ti;
+                // no gradient to position or opacity through the 0.99 clamp
+                glo = __fmul2_rn(dA, raw);                              // dL/d ln(sigma)
+                glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
+                glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+                const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
+                dp1 = __fmul2_rn(p1[p], ds2);
+                dp2 = __fmul2_rn(p2[p], ds2);
+            };
+            bool all_rows = false;
+            if constexpr (NP == 2) all_rows = m[0] != 0u && m[1] != 0u && m[2] != 0u && m[3] != 0u;
+            if (all_rows) {
+                // every row reached: both pairs in one straight run, so that
+                // their independent chains interleave
+                float2 dp1[NP], dp2[NP], glo[NP], w[NP];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const unsigned ma = m[2 * p], mb = m[2 * p + 1];
-                if ((ma | mb) == 0u) {
-                    if (p == 0) {
+                for (int p = 0; p < NP; ++p) packed(p, dp1[p], dp2[p], glo[p], w[p]);
+                pair_sums<true>(A, dp1[0], dp2[0], glo[0], w[0], dy[0], gR[0], gG[0], gB[0], gZ[0]);
 #pragma unroll
-                        for (int k = 0; k < kVGGrads; ++k) A[k] = make_float2(0.f, 0.f);
+                for (int p = 1; p < NP; ++p)
+                    pair_sums<false>(A, dp1[p], dp2[p], glo[p], w[p], dy[p], gR[p], gG[p], gB[p], gZ[p]);
+            } else {
+                // pair 0 sets the sums (to zero when it is not reached), later pairs add
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const unsigned ma = m[2 * p], mb = m[2 * p + 1];
+                    if ((ma | mb) == 0u) {
+                        if (p == 0) {
+#pragma unroll
+                            for (int k = 0; k < kVGGrads; ++k) A[k] = make_float2(0.f, 0.f);
+                        }
+                        continue;
                     }
-                    continue;
-                }
-                float2 dp1, dp2, glo, w;
-                if (ma != 0u && mb != 0u) {
-                    // Both rows of the pair, packed.  Branch-free: a pixel
-                    // without a contribution runs with alpha = 0, which leaves
-                    // its T and Q unchanged and makes every gradient term zero.
-                    const float2 arg = __ffma2_rn(s[p], neg2, hi2(e2));
-                    const float2 raw = make_float2(c[2 * p] ? ex2_approx(arg.x) : 0.f,
-                                                   c[2 * p + 1] ? ex2_approx(arg.y) : 0.f);
-                    const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-                    const float2 om = __ffma2_rn(al, neg2, one2);
-                    const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-                    const float2 Ti = __fmul2_rn(T[p], rom);
-                    w = __fmul2_rn(al, Ti);
-                    // dL/dalpha = T_i (g.c_i - Q) + gA T_final / (1 - alpha), and
-                    // Q <- Q (1 - alpha) + alpha g.c_i, with g.c = gC.rgb + gD z
-                    const float2 gc = __ffma2_rn(gR[p], lo2(e3),
-                                                 __ffma2_rn(gG[p], hi2(e3),
-                                                            __ffma2_rn(gB[p], lo2(e4), __fmul2_rn(gZ[p], hi2(e4)))));
-                    const float2 dgq = __ffma2_rn(Q[p], neg2, gc);
-                    const float2 dA = __ffma2_rn(Ti, dgq, __fmul2_rn(gA[p], rom));
-                    Q[p] = __ffma2_rn(al, dgq, Q[p]);
-                    T[p] = Ti;
-                    // no gradient to position or opacity through the 0.99 clamp
-                    glo = __fmul2_rn(dA, raw);                              // dL/d ln(sigma)
-                    glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
-                    glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
-                    const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
-                    dp1 = __fmul2_rn(p1[p], ds2);
-                    dp2 = __fmul2_rn(p2[p], ds2);
-                } else {
-                    // Only one row of the pair is reached in the warp: scalar
-                    // work on it, its results in its own half of the pairs.
-                    auto one_row = [&](auto tag) {
-                        constexpr int R = decltype(tag)::value;
-                        const bool cq = c[2 * p + R];
-                        const float sq = R ? s[p].y : s[p].x;
-                        const float p1q = R ? p1[p].y : p1[p].x, p2q = R ? p2[p].y : p2[p].x;
-                        float &Tq = R ? T[p].y : T[p].x;
-                        float &Qq = R ? Q[p].y : Q[p].x;
-                        const float gRq = R ? gR[p].y : gR[p].x, gGq = R ? gG[p].y : gG[p].x;
-                        const float gBq = R ? gB[p].y : gB[p].x, gZq = R ? gZ[p].y : gZ[p].x;
-                        const float gAq = R ? gA[p].y : gA[p].x;
-                        const float raw = cq ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
-                        const float al = fminf(kAlphaMax, raw);
-                        const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
-                        const float Ti = Tq * rom;
-                        const float wq = al * Ti;
-                        const float gc = fmaf(gRq, e3.x, fmaf(gGq, e3.z, fmaf(gBq, e4.x, gZq * e4.z)));
-                        const float dgq = __fmaf_rn(Qq, -1.f, gc);
-                        const float dA = fmaf(Ti, dgq, gAq * rom);
-                        Qq = fmaf(al, dgq, Qq);
-                        Tq = Ti;
-                        const float gl = raw <= kAlphaMax ? dA * raw : 0.f;
-                        const float ds2 = (-2.f * kLn2) * gl;
-                        auto put = [](float v) { return R ? make_float2(0.f, v) : make_float2(v, 0.f); };
-                        dp1 = put(p1q * ds2);
-                        dp2 = put(p2q * ds2);
-                        glo = put(gl);
-                        w = put(wq);
-                    };
-                    if (ma == 0u)
-                        one_row(RowTag<1>{});
+                    float2 dp1, dp2, glo, w;
+                    if (ma != 0u && mb != 0u) {
+                        packed(p, dp1, dp2, glo, w);
+                    } else {
+                        // Only one row of the pair is reached in the warp: scalar
+                        // work on it, its results in its own half of the pairs.
+                        auto one_row = [&](auto tag) {
+                            constexpr int R = decltype(tag)::value;
+                            const bool cq = c[2 * p + R];
+                            const float sq = R ? s[p].y : s[p].x;
+                            const float p1q = R ? p1[p].y : p1[p].x, p2q = R ? p2[p].y : p2[p].x;
+                            float &Tq = R ? T[p].y : T[p].x;
+                            float &Qq = R ? Q[p].y : Q[p].x;
+                            const float gRq = R ? gR[p].y : gR[p].x, gGq = R ? gG[p].y : gG[p].x;
+                            const float gBq = R ? gB[p].y : gB[p].x, gZq = R ? gZ[p].y : gZ[p].x;
+                            const float gAq = R ? gA[p].y : gA[p].x;
+                            const float raw = cq ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
+                            const float al = fminf(kAlphaMax, raw);
+                            const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
+                            const float Ti = Tq * rom;
+                            const float wq = al * Ti;
+                            const float gc = fmaf(gRq, e3.x, fmaf(gGq, e3.z, fmaf(gBq, e4.x, gZq * e4.z)));
+                            const float dgq = __fmaf_rn(Qq, -1.f, gc);
+                            const float dA = fmaf(Ti, dgq, gAq * rom);
+                            Qq = fmaf(al, dgq, Qq);
+                            Tq = Ti;
+                            const float gl = raw <= kAlphaMax ? dA * raw : 0.f;
+                            const float ds2 = (-2.f * kLn2) * gl;
+                            auto put = [](float v) { return R ? make_float2(0.f, v) : make_float2(v, 0.f); };
+                            dp1 = put(p1q * ds2);
+                            dp2 = put(p2q * ds2);
+                            glo = put(gl);
+                            w = put(wq);
+                        };
+                        if (ma == 0u)
+                            one_row(RowTag<1>{});
+                        else
+                            one_row(RowTag<0>{});
+                    }
+                    if (p == 0)
+                        pair_sums<true>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
                     else
-                        one_row(RowTag<0>{});
+                        pair_sums<false>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
                 }
-                if (p == 0)
-                    pair_sums<true>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
-                else
-                    pair_sums<false>(A, dp1, dp2, glo, w, dy[p], gR[p], gG[p], gB[p], gZ[p]);
             }
             float gv[kVGGrads];
             gv[0] = A[0].x + A[0].y;                                    // du, dv follow from these and m
