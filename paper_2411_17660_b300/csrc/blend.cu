@@ -51,10 +51,11 @@ struct BlendShape {
 };
 
 // s = 0.5 log2(e) d^2 of a pixel at offset (dx, dy) from the mean, with the
-// Cholesky factor m of 0.5 log2(e) Sigma'^-1.  Round-to-nearest intrinsics:
-// the forward and the backward take bit-identical decisions.
-__device__ __forceinline__ float pair_s(float dx, float dy, float m00, float m01, float m11, float &p1, float &p2) {
-    p1 = __fmaf_rn(m00, dx, __fmul_rn(m01, dy));
+// Cholesky factor m of 0.5 log2(e) Sigma'^-1: p1 = m00 dx + m01 dy, p2 = m11 dy
+// (m00dx = m00 dx, shared by the rows of a column).  Round-to-nearest
+// intrinsics: the forward and the backward take bit-identical decisions.
+__device__ __forceinline__ float pair_s(float m00dx, float dy, float m01, float m11, float &p1, float &p2) {
+    p1 = __fmaf_rn(m01, dy, m00dx);
     p2 = __fmul_rn(m11, dy);
     return __fmaf_rn(p1, p1, __fmul_rn(p2, p2));
 }
@@ -80,9 +81,8 @@ __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z,
 // (dx, dy.y) from the mean, with the Cholesky factor m of 0.5 log2(e)
 // Sigma'^-1.  Round-to-nearest throughout: the forward and the backward take
 // bit-identical decisions.
-__device__ __forceinline__ float2 pair_s2(float2 dx, float2 dy, float2 m00, float2 m01, float2 m11, float2 &p1,
-                                          float2 &p2) {
-    p1 = __ffma2_rn(m00, dx, __fmul2_rn(m01, dy));
+__device__ __forceinline__ float2 pair_s2(float2 m00dx, float2 dy, float2 m01, float2 m11, float2 &p1, float2 &p2) {
+    p1 = __ffma2_rn(m01, dy, m00dx);
     p2 = __fmul2_rn(m11, dy);
     return __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
 }
@@ -264,12 +264,12 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
                                   });
         for (int j = 0; j < n; ++j) {
             const float4 a = sA[warp][j], b = sB[warp][j];
-            const float dx = __fsub_rn(lxf, a.x);
+            const float m00dx = __fmul_rn(a.z, __fsub_rn(lxf, a.x));
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
                 if (done[q]) continue;
                 float p1, p2;
-                const float s = pair_s(dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.z, a.w, b.x, p1, p2);
+                const float s = pair_s(m00dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.w, b.x, p1, p2);
                 if (s <= b.y) {
                     const float alpha = fminf(kAlphaMax, ex2_approx(__fsub_rn(b.z, s)));
                     const float Tn = T[q] * (1.f - alpha);
@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             const float4 x = sX[warp][j];
             const uint32_t eidx = __float_as_uint(x.y);
             const float2 dx = __fadd2_rn(lx2, lo2(e0));
+            const float2 m00dx = __fmul2_rn(lo2(e1), dx);
             float2 dy[NP], s[NP], p1[NP], p2[NP];
             bool c[NR];
             unsigned m[NR], cmask = 0u;
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             for (int p = 0; p < NP; ++p) {
                 const float2 ly = make_float2(lyf + (float)(2 * p * kRowStep), lyf + (float)((2 * p + 1) * kRowStep));
                 dy[p] = __fadd2_rn(ly, hi2(e0));
-                s[p] = pair_s2(dx, dy[p], lo2(e1), hi2(e1), lo2(e2), p1[p], p2[p]);
+                s[p] = pair_s2(m00dx, dy[p], hi2(e1), lo2(e2), p1[p], p2[p]);
                 c[2 * p] = eidx < last[2 * p] && s[p].x <= x.x;
                 c[2 * p + 1] = eidx < last[2 * p + 1] && s[p].y <= x.x;
                 m[2 * p] = __ballot_sync(kFull, c[2 * p]);
