@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
                 const float s = pair_s(m00dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.w, b.x, p1, p2);
                 if (s <= b.y) {
                     const float alpha = fminf(kAlphaMax, ex2_approx(__fsub_rn(b.z, s)));
-                    const float Tn = T[q] * (1.f - alpha);
+                    const float w = alpha * T[q];
+                    const float Tn = T[q] - w;   // T (1 - alpha)
                     if (Tn < kTStop) {
                         done[q] = true;
                     } else {
                         const float4 c = sC[warp][j];
-                        const float w = alpha * T[q];
                         C0[q] = fmaf(w, c.x, C0[q]);
                         C1[q] = fmaf(w, c.y, C1[q]);
                         C2[q] = fmaf(w, c.z, C2[q]);
