@@ -264,13 +264,13 @@ __global__ void __launch_bounds__(Shape<TS>::THREADS) surfel_blend_fwd_kernel(co
                 surfel_hit(e0, e1, e2, lxf, lyf + (float)(q * kRowStep), h);
                 if (!(h.s <= e2.z)) continue;
                 const float alpha = fminf(kAlphaMax, ex2_approx(__fsub_rn(e1.w, h.s)));
-                const float Tn = T[q] * (1.f - alpha);
+                const float w = alpha * T[q];
+                const float Tn = T[q] - w;   // T (1 - alpha)
                 if (Tn < kTStop) {
                     done[q] = true;
                     continue;
                 }
                 const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
-                const float w = alpha * T[q];
                 // the intersection's depth where the disk term decides alpha, else the centre's
                 const float z = h.rho3 <= h.rho2 ? fmaf(e1.x, h.u, fmaf(e1.y, h.v, e1.z)) : e1.z;
                 C[q][0] = fmaf(w, e3.x, C[q][0]);
