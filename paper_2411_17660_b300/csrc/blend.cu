@@ -126,7 +126,10 @@ __device__ __forceinline__ bool touches_block(float ur, float vr, float m00, flo
     smin = fminf(smin, f(cl(0.f)));
     smin = fminf(smin, f(cl(-m01 * a0 * inv_den)));
     smin = fminf(smin, f(cl(-m01 * a1 * inv_den)));
-    return smin <= smax + 1e-3f * (1.f + smax) + 1e-2f;
+    // tolerance for the rounding of both this minimum and the per-pixel s:
+    // a few units in the last place of the largest term of the linear forms
+    const float A = fabsf(m00) * fmaxf(fabsf(dx0), fabsf(dx1)) + (fabsf(m01) + fabsf(m11)) * fmaxf(fabsf(dy0), fabsf(dy1));
+    return smin <= smax + 1e-3f * (1.f + smax) + 1e-2f + 0x1p-17f * A;
 }
 
 // One level of a transposing butterfly: L values per lane become ceil(L/2)

@@ -116,16 +116,20 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
                     project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
                     vis = isfinite(uh) && isfinite(vh);
                     // densification visibility: the cutoff ellipse meets the
-                    // rectangle of pixel centres
+                    // rectangle of pixel centres.  The same minimum, with the
+                    // blend's culling tolerance, drops the pairs that reach no
+                    // pixel centre before the tile count and the SH colour.
                     if (vis) {
                         const float u = uh + ul, w = vh + vl;
-                        const float smin = quad_min_over_box(-u, (float)(vp.W - 1) - u, -w, (float)(vp.H - 1) - w,
-                                                             kSqrtHalfLog2e * p.l00, kSqrtHalfLog2e * p.l01,
-                                                             kSqrtHalfLog2e * p.l11);
+                        const float dx0 = -u, dx1 = (float)(vp.W - 1) - u, dy0 = -w, dy1 = (float)(vp.H - 1) - w;
+                        const float m00 = kSqrtHalfLog2e * p.l00, m01 = kSqrtHalfLog2e * p.l01,
+                                    m11 = kSqrtHalfLog2e * p.l11;
+                        const float smin = quad_min_over_box(dx0, dx1, dy0, dy1, m00, m01, m11);
                         if (smin <= G.smax) {
                             const float mid = 0.5f * (p.sxx + p.syy);
                             rad = 3.f * sqrtf(mid + sqrtf(fmaxf(mid * mid - p.det, 0.f)));
                         }
+                        vis = smin <= G.smax + cull_slack(dx0, dx1, dy0, dy1, m00, m01, m11, G.smax);
                     }
                 }
                 if (!vis) ws.counts[(size_t)v * N + g] = 0u;

@@ -199,4 +199,17 @@ __device__ __forceinline__ float quad_min_over_box(float dx0, float dx1, float d
     return smin;
 }
 
+// Tolerance of a cull that compares quad_min_over_box with s_max against the
+// blend's per-pixel test s <= s_max.  Both evaluate the same linear forms in
+// FP32, each with an error of a few units in the last place of
+// A = |m00| max|dx| + (|m01| + |m11|) max|dy|; near the cutoff
+// (sqrt(s) <= 2.6) that moves s by at most about 2.6 * 2 * 4 eps A, inside
+// the 2^-17 A term.  The rest covers the rounding of s_max itself.
+__device__ __forceinline__ float cull_slack(float dx0, float dx1, float dy0, float dy1, float m00, float m01,
+                                            float m11, float smax) {
+    const float A = fabsf(m00) * fmaxf(fabsf(dx0), fabsf(dx1)) +
+                    (fabsf(m01) + fabsf(m11)) * fmaxf(fabsf(dy0), fabsf(dy1));
+    return 1e-3f * (1.f + smax) + 1e-2f + 0x1p-17f * A;
+}
+
 }  // namespace gsr
