@@ -367,9 +367,10 @@ def launches_per_step(rast, win):
         tbits += 1
     # init, preprocess, 3 scan kernels, duplicate, histogram, the radix
     # passes, ranges, blend, loss, blend backward, preprocess backward, pose
-    # sums; per-tile binning sorts the tile bits only and adds 2 tile sorts
+    # sums; per-tile binning emits its keys in the preprocess (no scan, no
+    # duplicate), sorts the tile bits only and adds 2 tile sorts
     if rast.binning == "tile":
-        return 13 + (tbits + 7) // 8 + 2
+        return 9 + (tbits + 7) // 8 + 2
     return 13 + (32 + tbits + 7) // 8
 
 

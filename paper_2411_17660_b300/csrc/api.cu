@@ -186,9 +186,11 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     return w;
 }
 
-__global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles) {
+// Clears the header and the radix histograms of the sort.
+__global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles, uint32_t *hist) {
     uint32_t *p = reinterpret_cast<uint32_t *>(h);
     for (int i = threadIdx.x; i < (int)(sizeof(WsHeader) / 4); i += blockDim.x) p[i] = 0u;
+    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     if (threadIdx.x == 0) {
         h->key_capacity = cap;
@@ -197,7 +199,7 @@ __global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles) {
 }
 
 void launch_init(const Ws &w, uint32_t cap, cudaStream_t st) {
-    init_header_kernel<<<1, 64, 0, st>>>(w.hdr, cap, w.total_tiles);
+    init_header_kernel<<<1, 256, 0, st>>>(w.hdr, cap, w.total_tiles, w.hist);
 }
 
 gsr_status fail(gsr_ctx *ctx, gsr_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -610,7 +612,7 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
     e = cudaMemcpy(&h, ws, sizeof h, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read header");
     info->status = h.status;
-    info->keys = h.keys;
+    info->keys = h.keys > 0xffffffffull ? 0xffffffffu : (uint32_t)h.keys;
     info->key_capacity = h.key_capacity;
     info->tiles = h.tiles;
     info->pairs_contributing = h.pairs_contrib;

@@ -32,7 +32,9 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 
-__device__ __forceinline__ uint32_t key_count(const Ws &ws) { return min(ws.hdr->keys, ws.cap); }
+__device__ __forceinline__ uint32_t key_count(const Ws &ws) {
+    return (uint32_t)min(ws.hdr->keys, (unsigned long long)ws.cap);
+}
 
 constexpr unsigned long long kNoKey = ~0ull;   // padding, after every real (depth, id) word
 
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(const Ws ws) {
         carry += total;
     }
     if (threadIdx.x == 0) {
-        ws.hdr->keys = carry > 0xffffffffull ? 0xffffffffu : (uint32_t)carry;
+        ws.hdr->keys = carry;
         if (carry > ws.cap) set_status(ws.hdr, GSR_ECAPACITY);
     }
 }
@@ -752,13 +754,12 @@ cudaError_t launch_ranges_of(const Ws &ws, int sm_count, cudaStream_t st) {
 
 }  // namespace
 
+// Gaussians binned per tile emit their keys in the preprocess (keys_in_preprocess).
 cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
-    if (ws.VN == 0) return cudaSuccess;
+    if (ws.VN == 0 || keys_in_preprocess(ws)) return cudaSuccess;
     scan_reduce_kernel<<<ws.scan_blocks, kScanThreads, 0, st>>>(ws);
     scan_partials_kernel<<<1, 1024, 0, st>>>(ws);
     scan_down_kernel<<<ws.scan_blocks, kScanThreads, 0, st>>>(ws);
-    cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st);
-    if (e != cudaSuccess) return e;
     duplicate_kernel<<<(unsigned)((ws.VN + 255) / 256), 256, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }

@@ -71,13 +71,13 @@ struct GaussianPtrs {
 // Device-side state at the start of the workspace.
 struct WsHeader {
     int32_t status;                 // first device error (gsr_status)
-    uint32_t keys;                  // keys produced by the scan (clamped to 2^32-1)
     uint32_t key_capacity;
     uint32_t tiles;
-    unsigned long long pairs_contrib;
     uint32_t sort_final;            // key buffer holding the sorted result
+    unsigned long long keys;        // tile keys of all pairs: the scan's total, or the sum of the reservations
+    unsigned long long pairs_contrib;
     uint32_t sort_counter[kMaxPasses];
-    uint32_t pad[64 - 7 - kMaxPasses];
+    uint32_t pad[64 - 8 - kMaxPasses];
 };
 static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
 
@@ -121,6 +121,13 @@ struct Ws {
     int test_flags;
 };
 
+// Gaussians (not surfels) binned per tile emit their tile keys in the
+// preprocess: each warp reserves its pairs' keys with one atomic on the key
+// count.  Every tile's words are sorted completely afterwards, so the order
+// in which the unsorted keys land does not matter.  The other paths place
+// the keys by an exclusive scan of the tile counts.
+__host__ __device__ __forceinline__ bool keys_in_preprocess(const Ws &w) { return w.bin_tile && !w.surfels; }
+
 __device__ __forceinline__ void set_status(WsHeader *h, int code) {
     atomicCAS(reinterpret_cast<int *>(&h->status), 0, code);
 }
@@ -140,7 +147,7 @@ __device__ __forceinline__ void set_status(WsHeader *h, int code) {
 // when the check fails).
 __device__ __forceinline__ uint2 checked_range(const uint2 *ranges, uint32_t tile, WsHeader *hdr, uint32_t cap) {
     uint2 r = ranges[tile];
-    if (!GSR_CHECK(hdr, r.x <= r.y && r.y <= min(hdr->keys, cap))) r = make_uint2(0u, 0u);
+    if (!GSR_CHECK(hdr, r.x <= r.y && r.y <= min(hdr->keys, (unsigned long long)cap))) r = make_uint2(0u, 0u);
     return r;
 }
 

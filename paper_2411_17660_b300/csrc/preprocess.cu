@@ -40,12 +40,14 @@ struct WarpQueue {
     int v[kQueue], g[kQueue];
 };
 
-// Phase B for queue entry k of one lane.
+// Phase B for queue entry k of one lane; called by the whole warp, the lanes
+// without an entry (a partly filled queue at the end) with active false.
 template <int DEG>
 __device__ __forceinline__ void preprocess_fwd_pair(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
-                                                    const Pose *s_pose, const WarpQueue &q, int k) {
+                                                    const Pose *s_pose, const WarpQueue &q, int k, bool active) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const size_t N = (size_t)gp.N;
+    if (!active) k = 0;   // entry 0 is filled whenever a lane is active
     const int pv = q.v[k], pg = q.g[k];
     const ViewParams &vp = vt.v[pv];
     const size_t i = (size_t)pv * N + pg;
@@ -55,9 +57,45 @@ __device__ __forceinline__ void preprocess_fwd_pair(const ViewTable &vt, const G
     const float o = 1.0f / (1.0f + expf(-gp.opacity_logits[pg]));
     const float log2o = log2f(o);
     const float smax = fminf(kCutoffD2 * kHalfLog2e, log2o + kLog2_255);
-    const uint32_t count =
-        visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [](int, int, int) {});
-    ws.counts[i] = count;
+    uint32_t count = 0u;
+    if (active) {
+        count = visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [](int, int, int) {});
+        ws.counts[i] = count;
+    }
+    if (keys_in_preprocess(ws)) {
+        // the warp's keys: an inclusive scan of the counts (at most 32 views'
+        // worth of tiles, 2^27, so 32 bits hold it) and one reservation
+        const int lane = threadIdx.x & 31;
+        uint32_t incl = count;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o2);
+            if (lane >= o2) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0ull;
+        if (lane == 31 && total != 0u) {
+            base = atomicAdd(&ws.hdr->keys, (unsigned long long)total);
+            if (base + total > ws.cap) set_status(ws.hdr, GSR_ECAPACITY);
+        }
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (count != 0u) {
+            // per-tile key layout: tile id in vals, (depth bits, id) word in keys
+            const unsigned long long word = ((unsigned long long)__float_as_uint(q.zh[k]) << 32) | (uint32_t)pg;
+            const uint32_t cap = ws.cap;
+            unsigned long long pos = base + (incl - count);
+            const uint32_t emitted =
+                visit_tile_spans(puh, pvh, sxx, sxy, syy, m00, smax, vp.W, vp.H, vt.tile, [&](int ty, int tx0, int tx1) {
+                    const uint32_t row = vp.tile_offset + (uint32_t)ty * vp.tiles_x;
+                    for (int tx = tx0; tx <= tx1; ++tx, ++pos)
+                        if (pos < cap) {
+                            ws.vals[0][pos] = row + (uint32_t)tx;
+                            ws.keys[0][pos] = word;
+                        }
+                });
+            if (emitted != count) set_status(ws.hdr, GSR_EINTERNAL);
+        }
+    }
     if (count == 0u) return;
     const Pose &ps = s_pose[pv];
     float dx = gp.means[pg] - ps.C[0], dy = gp.means[N + pg] - ps.C[1], dz = gp.means[2 * N + pg] - ps.C[2];
@@ -155,7 +193,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
             qn += __popc(ball);
             if (qn >= 32) {   // phase B on the first 32, then move the rest to the front
                 __syncwarp();
-                preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane);
+                preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane, true);
                 __syncwarp();
                 if (lane < qn - 32) {
                     const int k = 32 + lane;
@@ -179,7 +217,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
         }
     }
     __syncwarp();
-    if (lane < qn) preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane);
+    if (qn > 0) preprocess_fwd_pair<DEG>(vt, gp, ws, s_pose, q, lane, lane < qn);
 }
 
 // ------------------------------------------------------------------ backward

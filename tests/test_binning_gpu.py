@@ -68,6 +68,27 @@ def test_strategies_give_identical_images(name):
         assert U.rel_l2(ga[k], gb[k]) < 1e-5, k
 
 
+@pytest.mark.parametrize("name", list(REDUCED))
+def test_keys_reserved_in_the_preprocess_match_the_scan(name):
+    """Per-tile binning reserves each warp's keys with an atomic, so the
+    unsorted keys land in a timing-dependent order: the key count must equal
+    the radix path's scan total, and repeated renders must agree bit for bit."""
+    sc = REDUCED[name]()
+    params, cams, vm = U.to_device(sc)
+    counts, images = [], []
+    for binning in ("radix", "tile", "tile", "tile"):
+        rast = R.GaussianRasterizer(16, binning=binning)
+        c, d, a, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+        info = rast.info(ws)
+        assert info.status == B.OK
+        counts.append(info.keys)
+        images.append([t.cpu().numpy() for t in (c, d, a)])
+    assert len(set(counts)) == 1 and counts[0] > 0
+    for im in images[2:]:
+        for x, y in zip(images[1], im):
+            np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_strategies_agree_on_every_tile_size(tile):
     sc = REDUCED["uneven"]()
