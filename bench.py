@@ -55,6 +55,9 @@ def parse():
                    help="window (8 x 640x480, 100k Gaussians) is the metric's workload; the others are for reports")
     p.add_argument("--loss", default="l1", choices=["l1", "paper"],
                    help="l1: L1 colour + weighted L1 depth; paper: the mixed L1 + SSIM + depth loss (0.8, 0.2)")
+    p.add_argument("--separate-loss", action="store_true",
+                   help="run the L1 loss as its own kernel after the forward (gsr_render + gsr_l1_loss) instead of "
+                        "fused into the forward blend (gsr_render_l1)")
     p.add_argument("--primitive", default="gaussians", choices=["gaussians", "surfels"],
                    help="surfels: the 2-D surfel renderer (with normal and distortion outputs and gradients)")
     p.add_argument("--median", action="store_true", help="also render median depth and feed it a gradient")
@@ -286,13 +289,14 @@ class Window:
     """Device state of one mapping window (inputs, outputs, workspace)."""
 
     def __init__(self, scene, rast, views=None, dev="cuda", loss="l1", primitive="gaussians", median=False,
-                 densify=False):
+                 densify=False, fuse_l1=True):
         import torch
         from paper_2411_17660_b300 import render as R
         self.R, self.torch = R, torch
         idx = list(range(scene.V)) if views is None else views
         self.scene = scene
         self.loss_kind = loss
+        self.fuse_l1 = fuse_l1 and loss == "l1" and primitive == "gaussians"
         self.surfels = primitive == "surfels"
         self.median, self.densify = median, densify
         self.cams = [R.Intrinsics(scene.cameras[v].H, scene.cameras[v].W, scene.cameras[v].fx,
@@ -341,10 +345,16 @@ class Window:
         if self.surfels:
             self.rast.surfels_forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color,
                                           self.depth, self.alpha, self.normal, self.dist)
+        elif self.fuse_l1:   # the forward blend also takes the L1 loss
+            self.rast.forward_l1_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
+                                     self.alpha, self.tc, self.td, 1.0, sc.depth_weight, self.dC, self.dD, self.loss,
+                                     self.med)
         else:
             self.rast.forward_raw(self.params, sc.sh_degree, self.cams, self.vm, self.ws, self.color, self.depth,
                                   self.alpha, self.med)
-        if self.loss_kind == "l1":
+        if self.fuse_l1:
+            pass
+        elif self.loss_kind == "l1":
             R.l1_loss(self.rast, self.cams, self.vm, self.color, self.depth, self.tc, self.td, 1.0,
                       sc.depth_weight, self.dC, self.dD, self.loss)
         else:
@@ -368,10 +378,12 @@ def launches_per_step(rast, win):
     # init, preprocess, 3 scan kernels, duplicate, histogram, the radix
     # passes, ranges, blend, loss, blend backward, preprocess backward, pose
     # sums; per-tile binning emits its keys in the preprocess (no scan, no
-    # duplicate), sorts the tile bits only and adds 2 tile sorts
+    # duplicate), sorts the tile bits only and adds 2 tile sorts; the L1 loss
+    # fused into the forward blend has no kernel of its own
+    loss = 0 if win.fuse_l1 else 1
     if rast.binning == "tile":
-        return 9 + (tbits + 7) // 8 + 2
-    return 13 + (32 + tbits + 7) // 8
+        return 8 + loss + (tbits + 7) // 8 + 2
+    return 12 + loss + (32 + tbits + 7) // 8
 
 
 def time_steps(torch, fn, K, flush, events_per_step=None):
@@ -430,7 +442,8 @@ def main():
         tile, args.binning = tuned["tile"], tuned["binning"]
         del w0
     rast = R.GaussianRasterizer(tile, binning=args.binning)
-    opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify)
+    opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify,
+                fuse_l1=not args.separate_loss)
     win = Window(scene, rast, **opts)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
@@ -542,6 +555,7 @@ def main():
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
                    "sh_degree": scene.sh_degree, "tile": tile, "binning": args.binning, "autotune": tuned,
                    "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
+                   "loss_in_forward_blend": win.fuse_l1,
                    "primitive": args.primitive,
                    "extras": [k for k, on in (("median depth", args.median), ("densification statistics", args.densify),
                                               ("normal + distortion", args.primitive == "surfels")) if on],

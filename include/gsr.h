@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 4
+#define GSR_ABI_VERSION 5
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -216,6 +216,18 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
  * rendered color/depth of views[v].  loss: device float, overwritten. */
 gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V,
                        float color_weight, float depth_weight, float *loss, gsr_stream stream);
+
+/* gsr_render and gsr_l1_loss in one pass: the forward blend takes the L1
+ * terms of each pixel it has just composited, so the rendered images are not
+ * read back and no loss kernel runs.  Arguments are those of gsr_render and
+ * gsr_l1_loss; the depth term is on wherever targets[v].target_depth is
+ * non-NULL (views[v].depth may then be NULL).  d_color and d_depth equal
+ * gsr_l1_loss's bit for bit; loss (device float, overwritten) equals it up to
+ * the order of the FP32 sum.  Errors: those of gsr_render, and GSR_EINVAL for
+ * a NULL targets, loss, target_color or d_color. */
+gsr_status gsr_render_l1(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
+                         const gsr_l1_view *targets, float color_weight, float depth_weight, float *loss,
+                         void *ws, size_t ws_bytes, gsr_stream stream);
 
 /* Mixed rendering loss of Eq. "rnd_loss" (Sec. 3.3), summed over views:
  *   lambda1 [(1 - lambda2) mean|C - C*| + lambda2 (1 - SSIM(C, C*))]

@@ -17,7 +17,7 @@ LIB_PATH = os.environ.get("GSR_LIBRARY") or os.path.join(_PKG, "_build", "libgsr
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
-ABI_VERSION = 4   # GSR_ABI_VERSION these structs follow
+ABI_VERSION = 5   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_destroy": (c_int, [_p]),
         "gsr_workspace_size": (c_int, [_p, c_int, ctypes.POINTER(View), c_int, c_size, ctypes.POINTER(c_size)]),
         "gsr_render": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, _p, c_size, _p]),
+        "gsr_render_l1": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int,
+                                  ctypes.POINTER(L1View), ctypes.c_float, ctypes.c_float, _p, _p, c_size, _p]),
         "gsr_render_backward": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
                                          ctypes.POINTER(ViewGrad), c_int, ctypes.POINTER(Grads), _p, c_size, _p]),
         "gsr_read_info": (c_int, [_p, _p, c_size, ctypes.POINTER(Info), _p]),
@@ -183,6 +185,13 @@ class Context:
     def render(self, g: Gaussians, views, ws_ptr: int, ws_bytes: int, stream: int) -> int:
         arr = (View * len(views))(*views)
         return self.lib.gsr_render(self.h, ctypes.byref(g), arr, len(views), ws_ptr, ws_bytes, stream)
+
+    def render_l1(self, g: Gaussians, views, targets, color_weight: float, depth_weight: float, loss_ptr: int,
+                  ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        arr = (View * len(views))(*views)
+        tarr = (L1View * len(targets))(*targets)
+        return self.lib.gsr_render_l1(self.h, ctypes.byref(g), arr, len(views), tarr, color_weight, depth_weight,
+                                      loss_ptr, ws_ptr, ws_bytes, stream)
 
     def render_backward(self, g: Gaussians, views, vgrads, out: Grads, ws_ptr: int, ws_bytes: int,
                         stream: int) -> int:

@@ -403,8 +403,17 @@ gsr_status gsr_workspace_size(gsr_ctx *ctx, int N, const gsr_view *views, int V,
     return GSR_OK;
 }
 
-gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, void *ws_ptr,
-                      size_t ws_bytes, gsr_stream stream) {
+namespace {
+
+// The L1 loss that gsr_render_l1 fuses into the forward blend.
+struct FusedL1 {
+    const gsr_l1_view *targets;
+    float color_weight, depth_weight;
+    float *loss;
+};
+
+gsr_status render_impl(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, const FusedL1 *l1,
+                       void *ws_ptr, size_t ws_bytes, gsr_stream stream) {
     if (!ctx) return GSR_EINVAL;
     gsr_status s = check_views(ctx, views, V, true);
     if (s != GSR_OK) return s;
@@ -417,11 +426,22 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
     fill_views(vt, views, nullptr, V, ctx->tile);
+    if (l1) {
+        for (int v = 0; v < V; ++v) {
+            vt.v[v].l1_target_color = l1->targets[v].target_color;
+            vt.v[v].l1_target_depth = l1->targets[v].target_depth;
+            vt.v[v].l1_d_color = l1->targets[v].d_color;
+            vt.v[v].l1_d_depth = l1->targets[v].d_depth;
+        }
+        vt.l1_loss = l1->loss;
+        vt.l1_color_weight = l1->color_weight;
+        vt.l1_depth_weight = l1->depth_weight;
+    }
     const Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-    CallTrace tr("gsr_render");
+    CallTrace tr(l1 ? "gsr_render_l1" : "gsr_render");
     ctx->mark(0, st);
     tr.stage("preprocess");
     launch_init(w, cap, st);
@@ -439,11 +459,33 @@ gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vie
     if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
     ctx->mark(4, st);
     tr.stage("blend");
+    if (l1 && (e = cudaMemsetAsync(l1->loss, 0, sizeof(float), st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "clear loss");
     if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
 
     remember_forward(ctx, ws_ptr, ws_bytes, gs, views, V, want_median(views, V), false);
     return GSR_OK;
+}
+
+}  // namespace
+
+gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, void *ws_ptr,
+                      size_t ws_bytes, gsr_stream stream) {
+    return render_impl(ctx, gs, views, V, nullptr, ws_ptr, ws_bytes, stream);
+}
+
+gsr_status gsr_render_l1(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
+                         const gsr_l1_view *targets, float color_weight, float depth_weight, float *loss,
+                         void *ws_ptr, size_t ws_bytes, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    if (!targets || !loss || !views || V < 1 || V > GSR_MAX_VIEWS)
+        return fail(ctx, GSR_EINVAL, "targets, loss and views must be non-NULL and 1 <= V <= %d", GSR_MAX_VIEWS);
+    for (int v = 0; v < V; ++v)
+        if (!targets[v].target_color || !targets[v].d_color)
+            return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
+    const FusedL1 l1{targets, color_weight, depth_weight, loss};
+    return render_impl(ctx, gs, views, V, &l1, ws_ptr, ws_bytes, stream);
 }
 
 gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views,

@@ -230,7 +230,10 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 
 // MED: also record, per pixel, the median-depth contributor (the last one
 // entered with transmittance above 0.5) and its depth.
-template <int TS, bool MED>
+// L1: the epilogue also takes the L1 loss terms of its pixels (gsr_render_l1),
+// with the expressions of the stand-alone L1 kernel, so that the gradients
+// match it bit for bit.
+template <int TS, bool MED, bool L1>
 __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     constexpr int BH = FwdBlock<TS>::H, NR = BH / kRowStep;
@@ -298,6 +301,21 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
         }
         __syncwarp();
     }
+    // L1: the targets of the lane's pixels, loaded together before any store
+    // (a store to a gradient image could otherwise alias the next load)
+    float tgt[L1 ? NR : 1][4];
+    if constexpr (L1) {
+        const size_t HW = (size_t)vp.H * vp.W;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int py = wt.py + q * kRowStep;
+            const bool in = wt.px < vp.W && py < vp.H;
+            const size_t pix = in ? (size_t)py * vp.W + wt.px : 0;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) tgt[q][ch] = in ? __ldg(vp.l1_target_color + ch * HW + pix) : 0.f;
+            tgt[q][3] = in && vp.l1_target_depth ? __ldg(vp.l1_target_depth + pix) : 0.f;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
         const int py = wt.py + q * kRowStep;
@@ -318,6 +336,47 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
     }
     const uint32_t tot = __reduce_add_sync(kFull, ncon);
     if (lane == 0 && tot) atomicAdd(&ws.hdr->pairs_contrib, (unsigned long long)tot);
+    if constexpr (L1) {
+        // mean over the view's pixels (and 3 channels) of |C - C*|, |D - D*|
+        const size_t HW = (size_t)vp.H * vp.W;
+        const float kc = vt.l1_color_weight / (3.f * (float)HW), kd = vt.l1_depth_weight / (float)HW;
+        const bool dterm = vp.l1_target_depth != nullptr;
+        auto sgn = [](float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); };
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int py = wt.py + q * kRowStep;
+            if (wt.px < vp.W && py < vp.H) {
+                const size_t pix = (size_t)py * vp.W + wt.px;
+                const float c[3] = {C0[q], C1[q], C2[q]};
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float d = c[ch] - tgt[q][ch];
+                    part += fabsf(d) * kc;
+                    vp.l1_d_color[ch * HW + pix] = sgn(d) * kc;
+                }
+                float g = 0.f;
+                if (dterm) {
+                    const float d = D[q] - tgt[q][3];
+                    part += fabsf(d) * kd;
+                    g = sgn(d) * kd;
+                }
+                if (vp.l1_d_depth) vp.l1_d_depth[pix] = g;
+            }
+        }
+        // one atomic per block: every warp of the block reaches this point
+        __shared__ float s_part[S::WARPS];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+        if (lane == 0) s_part[warp] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < S::WARPS; ++k) s += s_part[k];
+            atomicAdd(vt.l1_loss, s);
+        }
+    }
 }
 
 // A lane's gradient sums over its pixels, kept as pairs (A[2] is not used: the
@@ -580,10 +639,16 @@ template <int TS>
 cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
-    if (med)
-        blend_fwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS, FwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
+    constexpr int T = BlendShape<TS, FwdBlock<TS>::H>::THREADS;
+    const bool l1 = vt.l1_loss != nullptr;
+    if (med && l1)
+        blend_fwd_kernel<TS, true, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+    else if (med)
+        blend_fwd_kernel<TS, true, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+    else if (l1)
+        blend_fwd_kernel<TS, false, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS, FwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, false, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,9 @@ struct ViewParams {
     float *normal, *distortion;               // surfels only
     const float *d_normal, *d_distortion;     // surfels only
     float *d_pose;
+    // L1 loss fused into the forward blend (gsr_render_l1); NULL otherwise
+    const float *l1_target_color, *l1_target_depth;
+    float *l1_d_color, *l1_d_depth;
     int tiles_x, tiles_y;
     uint32_t tile_offset;   // first global tile id of this view
     uint32_t pixel_offset;  // first pixel in the concatenated per-pixel buffers
@@ -60,6 +63,8 @@ struct ViewTable {
     int tile;
     uint32_t total_tiles;
     uint32_t total_pixels;
+    float *l1_loss;           // fused L1 loss: the device scalar it adds to, or NULL
+    float l1_color_weight, l1_depth_weight;
     ViewParams v[GSR_MAX_VIEWS];
 };
 

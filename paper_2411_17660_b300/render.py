@@ -128,6 +128,19 @@ class GaussianRasterizer:
         st = self.ctx.render(g, views, ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
         self.ctx.check(st, "gsr_render")
 
+    def forward_l1_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
+                       color: torch.Tensor, depth: Optional[torch.Tensor], alpha: Optional[torch.Tensor],
+                       target_color, target_depth, color_weight: float, depth_weight: float, d_color, d_depth,
+                       loss, median_depth: Optional[torch.Tensor] = None):
+        """forward_raw and l1_loss in one call (gsr_render_l1): the forward
+        blend also writes d_color, d_depth and the device scalar loss."""
+        g = gaussians_struct(*[params[k] for k in PARAM_NAMES], sh_degree)
+        views = view_structs(cams, viewmats, color, depth, alpha, median_depth)
+        t = l1_views(cams, target_color, target_depth, d_color, d_depth)
+        st = self.ctx.render_l1(g, views, t, color_weight, depth_weight, loss.data_ptr(), ws.data_ptr(), ws.numel(),
+                                torch.cuda.current_stream().cuda_stream)
+        self.ctx.check(st, "gsr_render_l1")
+
     def backward_raw(self, params, sh_degree: int, cams, viewmats: torch.Tensor, ws: torch.Tensor,
                      d_color, d_depth, d_alpha, grads: dict, d_pose: Optional[torch.Tensor], accumulate=False,
                      d_median_depth: Optional[torch.Tensor] = None, densify: Optional[dict] = None):
@@ -242,12 +255,9 @@ class _RenderFn(torch.autograd.Function):
                 grads["opacity_logits"], grads["sh"], d_pose)
 
 
-def l1_loss(rast: GaussianRasterizer, cams, viewmats, color, depth, target_color, target_depth,
-            color_weight: float, depth_weight: float, d_color, d_depth, loss):
-    """L1 colour + depth loss (library kernel): fills d_color, d_depth and the
-    device scalar loss.  All arguments are flat buffers laid out like the
-    render outputs."""
-    views = view_structs(cams, viewmats, color, depth, None)
+def l1_views(cams, target_color, target_depth, d_color, d_depth):
+    """The per-view gsr_l1_view structs of flat target / gradient buffers laid
+    out like the render outputs."""
     off = pixel_offsets(cams)
     t = []
     for v in range(len(cams)):
@@ -255,6 +265,16 @@ def l1_loss(rast: GaussianRasterizer, cams, viewmats, color, depth, target_color
                            0 if target_depth is None else target_depth.data_ptr() + 4 * off[v],
                            d_color.data_ptr() + 12 * off[v],
                            0 if d_depth is None else d_depth.data_ptr() + 4 * off[v]))
+    return t
+
+
+def l1_loss(rast: GaussianRasterizer, cams, viewmats, color, depth, target_color, target_depth,
+            color_weight: float, depth_weight: float, d_color, d_depth, loss):
+    """L1 colour + depth loss (library kernel): fills d_color, d_depth and the
+    device scalar loss.  All arguments are flat buffers laid out like the
+    render outputs."""
+    views = view_structs(cams, viewmats, color, depth, None)
+    t = l1_views(cams, target_color, target_depth, d_color, d_depth)
     rast.ctx.l1_loss(views, t, color_weight, depth_weight, loss.data_ptr(), torch.cuda.current_stream().cuda_stream)
 
 
