@@ -512,32 +512,88 @@ __device__ __forceinline__ void warp_sort_tile(const unsigned long long *in, uin
     }
 }
 
-// Stable LSD radix sort of the n <= THREADS * ITEMS words in s by their depth
-// bits (the high halves), 8 bits per pass, skipping the digits that are the
-// same in every word.  The words arrive in id order (the tile-key passes are
-// stable and keys are emitted in pair order), so equal depths stay in id
-// order.  Ranking as in onesweep_kernel: warp w takes words
+// One stable 8-bit LSD pass (digit at bit shift) over the n <= THREADS *
+// ITEMS words in s.  Ranking as in onesweep_kernel: warp w takes words
 // [w 32 ITEMS, (w + 1) 32 ITEMS) in order, ranks them per digit with
 // __match_any_sync and per-warp counters, and the (digit, warp) offsets come
 // from one scan.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ void block_radix_pass(unsigned long long *s, uint32_t n, int shift,
+                                                 uint32_t (*s_whist)[kRadix], uint32_t *s_red) {
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = (uint32_t)warp * (ITEMS * 32);
+    unsigned long long x[ITEMS];
+    uint32_t rank[ITEMS];
+    for (int d = lane; d < kRadix; d += 32) s_whist[warp][d] = 0u;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const uint32_t idx = base + it * 32 + lane;
+        x[it] = idx < n ? s[idx] : 0ull;
+    }
+    __syncthreads();   // all words are in registers before the scatter overwrites s
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const bool valid = base + it * 32 + lane < n;
+        const uint32_t d = valid ? (uint32_t)(x[it] >> shift) & 0xffu : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            old = s_whist[warp][d];
+            s_whist[warp][d] = old + __popc(peers);
+        }
+        rank[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lanemask_lt());
+        __syncwarp();
+    }
+    __syncthreads();
+    // offsets: digit-major, then warp order
+    uint32_t cnt = 0;
+    if (threadIdx.x < kRadix)
+        for (int w = 0; w < WARPS; ++w) cnt += s_whist[w][threadIdx.x];
+    uint32_t total;
+    const uint32_t start = block_exclusive_scan<uint32_t, THREADS>(cnt, s_red, total);
+    if (threadIdx.x < kRadix) {
+        uint32_t c = start;
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t t = s_whist[w][threadIdx.x];
+            s_whist[w][threadIdx.x] = c;
+            c += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        if (base + it * 32 + lane < n) {
+            const uint32_t d = (uint32_t)(x[it] >> shift) & 0xffu;
+            s[s_whist[warp][d] + rank[it]] = x[it];
+        }
+    }
+    __syncthreads();
+}
+
+// Sorts the n <= THREADS * ITEMS (depth bits << 32 | id) words in s, which
+// arrive in any order, ascending.  Passes skip the digits that are the same
+// in every word.  The depth digits alone almost always suffice: the words
+// are unique, so only equal depths need the id digits.  After them the block
+// looks for neighbours of equal depth and, if it finds any, sorts again from
+// the id digits up (a full LSD sort of the words).
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ void block_radix_depth(unsigned long long *s, uint32_t n, uint32_t (*s_whist)[kRadix],
                                                   uint32_t *s_red) {
     static_assert(THREADS >= kRadix, "one thread per digit");
     constexpr int WARPS = THREADS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = (uint32_t)warp * (ITEMS * 32);
-    uint32_t vor = 0u, vand = ~0u;
+    unsigned long long vor = 0ull, vand = ~0ull;
     for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
-        const uint32_t d = (uint32_t)(s[i] >> 32);
-        vor |= d;
-        vand &= d;
+        vor |= s[i];
+        vand &= s[i];
     }
-    vor = __reduce_or_sync(0xffffffffu, vor);
-    vand = __reduce_and_sync(0xffffffffu, vand);
+    uint32_t olo = __reduce_or_sync(0xffffffffu, (uint32_t)vor), ohi = __reduce_or_sync(0xffffffffu, (uint32_t)(vor >> 32));
+    uint32_t alo = __reduce_and_sync(0xffffffffu, (uint32_t)vand), ahi = __reduce_and_sync(0xffffffffu, (uint32_t)(vand >> 32));
     if (lane == 0) {
-        s_red[warp] = vor;
-        s_red[WARPS + warp] = vand;
+        s_red[warp] = olo;
+        s_red[WARPS + warp] = alo;
     }
     __syncthreads();
     uint32_t o = 0u, a = ~0u;
@@ -545,58 +601,34 @@ __device__ __forceinline__ void block_radix_depth(unsigned long long *s, uint32_
         o |= s_red[w];
         a &= s_red[WARPS + w];
     }
-    const uint32_t differ = o ^ a;   // depth bits that are not the same in every word
+    const uint32_t differ_id = o ^ a;
     __syncthreads();
-    for (int pass = 0; pass < 4; ++pass) {
-        if (((differ >> (8 * pass)) & 0xffu) == 0u) continue;
-        const int shift = 32 + 8 * pass;
-        unsigned long long x[ITEMS];
-        uint32_t rank[ITEMS];
-        for (int d = lane; d < kRadix; d += 32) s_whist[warp][d] = 0u;
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const uint32_t idx = base + it * 32 + lane;
-            x[it] = idx < n ? s[idx] : 0ull;
+    if (lane == 0) {
+        s_red[warp] = ohi;
+        s_red[WARPS + warp] = ahi;
+    }
+    __syncthreads();
+    o = 0u;
+    a = ~0u;
+    for (int w = 0; w < WARPS; ++w) {
+        o |= s_red[w];
+        a &= s_red[WARPS + w];
+    }
+    const uint32_t differ_depth = o ^ a;
+    __syncthreads();
+    // steps 0-3: depth digits; then, only with a tie, 4-7: id digits and
+    // 8-11: depth digits again (one call site keeps the pass inlined once)
+#pragma unroll 1
+    for (int step = 0; step < 12; ++step) {
+        if (step == 4) {
+            bool tie = false;
+            for (uint32_t i = threadIdx.x; i + 1 < n; i += THREADS) tie |= (s[i] >> 32) == (s[i + 1] >> 32);
+            if (!__syncthreads_or(tie)) break;
         }
-        __syncthreads();   // all words are in registers before the scatter overwrites s
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const bool valid = base + it * 32 + lane < n;
-            const uint32_t d = valid ? (uint32_t)(x[it] >> shift) & 0xffu : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (valid && lane == leader) {
-                old = s_whist[warp][d];
-                s_whist[warp][d] = old + __popc(peers);
-            }
-            rank[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lanemask_lt());
-            __syncwarp();
-        }
-        __syncthreads();
-        // offsets: digit-major, then warp order
-        uint32_t cnt = 0;
-        if (threadIdx.x < kRadix)
-            for (int w = 0; w < WARPS; ++w) cnt += s_whist[w][threadIdx.x];
-        uint32_t total;
-        const uint32_t start = block_exclusive_scan<uint32_t, THREADS>(cnt, s_red, total);
-        if (threadIdx.x < kRadix) {
-            uint32_t c = start;
-            for (int w = 0; w < WARPS; ++w) {
-                const uint32_t t = s_whist[w][threadIdx.x];
-                s_whist[w][threadIdx.x] = c;
-                c += t;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            if (base + it * 32 + lane < n) {
-                const uint32_t d = (uint32_t)(x[it] >> shift) & 0xffu;
-                s[s_whist[warp][d] + rank[it]] = x[it];
-            }
-        }
-        __syncthreads();
+        const bool depth = step < 4 || step >= 8;
+        const int pass = step & 3;
+        if ((((depth ? differ_depth : differ_id) >> (8 * pass)) & 0xffu) == 0u) continue;
+        block_radix_pass<THREADS, ITEMS>(s, n, (depth ? 32 : 0) + 8 * pass, s_whist, s_red);
     }
 }
 

@@ -111,6 +111,21 @@ def test_block_sort_path_and_depth_ties_against_oracle():
     U.compare_grads(gref, g, label="clump")
 
 
+@pytest.mark.parametrize("N,log_scale", [(1500, -1.2), (8000, -0.6)])
+def test_depth_ties_between_distant_ids(N, log_scale):
+    """Gaussians k and k + N/2 share their mean (so their depth) but not their
+    shape, opacity or colour: far apart in id, they are emitted by different
+    warps in either order, and the block and big-tile sorts must still put
+    the lower id first (the radix strategy orders them by pair order)."""
+    sc = _clump(N, log_scale=log_scale, pair_ties=False)
+    h = N // 2
+    sc.means[:, h:2 * h] = sc.means[:, :h]
+    a, sa = _forward(sc, "tile")
+    big = log_scale > -1.0
+    assert sa[0].info(sa[4]).keys > 12 * (2048 if big else 256)
+    _assert_same_images(a, _forward(sc, "radix")[0])
+
+
 def test_merge_sort_path_matches_radix():
     # 40,000 faint Gaussians (sigma ~ 0.011, so that 255 sigma > 1 still
     # leaves a cutoff ellipse) wider than the view: each of the 12 tiles holds
