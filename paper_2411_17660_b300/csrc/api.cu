@@ -62,7 +62,7 @@ struct CallTrace {
 
 struct Layout {
     size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, rec4, rec5, radius, aux;
-    size_t keys0, keys1, vals0, vals1, hist, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
+    size_t keys0, keys1, vals0, vals1, hist, tile_cursor, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
     size_t total;
     uint64_t VN;
     uint32_t cap, lb_tiles, scan_blocks, pose_blocks, total_pixels, total_tiles;
@@ -106,6 +106,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.aux = take(8ull * L.total_pixels);
     L.hist = take(4ull * kMaxPasses * kRadix);
     L.ranges = take(8ull * L.total_tiles);
+    L.tile_cursor = take(4ull * L.total_tiles);
     L.T_final = take(4ull * L.total_pixels);
     L.last = take(4ull * L.total_pixels);
     L.median = take(4ull * L.total_pixels);
@@ -138,6 +139,18 @@ uint32_t capacity_for(int N, const gsr_view *views, int V, int tile, size_t byte
     return (uint32_t)cap;
 }
 
+// Which key buffers the sort passes through and where the sorted ids end:
+// radix, 8-bit passes over (tile, depth bits); per-tile, passes over the tile
+// id only (or one bucket scatter), then each tile's words are sorted in
+// shared memory.  Depends on the primitive, so it is set again for surfels.
+void set_sort_plan(Ws &w, int tbits) {
+    if (bucket_binning(w))
+        w.passes = 1;   // the scatter writes keys[1]
+    else
+        w.passes = w.bin_tile ? (tbits + 7) / 8 : (32 + tbits + 7) / 8;
+    w.sorted = w.vals[w.bin_tile ? (w.passes + 1) & 1 : w.passes & 1];
+}
+
 Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     char *b = static_cast<char *>(base);
     Ws w;
@@ -159,12 +172,9 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     w.keys[1] = reinterpret_cast<unsigned long long *>(b + L.keys1);
     w.vals[0] = reinterpret_cast<uint32_t *>(b + L.vals0);
     w.vals[1] = reinterpret_cast<uint32_t *>(b + L.vals1);
-    // radix: 8-bit passes over (tile, depth bits); per-tile: over the tile id
-    // only, then each tile's words are sorted in shared memory
     w.bin_tile = ctx.binning == GSR_BIN_TILE;
-    w.passes = w.bin_tile ? (L.tbits + 7) / 8 : (32 + L.tbits + 7) / 8;
-    w.sorted = w.vals[w.bin_tile ? (w.passes + 1) & 1 : w.passes & 1];
     w.hist = reinterpret_cast<uint32_t *>(b + L.hist);
+    w.tile_cursor = reinterpret_cast<uint32_t *>(b + L.tile_cursor);
     w.lookback = reinterpret_cast<uint32_t *>(b + L.lookback);
     w.ranges = reinterpret_cast<uint2 *>(b + L.ranges);
     w.T_final = reinterpret_cast<float *>(b + L.T_final);
@@ -183,6 +193,7 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     w.total_tiles = L.total_tiles;
     w.spin_limit = ctx.spin;
     w.test_flags = ctx.flags;
+    set_sort_plan(w, L.tbits);
     return w;
 }
 
@@ -563,6 +574,7 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
     Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     w.surfels = 1;
     w.vg_stride = kVGGradsMax;
+    set_sort_plan(w, L.tbits);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
@@ -620,6 +632,7 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
     Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     w.surfels = 1;
     w.vg_stride = kVGGradsMax;
+    set_sort_plan(w, L.tbits);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     GradPtrs gout;
     gout.means = out->means;

@@ -10,11 +10,13 @@
 //   pass; equal depths keep the pair order, i.e. the id order), and a boundary
 //   pass for the ranges.
 // per-tile (default): u32 tile keys with (depth bits << 32 | id) words as
-//   values; the onesweep sort runs over the tile bits only (2 passes for up to
-//   65,536 tiles instead of 6), the boundary pass gives the ranges, and each
-//   tile's words -- unique, since a Gaussian meets a tile once -- are sorted
-//   in registers (a warp) or shared memory (a block), which orders them by
-//   depth and then id.
+//   values, grouped by tile, after which each tile's words -- unique, since a
+//   Gaussian meets a tile once -- are sorted in registers (a warp) or shared
+//   memory (a block), which orders them by depth and then id.  Grouping: with
+//   up to 65,536 tiles the preprocess counts the keys of every tile as it
+//   emits them, one block scans the counts into the ranges, and each key
+//   takes the next slot of its tile (bucket_binning); beyond, the onesweep
+//   sort runs over the tile bits only and the boundary pass gives the ranges.
 //
 // All sizes the host cannot know (the key count) are read on the device, so
 // either sequence needs no host sync and can be captured in a CUDA graph.
@@ -446,6 +448,103 @@ __global__ void __launch_bounds__(256) ranges_kernel(const Ws ws, const K *keys)
     }
 }
 
+// ------------------------------------------------------------------ per-tile: bucket grouping
+// A block per SM takes one contiguous slice of the unsorted keys and counts
+// them per tile in shared memory (a counter per tile), so that a crowded tile
+// costs one global atomic per block instead of one per key:
+//   count:   tile_cursor[t] += the slice's keys of tile t;
+//   ranges:  one block scans the counts into [start, end) and sets
+//            tile_cursor[t] = start;
+//   scatter: the block reserves its keys' slots of every tile with one
+//            atomic each, then places each key at the next reserved slot.
+// The order within a tile depends on timing; the per-tile sort below makes
+// it (depth, id).
+constexpr int kBucketThreads = 1024;
+
+__device__ __forceinline__ void bucket_slice(const Ws &ws, uint32_t n, uint32_t &b0, uint32_t &b1) {
+    const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+    b0 = min(n, blockIdx.x * per);
+    b1 = min(n, b0 + per);
+}
+
+// Counts of the slice's keys per tile in s_bins (zeroed here).
+__device__ __forceinline__ void bucket_block_counts(const Ws &ws, uint32_t *s_bins, uint32_t b0, uint32_t b1) {
+    const uint32_t T = ws.total_tiles;
+    const uint32_t *tiles = ws.vals[0];
+    for (uint32_t i = threadIdx.x; i < T; i += kBucketThreads) s_bins[i] = 0u;
+    __syncthreads();
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
+        const uint32_t t = tiles[i];
+        if (t < T)
+            atomicAdd(s_bins + t, 1u);
+        else
+            (void)GSR_CHECK(ws.hdr, false);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const Ws ws) {
+    extern __shared__ uint32_t s_bins[];
+    uint32_t b0, b1;
+    bucket_slice(ws, key_count(ws), b0, b1);
+    bucket_block_counts(ws, s_bins, b0, b1);
+    for (uint32_t t = threadIdx.x; t < ws.total_tiles; t += kBucketThreads)
+        if (s_bins[t]) atomicAdd(ws.tile_cursor + t, s_bins[t]);
+}
+
+// Exclusive scan of the per-tile key counts by one block: each tile's
+// [start, end) range (the counts add up to the key count, which is at most
+// the capacity) and its first free slot in tile_cursor.
+constexpr int kBucketScanItems = 16;
+__global__ void __launch_bounds__(kBucketThreads) bucket_ranges_kernel(const Ws ws) {
+    __shared__ uint32_t s_warp[kBucketThreads / 32];
+    constexpr uint32_t kChunk = kBucketThreads * kBucketScanItems;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < ws.total_tiles; c0 += kChunk) {
+        const uint32_t t0 = c0 + threadIdx.x * kBucketScanItems;
+        uint32_t cnt[kBucketScanItems], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kBucketScanItems; ++k) {
+            cnt[k] = t0 + k < ws.total_tiles ? ws.tile_cursor[t0 + k] : 0u;
+            sum += cnt[k];
+        }
+        uint32_t total;
+        uint32_t at = carry + block_exclusive_scan<uint32_t, kBucketThreads>(sum, s_warp, total);
+#pragma unroll
+        for (int k = 0; k < kBucketScanItems; ++k) {
+            if (t0 + k < ws.total_tiles) {
+                const uint32_t e = at + cnt[k];
+                if (!GSR_CHECK(ws.hdr, e <= ws.cap)) break;
+                ws.ranges[t0 + k] = make_uint2(at, e);
+                ws.tile_cursor[t0 + k] = at;
+            }
+            at += cnt[k];
+        }
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kBucketThreads) bucket_scatter_kernel(const Ws ws) {
+    extern __shared__ uint32_t s_bins[];
+    uint32_t b0, b1;
+    bucket_slice(ws, key_count(ws), b0, b1);
+    bucket_block_counts(ws, s_bins, b0, b1);
+    for (uint32_t t = threadIdx.x; t < ws.total_tiles; t += kBucketThreads) {
+        const uint32_t c = s_bins[t];
+        if (c) s_bins[t] = atomicAdd(ws.tile_cursor + t, c);   // the block's first slot of tile t
+    }
+    __syncthreads();
+    const uint32_t *tiles = ws.vals[0];
+    const unsigned long long *words = ws.keys[0];
+    unsigned long long *out = ws.keys[1];
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
+        const uint32_t t = tiles[i];
+        if (t >= ws.total_tiles) continue;   // reported by the count
+        const uint32_t pos = atomicAdd(s_bins + t, 1u);
+        if (GSR_CHECK(ws.hdr, pos < ws.cap)) out[pos] = words[i];
+    }
+}
+
 // ------------------------------------------------------------------ per-tile: sort within each tile
 // After the tile-key passes, tile t's (depth bits << 32 | id) words sit in
 // words[start, end) in pair order; ascending words are the list order.  Up to
@@ -784,6 +883,24 @@ cudaError_t launch_ranges_of(const Ws &ws, int sm_count, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// More than 48 KB of dynamic shared memory needs an opt-in (a host-side
+// attribute of the kernel), once per kernel and device.
+template <auto Kernel>
+cudaError_t allow_smem(size_t bytes) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
+constexpr size_t kBucketSmemMax = 4ull * kBucketMaxTiles;
+
 }  // namespace
 
 // Gaussians binned per tile emit their keys in the preprocess (keys_in_preprocess).
@@ -799,24 +916,25 @@ cudaError_t launch_scan_duplicate(const ViewTable &vt, const Ws &ws, cudaStream_
 // Per-tile binning also makes the ranges and sorts within the tiles here.
 cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     if (!ws.bin_tile) return ws.VN == 0 ? cudaSuccess : launch_radix<unsigned long long, uint32_t>(ws, sm_count, st);
-    cudaError_t e = ws.VN == 0 ? cudaSuccess : launch_radix<uint32_t, unsigned long long>(ws, sm_count, st);
-    if (e == cudaSuccess) e = launch_ranges_of(ws, sm_count, st);   // clears the ranges even with no pairs
+    cudaError_t e = cudaSuccess;
+    if (bucket_binning(ws)) {   // writes every tile's range, even with no pairs
+        const size_t smem = 4ull * ws.total_tiles;
+        if ((e = cudaMemsetAsync(ws.tile_cursor, 0, smem, st)) != cudaSuccess) return e;
+        if ((e = allow_smem<bucket_count_kernel>(kBucketSmemMax)) != cudaSuccess ||
+            (e = allow_smem<bucket_scatter_kernel>(kBucketSmemMax)) != cudaSuccess)
+            return e;
+        if (ws.VN > 0) bucket_count_kernel<<<sm_count, kBucketThreads, smem, st>>>(ws);
+        bucket_ranges_kernel<<<1, kBucketThreads, 0, st>>>(ws);
+        if (ws.VN > 0) bucket_scatter_kernel<<<sm_count, kBucketThreads, smem, st>>>(ws);
+        e = cudaGetLastError();
+    } else {
+        e = ws.VN == 0 ? cudaSuccess : launch_radix<uint32_t, unsigned long long>(ws, sm_count, st);
+        if (e == cudaSuccess) e = launch_ranges_of(ws, sm_count, st);   // clears the ranges even with no pairs
+    }
     if (e != cudaSuccess || ws.VN == 0 || ws.total_tiles == 0) return e;
     tile_sort_kernel<<<(ws.total_tiles + kTilesPerSortBlock - 1) / kTilesPerSortBlock, 32 * kTilesPerSortBlock, 0,
                        st>>>(ws);
-    // more than 48 KB of dynamic shared memory needs an opt-in, once per device
-    static std::mutex mu;
-    static bool done[64] = {};
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (dev < 0 || dev >= 64 || !done[dev]) {
-            e = cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigSortSmem);
-            if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) done[dev] = true;
-        }
-    }
+    if ((e = allow_smem<tile_sort_big_kernel>(kBigSortSmem)) != cudaSuccess) return e;
     const unsigned blocks = std::min<unsigned>(ws.total_tiles, (unsigned)sm_count);
     tile_sort_big_kernel<<<blocks, kBigSortThreads, kBigSortSmem, st>>>(ws);
     return cudaGetLastError();

@@ -111,6 +111,7 @@ struct Ws {
     uint32_t *sorted;        // [keys] Gaussian ids in (tile, depth, id) order
     int bin_tile;
     uint32_t *hist;          // [kMaxPasses][256]
+    uint32_t *tile_cursor;   // [total_tiles] bucket binning: keys per tile, then each tile's next free slot
     uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
     uint2 *ranges;           // [total_tiles] [start, end) in the sorted list
     float *T_final;          // [total_pixels]
@@ -132,6 +133,14 @@ struct Ws {
 // in which the unsorted keys land does not matter.  The other paths place
 // the keys by an exclusive scan of the tile counts.
 __host__ __device__ __forceinline__ bool keys_in_preprocess(const Ws &w) { return w.bin_tile && !w.surfels; }
+
+// With at most kBucketMaxTiles tiles (a shared-memory counter each) those
+// keys are grouped by tile with counting kernels instead of the onesweep
+// passes over the tile bits.
+constexpr uint32_t kBucketMaxTiles = 1u << 15;
+__host__ __device__ __forceinline__ bool bucket_binning(const Ws &w) {
+    return keys_in_preprocess(w) && w.total_tiles <= kBucketMaxTiles;
+}
 
 __device__ __forceinline__ void set_status(WsHeader *h, int code) {
     atomicCAS(reinterpret_cast<int *>(&h->status), 0, code);

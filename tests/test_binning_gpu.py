@@ -126,6 +126,16 @@ def test_depth_ties_between_distant_ids(N, log_scale):
     _assert_same_images(a, _forward(sc, "radix")[0])
 
 
+def test_onesweep_tile_grouping_beyond_the_bucket_limit():
+    """More than 65,536 tiles (4 views of 1280x1024 at tile 8: 81,920): the
+    per-tile strategy groups the keys with the onesweep passes over the tile
+    bits instead of the bucket scatter, and must still match the radix one."""
+    sc = scenes.config_window(N=3000, V=4, H=1024, W=1280, f=900.0)
+    a, sa = _forward(sc, "tile", tile=8)
+    assert sa[0].info(sa[4]).tiles > 65536
+    _assert_same_images(a, _forward(sc, "radix", tile=8)[0])
+
+
 def test_merge_sort_path_matches_radix():
     # 40,000 faint Gaussians (sigma ~ 0.011, so that 255 sigma > 1 still
     # leaves a cutoff ellipse) wider than the view: each of the 12 tiles holds
