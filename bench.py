@@ -385,9 +385,9 @@ def launches_per_step(rast, win):
     loss = 0 if win.fuse_l1 else 1
     if rast.binning == "tile" and not win.surfels:
         group = 3 if tiles <= 32768 else 2 + (tbits + 7) // 8
-        return 7 + loss + group + 2
-    if rast.binning == "tile":   # surfels: scan + duplicate, then as above without the bucket path
-        return 11 + loss + (tbits + 7) // 8 + 2
+        return 6 + loss + group + 2
+    if rast.binning == "tile":   # surfels: scan + duplicate, then the onesweep grouping
+        return 12 + loss + (tbits + 7) // 8 + 2
     return 12 + loss + (32 + tbits + 7) // 8
 
 
