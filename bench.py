@@ -378,13 +378,13 @@ def launches_per_step(rast, win):
     # init, preprocess, 3 scan kernels, duplicate, histogram, the radix
     # passes, ranges, blend, loss, blend backward, preprocess backward, pose
     # sums; per-tile binning emits its keys in the preprocess (no scan, no
-    # duplicate), groups the keys by tile -- up to 32,768 tiles with a count,
-    # a scan and a scatter, beyond with a histogram, the radix passes over the
+    # duplicate), groups the keys by tile -- up to 32,768 tiles with a count (with
+    # the scan in its last block) and a scatter, beyond with a histogram, the radix passes over the
     # tile bits and the ranges -- and adds 2 tile sorts; the L1 loss fused into
     # the forward blend has no kernel of its own
     loss = 0 if win.fuse_l1 else 1
     if rast.binning == "tile" and not win.surfels:
-        group = 3 if tiles <= 32768 else 2 + (tbits + 7) // 8
+        group = 2 if tiles <= 32768 else 2 + (tbits + 7) // 8
         return 6 + loss + group + 2
     if rast.binning == "tile":   # surfels: scan + duplicate, then the onesweep grouping
         return 12 + loss + (tbits + 7) // 8 + 2

@@ -452,16 +452,19 @@ __global__ void __launch_bounds__(256) ranges_kernel(const Ws ws, const K *keys)
 // A block per SM takes one contiguous slice of the unsorted keys and counts
 // them per tile in shared memory (a counter per tile), so that a crowded tile
 // costs one global atomic per block instead of one per key:
-//   count:   tile_cursor[t] += the slice's keys of tile t;
-//   ranges:  one block scans the counts into [start, end) and sets
+//   count:   tile_cursor[t] += the slice's keys of tile t; the last block to
+//            finish scans the counts into the ranges [start, end) and sets
 //            tile_cursor[t] = start;
 //   scatter: the block reserves its keys' slots of every tile with one
 //            atomic each, then places each key at the next reserved slot.
 // The order within a tile depends on timing; the per-tile sort below makes
 // it (depth, id).
 constexpr int kBucketThreads = 1024;
+constexpr int kBucketScanItems = kBucketMaxTiles / kBucketThreads;   // tiles per thread in the scan
+constexpr int kBucketReserve = 8;                                     // reservations in flight per thread
+constexpr int kBucketLoads = 4;                                       // keys loaded ahead per thread
 
-__device__ __forceinline__ void bucket_slice(const Ws &ws, uint32_t n, uint32_t &b0, uint32_t &b1) {
+__device__ __forceinline__ void bucket_slice(uint32_t n, uint32_t &b0, uint32_t &b1) {
     const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
     b0 = min(n, blockIdx.x * per);
     b1 = min(n, b0 + per);
@@ -473,75 +476,134 @@ __device__ __forceinline__ void bucket_block_counts(const Ws &ws, uint32_t *s_bi
     const uint32_t *tiles = ws.vals[0];
     for (uint32_t i = threadIdx.x; i < T; i += kBucketThreads) s_bins[i] = 0u;
     __syncthreads();
-    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
-        const uint32_t t = tiles[i];
-        if (t < T)
-            atomicAdd(s_bins + t, 1u);
-        else
-            (void)GSR_CHECK(ws.hdr, false);
+    for (uint32_t i0 = b0 + threadIdx.x; i0 < b1; i0 += kBucketThreads * kBucketLoads) {
+        uint32_t t[kBucketLoads];
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u) {
+            const uint32_t i = i0 + u * kBucketThreads;
+            t[u] = i < b1 ? tiles[i] : T;
+        }
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u) {
+            if (t[u] < T)
+                atomicAdd(s_bins + t[u], 1u);
+            else if (i0 + u * kBucketThreads < b1)
+                (void)GSR_CHECK(ws.hdr, false);
+        }
     }
     __syncthreads();
 }
 
+// Tile t's word in the scan's staging buffer: one word of padding after
+// every 32, so that a thread walking its kBucketScanItems consecutive tiles
+// and a warp reading 32 consecutive ones both meet 32 different banks.
+__device__ __forceinline__ uint32_t bucket_pad(uint32_t t) { return t + (t >> 5); }
+constexpr size_t kBucketSmemMax = 4ull * (kBucketMaxTiles + kBucketMaxTiles / 32 + 1);
+__host__ __device__ constexpr size_t bucket_smem(uint32_t T) { return 4ull * (T + T / 32 + 1); }
+
+// Exclusive scan of the T <= kBucketMaxTiles tile counts (complete in
+// tile_cursor) by one block, staged in s (bucket_smem(T) bytes): ranges and
+// first slots.
+__device__ __forceinline__ void bucket_scan(const Ws &ws, uint32_t *s, uint32_t *s_warp) {
+    const uint32_t T = ws.total_tiles;
+    {   // all of a thread's loads in flight at once
+        uint32_t c[kBucketScanItems];
+#pragma unroll
+        for (int k = 0; k < kBucketScanItems; ++k) {
+            const uint32_t i = threadIdx.x + k * kBucketThreads;
+            c[k] = i < T ? __ldcg(ws.tile_cursor + i) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kBucketScanItems; ++k) {
+            const uint32_t i = threadIdx.x + k * kBucketThreads;
+            if (i < T) s[bucket_pad(i)] = c[k];
+        }
+    }
+    __syncthreads();
+    const uint32_t t0 = threadIdx.x * kBucketScanItems;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kBucketScanItems; ++k) sum += t0 + k < T ? s[bucket_pad(t0 + k)] : 0u;
+    uint32_t total;
+    uint32_t at = block_exclusive_scan<uint32_t, kBucketThreads>(sum, s_warp, total);
+#pragma unroll
+    for (int k = 0; k < kBucketScanItems; ++k) {
+        if (t0 + k < T) {
+            const uint32_t c = s[bucket_pad(t0 + k)];
+            s[bucket_pad(t0 + k)] = at;
+            at += c;
+        }
+    }
+    __syncthreads();
+    // the counts add up to the key count, which is at most the capacity
+    if (!GSR_CHECK(ws.hdr, total <= ws.cap)) return;
+    for (uint32_t i = threadIdx.x; i < T; i += kBucketThreads) {
+        const uint32_t a = s[bucket_pad(i)], e = i + 1 < T ? s[bucket_pad(i + 1)] : total;
+        ws.ranges[i] = make_uint2(a, e);
+        ws.tile_cursor[i] = a;
+    }
+}
+
 __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const Ws ws) {
     extern __shared__ uint32_t s_bins[];
+    __shared__ uint32_t s_warp[kBucketThreads / 32];
+    __shared__ bool s_last;
     uint32_t b0, b1;
-    bucket_slice(ws, key_count(ws), b0, b1);
+    bucket_slice(key_count(ws), b0, b1);
     bucket_block_counts(ws, s_bins, b0, b1);
     for (uint32_t t = threadIdx.x; t < ws.total_tiles; t += kBucketThreads)
         if (s_bins[t]) atomicAdd(ws.tile_cursor + t, s_bins[t]);
-}
-
-// Exclusive scan of the per-tile key counts by one block: each tile's
-// [start, end) range (the counts add up to the key count, which is at most
-// the capacity) and its first free slot in tile_cursor.
-constexpr int kBucketScanItems = 16;
-__global__ void __launch_bounds__(kBucketThreads) bucket_ranges_kernel(const Ws ws) {
-    __shared__ uint32_t s_warp[kBucketThreads / 32];
-    constexpr uint32_t kChunk = kBucketThreads * kBucketScanItems;
-    uint32_t carry = 0;
-    for (uint32_t c0 = 0; c0 < ws.total_tiles; c0 += kChunk) {
-        const uint32_t t0 = c0 + threadIdx.x * kBucketScanItems;
-        uint32_t cnt[kBucketScanItems], sum = 0;
-#pragma unroll
-        for (int k = 0; k < kBucketScanItems; ++k) {
-            cnt[k] = t0 + k < ws.total_tiles ? ws.tile_cursor[t0 + k] : 0u;
-            sum += cnt[k];
-        }
-        uint32_t total;
-        uint32_t at = carry + block_exclusive_scan<uint32_t, kBucketThreads>(sum, s_warp, total);
-#pragma unroll
-        for (int k = 0; k < kBucketScanItems; ++k) {
-            if (t0 + k < ws.total_tiles) {
-                const uint32_t e = at + cnt[k];
-                if (!GSR_CHECK(ws.hdr, e <= ws.cap)) break;
-                ws.ranges[t0 + k] = make_uint2(at, e);
-                ws.tile_cursor[t0 + k] = at;
-            }
-            at += cnt[k];
-        }
-        carry += total;
-    }
+    // the last block to finish (its counts and every other block's are in
+    // tile_cursor once each block has fenced them) scans
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ws.hdr->sort_counter[0], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    bucket_scan(ws, s_bins, s_warp);
 }
 
 __global__ void __launch_bounds__(kBucketThreads) bucket_scatter_kernel(const Ws ws) {
     extern __shared__ uint32_t s_bins[];
     uint32_t b0, b1;
-    bucket_slice(ws, key_count(ws), b0, b1);
+    bucket_slice(key_count(ws), b0, b1);
     bucket_block_counts(ws, s_bins, b0, b1);
-    for (uint32_t t = threadIdx.x; t < ws.total_tiles; t += kBucketThreads) {
-        const uint32_t c = s_bins[t];
-        if (c) s_bins[t] = atomicAdd(ws.tile_cursor + t, c);   // the block's first slot of tile t
+    // the block's first slot of every tile it has keys of; kBucketReserve
+    // atomics in flight per thread
+    for (uint32_t t0 = threadIdx.x; t0 < ws.total_tiles; t0 += kBucketThreads * kBucketReserve) {
+        uint32_t c[kBucketReserve], at[kBucketReserve];
+#pragma unroll
+        for (int k = 0; k < kBucketReserve; ++k) {
+            const uint32_t t = t0 + k * kBucketThreads;
+            c[k] = t < ws.total_tiles ? s_bins[t] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kBucketReserve; ++k)
+            if (c[k]) at[k] = atomicAdd(ws.tile_cursor + t0 + k * kBucketThreads, c[k]);
+#pragma unroll
+        for (int k = 0; k < kBucketReserve; ++k)
+            if (c[k]) s_bins[t0 + k * kBucketThreads] = at[k];
     }
     __syncthreads();
     const uint32_t *tiles = ws.vals[0];
     const unsigned long long *words = ws.keys[0];
     unsigned long long *out = ws.keys[1];
-    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kBucketThreads) {
-        const uint32_t t = tiles[i];
-        if (t >= ws.total_tiles) continue;   // reported by the count
-        const uint32_t pos = atomicAdd(s_bins + t, 1u);
-        if (GSR_CHECK(ws.hdr, pos < ws.cap)) out[pos] = words[i];
+    for (uint32_t i0 = b0 + threadIdx.x; i0 < b1; i0 += kBucketThreads * kBucketLoads) {
+        uint32_t t[kBucketLoads];
+        unsigned long long w[kBucketLoads];
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u) {
+            const uint32_t i = i0 + u * kBucketThreads;
+            t[u] = i < b1 ? tiles[i] : ws.total_tiles;
+            w[u] = i < b1 ? words[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u) {
+            if (t[u] >= ws.total_tiles) continue;   // past the slice, or reported by the count
+            const uint32_t pos = atomicAdd(s_bins + t[u], 1u);
+            if (GSR_CHECK(ws.hdr, pos < ws.cap)) out[pos] = w[u];
+        }
     }
 }
 
@@ -899,7 +961,6 @@ cudaError_t allow_smem(size_t bytes) {
     return e;
 }
 
-constexpr size_t kBucketSmemMax = 4ull * kBucketMaxTiles;
 
 }  // namespace
 
@@ -918,13 +979,12 @@ cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     if (!ws.bin_tile) return ws.VN == 0 ? cudaSuccess : launch_radix<unsigned long long, uint32_t>(ws, sm_count, st);
     cudaError_t e = cudaSuccess;
     if (bucket_binning(ws)) {   // writes every tile's range, even with no pairs
-        const size_t smem = 4ull * ws.total_tiles;
-        if ((e = cudaMemsetAsync(ws.tile_cursor, 0, smem, st)) != cudaSuccess) return e;
+        const size_t smem = bucket_smem(ws.total_tiles);
+        if ((e = cudaMemsetAsync(ws.tile_cursor, 0, 4ull * ws.total_tiles, st)) != cudaSuccess) return e;
         if ((e = allow_smem<bucket_count_kernel>(kBucketSmemMax)) != cudaSuccess ||
             (e = allow_smem<bucket_scatter_kernel>(kBucketSmemMax)) != cudaSuccess)
             return e;
-        if (ws.VN > 0) bucket_count_kernel<<<sm_count, kBucketThreads, smem, st>>>(ws);
-        bucket_ranges_kernel<<<1, kBucketThreads, 0, st>>>(ws);
+        bucket_count_kernel<<<sm_count, kBucketThreads, smem, st>>>(ws);   // also scans: always
         if (ws.VN > 0) bucket_scatter_kernel<<<sm_count, kBucketThreads, smem, st>>>(ws);
         e = cudaGetLastError();
     } else {
