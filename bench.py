@@ -383,11 +383,11 @@ def launches_per_step(rast, win):
     # tile bits and the ranges -- and adds 2 tile sorts; the L1 loss fused into
     # the forward blend has no kernel of its own
     loss = 0 if win.fuse_l1 else 1
+    group = 2 if tiles <= 32768 else 2 + (tbits + 7) // 8
     if rast.binning == "tile" and not win.surfels:
-        group = 2 if tiles <= 32768 else 2 + (tbits + 7) // 8
         return 6 + loss + group + 2
-    if rast.binning == "tile":   # surfels: scan + duplicate, then the onesweep grouping
-        return 12 + loss + (tbits + 7) // 8 + 2
+    if rast.binning == "tile":   # surfels: scan + duplicate, then the same grouping
+        return 10 + loss + group + 2
     return 12 + loss + (32 + tbits + 7) // 8
 
 

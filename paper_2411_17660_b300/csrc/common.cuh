@@ -131,15 +131,18 @@ struct Ws {
 // preprocess: each warp reserves its pairs' keys with one atomic on the key
 // count.  Every tile's words are sorted completely afterwards, so the order
 // in which the unsorted keys land does not matter.  The other paths place
-// the keys by an exclusive scan of the tile counts.
+// the keys by an exclusive scan of the tile counts.  (The surfel preprocess
+// takes one Gaussian per thread, so a warp with one large surfel would emit
+// its keys with one lane for every view: 0.054 -> 0.39 ms measured.)
 __host__ __device__ __forceinline__ bool keys_in_preprocess(const Ws &w) { return w.bin_tile && !w.surfels; }
 
-// With at most kBucketMaxTiles tiles (a shared-memory counter each) those
-// keys are grouped by tile with counting kernels instead of the onesweep
-// passes over the tile bits.
+// With per-tile binning and at most kBucketMaxTiles tiles (a shared-memory
+// counter each) the unsorted keys -- from the preprocess, or from the
+// duplication for surfels -- are grouped by tile with counting kernels
+// instead of the onesweep passes over the tile bits.
 constexpr uint32_t kBucketMaxTiles = 1u << 15;
 __host__ __device__ __forceinline__ bool bucket_binning(const Ws &w) {
-    return keys_in_preprocess(w) && w.total_tiles <= kBucketMaxTiles;
+    return w.bin_tile && w.total_tiles <= kBucketMaxTiles;
 }
 
 __device__ __forceinline__ void set_status(WsHeader *h, int code) {
