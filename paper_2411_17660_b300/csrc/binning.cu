@@ -735,10 +735,13 @@ __device__ __forceinline__ void block_radix_pass(unsigned long long *s, uint32_t
 
 // Sorts the n <= THREADS * ITEMS (depth bits << 32 | id) words in s, which
 // arrive in any order, ascending.  Passes skip the digits that are the same
-// in every word.  The depth digits alone almost always suffice: the words
-// are unique, so only equal depths need the id digits.  After them the block
-// looks for neighbours of equal depth and, if it finds any, sorts again from
-// the id digits up (a full LSD sort of the words).
+// in every word.  The depth digits leave only equal depths out of order (the
+// words are unique); in big tiles some equal depths are all but certain, in
+// short runs, so odd-even transposition rounds over neighbours of equal depth
+// put them in id order (a depth-sorted array whose equal-depth neighbours are
+// in order is sorted).  Runs too long for kTieRounds rounds (many Gaussians
+// at one depth) get a full LSD sort from the id digits up.
+constexpr int kTieRounds = 8;
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ void block_radix_depth(unsigned long long *s, uint32_t n, uint32_t (*s_whist)[kRadix],
                                                   uint32_t *s_red) {
@@ -777,14 +780,31 @@ __device__ __forceinline__ void block_radix_depth(unsigned long long *s, uint32_
     }
     const uint32_t differ_depth = o ^ a;
     __syncthreads();
-    // steps 0-3: depth digits; then, only with a tie, 4-7: id digits and
-    // 8-11: depth digits again (one call site keeps the pass inlined once)
+    // steps 0-3: depth digits; then, only with ties the transposition rounds
+    // leave out of order, 4-7: id digits and 8-11: depth digits again (one
+    // call site keeps the pass inlined once)
 #pragma unroll 1
     for (int step = 0; step < 12; ++step) {
         if (step == 4) {
-            bool tie = false;
-            for (uint32_t i = threadIdx.x; i + 1 < n; i += THREADS) tie |= (s[i] >> 32) == (s[i + 1] >> 32);
-            if (!__syncthreads_or(tie)) break;
+            bool sorted = false;
+#pragma unroll 1
+            for (int round = 0; round < kTieRounds && !sorted; ++round) {
+                bool swapped = false;
+#pragma unroll 1
+                for (uint32_t phase = 0; phase < 2; ++phase) {
+                    for (uint32_t i = 2 * threadIdx.x + phase; i + 1 < n; i += 2 * THREADS) {
+                        const unsigned long long a = s[i], b = s[i + 1];
+                        if ((a >> 32) == (b >> 32) && a > b) {
+                            s[i] = b;
+                            s[i + 1] = a;
+                            swapped = true;
+                        }
+                    }
+                    __syncthreads();
+                }
+                sorted = !__syncthreads_or(swapped);
+            }
+            if (sorted) break;
         }
         const bool depth = step < 4 || step >= 8;
         const int pass = step & 3;

@@ -126,6 +126,18 @@ def test_depth_ties_between_distant_ids(N, log_scale):
     _assert_same_images(a, _forward(sc, "radix")[0])
 
 
+def test_long_runs_of_equal_depth():
+    """40 Gaussians share each of 75 means (ids k, k + 75, ...): runs of 40
+    equal depths, too long for the transposition rounds, take the block sort's
+    full re-sort from the id digits, and must match the radix strategy."""
+    N = 3000
+    sc = _clump(N, pair_ties=False)
+    sc.means[:] = sc.means[:, np.arange(N) % 75]
+    a, sa = _forward(sc, "tile")
+    assert sa[0].info(sa[4]).keys > 12 * 256
+    _assert_same_images(a, _forward(sc, "radix")[0])
+
+
 def test_onesweep_tile_grouping_beyond_the_bucket_limit():
     """More than 65,536 tiles (4 views of 1280x1024 at tile 8: 81,920): the
     per-tile strategy groups the keys with the onesweep passes over the tile
