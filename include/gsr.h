@@ -189,7 +189,10 @@ gsr_status gsr_workspace_size(gsr_ctx *ctx, int N, const gsr_view *views, int V,
  * front-to-back compositing (Sec. 3.3, Eq. "rendering").  Writes each view's
  * color/depth/alpha and keeps in the workspace what the backward needs.
  * ws must be 256-byte aligned and ws_bytes >= gsr_workspace_size(..., cap)
- * for some cap; the key capacity is derived from ws_bytes. */
+ * for some cap; the key capacity is derived from ws_bytes.  The first render
+ * on a device also raises some binning kernels' shared-memory limit (a
+ * host-side setting), so make one render call before capturing the stream
+ * into a CUDA graph. */
 gsr_status gsr_render(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
                       void *ws, size_t ws_bytes, gsr_stream stream);
 
