@@ -220,9 +220,12 @@ def test_full_size_sampled_pixels(name):
     U.compare_grads(orc, gpu, label=name)
 
 
-def test_cuda_graph_replay_matches_eager():
+@pytest.mark.parametrize("fused", [False, True])
+def test_cuda_graph_replay_matches_eager(fused):
     """Forward + loss + backward captured once in a CUDA graph, replayed on
-    changed inputs (same buffers), equals the eager calls on those inputs."""
+    changed inputs (same buffers), equals the eager calls on those inputs;
+    fused: the L1 loss taken in the forward blend (gsr_render_l1), as the
+    benchmark runs it."""
     sc = REDUCED["window"]()
     rast = R.GaussianRasterizer(16)
     params, cams, vm = U.to_device(sc)
@@ -236,8 +239,12 @@ def test_cuda_graph_replay_matches_eager():
     d_pose = torch.empty(len(cams), 6, device="cuda")
 
     def step():
-        rast.forward_raw(params, sc.sh_degree, cams, vm, ws, color, depth, alpha)
-        R.l1_loss(rast, cams, vm, color, depth, tc, td, 1.0, 0.1, dC, dD, loss)
+        if fused:
+            rast.forward_l1_raw(params, sc.sh_degree, cams, vm, ws, color, depth, alpha, tc, td, 1.0, 0.1, dC, dD,
+                                loss)
+        else:
+            rast.forward_raw(params, sc.sh_degree, cams, vm, ws, color, depth, alpha)
+            R.l1_loss(rast, cams, vm, color, depth, tc, td, 1.0, 0.1, dC, dD, loss)
         rast.backward_raw(params, sc.sh_degree, cams, vm, ws, dC, dD, None, grads, d_pose)
 
     side = torch.cuda.Stream()

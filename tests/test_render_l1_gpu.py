@@ -11,6 +11,7 @@ import torch
 
 from paper_2411_17660_b300 import binding as B
 from paper_2411_17660_b300 import render as R
+from paper_2411_17660_b300 import scenes
 from tests import gsr_testutil as U
 from tests.test_parity_gpu import REDUCED
 
@@ -37,8 +38,8 @@ def _outputs(P, median):
                 med=nan(P) if median else None)
 
 
-def _both(name, with_depth=True, median=False, depth_out=True, d_depth=True, cw=1.0, dw=0.3):
-    sc = REDUCED[name]()
+def _both(name, with_depth=True, median=False, depth_out=True, d_depth=True, cw=1.0, dw=0.3, sc=None):
+    sc = REDUCED[name]() if sc is None else sc
     params, cams, vm = U.to_device(sc)
     rast = R.GaussianRasterizer(16)
     _, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
@@ -68,6 +69,15 @@ def test_fused_l1_equals_render_then_l1(name):
         _same(fus[k], sep[k])
     assert fus["loss"].item() == pytest.approx(sep["loss"].item(), rel=1e-5)
     assert sep["loss"].item() > 0
+
+
+def test_fused_l1_at_the_benchmark_size():
+    """The full 8-view 640x480 window with 100k Gaussians, the benchmark's
+    workload and launch configuration (per-tile binning, tile 16)."""
+    sep, fus, _ = _both("window", sc=scenes.config_window())
+    for k in ("color", "depth", "alpha", "dC", "dD"):
+        _same(fus[k], sep[k])
+    assert fus["loss"].item() == pytest.approx(sep["loss"].item(), rel=1e-5)
 
 
 def test_fused_l1_without_depth_target_and_without_depth_outputs():
