@@ -197,11 +197,17 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     return w;
 }
 
-// Clears the header and the radix histograms of the sort.
-__global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles, uint32_t *hist) {
+// Clears the header, the radix histograms of the sort, the bucket grouping's
+// tile counters (tile_counts, when it runs) and the fused loss's scalar
+// (loss, when there is one).
+__global__ void __launch_bounds__(1024) init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles, uint32_t *hist,
+                                                           uint32_t *tile_counts, float *loss) {
     uint32_t *p = reinterpret_cast<uint32_t *>(h);
     for (int i = threadIdx.x; i < (int)(sizeof(WsHeader) / 4); i += blockDim.x) p[i] = 0u;
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) hist[i] = 0u;
+    if (tile_counts)
+        for (uint32_t i = threadIdx.x; i < tiles; i += blockDim.x) tile_counts[i] = 0u;
+    if (loss && threadIdx.x == 0) *loss = 0.f;
     __syncthreads();
     if (threadIdx.x == 0) {
         h->key_capacity = cap;
@@ -209,8 +215,9 @@ __global__ void init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles, ui
     }
 }
 
-void launch_init(const Ws &w, uint32_t cap, cudaStream_t st) {
-    init_header_kernel<<<1, 256, 0, st>>>(w.hdr, cap, w.total_tiles, w.hist);
+void launch_init(const Ws &w, uint32_t cap, float *loss, cudaStream_t st) {
+    init_header_kernel<<<1, 1024, 0, st>>>(w.hdr, cap, w.total_tiles, w.hist,
+                                           bucket_binning(w) ? w.tile_cursor : nullptr, loss);
 }
 
 gsr_status fail(gsr_ctx *ctx, gsr_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -455,7 +462,7 @@ gsr_status render_impl(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vi
     CallTrace tr(l1 ? "gsr_render_l1" : "gsr_render");
     ctx->mark(0, st);
     tr.stage("preprocess");
-    launch_init(w, cap, st);
+    launch_init(w, cap, l1 ? l1->loss : nullptr, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_preprocess_fwd(vt, gp, w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");
@@ -470,8 +477,6 @@ gsr_status render_impl(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vi
     if ((e = launch_ranges(w, sm_count(ctx), st)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
     ctx->mark(4, st);
     tr.stage("blend");
-    if (l1 && (e = cudaMemsetAsync(l1->loss, 0, sizeof(float), st)) != cudaSuccess)
-        return cuda_fail(ctx, e, "clear loss");
     if ((e = launch_blend_fwd(vt, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "blend");
     ctx->mark(5, st);
 
@@ -581,7 +586,7 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
     CallTrace tr("gsr_render_surfels");
     ctx->mark(0, st);
     tr.stage("preprocess");
-    launch_init(w, cap, st);
+    launch_init(w, cap, nullptr, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
     if ((e = launch_surfel_preprocess_fwd(vt, gp, w, st)) != cudaSuccess) return cuda_fail(ctx, e, "preprocess");

@@ -999,8 +999,7 @@ cudaError_t launch_sort(const Ws &ws, int sm_count, cudaStream_t st) {
     if (!ws.bin_tile) return ws.VN == 0 ? cudaSuccess : launch_radix<unsigned long long, uint32_t>(ws, sm_count, st);
     cudaError_t e = cudaSuccess;
     if (bucket_binning(ws)) {   // writes every tile's range, even with no pairs
-        const size_t smem = bucket_smem(ws.total_tiles);
-        if ((e = cudaMemsetAsync(ws.tile_cursor, 0, 4ull * ws.total_tiles, st)) != cudaSuccess) return e;
+        const size_t smem = bucket_smem(ws.total_tiles);   // the tile counters were cleared by the init kernel
         if ((e = allow_smem<bucket_count_kernel>(kBucketSmemMax)) != cudaSuccess ||
             (e = allow_smem<bucket_scatter_kernel>(kBucketSmemMax)) != cudaSuccess)
             return e;
