@@ -27,9 +27,9 @@ constexpr float kSplitLog = 0.47000362924573558f;   // ln 1.6
 constexpr float kNoiseK = 100.f, kNoiseT = 0.005f;
 
 // ---------------------------------------------------------------- device-wide scan of u64 values
-// Block b scans values [b kDChunk, (b + 1) kDChunk), kDItems consecutive ones
-// per thread; the block totals are scanned by one block; a last pass adds
-// each block's offset.
+// Block b scans values [b kDChunk, (b + 1) kDChunk), each warp a run of
+// kDItems * 32 of them in coalesced rounds; the block totals are scanned by
+// one block; a last pass adds each block's offset.
 template <int THREADS>
 __device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x, unsigned long long *s_warp,
                                                             unsigned long long &total) {
@@ -61,23 +61,44 @@ __device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x
 
 // vals[i] := exclusive (or inclusive) prefix of vals within its block; block
 // totals to partials.
+// Warp w of block b takes the kDItems * 32 values from b kDChunk + w kDItems 32,
+// in kDItems coalesced rounds of 32 with a warp scan each.
 __global__ void __launch_bounds__(kDThreads) scan_local_kernel(unsigned long long *vals, size_t n,
                                                                unsigned long long *partials, int inclusive) {
     __shared__ unsigned long long s_warp[kDThreads / 32];
-    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)threadIdx.x * kDItems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)warp * (32 * kDItems);
     unsigned long long v[kDItems], run = 0;
 #pragma unroll
     for (int k = 0; k < kDItems; ++k) {
-        v[k] = base + k < n ? vals[base + k] : 0ull;
-        run += v[k];
+        const size_t i = base + (size_t)k * 32 + lane;
+        v[k] = i < n ? vals[i] : 0ull;
     }
-    unsigned long long total;
-    unsigned long long ex = block_scan_ex<kDThreads>(run, s_warp, total);
 #pragma unroll
     for (int k = 0; k < kDItems; ++k) {
-        ex += inclusive ? v[k] : 0ull;
-        if (base + k < n) vals[base + k] = ex;
-        ex += inclusive ? 0ull : v[k];
+        unsigned long long incl = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned long long x = v[k];
+        v[k] = run + (inclusive ? incl : incl - x);   // warp-local prefix
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) s_warp[warp] = run;
+    __syncthreads();
+    unsigned long long before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kDThreads / 32; ++w) {
+        const unsigned long long c = s_warp[w];
+        before += w < warp ? c : 0ull;
+        total += c;
+    }
+#pragma unroll
+    for (int k = 0; k < kDItems; ++k) {
+        const size_t i = base + (size_t)k * 32 + lane;
+        if (i < n) vals[i] = v[k] + before;
     }
     if (threadIdx.x == 0) partials[blockIdx.x] = total;
 }
@@ -162,37 +183,81 @@ __device__ __forceinline__ int adc_decide(const GaussianPtrs &gp, const float *g
     return pruned ? 0 : (dense ? (big ? 3 : 2) : 1);
 }
 
-__global__ void __launch_bounds__(kDThreads) adc_count_kernel(const GaussianPtrs gp, const float *grad,
-                                                              const float *count, const float *radius,
-                                                              const AdcParams p, unsigned long long *outs) {
-    const int g = blockIdx.x * kDThreads + threadIdx.x;
-    if (g >= gp.N) return;
-    const int c = adc_decide(gp, grad, count, radius, p, g);
-    outs[g] = c == 0 ? 0ull : (c == 1 ? 1ull : 2ull);
+// The decisions and the in-block exclusive prefix of their output counts,
+// in one pass: block b takes Gaussians [b kDChunk, (b + 1) kDChunk), warp w
+// the 32 kDRounds from b kDChunk + 32 kDRounds w, in kDRounds coalesced
+// rounds of 32 with a warp scan each.  code[g] = in-block output offset << 2
+// | decision; the block's output count goes to partials[b].
+constexpr int kDRounds = kDChunk / kDThreads;
+__global__ void __launch_bounds__(kDThreads) adc_decide_scan_kernel(const GaussianPtrs gp, const float *grad,
+                                                                    const float *count, const float *radius,
+                                                                    const AdcParams p, uint32_t *code,
+                                                                    unsigned long long *partials) {
+    __shared__ uint32_t s_wsum[kDThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)warp * (32 * kDRounds);
+    uint32_t oc[kDRounds], run = 0;   // warp-exclusive offset << 2 | decision
+#pragma unroll
+    for (int r = 0; r < kDRounds; ++r) {
+        const size_t g = base + (size_t)r * 32 + lane;
+        const int c = g < (size_t)gp.N ? adc_decide(gp, grad, count, radius, p, (int)g) : 0;
+        const uint32_t n = c == 0 ? 0u : (c == 1 ? 1u : 2u);
+        uint32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        oc[r] = ((run + incl - n) << 2) | (uint32_t)c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) s_wsum[warp] = run;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kDThreads / 32; ++w) {
+        const uint32_t c = s_wsum[w];
+        before += w < warp ? c : 0u;
+        total += c;
+    }
+#pragma unroll
+    for (int r = 0; r < kDRounds; ++r) {
+        const size_t g = base + (size_t)r * 32 + lane;
+        if (g < (size_t)gp.N) code[g] = oc[r] + (before << 2);
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+// Output slot of Gaussian g from its code and its block's exclusive prefix.
+__device__ __forceinline__ unsigned long long adc_slot(const uint32_t *code, const unsigned long long *partials,
+                                                       size_t g, int &c) {
+    const uint32_t v = code[g];
+    c = (int)(v & 3u);
+    return partials[g / kDChunk] + (v >> 2);
 }
 
 // Every kept Gaussian to its output slots (a split one to both children's).
-__global__ void __launch_bounds__(kDThreads) adc_write_kernel(const DensityPtrs d, const float *grad,
-                                                              const float *count, const float *radius,
-                                                              const AdcParams p, const unsigned long long *at,
+__global__ void __launch_bounds__(kDThreads) adc_write_kernel(const DensityPtrs d, const uint32_t *code,
+                                                              const unsigned long long *partials,
                                                               const unsigned long long *total, int *out_count) {
     const int g = blockIdx.x * kDThreads + threadIdx.x;
     if (g == 0) *out_count = *total > 0x7fffffffull ? 0x7fffffff : (int)*total;
     if (g >= d.in.N) return;
-    const int c = adc_decide(d.in, grad, count, radius, p, g);
-    const unsigned long long k0 = at[g];
+    int c;
+    const unsigned long long k0 = adc_slot(code, partials, (size_t)g, c);
     if (c != 0 && k0 < d.cap) copy_gaussian(d, g, (uint32_t)k0, c == 1 ? 1 : 2);
 }
 
 // The children of the split Gaussians (already copied there): means
 // mu + R diag(s) eps_c and log-scales - ln 1.6.
-__global__ void __launch_bounds__(kDThreads) adc_split_kernel(const DensityPtrs d, const float *grad,
-                                                              const float *count, const float *radius,
-                                                              const AdcParams p, const float *normals,
-                                                              const unsigned long long *at) {
+__global__ void __launch_bounds__(kDThreads) adc_split_kernel(const DensityPtrs d, const float *normals,
+                                                              const uint32_t *code,
+                                                              const unsigned long long *partials) {
     const int g = blockIdx.x * kDThreads + threadIdx.x;
-    if (g >= d.in.N || adc_decide(d.in, grad, count, radius, p, g) != 3) return;
-    const unsigned long long k0 = at[g];
+    if (g >= d.in.N) return;
+    int c;
+    const unsigned long long k0 = adc_slot(code, partials, (size_t)g, c);
+    if (c != 3) return;
     GaussPre G;
     gauss_pre(d.in, g, G);
     const size_t N = (size_t)d.in.N, cap = d.cap;
@@ -401,13 +466,14 @@ cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const 
     p.logit_min = std::log(m / (1.0 - m));
     p.log_world = prm.max_world_scale > 0.f ? std::log((double)prm.max_world_scale) : HUGE_VAL;
     if (gp.N == 0) return cudaMemsetAsync(out_count, 0, sizeof(int), st);
-    const unsigned nb = blocks_of((size_t)gp.N, kDThreads);
-    adc_count_kernel<<<nb, kDThreads, 0, st>>>(gp, grad, count, radius, p, w.vals);
-    cudaError_t e = scan(w.vals, (size_t)gp.N, w.partials, w.total, false, st);
-    if (e != cudaSuccess) return e;
+    // the decision codes use the first half of the scan buffer
+    uint32_t *code = reinterpret_cast<uint32_t *>(w.vals);
+    const unsigned nc = blocks_of((size_t)gp.N, kDChunk), nb = blocks_of((size_t)gp.N, kDThreads);
+    adc_decide_scan_kernel<<<nc, kDThreads, 0, st>>>(gp, grad, count, radius, p, code, w.partials);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(w.partials, nc, w.total);
     const DensityPtrs d = density_ptrs(gp, out);
-    adc_write_kernel<<<nb, kDThreads, 0, st>>>(d, grad, count, radius, p, w.vals, w.total, out_count);
-    adc_split_kernel<<<nb, kDThreads, 0, st>>>(d, grad, count, radius, p, normals, w.vals);
+    adc_write_kernel<<<nb, kDThreads, 0, st>>>(d, code, w.partials, w.total, out_count);
+    adc_split_kernel<<<nb, kDThreads, 0, st>>>(d, normals, code, w.partials);
     return cudaGetLastError();
 }
 
