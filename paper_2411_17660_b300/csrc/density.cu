@@ -62,18 +62,17 @@ __device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x
 // vals[i] := exclusive (or inclusive) prefix of vals within its block; block
 // totals to partials.
 // Warp w of block b takes the kDItems * 32 values from b kDChunk + w kDItems 32,
-// in kDItems coalesced rounds of 32 with a warp scan each.
-__global__ void __launch_bounds__(kDThreads) scan_local_kernel(unsigned long long *vals, size_t n,
-                                                               unsigned long long *partials, int inclusive) {
-    __shared__ unsigned long long s_warp[kDThreads / 32];
+// in kDItems coalesced rounds of 32 with a warp scan each: v[k] holds the
+// value of index rounds_base() + 32 k + lane and becomes its block-local
+// (inclusive or exclusive) prefix; returns the block total.
+__device__ __forceinline__ size_t rounds_base() {
+    return (size_t)blockIdx.x * kDChunk + (size_t)(threadIdx.x >> 5) * (32 * kDItems);
+}
+
+__device__ __forceinline__ unsigned long long block_rounds_scan(unsigned long long (&v)[kDItems], bool inclusive,
+                                                                unsigned long long *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)warp * (32 * kDItems);
-    unsigned long long v[kDItems], run = 0;
-#pragma unroll
-    for (int k = 0; k < kDItems; ++k) {
-        const size_t i = base + (size_t)k * 32 + lane;
-        v[k] = i < n ? vals[i] : 0ull;
-    }
+    unsigned long long run = 0;
 #pragma unroll
     for (int k = 0; k < kDItems; ++k) {
         unsigned long long incl = v[k];
@@ -96,11 +95,8 @@ __global__ void __launch_bounds__(kDThreads) scan_local_kernel(unsigned long lon
         total += c;
     }
 #pragma unroll
-    for (int k = 0; k < kDItems; ++k) {
-        const size_t i = base + (size_t)k * 32 + lane;
-        if (i < n) vals[i] = v[k] + before;
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+    for (int k = 0; k < kDItems; ++k) v[k] += before;
+    return total;
 }
 
 // partials := exclusive prefix of the block totals; *total := their sum.
@@ -296,15 +292,36 @@ __device__ __forceinline__ float exp_rn(float x) {
 
 __device__ __forceinline__ float sigmoid_rn(float l) { return __fdiv_rn(1.f, __fadd_rn(1.f, exp_rn(-l))); }
 
-// weights (then, after the scan, their inclusive prefix) and the dead flags
-__global__ void __launch_bounds__(kDThreads) mcmc_weight_kernel(const GaussianPtrs gp, float min_opacity,
-                                                                unsigned long long *w, uint32_t *dead) {
-    const int g = blockIdx.x * kDThreads + threadIdx.x;
-    if (g >= gp.N) return;
-    const float o = sigmoid_rn(gp.opacity_logits[g]);
-    const bool d = o <= min_opacity;
-    dead[g] = d ? 1u : 0u;
-    w[g] = d ? 0ull : (unsigned long long)(o * 16777216.f);   // exact scaling; truncation = floor
+// The sampling weights floor(o 2^24) of the live Gaussians (0 for dead
+// ones) and the dead flags, formed in the first pass of the weights'
+// inclusive scan (block-local prefix to w, block totals to partials); also
+// clears the draw counters.
+__global__ void __launch_bounds__(kDThreads) mcmc_weight_scan_kernel(const GaussianPtrs gp, float min_opacity,
+                                                                     unsigned long long *w, uint32_t *dead,
+                                                                     uint32_t *drawn, unsigned long long *partials) {
+    __shared__ unsigned long long s_warp[kDThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const size_t base = rounds_base(), N = (size_t)gp.N;
+    unsigned long long v[kDItems];
+#pragma unroll
+    for (int k = 0; k < kDItems; ++k) {
+        const size_t g = base + (size_t)k * 32 + lane;
+        v[k] = 0ull;
+        if (g < N) {
+            const float o = sigmoid_rn(gp.opacity_logits[g]);
+            const bool d = o <= min_opacity;
+            dead[g] = d ? 1u : 0u;
+            drawn[g] = 0u;
+            v[k] = d ? 0ull : (unsigned long long)(o * 16777216.f);   // exact scaling; truncation = floor
+        }
+    }
+    const unsigned long long total = block_rounds_scan(v, true, s_warp);
+#pragma unroll
+    for (int k = 0; k < kDItems; ++k) {
+        const size_t g = base + (size_t)k * 32 + lane;
+        if (g < N) w[g] = v[k];
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
 }
 
 // Each dead slot draws its source: the first Gaussian whose inclusive weight
@@ -396,15 +413,6 @@ __global__ void __launch_bounds__(kDThreads) mcmc_noise_kernel(const GaussianPtr
 
 unsigned blocks_of(size_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
-cudaError_t scan(unsigned long long *vals, size_t n, unsigned long long *partials, unsigned long long *total,
-                 bool inclusive, cudaStream_t st) {
-    const unsigned nb = blocks_of(n, kDChunk);
-    scan_local_kernel<<<nb, kDThreads, 0, st>>>(vals, n, partials, inclusive ? 1 : 0);
-    scan_partials_kernel<<<1, 1024, 0, st>>>(partials, nb, total);
-    scan_add_kernel<<<blocks_of(n, kDThreads), kDThreads, 0, st>>>(vals, n, partials);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 size_t density_workspace_bytes(int N) {
@@ -482,10 +490,10 @@ cudaError_t launch_mcmc_relocate(const GaussianPtrs &gp, const uint32_t *draws, 
     const DensityWs w = density_ws(ws, gp.N);
     cudaError_t e = cudaMemsetAsync(relocated, 0, sizeof(int), st);
     if (e != cudaSuccess || gp.N == 0) return e;
-    if ((e = cudaMemsetAsync(w.drawn, 0, 4 * (size_t)gp.N, st)) != cudaSuccess) return e;
-    const unsigned nb = blocks_of((size_t)gp.N, kDThreads);
-    mcmc_weight_kernel<<<nb, kDThreads, 0, st>>>(gp, min_opacity, w.vals, w.dead);
-    if ((e = scan(w.vals, (size_t)gp.N, w.partials, w.total, true, st)) != cudaSuccess) return e;
+    const unsigned nb = blocks_of((size_t)gp.N, kDThreads), nc = blocks_of((size_t)gp.N, kDChunk);
+    mcmc_weight_scan_kernel<<<nc, kDThreads, 0, st>>>(gp, min_opacity, w.vals, w.dead, w.drawn, w.partials);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(w.partials, nc, w.total);
+    scan_add_kernel<<<nb, kDThreads, 0, st>>>(w.vals, (size_t)gp.N, w.partials);
     mcmc_draw_kernel<<<nb, kDThreads, 0, st>>>(gp.N, draws, w.vals, w.total, w.dead, w.src, w.drawn, relocated);
     mcmc_write_kernel<<<nb, kDThreads, 0, st>>>(density_ptrs(gp, out), min_opacity, w.src, w.drawn);
     return cudaGetLastError();
