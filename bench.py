@@ -369,6 +369,37 @@ class Window:
                                    densify=self.dens)
 
 
+def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, binning="tile", tiles=1):
+    """Every stage against its bound: the blends against the FP32 lanes
+    (composited pairs x FP32 instructions per pair), the rest against HBM with
+    the bytes the host can count -- a lower bound for the preprocesses, whose
+    records of visible pairs are counted on the device only."""
+    K = (scene.sh_degree + 1) ** 2
+    param_b = scene.N * 4 * (3 + 3 + 4 + 1 + 3 * K)
+    VN = scene.V * scene.N
+    out = {}
+    for s in ("blend_fwd", "blend_bwd"):
+        a = pairs * ops[s] / (stage_ms[s] * 1e-3) / 1e9
+        out[s] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Gop/s", "frac": a / alu_peak}
+    hbm = {
+        # parameters once, a 4-byte count per pair, 12 bytes per emitted key
+        "preprocess": (param_b + 4 * VN + 12 * keys, "lower bound: + 64 B of records per visible pair"),
+        # per-tile: count reads tile ids; scatter reads tile ids and words, writes words; tile sort
+        # reads words, writes ids.  radix: 24 B per key per 8-bit pass (sort) + 8 (ranges)
+        "sort": (36 * keys, "36 B per key") if binning == "tile" else
+                (24 * keys * ((32 + max(1, (tiles - 1).bit_length()) + 7) // 8), "24 B per key per pass"),
+        # parameters in, gradients out, a 4-byte count per pair
+        "preprocess_bwd": (2 * param_b + 4 * VN, "lower bound: + 40 B of screen gradients per visible pair"),
+    }
+    for s, (b, note) in hbm.items():
+        if s not in stage_ms or stage_ms[s] <= 0:
+            continue
+        a = b / (stage_ms[s] * 1e-3) / 1e9
+        out[s] = {"bound": "hbm", "achieved": a, "peak": hbm_gbs, "unit": "GB/s", "frac": a / hbm_gbs,
+                  "bytes": b, "note": note}
+    return out
+
+
 def launches_per_step(rast, win):
     info = rast.info(win.ws)
     tiles = info.tiles
@@ -547,6 +578,8 @@ def main():
     else:
         roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "traffic": traffic_for(dominant)}
+    stage_roof = stage_rooflines(stage_ms, ops, pairs, alu_peak, peaks["hbm_gbs"], scene, win.P, info.keys,
+                                 args.binning, info.tiles)
 
     P_all = win.P * world
     # headline: the step as one replayed CUDA graph (the batched path's launch
@@ -575,6 +608,7 @@ def main():
         "stages_ms": stage_ms,
         "keys": info.keys, "pairs_contributing": pairs,
         "roofline": roof,
+        "stage_rooflines": stage_roof,
         "graph_replay": None if graph_ms is None else {
             "ms_per_step": graph_ms, "value": P_all / (graph_ms / 1000) / 1e6, "unit": "Mpix/s"},
         "gpu_launches": launches_per_step(rast, win) * K,
