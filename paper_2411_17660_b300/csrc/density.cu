@@ -22,13 +22,17 @@ namespace {
 constexpr int kDThreads = 256;
 constexpr int kDItems = 16;
 constexpr int kDChunk = kDThreads * kDItems;   // values per scan block
+// The scans' first passes take a chunk with 1024 threads, 4 coalesced rounds
+// of 32 per warp: enough warps in flight to hide the loads of each round.
+constexpr int kDScanThreads = 1024;
+constexpr int kDScanRounds = kDChunk / kDScanThreads;
 constexpr int kMaxCopies = 51;
 constexpr float kSplitLog = 0.47000362924573558f;   // ln 1.6
 constexpr float kNoiseK = 100.f, kNoiseT = 0.005f;
 
 // ---------------------------------------------------------------- device-wide scan of u64 values
 // Block b scans values [b kDChunk, (b + 1) kDChunk), each warp a run of
-// kDItems * 32 of them in coalesced rounds; the block totals are scanned by
+// kDScanRounds * 32 of them in coalesced rounds; the block totals are scanned by
 // one block; a last pass adds each block's offset.
 template <int THREADS>
 __device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x, unsigned long long *s_warp,
@@ -61,20 +65,20 @@ __device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x
 
 // vals[i] := exclusive (or inclusive) prefix of vals within its block; block
 // totals to partials.
-// Warp w of block b takes the kDItems * 32 values from b kDChunk + w kDItems 32,
-// in kDItems coalesced rounds of 32 with a warp scan each: v[k] holds the
+// Warp w of block b takes the kDScanRounds * 32 values from b kDChunk + w kDScanRounds 32,
+// in kDScanRounds coalesced rounds of 32 with a warp scan each: v[k] holds the
 // value of index rounds_base() + 32 k + lane and becomes its block-local
 // (inclusive or exclusive) prefix; returns the block total.
 __device__ __forceinline__ size_t rounds_base() {
-    return (size_t)blockIdx.x * kDChunk + (size_t)(threadIdx.x >> 5) * (32 * kDItems);
+    return (size_t)blockIdx.x * kDChunk + (size_t)(threadIdx.x >> 5) * (32 * kDScanRounds);
 }
 
-__device__ __forceinline__ unsigned long long block_rounds_scan(unsigned long long (&v)[kDItems], bool inclusive,
+__device__ __forceinline__ unsigned long long block_rounds_scan(unsigned long long (&v)[kDScanRounds], bool inclusive,
                                                                 unsigned long long *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long run = 0;
 #pragma unroll
-    for (int k = 0; k < kDItems; ++k) {
+    for (int k = 0; k < kDScanRounds; ++k) {
         unsigned long long incl = v[k];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -89,13 +93,13 @@ __device__ __forceinline__ unsigned long long block_rounds_scan(unsigned long lo
     __syncthreads();
     unsigned long long before = 0, total = 0;
 #pragma unroll
-    for (int w = 0; w < kDThreads / 32; ++w) {
+    for (int w = 0; w < kDScanThreads / 32; ++w) {
         const unsigned long long c = s_warp[w];
         before += w < warp ? c : 0ull;
         total += c;
     }
 #pragma unroll
-    for (int k = 0; k < kDItems; ++k) v[k] += before;
+    for (int k = 0; k < kDScanRounds; ++k) v[k] += before;
     return total;
 }
 
@@ -181,20 +185,19 @@ __device__ __forceinline__ int adc_decide(const GaussianPtrs &gp, const float *g
 
 // The decisions and the in-block exclusive prefix of their output counts,
 // in one pass: block b takes Gaussians [b kDChunk, (b + 1) kDChunk), warp w
-// the 32 kDRounds from b kDChunk + 32 kDRounds w, in kDRounds coalesced
+// the 32 kDScanRounds from b kDChunk + 32 kDScanRounds w, in kDScanRounds coalesced
 // rounds of 32 with a warp scan each.  code[g] = in-block output offset << 2
 // | decision; the block's output count goes to partials[b].
-constexpr int kDRounds = kDChunk / kDThreads;
-__global__ void __launch_bounds__(kDThreads) adc_decide_scan_kernel(const GaussianPtrs gp, const float *grad,
+__global__ void __launch_bounds__(kDScanThreads) adc_decide_scan_kernel(const GaussianPtrs gp, const float *grad,
                                                                     const float *count, const float *radius,
                                                                     const AdcParams p, uint32_t *code,
                                                                     unsigned long long *partials) {
-    __shared__ uint32_t s_wsum[kDThreads / 32];
+    __shared__ uint32_t s_wsum[kDScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)warp * (32 * kDRounds);
-    uint32_t oc[kDRounds], run = 0;   // warp-exclusive offset << 2 | decision
+    const size_t base = (size_t)blockIdx.x * kDChunk + (size_t)warp * (32 * kDScanRounds);
+    uint32_t oc[kDScanRounds], run = 0;   // warp-exclusive offset << 2 | decision
 #pragma unroll
-    for (int r = 0; r < kDRounds; ++r) {
+    for (int r = 0; r < kDScanRounds; ++r) {
         const size_t g = base + (size_t)r * 32 + lane;
         const int c = g < (size_t)gp.N ? adc_decide(gp, grad, count, radius, p, (int)g) : 0;
         const uint32_t n = c == 0 ? 0u : (c == 1 ? 1u : 2u);
@@ -211,13 +214,13 @@ __global__ void __launch_bounds__(kDThreads) adc_decide_scan_kernel(const Gaussi
     __syncthreads();
     uint32_t before = 0, total = 0;
 #pragma unroll
-    for (int w = 0; w < kDThreads / 32; ++w) {
+    for (int w = 0; w < kDScanThreads / 32; ++w) {
         const uint32_t c = s_wsum[w];
         before += w < warp ? c : 0u;
         total += c;
     }
 #pragma unroll
-    for (int r = 0; r < kDRounds; ++r) {
+    for (int r = 0; r < kDScanRounds; ++r) {
         const size_t g = base + (size_t)r * 32 + lane;
         if (g < (size_t)gp.N) code[g] = oc[r] + (before << 2);
     }
@@ -296,15 +299,15 @@ __device__ __forceinline__ float sigmoid_rn(float l) { return __fdiv_rn(1.f, __f
 // ones) and the dead flags, formed in the first pass of the weights'
 // inclusive scan (block-local prefix to w, block totals to partials); also
 // clears the draw counters.
-__global__ void __launch_bounds__(kDThreads) mcmc_weight_scan_kernel(const GaussianPtrs gp, float min_opacity,
+__global__ void __launch_bounds__(kDScanThreads) mcmc_weight_scan_kernel(const GaussianPtrs gp, float min_opacity,
                                                                      unsigned long long *w, uint32_t *dead,
                                                                      uint32_t *drawn, unsigned long long *partials) {
-    __shared__ unsigned long long s_warp[kDThreads / 32];
+    __shared__ unsigned long long s_warp[kDScanThreads / 32];
     const int lane = threadIdx.x & 31;
     const size_t base = rounds_base(), N = (size_t)gp.N;
-    unsigned long long v[kDItems];
+    unsigned long long v[kDScanRounds];
 #pragma unroll
-    for (int k = 0; k < kDItems; ++k) {
+    for (int k = 0; k < kDScanRounds; ++k) {
         const size_t g = base + (size_t)k * 32 + lane;
         v[k] = 0ull;
         if (g < N) {
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kDThreads) mcmc_weight_scan_kernel(const Gauss
     }
     const unsigned long long total = block_rounds_scan(v, true, s_warp);
 #pragma unroll
-    for (int k = 0; k < kDItems; ++k) {
+    for (int k = 0; k < kDScanRounds; ++k) {
         const size_t g = base + (size_t)k * 32 + lane;
         if (g < N) w[g] = v[k];
     }
@@ -477,7 +480,7 @@ cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const 
     // the decision codes use the first half of the scan buffer
     uint32_t *code = reinterpret_cast<uint32_t *>(w.vals);
     const unsigned nc = blocks_of((size_t)gp.N, kDChunk), nb = blocks_of((size_t)gp.N, kDThreads);
-    adc_decide_scan_kernel<<<nc, kDThreads, 0, st>>>(gp, grad, count, radius, p, code, w.partials);
+    adc_decide_scan_kernel<<<nc, kDScanThreads, 0, st>>>(gp, grad, count, radius, p, code, w.partials);
     scan_partials_kernel<<<1, 1024, 0, st>>>(w.partials, nc, w.total);
     const DensityPtrs d = density_ptrs(gp, out);
     adc_write_kernel<<<nb, kDThreads, 0, st>>>(d, code, w.partials, w.total, out_count);
@@ -491,7 +494,7 @@ cudaError_t launch_mcmc_relocate(const GaussianPtrs &gp, const uint32_t *draws, 
     cudaError_t e = cudaMemsetAsync(relocated, 0, sizeof(int), st);
     if (e != cudaSuccess || gp.N == 0) return e;
     const unsigned nb = blocks_of((size_t)gp.N, kDThreads), nc = blocks_of((size_t)gp.N, kDChunk);
-    mcmc_weight_scan_kernel<<<nc, kDThreads, 0, st>>>(gp, min_opacity, w.vals, w.dead, w.drawn, w.partials);
+    mcmc_weight_scan_kernel<<<nc, kDScanThreads, 0, st>>>(gp, min_opacity, w.vals, w.dead, w.drawn, w.partials);
     scan_partials_kernel<<<1, 1024, 0, st>>>(w.partials, nc, w.total);
     scan_add_kernel<<<nb, kDThreads, 0, st>>>(w.vals, (size_t)gp.N, w.partials);
     mcmc_draw_kernel<<<nb, kDThreads, 0, st>>>(gp.N, draws, w.vals, w.total, w.dead, w.src, w.drawn, relocated);
