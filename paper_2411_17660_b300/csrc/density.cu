@@ -167,18 +167,35 @@ __device__ __forceinline__ void copy_gaussian(const DensityPtrs &d, int g, uint3
 struct AdcParams {
     float grad_threshold, max_screen_radius;
     double log_split, logit_min, log_world;   // ln(split_scale), logit(min_opacity), ln(max_world_scale) or +inf
+    // The same thresholds for FP32 compares of FP32 inputs: x > t <=> x > the
+    // largest float <= t, x < t <=> x < the smallest float >= t.
+    float log_split_f, logit_min_f, log_world_f;
     int screen_on;
 };
 
-// 0: pruned, 1: kept, 2: kept and cloned, 3: split into two
+// 0: pruned, 1: kept, 2: kept and cloned, 3: split into two.  Every compare
+// is exact (the decisions of the FP64 oracle): FP32 inputs against FP64
+// thresholds through their FP32 bounds, and grad >= threshold count -- a
+// product exact in FP64 -- as grad against the rounded product p and its
+// exact error e = fma(threshold, count, -p) (grad > p, or grad == p and
+// e <= 0).  e is exact while p lies in [2^-80, 2^100] (its lowest bit, at
+// most 47 binades below p, stays above the smallest subnormal); other
+// products take FP64, whose rate on this part is low.
 __device__ __forceinline__ int adc_decide(const GaussianPtrs &gp, const float *grad, const float *count,
                                           const float *radius, const AdcParams &p, int g) {
     const size_t N = (size_t)gp.N;
     const float ls = fmaxf(gp.log_scales[g], fmaxf(gp.log_scales[N + g], gp.log_scales[2 * N + g]));
-    const float cnt = count[g];
-    const bool dense = cnt > 0.f && (double)grad[g] >= (double)p.grad_threshold * (double)cnt;
-    const bool big = (double)ls > p.log_split;
-    bool pruned = (double)gp.opacity_logits[g] < p.logit_min || (double)ls > p.log_world;
+    const float cnt = count[g], gr = grad[g];
+    const float prod = __fmul_rn(p.grad_threshold, cnt);
+    bool dense;
+    if (prod >= 0x1p-80f && prod <= 0x1p100f) {
+        const float err = __fmaf_rn(p.grad_threshold, cnt, -prod);
+        dense = cnt > 0.f && (gr > prod || (gr == prod && err <= 0.f));
+    } else {
+        dense = cnt > 0.f && (double)gr >= (double)p.grad_threshold * (double)cnt;
+    }
+    const bool big = ls > p.log_split_f;
+    bool pruned = gp.opacity_logits[g] < p.logit_min_f || ls > p.log_world_f;
     if (p.screen_on) pruned |= radius[g] > p.max_screen_radius;
     return pruned ? 0 : (dense ? (big ? 3 : 2) : 1);
 }
@@ -476,6 +493,19 @@ cudaError_t launch_densify_adc(const GaussianPtrs &gp, const float *grad, const 
     const double m = (double)prm.min_opacity;
     p.logit_min = std::log(m / (1.0 - m));
     p.log_world = prm.max_world_scale > 0.f ? std::log((double)prm.max_world_scale) : HUGE_VAL;
+    auto below = [](double t) {   // the largest float <= t
+        float f = (float)t;
+        if ((double)f > t) f = std::nextafter(f, -HUGE_VALF);
+        return f;
+    };
+    auto above = [](double t) {   // the smallest float >= t
+        float f = (float)t;
+        if ((double)f < t) f = std::nextafter(f, HUGE_VALF);
+        return f;
+    };
+    p.log_split_f = below(p.log_split);
+    p.logit_min_f = above(p.logit_min);
+    p.log_world_f = below(p.log_world);
     if (gp.N == 0) return cudaMemsetAsync(out_count, 0, sizeof(int), st);
     // the decision codes use the first half of the scan buffer
     uint32_t *code = reinterpret_cast<uint32_t *>(w.vals);

@@ -77,6 +77,57 @@ def test_adc_matches_oracle(N):
             np.testing.assert_array_equal(a, b)
 
 
+def _around(rng, t, n):
+    """n floats within one unit in the last place of the double t."""
+    c = np.float32(t)
+    k = rng.integers(-1, 2, n)
+    lo, hi = np.nextafter(c, np.float32(-np.inf)), np.nextafter(c, np.float32(np.inf))
+    return np.where(k < 0, lo, np.where(k > 0, hi, c)).astype(np.float32)
+
+
+def test_adc_decisions_at_the_thresholds():
+    """Inputs one float apart around every threshold (the density test's
+    grad = threshold x count, ln split_scale, logit(min_opacity),
+    ln max_world_scale): the kernel's FP32 compares must take the decisions of
+    the oracle's FP64 ones."""
+    N = 3 * 4096 + 5
+    rng = np.random.default_rng(77)
+    g, _, _, radius = _scene(N, seed=77)
+    radius[:] = 0.0
+    count = rng.integers(1, 9, N).astype(np.float32)
+    thr = float(np.float32(ADC["grad_threshold"]))
+    grad = _around(rng, 0.0, N)
+    for c in range(1, 9):   # the product is exact in FP64; its neighbours in FP32
+        sel = count == c
+        grad[sel] = _around(rng, thr * c, int(sel.sum()))
+    ls_split = math.log(float(np.float32(ADC["split_scale"])))
+    ls_world = math.log(float(np.float32(ADC["max_world_scale"])))
+    g.log_scales[0] = _around(rng, ls_split, N)
+    g.log_scales[0, 1::4] = _around(rng, ls_world, len(range(1, N, 4)))
+    g.log_scales[1:] = g.log_scales[0] - 1.0
+    mo = float(np.float32(ADC["min_opacity"]))
+    g.opacity_logits[:] = _around(rng, math.log(mo / (1.0 - mo)), N)
+    g.opacity_logits[::2] = 2.0   # opaque: the split and clone branches too
+    normals = rng.normal(0, 1, (2, 3, N)).astype(np.float32)
+    dc = DensityControl(R.GaussianRasterizer(16))
+    out, n = dc.densify_adc(_dev(g), 3, _t(grad), _t(count), _t(radius), _t(normals), **ADC)
+    d = OD.adc_decisions(g, grad, count, radius, **ADC)
+    for k in ("dense", "big", "pruned"):   # every branch is taken on both sides of its threshold
+        assert 0 < int(d[k].sum()) < N, k
+    assert int(n.item()) == int(d["n_out"].sum())
+    ref = OD.adc(g, grad, count, radius, normals, **ADC)
+    got = _host(out)
+    split_rows = np.repeat(d["split"][~d["pruned"]], np.where(d["clone"] | d["split"], 2, 1)[~d["pruned"]])
+    for k in R.PARAM_NAMES:
+        a, b = getattr(got, k), getattr(ref, k)
+        assert a.shape == b.shape, k
+        if k in ("means", "log_scales"):
+            np.testing.assert_array_equal(a[..., ~split_rows], b[..., ~split_rows])
+            np.testing.assert_allclose(a[..., split_rows], b[..., split_rows], rtol=2e-6, atol=2e-7)
+        else:
+            np.testing.assert_array_equal(a, b)
+
+
 def test_adc_truncates_at_capacity_and_reports_the_count():
     g, grad, count, radius = _scene(5000, seed=3)
     normals = np.zeros((2, 3, 5000), np.float32)
