@@ -82,7 +82,8 @@ struct WsHeader {
     unsigned long long keys;        // tile keys of all pairs: the scan's total, or the sum of the reservations
     unsigned long long pairs_contrib;
     uint32_t sort_counter[kMaxPasses];
-    uint32_t pad[64 - 8 - kMaxPasses];
+    uint32_t bwd_groups;            // preprocess backward: groups taken (reset by the pose reduction)
+    uint32_t pad[64 - 9 - kMaxPasses];
 };
 static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
 

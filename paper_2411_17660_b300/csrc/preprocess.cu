@@ -407,7 +407,12 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
 template <int VW>
 struct BwdShape {
     static constexpr int GB = kPreThreads / VW;                   // Gaussians per round
-    static constexpr int R = VW <= 8 ? 3 : 3 * VW / 8;            // at least 96 Gaussians per block
+    // Candidate rounds per group: 6 (192 Gaussians at 8 views, 12 rounds at
+    // 16) fill the chunks better than 3 (window backward 0.056 -> 0.045 ms);
+    // one view keeps 3 (768 Gaussians, enough groups for the blocks), two
+    // views and 32 or more keep 3 rounds per 8 views (so that two blocks'
+    // shared memory still fits an SM).
+    static constexpr int R = (VW == 4 || VW == 8) ? 6 : (VW == 16 ? 12 : (VW <= 8 ? 3 : 3 * VW / 8));
     static constexpr int GBT = R * GB;
     static constexpr int LC = R * kPreThreads;                    // list capacity
 };
@@ -470,10 +475,10 @@ __device__ __forceinline__ void bwd_finish(const GaussianPtrs &gp, const GradPtr
     *po = ac ? *po + dlogit : dlogit;
 }
 
+// One group of GBT Gaussians (group grp: Gaussians grp GBT ...) with all views.
 template <int DEG, int VW>
-__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                        const GaussianPtrs gp, const Ws ws,
-                                                                        const GradPtrs out) {
+__device__ __forceinline__ void preprocess_bwd_group(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws,
+                                                     const GradPtrs &out, const Pose *s_poses, int grp) {
     using S = BwdShape<VW>;
     constexpr int K = BwdAcc<DEG>::K, NV = BwdAcc<DEG>::NV, NS = BwdAcc<DEG>::NS, NVP = BwdAcc<DEG>::NVP;
     constexpr int GB = S::GB, GBT = S::GBT, WARPS = kPreThreads / 32;
@@ -493,10 +498,8 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
     __shared__ int s_wcnt[WARPS];
     __shared__ unsigned s_wbal[WARPS];
     __shared__ int s_end[kPreThreads];                 // chunk positions where a run ends
-    __shared__ Pose s_poses[GSR_MAX_VIEWS];
-    load_poses(vt, s_poses);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gbase = blockIdx.x * GBT;
+    const int gbase = grp * GBT;
     const size_t N = (size_t)gp.N;
     const bool ac = out.accumulate != 0, dens = out.densify_grad != nullptr;
     for (int k = tid; k < 6 * VW; k += kPreThreads) s_vpose[k] = 0.f;
@@ -698,12 +701,34 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __
     }
     for (int i = tid; i < 6 * vt.V; i += kPreThreads) {
         const int v = i / 6, c = i - v * 6;
-        ws.pose_partials[((size_t)v * ws.pose_blocks + blockIdx.x) * 6 + c] = s_vpose[v * 6 + c];
+        ws.pose_partials[((size_t)v * ws.pose_blocks + grp) * 6 + c] = s_vpose[v * 6 + c];
     }
     if (dens)
         for (int gl = tid; gl < GBT; gl += kPreThreads)
             if (gbase + gl < gp.N)
                 densify_write(out, gbase + gl, s_dgrad[gl], (float)s_dcount[gl], __int_as_float(s_drad[gl]));
+}
+
+// Persistent blocks take the groups in turn from a counter in the workspace
+// header (zeroed by the render's init kernel, and again by the pose
+// reduction after every backward): no group waits for a wave, whatever N.
+// Each group writes its own pose partials, so their sum is deterministic.
+template <int DEG, int VW>
+__global__ void __launch_bounds__(kPreThreads, 2) preprocess_bwd_kernel(const __grid_constant__ ViewTable vt,
+                                                                        const GaussianPtrs gp, const Ws ws,
+                                                                        const GradPtrs out) {
+    __shared__ Pose s_poses[GSR_MAX_VIEWS];
+    __shared__ int s_group;
+    load_poses(vt, s_poses);
+    const int ngroups = (gp.N + BwdShape<VW>::GBT - 1) / BwdShape<VW>::GBT;
+    for (;;) {
+        __syncthreads();   // the previous group is done with the shared memory
+        if (threadIdx.x == 0) s_group = (int)atomicAdd(&ws.hdr->bwd_groups, 1u);
+        __syncthreads();
+        const int grp = s_group;
+        if (grp >= ngroups) break;
+        preprocess_bwd_group<DEG, VW>(vt, gp, ws, out, s_poses, grp);
+    }
 }
 
 // Sum of the per-block pose partials of each view, in a fixed order.
@@ -726,6 +751,7 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant_
     }
     float *dst = vt.v[v].d_pose;
     if (threadIdx.x < 6 && dst) dst[threadIdx.x] = accumulate ? dst[threadIdx.x] + s[0][threadIdx.x] : s[0][threadIdx.x];
+    if (v == 0 && threadIdx.x == 0) ws.hdr->bwd_groups = 0u;   // for the next backward on this workspace
 }
 
 // ------------------------------------------------------------------ launchers
@@ -764,23 +790,39 @@ static cudaError_t launch_pre_bwd_vw(const ViewTable &vt, const GaussianPtrs &gp
     const size_t smem = bwd_smem_bytes<DEG, VW>();
     // More than 48 KB of dynamic shared memory needs an opt-in, set once per
     // device (the first backward on a device, which should precede capture).
+    // The resident blocks (all of them work through the groups) are counted
+    // once per device too.
     static std::mutex mu;
     static bool done[64] = {};
+    static int resident[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    int slots = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (dev < 0 || dev >= 64 || !done[dev]) {
+        const bool cached = dev >= 0 && dev < 64 && done[dev];
+        if (!cached) {
             e = cudaFuncSetAttribute(preprocess_bwd_kernel<DEG, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
             if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) done[dev] = true;
+            int per_sm = 0, sms = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, preprocess_bwd_kernel<DEG, VW>,
+                                                                   kPreThreads, smem)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return e;
+            slots = std::max(1, per_sm) * std::max(1, sms);
+            if (dev >= 0 && dev < 64) {
+                resident[dev] = slots;
+                done[dev] = true;
+            }
+        } else {
+            slots = resident[dev];
         }
     }
-    const int blocks = (gp.N + BwdShape<VW>::GBT - 1) / BwdShape<VW>::GBT;
-    ws.pose_blocks = (uint32_t)blocks;   // at most (N + 31) / 32, the workspace's allotment
-    preprocess_bwd_kernel<DEG, VW><<<blocks, kPreThreads, smem, st>>>(vt, gp, ws, out);
+    const int groups = (gp.N + BwdShape<VW>::GBT - 1) / BwdShape<VW>::GBT;
+    ws.pose_blocks = (uint32_t)groups;   // one pose partial per group: at most (N + 31) / 32, the allotment
+    preprocess_bwd_kernel<DEG, VW><<<std::min(groups, slots), kPreThreads, smem, st>>>(vt, gp, ws, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_pose_reduce(vt, ws, out.accumulate, st);
