@@ -7,7 +7,7 @@ gradient, or the MCMC strategy that relocates low-opacity Gaussians and adds
 noise, with an upper bound on their number and lr_noise = 1e4 (Sec. 3.3, last
 paragraph; Supp. "Monte Carlo Markov Chain Gaussian Splatting").  It cites
 both methods without restating them; these are restatements of the published
-steps, with the readings below (all listed in the design doc).
+steps, with the readings below.
 
 Adaptive density control (3DGS), one pass over Gaussians g = 0..N-1:
   mean gradient  g_bar = grad_g / count_g (0 without views)
