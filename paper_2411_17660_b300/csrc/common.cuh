@@ -83,7 +83,8 @@ struct WsHeader {
     unsigned long long pairs_contrib;
     uint32_t sort_counter[kMaxPasses];
     uint32_t bwd_groups;            // preprocess backward: groups taken (reset by the pose reduction)
-    uint32_t pad[64 - 9 - kMaxPasses];
+    uint32_t pre_items;             // preprocess forward: work items taken (zeroed by the init kernel)
+    uint32_t pad[64 - 10 - kMaxPasses];
 };
 static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
 

@@ -32,6 +32,7 @@ constexpr int kPreThreads = 32 * kPreWarps;
 // records.  Warps never wait for each other, and the expensive part runs
 // with full warps however few pairs are visible.
 constexpr int kQueue = 64;   // a warp's queue: up to 31 waiting + 32 appended
+constexpr int kPreItemViews = 4;   // views of one forward work item
 
 struct WarpQueue {
     float uh[kQueue], vh[kQueue], ul[kQueue], vl[kQueue];
@@ -134,14 +135,29 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpQueue &q = s_q[warp];
     const size_t N = (size_t)gp.N;
-    const int nbatch = (gp.N + 31) / 32, nwarps = gridDim.x * kPreWarps;
+    // Work items: a batch of 32 Gaussians with up to kPreItemViews views.
+    // With more views than that, warps take the items in turn from a counter
+    // in the workspace header (zeroed by the init kernel), so that warps with
+    // light items take more of them (window preprocess 0.066 -> 0.060 ms,
+    // 32 views 5.1 -> 4.3 ms); with one item per batch the warps take the
+    // batches in a fixed order.
+    const int nbatch = (gp.N + 31) / 32, nsplit = (vt.V + kPreItemViews - 1) / kPreItemViews;
+    const int nitems = nbatch * nsplit, nwarps = gridDim.x * kPreWarps;
+    const bool dynamic = nsplit > 1;
     int qn = 0;   // queued pairs (the same in every lane)
-    for (int b = blockIdx.x * kPreWarps + warp; b < nbatch; b += nwarps) {
+    int it = blockIdx.x * kPreWarps + warp;
+    if (dynamic) {
+        if (lane == 0) it = (int)atomicAdd(&ws.hdr->pre_items, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+    }
+    while (it < nitems) {
+        const int b = it / nsplit, part = it - b * nsplit;
+        const int v0 = part * kPreItemViews, v1 = min(vt.V, v0 + kPreItemViews);
         const int g = b * 32 + lane;
         const bool real = g < gp.N;
         GaussPre G;
         if (real) gauss_pre(gp, g, G);
-        for (int v = 0; v < vt.V; ++v) {
+        for (int v = v0; v < v1; ++v) {
             // phase A: projection and visibility of (v, the 32 Gaussians)
             bool vis = false;
             float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
@@ -214,6 +230,12 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
                 qn -= 32;
                 __syncwarp();
             }
+        }
+        if (dynamic) {
+            if (lane == 0) it = (int)atomicAdd(&ws.hdr->pre_items, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+        } else {
+            it += nwarps;
         }
     }
     __syncwarp();
@@ -767,7 +789,8 @@ template <int DEG>
 static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,
                                   cudaStream_t st) {
     const long long batches = ((long long)gp.N + 31) / 32;
-    const long long need = (batches + kPreWarps - 1) / kPreWarps;
+    const long long items = batches * ((vt.V + kPreItemViews - 1) / kPreItemViews);
+    const long long need = (items + kPreWarps - 1) / kPreWarps;
     const unsigned blocks = (unsigned)std::min<long long>(need, (long long)sm_count * kPreFwdBlocksPerSM);
     preprocess_fwd_kernel<DEG><<<blocks, kPreThreads, 0, st>>>(vt, gp, ws);
     return cudaGetLastError();
