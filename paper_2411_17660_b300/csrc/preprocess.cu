@@ -32,7 +32,10 @@ constexpr int kPreThreads = 32 * kPreWarps;
 // records.  Warps never wait for each other, and the expensive part runs
 // with full warps however few pairs are visible.
 constexpr int kQueue = 64;   // a warp's queue: up to 31 waiting + 32 appended
-constexpr int kPreItemViews = 4;   // views of one forward work item
+// Views of one forward work item: 4, or 2 when 4 would leave the warps fewer
+// than kPreItemsPerWarp items each (the window: 0.060 -> 0.057 ms; 2 on the
+// 16- and 32-view workloads measured 7 % slower, 1 view per item slower still).
+constexpr int kPreItemsPerWarp = 4;
 
 struct WarpQueue {
     float uh[kQueue], vh[kQueue], ul[kQueue], vl[kQueue];
@@ -128,20 +131,21 @@ __device__ __forceinline__ void preprocess_fwd_pair(const ViewTable &vt, const G
 
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                     const GaussianPtrs gp, const Ws ws) {
+                                                                     const GaussianPtrs gp, const Ws ws,
+                                                                     int item_views) {
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
     __shared__ WarpQueue s_q[kPreWarps];
     load_poses(vt, s_pose);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpQueue &q = s_q[warp];
     const size_t N = (size_t)gp.N;
-    // Work items: a batch of 32 Gaussians with up to kPreItemViews views.
+    // Work items: a batch of 32 Gaussians with up to item_views views.
     // With more views than that, warps take the items in turn from a counter
     // in the workspace header (zeroed by the init kernel), so that warps with
     // light items take more of them (window preprocess 0.066 -> 0.060 ms,
     // 32 views 5.1 -> 4.3 ms); with one item per batch the warps take the
     // batches in a fixed order.
-    const int nbatch = (gp.N + 31) / 32, nsplit = (vt.V + kPreItemViews - 1) / kPreItemViews;
+    const int nbatch = (gp.N + 31) / 32, nsplit = (vt.V + item_views - 1) / item_views;
     const int nitems = nbatch * nsplit, nwarps = gridDim.x * kPreWarps;
     const bool dynamic = nsplit > 1;
     int qn = 0;   // queued pairs (the same in every lane)
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
     }
     while (it < nitems) {
         const int b = it / nsplit, part = it - b * nsplit;
-        const int v0 = part * kPreItemViews, v1 = min(vt.V, v0 + kPreItemViews);
+        const int v0 = part * item_views, v1 = min(vt.V, v0 + item_views);
         const int g = b * 32 + lane;
         const bool real = g < gp.N;
         GaussPre G;
@@ -789,10 +793,12 @@ template <int DEG>
 static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,
                                   cudaStream_t st) {
     const long long batches = ((long long)gp.N + 31) / 32;
-    const long long items = batches * ((vt.V + kPreItemViews - 1) / kPreItemViews);
+    const long long max_warps = (long long)sm_count * kPreFwdBlocksPerSM * kPreWarps;
+    const int item_views = batches * ((vt.V + 3) / 4) < kPreItemsPerWarp * max_warps ? 2 : 4;
+    const long long items = batches * ((vt.V + item_views - 1) / item_views);
     const long long need = (items + kPreWarps - 1) / kPreWarps;
     const unsigned blocks = (unsigned)std::min<long long>(need, (long long)sm_count * kPreFwdBlocksPerSM);
-    preprocess_fwd_kernel<DEG><<<blocks, kPreThreads, 0, st>>>(vt, gp, ws);
+    preprocess_fwd_kernel<DEG><<<blocks, kPreThreads, 0, st>>>(vt, gp, ws, item_views);
     return cudaGetLastError();
 }
 
