@@ -38,6 +38,7 @@ METRIC = "fwd+bwd Mpix/s & mapping it/s (8-view batch) vs per-view launches; % F
 PAPER_LAMBDA1, PAPER_LAMBDA2 = 0.8, 0.2
 LOSS_NAMES = {"l1": "L1 colour/depth loss", "paper": "L1 + SSIM colour / L1 depth loss (0.8, 0.2)"}
 FWD_OPS_PER_PAIR = 17   # FP32-pipe instructions per composited (pixel, Gaussian) pair, blend forward
+STAGE_SLEEP_CYCLES = 4_000_000   # about 2 ms of GPU sleep before each stage-timing step
 BWD_OPS_PER_PAIR = 48   # the same for the blend backward (before the per-warp reduction)
 SURFEL_FWD_OPS_PER_PAIR = 47   # surfels: ray-disk intersection + compositing with normal and distortion
 SURFEL_BWD_OPS_PER_PAIR = 85   # surfels: recomputed intersection + its backward
@@ -510,6 +511,19 @@ def main():
     rast.ctx.set_stage_events(None)
     ms_step = dist_max(world, statistics.mean(ms))
 
+    # Per-stage device times (for the rooflines) from K more steps, each queued
+    # behind a short GPU sleep so that the host has enqueued the whole step
+    # before it runs: the eager steps above can be host-bound, and their stage
+    # events then count the GPU's idle gaps too.
+    rast.ctx.set_stage_events(None)
+    for k in range(K):
+        flush()
+        torch.cuda._sleep(STAGE_SLEEP_CYCLES)
+        set_events(k)
+        win.step()
+    torch.cuda.synchronize()
+    rast.ctx.set_stage_events(None)
+
     info = rast.info(win.ws)
     if info.status != 0:
         raise RuntimeError(f"device status {B.STATUS.get(info.status)} during the timed steps")
@@ -606,6 +620,8 @@ def main():
             "ms_per_step": per_view, "value": P_all / (per_view / 1000) / 1e6, "unit": "Mpix/s",
             "batched_speedup": per_view / ms_step, "note": "both launched eagerly"},
         "stages_ms": stage_ms,
+        "stage_timing": "device time per stage from CUDA events, in steps queued behind a ~2 ms GPU sleep "
+                        "so that host launch gaps do not count",
         "keys": info.keys, "pairs_contributing": pairs,
         "roofline": roof,
         "stage_rooflines": stage_roof,
