@@ -62,7 +62,7 @@ struct CallTrace {
 
 struct Layout {
     size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, rec4, rec5, radius, aux;
-    size_t keys0, keys1, vals0, vals1, hist, tile_cursor, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
+    size_t keys0, keys1, vals0, vals1, hist, tile_cursor, tile_order, lookback, ranges, T_final, last, median, vg_grads, pose_partials;
     size_t total;
     uint64_t VN;
     uint32_t cap, lb_tiles, scan_blocks, pose_blocks, total_pixels, total_tiles;
@@ -107,6 +107,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.hist = take(4ull * kMaxPasses * kRadix);
     L.ranges = take(8ull * L.total_tiles);
     L.tile_cursor = take(4ull * L.total_tiles);
+    L.tile_order = take(4ull * L.total_tiles);
     L.T_final = take(4ull * L.total_pixels);
     L.last = take(4ull * L.total_pixels);
     L.median = take(4ull * L.total_pixels);
@@ -149,6 +150,7 @@ void set_sort_plan(Ws &w, int tbits) {
     else
         w.passes = w.bin_tile ? (tbits + 7) / 8 : (32 + tbits + 7) / 8;
     w.sorted = w.vals[w.bin_tile ? (w.passes + 1) & 1 : w.passes & 1];
+    w.order_tiles = bucket_binning(w) && !w.surfels;
 }
 
 Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
@@ -175,6 +177,7 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     w.bin_tile = ctx.binning == GSR_BIN_TILE;
     w.hist = reinterpret_cast<uint32_t *>(b + L.hist);
     w.tile_cursor = reinterpret_cast<uint32_t *>(b + L.tile_cursor);
+    w.tile_order = reinterpret_cast<uint32_t *>(b + L.tile_order);
     w.lookback = reinterpret_cast<uint32_t *>(b + L.lookback);
     w.ranges = reinterpret_cast<uint2 *>(b + L.ranges);
     w.T_final = reinterpret_cast<float *>(b + L.T_final);

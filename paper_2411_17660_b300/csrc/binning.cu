@@ -536,11 +536,51 @@ __device__ __forceinline__ void bucket_scan(const Ws &ws, uint32_t *s, uint32_t 
     }
     __syncthreads();
     // the counts add up to the key count, which is at most the capacity
-    if (!GSR_CHECK(ws.hdr, total <= ws.cap)) return;
-    for (uint32_t i = threadIdx.x; i < T; i += kBucketThreads) {
-        const uint32_t a = s[bucket_pad(i)], e = i + 1 < T ? s[bucket_pad(i + 1)] : total;
-        ws.ranges[i] = make_uint2(a, e);
-        ws.tile_cursor[i] = a;
+    (void)GSR_CHECK(ws.hdr, total <= ws.cap);
+    // the blends' launch order: tiles by decreasing key count, bucketed by
+    // the count's bit length (so that the heaviest tiles start first and do
+    // not trail the last wave)
+    __shared__ uint32_t s_ob[2 * 33];
+    for (uint32_t i = threadIdx.x; i < 2 * 33; i += kBucketThreads) s_ob[i] = 0u;
+    __syncthreads();
+    // (a warp's lanes of one bucket add to it with one shared-memory atomic:
+    // 33 counters for thousands of tiles otherwise serialise)
+    auto bits = [](uint32_t c) { return c == 0u ? 0u : 32u - (uint32_t)__clz(c); };
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i0 = 0; i0 < T; i0 += kBucketThreads) {   // whole warps in every round
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t b = 33u;   // none
+        if (i < T) {
+            const uint32_t a = s[bucket_pad(i)], e = i + 1 < T ? s[bucket_pad(i + 1)] : total;
+            ws.ranges[i] = make_uint2(min(a, ws.cap), min(e, ws.cap));
+            ws.tile_cursor[i] = a;
+            b = bits(e - a);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b < 33u && lane == __ffs(peers) - 1) atomicAdd(s_ob + b, (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t at = 0;
+        for (int b = 32; b >= 0; --b) {
+            s_ob[33 + b] = at;
+            at += s_ob[b];
+        }
+    }
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 < T; i0 += kBucketThreads) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t b = 33u;
+        if (i < T) {
+            const uint32_t a = s[bucket_pad(i)], e = i + 1 < T ? s[bucket_pad(i + 1)] : total;
+            b = bits(e - a);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (b < 33u && lane == leader) base = atomicAdd(s_ob + 33 + b, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b < 33u) ws.tile_order[base + __popc(peers & ((1u << lane) - 1u))] = i;
     }
 }
 

@@ -187,7 +187,11 @@ template <int TS, int BH = kSubH>
 __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws) {
     using S = BlendShape<TS, BH>;
     WarpTile w;
-    const uint32_t tile = blockIdx.x;
+    uint32_t tile = blockIdx.x;
+    if (ws.order_tiles) {   // the bucket scan's order: tiles with the most keys first
+        const uint32_t t = ws.tile_order[blockIdx.x];
+        tile = t < vt.total_tiles ? t : blockIdx.x;
+    }
     w.v = view_of_tile(vt, tile);
     const ViewParams &vp = vt.v[w.v];
     const uint32_t lt = tile - vp.tile_offset;

@@ -114,6 +114,8 @@ struct Ws {
     int bin_tile;
     uint32_t *hist;          // [kMaxPasses][256]
     uint32_t *tile_cursor;   // [total_tiles] bucket binning: keys per tile, then each tile's next free slot
+    uint32_t *tile_order;    // [total_tiles] bucket binning: the blends' launch order, most keys first
+    int order_tiles;         // the blends take their tiles from tile_order
     uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
     uint2 *ranges;           // [total_tiles] [start, end) in the sorted list
     float *T_final;          // [total_pixels]
