@@ -107,19 +107,24 @@ def _split(flat, counts, sizes, full, tail_shape):
     return out
 
 
-_NOUT = 9   # per pixel: r, g, b, depth, opacity, T_final, margin, median depth, median margin
+# per pixel: r, g, b, depth, opacity, T_final, threshold margin, median depth, median margin,
+# depth-order margin
+_NOUT = 10
 
 
 def _pixel_dict(o, n):
     return dict(color=np.moveaxis(o[..., 0:3], -1, 0), depth=o[..., 3], alpha=o[..., 4], T=o[..., 5],
-                margin=o[..., 6], median_depth=o[..., 7], median_margin=o[..., 8], ncontrib=n)
+                margin=o[..., 6], median_depth=o[..., 7], median_margin=o[..., 8], zmargin=o[..., 9],
+                ncontrib=n)
 
 
 def render(scene, pixels: Optional[Sequence[np.ndarray]] = None, brute: bool = False,
            threads: int = 0, cameras=None):
     """Forward render.  pixels: per view arrays of linear indices y*W+x (None
     = all).  Returns per view dicts with color [3,...], depth, alpha, T,
-    ncontrib, margin, median_depth, median_margin (full images are [H, W])."""
+    ncontrib, margin (cutoff, alpha-skip and stop decisions), zmargin
+    (depth-order decisions), median_depth, median_margin (full images are
+    [H, W])."""
     lib = _load()
     pk = _Packed(scene, cameras)
     off, flat, counts = _pixels(pk, pixels)

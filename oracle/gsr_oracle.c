@@ -38,9 +38,10 @@
  *   - gradients through the alpha clamp, the colour clamp and a clamped
  *     Jacobian coordinate are zero (exact derivative of the clamped map).
  *
- * Per pixel the oracle also records the smallest relative margin of any
- * threshold decision it took (cutoff, alpha skip, transmittance stop, depth
- * order), so that tests can tell FP32-vs-FP64 decision flips from errors.
+ * Per pixel the oracle also records the smallest relative margin of the
+ * threshold decisions it took (cutoff, alpha skip, transmittance stop) and,
+ * apart from them, of its depth-order decisions, so that tests can tell
+ * FP32-vs-FP64 decision flips from errors.
  */
 #include <math.h>
 #include <pthread.h>
@@ -72,6 +73,7 @@ typedef struct {
 #define T_STOP 1e-4
 #define FOV_CLAMP 1.3
 #define PI 3.14159265358979323846
+#define OG_NOUT 10 /* doubles per pixel written by the render calls */
 
 /* ------------------------------------------------------------------ */
 /* Real spherical harmonics up to degree 3 (closed forms on the unit    */
@@ -419,8 +421,11 @@ static double fmin2(double a, double b) { return a < b ? a : b; }
 
 /* Composites one pixel from its candidate list.  Fills out[0..2] colour,
  * out[3] depth, out[4] opacity (sum of weights), out[5] final transmittance,
- * out[6] decision margin, out[7] median depth, out[8] the median's decision
- * margin (min over contributors of |T_i / 0.5 - 1|); returns the number of
+ * out[6] threshold margin (cutoff, alpha skip, transmittance stop),
+ * out[7] median depth, out[8] the median's decision margin (min over
+ * contributors of |T_i / 0.5 - 1|), out[9] depth-order margin (the smallest
+ * relative gap between the depths of consecutive candidates up to the one
+ * the walk stopped at, and the one after it); returns the number of
  * contributors written. */
 typedef struct {
     cand_t *buf;
@@ -442,7 +447,7 @@ static void scratch_reserve(scratch_t *s, int n, int want_bwd) {
 }
 
 static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px, double py,
-                         scratch_t *s, int want_bwd, double out[9], int *ncontrib) {
+                         scratch_t *s, int want_bwd, double out[OG_NOUT], int *ncontrib) {
     int n = 0;
     const double keep_d2 = CUTOFF_D2 * (1 + 1e-3);
     for (int k = 0; k < ncand; ++k) {
@@ -462,7 +467,7 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
     cand_t *buf = s->buf;
     contrib_t *con = want_bwd ? s->con : NULL;
     if (n > 0) qsort(buf, n, sizeof(cand_t), cand_cmp);
-    double T = 1, C[3] = {0, 0, 0}, D = 0, A = 0, margin = 1e30, Zmed = 0, mmed = 1e30;
+    double T = 1, C[3] = {0, 0, 0}, D = 0, A = 0, margin = 1e30, Zmed = 0, mmed = 1e30, zmargin = 1e30;
     int nc = 0;
     double prev_z = -1;
     for (int k = 0; k < n; ++k) {
@@ -471,7 +476,7 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         margin = fmin2(margin, fabs(d2 - CUTOFF_D2) / CUTOFF_D2);
         /* an exact tie is ordered by the index on either side, whatever the
          * precision; only distinct close depths can swap under rounding */
-        if (prev_z > 0 && p->z != prev_z) margin = fmin2(margin, fabs(p->z - prev_z) / p->z);
+        if (prev_z > 0 && p->z != prev_z) zmargin = fmin2(zmargin, fabs(p->z - prev_z) / p->z);
         prev_z = p->z;
         if (d2 > CUTOFF_D2) continue;
         const double Gexp = exp(-0.5 * d2);
@@ -482,7 +487,13 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         const double alpha = clamped ? ALPHA_MAX : a_raw;
         const double Tn = T * (1 - alpha);
         margin = fmin2(margin, fabs(Tn / T_STOP - 1));
-        if (Tn < T_STOP) break;
+        if (Tn < T_STOP) {
+            /* the candidate after the stop would have been reached first had
+             * the two depths swapped */
+            if (k + 1 < n && P[buf[k + 1].g].z != p->z)
+                zmargin = fmin2(zmargin, fabs(P[buf[k + 1].g].z - p->z) / P[buf[k + 1].g].z);
+            break;
+        }
         const double w = alpha * T;
         mmed = fmin2(mmed, fabs(T / 0.5 - 1));
         if (T > 0.5) Zmed = p->z;
@@ -502,7 +513,7 @@ static int pixel_forward(const og_proj *P, const int *cand, int ncand, double px
         T = Tn;
     }
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2];
-    out[3] = D; out[4] = A; out[5] = T; out[6] = margin; out[7] = Zmed; out[8] = mmed;
+    out[3] = D; out[4] = A; out[5] = T; out[6] = margin; out[7] = Zmed; out[8] = mmed; out[9] = zmargin;
     *ncontrib = nc;
     return nc;
 }
@@ -595,7 +606,7 @@ typedef struct {
     const int *all;        /* 0..N-1 for brute force */
     const int64_t *pix;    /* pixel linear indices (y*W + x) */
     int64_t p0, p1;        /* range of pixels for this worker */
-    double *out;           /* [npix][9] */
+    double *out;           /* [npix][OG_NOUT] */
     int32_t *ncontrib;
     /* backward */
     const double *gC, *gD, *gA, *gM;   /* gM may be NULL */
@@ -622,10 +633,10 @@ static void *worker(void *arg) {
             cand = w->all;
             ncand = w->N;
         }
-        double o[9];
+        double o[OG_NOUT];
         int nc = 0;
         pixel_forward(w->P, cand, ncand, (double)px, (double)py, &s, want_bwd, o, &nc);
-        if (w->out) memcpy(w->out + 9 * i, o, sizeof o);
+        if (w->out) memcpy(w->out + OG_NOUT * i, o, sizeof o);
         if (w->ncontrib) w->ncontrib[i] = nc;
         if (w->gC) {
             double *psg = s.psg;
@@ -741,8 +752,9 @@ static int64_t *full_pixels(const og_camera *cam, int64_t *npix) {
 
 /* Per-pixel forward over V views.  pix_off[V+1] and pix (concatenated
  * linear pixel indices y*W+x) select the pixels; pix == NULL renders every
- * pixel of every view in order.  out [P][9]: r, g, b, depth, opacity,
- * T_final, margin, median depth, median margin.  ncontrib [P]. */
+ * pixel of every view in order.  out [P][OG_NOUT]: r, g, b, depth, opacity,
+ * T_final, threshold margin, median depth, median margin, depth-order
+ * margin.  ncontrib [P]. */
 int og_render(const og_gaussians *G, int V, const og_camera *cams, const int64_t *pix_off,
               const int64_t *pix, int brute, int threads, double *out, int32_t *ncontrib) {
     const int nt = num_threads(threads);
@@ -759,7 +771,7 @@ int og_render(const og_gaussians *G, int V, const og_camera *cams, const int64_t
             own = full_pixels(&cams[v], &np);
             pv = own;
         }
-        run_view(G, &cams[v], pv, np, brute, nt, out + 9 * base, ncontrib + base, NULL, NULL, NULL, NULL, NULL, P);
+        run_view(G, &cams[v], pv, np, brute, nt, out + OG_NOUT * base, ncontrib + base, NULL, NULL, NULL, NULL, NULL, P);
         base += np;
         free(own);
     }
@@ -800,7 +812,7 @@ int og_render_backward(const og_gaussians *G, int V, const og_camera *cams, cons
             pv = own;
         }
         memset(sgrad, 0, sizeof(double) * 10 * (size_t)N);
-        run_view(G, &cams[v], pv, np, brute, nt, out + 9 * base, ncontrib + base, gC + 3 * base,
+        run_view(G, &cams[v], pv, np, brute, nt, out + OG_NOUT * base, ncontrib + base, gC + 3 * base,
                  gD + base, gA + base, gM ? gM + base : NULL, sgrad, P);
         for (int g = 0; g < N; ++g) {
             if (!P[g].valid) continue;

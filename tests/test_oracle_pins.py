@@ -281,7 +281,7 @@ def _fd_scene(seed, deg=3, N=6):
         sc = _random_scene(rng, N, 20, 24, 24.0, deg, logit_hi=2.0)
         out = oracle.render(sc)[0]
         P = oracle.project(sc, 0)
-        if out["margin"].min() > 2e-3 and (out["ncontrib"] > 0).mean() > 0.2 and \
+        if min(out["margin"].min(), out["zmargin"].min()) > 2e-3 and (out["ncontrib"] > 0).mean() > 0.2 and \
                 min(P["r"].min(), P["g"].min(), P["b"].min()) > 0.05:
             return sc
 
@@ -345,6 +345,216 @@ def test_pose_gradient_matches_central_fd(seed):
     _, g = oracle.render_backward(sc, [wC], [wD], [wA])
     fd = _pose_fd(sc, wC, wD, wA)
     np.testing.assert_allclose(g["pose"][0], fd, rtol=2e-6, atol=1e-7 * np.abs(fd).max())
+
+
+# ------------------------------------------------ clamped branches (3DGS conventions)
+
+def _fd_all(sc, wC, wD, wA, h=1e-6):
+    """Central differences of L = <wC, C> + <wD, D> + <wA, A> for every
+    parameter class and the six pose dofs of view 0."""
+    fd = {}
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        arr = getattr(sc, name)
+        out = np.zeros_like(arr, dtype=np.float64)
+        flat = arr.reshape(-1)
+        for i in range(flat.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = _loss(sc, wC, wD, wA)
+            flat[i] = keep - h
+            lm = _loss(sc, wC, wD, wA)
+            flat[i] = keep
+            out.reshape(-1)[i] = (lp - lm) / (2 * h)
+        fd[name] = out
+    fd["pose"] = _pose_fd(sc, wC, wD, wA, h)
+    return fd
+
+
+def _assert_matches_fd(g, fd, tol=1e-6):
+    for name, ref in fd.items():
+        an = g[name][0] if name == "pose" else g[name]
+        err = np.linalg.norm(an - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert err < tol, (name, err)
+
+
+def test_projection_beyond_the_jacobian_clamp():
+    """Beyond 1.3 x the half field of view the EWA Jacobian is taken at the
+    clamped direction: Sigma' = J W Sigma W^T J^T + 0.3 I with J the numerical
+    Jacobian of the pinhole model at (clip(x/z) z, clip(y/z) z, z), each ratio
+    clipped to +-1.3 (W/2)/fx, +-1.3 (H/2)/fy; the pixel mean (u, v) is the
+    unclamped pinhole image.  Points just inside the limit are not clamped."""
+    c = cam(40, 64, 50.0, cx=31.0, cy=20.5)
+    limx, limy = 1.3 * 32 / 50.0, 1.3 * 20 / 50.0
+    ratios = [(0.95, 0.0), (1.05, 0.0), (1.6, 0.2), (-1.3, 0.5), (0.3, 1.04), (-0.2, -2.0), (1.2, -1.4),
+              (-0.97, 0.99)]
+    N = len(ratios)
+    z = np.linspace(2.0, 5.0, N)
+    mu = np.stack([[rx * limx * zz for (rx, _), zz in zip(ratios, z)],
+                   [ry * limy * zz for (_, ry), zz in zip(ratios, z)], z])
+    rng = np.random.default_rng(7)
+    ls = rng.normal(-2.0, 0.3, (3, N))
+    q = rng.standard_normal((4, N))
+    sc = make_scene(mu, ls, q, np.zeros(N), np.zeros((3, N)), 0, [c])
+    P = oracle.project(sc, 0)
+
+    def pi(p):
+        return np.array([c.fx * p[0] / p[2] + c.cx, c.fy * p[1] / p[2] + c.cy])
+
+    for g, (rx, ry) in enumerate(ratios):
+        pc = mu[:, g]
+        assert P["clamp_x"][g] == (abs(rx) > 1) and P["clamp_y"][g] == (abs(ry) > 1)
+        np.testing.assert_allclose([P["u"][g], P["v"][g]], pi(pc), rtol=1e-14)
+        pt = np.array([np.clip(pc[0] / pc[2], -limx, limx) * pc[2], np.clip(pc[1] / pc[2], -limy, limy) * pc[2], pc[2]])
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = 1e-5 * pc[2]
+            J[:, k] = (pi(pt + e) - pi(pt - e)) / (2e-5 * pc[2])
+        R = Rotation.from_quat([q[1, g], q[2, g], q[3, g], q[0, g]]).as_matrix()
+        S2 = J @ R @ np.diag(np.exp(2 * ls[:, g])) @ R.T @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose([P["cov0"][g], P["cov1"][g], P["cov2"][g]],
+                                   [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=1e-8, atol=1e-9)
+
+
+def _clamped_jacobian_scene(seed):
+    """Gaussians whose means lie beyond the Jacobian clamp (x/z or y/z past
+    1.3 x the half field of view, by more than 5 %) with footprints that
+    still cover pixels, plus two on-screen ones; every threshold decision has
+    a margin > 2e-3 and every colour is above 0.05."""
+    rng = np.random.default_rng(seed)
+    H, W, f = 20, 24, 24.0
+    limx, limy = 1.3 * (W / 2) / f, 1.3 * (H / 2) / f
+    while True:
+        N = 6
+        z = rng.uniform(2, 3.5, N)
+        rx = np.concatenate([rng.choice([-1, 1], 3) * rng.uniform(1.08, 1.3, 3), rng.uniform(-0.5, 0.5, 3)])
+        ry = np.concatenate([rng.uniform(-0.5, 0.5, 3), rng.choice([-1, 1], 1) * rng.uniform(1.08, 1.3, 1),
+                             rng.uniform(-0.5, 0.5, 2)])
+        ry[0] = rng.choice([-1, 1]) * rng.uniform(1.08, 1.25)      # one clamped in both ratios
+        mu = np.stack([rx * limx * z, ry * limy * z, z])
+        ls = np.log(rng.uniform(3.5, 5.0, (3, N)) * z / f)         # ~4 px footprints
+        ls[:, 4:] = np.log(rng.uniform(1.5, 2.5, (3, 2)) * z[4:] / f)
+        sh = np.zeros((48, N))
+        sh[0:3] = dc_for_rgb(rng.uniform(0.2, 0.8, (3, N)))
+        sh[3:] = rng.normal(0, 0.05, (45, N))
+        Rwc = Rotation.from_rotvec(rng.normal(0, 0.02, 3)).as_matrix()
+        Tm = np.hstack([Rwc.T, np.zeros((3, 1))])
+        sc = make_scene(Rwc @ mu, ls, rng.standard_normal((4, N)), rng.uniform(-0.5, 1.5, N), sh, 3,
+                        [cam(H, W, f, Tm)])
+        out = oracle.render(sc)[0]
+        P = oracle.project(sc, 0)
+        pc = Rwc.T @ sc.means
+        ratio = np.maximum(np.abs(pc[0] / pc[2]) / limx, np.abs(pc[1] / pc[2]) / limy)
+        if min(out["margin"].min(), out["zmargin"].min()) > 2e-3 and \
+                np.all(np.abs(np.abs(pc[0] / pc[2]) / limx - 1) > 1e-2) and \
+                np.all(np.abs(np.abs(pc[1] / pc[2]) / limy - 1) > 1e-2) and \
+                min(P["r"].min(), P["g"].min(), P["b"].min()) > 0.05 and \
+                (P["clamp_x"] + P["clamp_y"] > 0).sum() >= 3 and (ratio > 1).sum() >= 3:
+            return sc, P
+
+
+@pytest.mark.parametrize("seed", [50, 51])
+def test_gradients_through_the_jacobian_clamp_match_central_fd(seed):
+    """With x/z, y/z clamped in the EWA Jacobian (and the clamp kept by a
+    margin, so the forward is smooth there), the analytic gradients of every
+    parameter and of the pose equal central differences of the forward."""
+    sc, P = _clamped_jacobian_scene(seed)
+    wC, wD, wA = _upstream(sc, seed)
+    _, g = oracle.render_backward(sc, [wC], [wD], [wA])
+    clamped = np.nonzero(P["clamp_x"] + P["clamp_y"] > 0)[0]
+    # the clamped Gaussians do reach the image: their parameters get gradients
+    assert all(np.abs(g["means"][:, k]).max() > 1e-6 for k in clamped)
+    _assert_matches_fd(g, _fd_all(sc, wC, wD, wA))
+
+
+def _alpha_clamp_scene():
+    """A wide, nearly opaque isotropic Gaussian A on the optical axis whose
+    alpha exceeds 0.99 at exactly the four pixels around its centre (pixel
+    centres at distance^2 0.5: d^2 = 0.005, sigma exp(-d^2/2) = 0.9974; the
+    next ring, at distance^2 2.5, gives 0.9875), and two smaller anisotropic
+    Gaussians B, C behind it."""
+    c = cam(22, 22, 20.0, cx=10.5, cy=10.5)
+    zA = 2.0
+    sA = np.sqrt(100.0 - 0.3) * zA / 20.0                      # Sigma' = 100 I px^2
+    sig_logit = np.log(0.9999 / 0.0001)
+    mu = np.array([[0.0, 0.02, -0.1], [0.0, -0.05, 0.08], [zA, 3.0, 3.4]])
+    ls = np.array([[np.log(sA), np.log(0.09), np.log(0.2)], [np.log(sA), np.log(0.25), np.log(0.07)],
+                   [np.log(sA), np.log(0.12), np.log(0.1)]])
+    q = np.array([[1.0, 0.9, 0.7], [0.0, 0.2, -0.3], [0.0, -0.3, 0.1], [0.0, 0.1, 0.5]])
+    rgb = np.array([[0.7, 0.3, 0.5], [0.2, 0.8, 0.4], [0.6, 0.5, 0.9]])
+    return make_scene(mu, ls, q, [sig_logit, 0.3, -0.2], dc_for_rgb(rgb), 0, [c])
+
+
+def test_alpha_clamp_pixels_pass_no_gradient_through_alpha():
+    """Where alpha is clamped at 0.99 it does not depend on the opacity or on
+    d^2: a loss on those four pixels alone has zero gradient w.r.t. A's
+    opacity logit, scales, rotation and in-plane position (A's depth still
+    moves the composited depth), and central differences agree."""
+    sc = _alpha_clamp_scene()
+    c = sc.cameras[0]
+    P = oracle.project(sc, 0)
+    a_raw = P["opacity"][0] * np.exp(-0.5 * 0.5 / 100.0)
+    assert a_raw > 0.99 * 1.005 and P["opacity"][0] * np.exp(-0.5 * 2.5 / 100.0) < 0.99 * 0.998
+    rng = np.random.default_rng(3)
+    mask = np.zeros((c.H, c.W))
+    mask[10:12, 10:12] = 1.0
+    wC, wD, wA = rng.uniform(-1, 1, (3, c.H, c.W)) * mask, rng.uniform(-1, 1, (c.H, c.W)) * mask, \
+        rng.uniform(-1, 1, (c.H, c.W)) * mask
+    out, g = oracle.render_backward(sc, [wC], [wD], [wA])
+    assert (out[0]["ncontrib"][10:12, 10:12] == 3).all()
+    assert g["opacity_logits"][0] == 0 and not g["log_scales"][:, 0].any() and not g["quats"][:, 0].any()
+    assert not g["means"][0:2, 0].any() and g["means"][2, 0] != 0
+    fd = _fd_all(sc, wC, wD, wA)
+    assert abs(fd["opacity_logits"][0]) < 1e-8 and np.abs(fd["log_scales"][:, 0]).max() < 1e-8
+    _assert_matches_fd(g, fd)
+
+
+def test_gradients_with_alpha_clamp_match_central_fd():
+    """The whole image, clamped and unclamped pixels together."""
+    sc = _alpha_clamp_scene()
+    out = oracle.render(sc)[0]
+    assert min(out["margin"].min(), out["zmargin"].min()) > 2e-3
+    wC, wD, wA = _upstream(sc, 4)
+    _, g = oracle.render_backward(sc, [wC], [wD], [wA])
+    _assert_matches_fd(g, _fd_all(sc, wC, wD, wA))
+
+
+def test_negative_colour_is_clamped_to_zero():
+    """Closed-form footprint of an isotropic Gaussian whose raw colour
+    SH_0 Y_0 + 0.5 is (-0.3, 0.5, 1.2): the rendered colour is
+    (0, 0.5 alpha, 1.2 alpha) -- clamped below at zero, not above at one."""
+    c = cam(30, 40, 60.0)
+    z, s, logit = 3.0, 0.08, 0.9
+    raw = np.array([-0.3, 0.5, 1.2])
+    sc = make_scene([[0.0], [0.0], [z]], np.full((3, 1), np.log(s)), [[1.0], [0.0], [0.0], [0.0]],
+                    [logit], dc_for_rgb(raw)[:, None], 0, [c])
+    out = oracle.render(sc)[0]
+    yy, xx = np.mgrid[0:c.H, 0:c.W]
+    a = _iso_alpha(1 / (1 + np.exp(-logit)), 60.0, s, z, (xx - 20.0) ** 2 + (yy - 15.0) ** 2)
+    np.testing.assert_allclose(out["color"][0], 0.0, atol=0)
+    np.testing.assert_allclose(out["color"][1], 0.5 * a, atol=1e-13)
+    np.testing.assert_allclose(out["color"][2], 1.2 * a, atol=1e-13)
+
+
+def test_clamped_colour_channel_passes_no_gradient():
+    """Degree-3 colours with channel 0 of one Gaussian negative in the view
+    (clamped to 0): that channel's SH coefficients get zero gradient, and
+    every gradient, the view-direction terms of the other channels included,
+    equals central differences."""
+    rng = np.random.default_rng(60)
+    while True:
+        sc = _random_scene(rng, 6, 20, 24, 24.0, 3, logit_hi=2.0)
+        sc.sh[0, 0] = (-0.35 - 0.5) / Y00                      # raw red of Gaussian 0 about -0.35
+        out = oracle.render(sc)[0]
+        P = oracle.project(sc, 0)
+        colours = np.stack([P["r"], P["g"], P["b"]])
+        if min(out["margin"].min(), out["zmargin"].min()) > 2e-3 and P["r"][0] == 0 and \
+                np.sort(colours.reshape(-1))[1] > 0.05 and (out["ncontrib"] > 0).mean() > 0.2:
+            break
+    wC, wD, wA = _upstream(sc, 61)
+    _, g = oracle.render_backward(sc, [wC], [wD], [wA])
+    assert not g["sh"][0::3, 0].any()                           # red coefficients of Gaussian 0
+    assert np.abs(g["sh"][1::3, 0]).max() > 0
+    _assert_matches_fd(g, _fd_all(sc, wC, wD, wA))
 
 
 def test_pose_translation_identity():
