@@ -240,7 +240,9 @@ def cpu_baseline(scene, seconds, images=None):
         worst_c = worst_d = all_c = all_d = 0.0
         near = over = 0
         for (col, dep), p, r in zip(images, pix, res):
-            ok = r["margin"] >= 1e-4          # pixels away from every FP32-vs-FP64 threshold decision
+            # pixels away from every FP32-vs-FP64 decision flip: threshold decisions (cutoff, alpha
+            # skip, stop) farther than 1e-5 relative, depth order farther than 1e-6
+            ok = (r["margin"] >= 1e-5) & (r["zmargin"] >= 1e-6)
             near += int((~ok).sum())
             dc = np.abs(col[:, p] - r["color"]).max(axis=0)
             dd = np.abs(dep[p] - r["depth"]) / np.maximum(np.abs(r["depth"]), 1e-3)
@@ -249,7 +251,8 @@ def cpu_baseline(scene, seconds, images=None):
             all_c = max(all_c, float(dc.max(initial=0.0)))
             all_d = max(all_d, float(dd.max(initial=0.0)))
             over += int(((dc > 1e-4) | (dd > 1e-4)).sum())
-        out["parity"] = {"pixels": npx, "near_threshold_pixels": near, "max_abs_color": worst_c,
+        out["parity"] = {"pixels": npx, "near_threshold_pixels": near, "near_threshold_share": near / max(npx, 1),
+                         "max_abs_color": worst_c,
                          "max_rel_depth": worst_d, "max_abs_color_all_pixels": all_c,
                          "max_rel_depth_all_pixels": all_d, "pixels_over_tolerance": over,
                          "tolerance": {"color": 1e-4, "depth": 1e-4},

@@ -5,10 +5,22 @@ under the tolerances of the specification:
   depth    |dD| <= 1e-4 * max(|D_ref|, 1e-3)
   opacity  |dA| <= 1e-4 absolute
   gradients: relative L2 <= 1e-3 per parameter tensor.
-Pixels whose oracle decision margin (the relative distance of any cutoff,
-alpha-skip, stop or depth-order decision from its threshold) is below
-MARGIN are FP32-vs-FP64 threshold flips: they are counted, and their share
-must stay below FLIP_SHARE; every other pixel must meet the tolerance.
+Pixels where the oracle took a decision close to its threshold may be
+FP32-vs-FP64 decision flips: those whose threshold margin (the relative
+distance of a cutoff, alpha-skip or stop decision from its threshold) is
+below MARGIN, or whose depth-order margin (the relative gap between two
+consecutive depths) is below ZMARGIN.  Out-of-tolerance pixels among them
+are counted, and their share must stay below FLIP_SHARE; every other pixel
+must meet the tolerance.
+
+MARGIN: the FP32 path computes d^2 from double-float pixel offsets and the
+Cholesky factor of the inverse covariance, each a few ulps off, so d^2,
+alpha = sigma exp(-d^2 / 2) and the transmittance product carry relative
+errors of a few 1e-7 to 1e-6; 1e-5 leaves a factor of ten.
+ZMARGIN: depths are sorted as FP32 values (the camera-frame z, formed with
+a compensated dot product: half an ulp, 6e-8 relative), so two depths more
+than one ulp (1.2e-7 relative) apart cannot swap; 1e-6 leaves a factor of
+eight.
 """
 from __future__ import annotations
 
@@ -23,8 +35,10 @@ COLOR_TOL = 1e-4
 DEPTH_TOL = 1e-4
 ALPHA_TOL = 1e-4
 GRAD_TOL = 1e-3
-MARGIN = 1e-4
+MARGIN = 1e-5
+ZMARGIN = 1e-6
 FLIP_SHARE = 1e-3
+SURFEL_MARGIN = 1e-4     # the surfel oracle's single margin (ray-splat decisions)
 
 
 def to_device(scene: Scene, dev="cuda"):
@@ -70,19 +84,25 @@ def gpu_backward(scene: Scene, state, gC, gD, gA):
     return out
 
 
+def near_threshold(ref):
+    """Pixels where a decision of the oracle lies within FP32 reach of its
+    threshold (see MARGIN, ZMARGIN)."""
+    return (ref["margin"] < MARGIN) | (ref["zmargin"] < ZMARGIN)
+
+
 def compare_images(ref, got, label=""):
     """Checks one view; returns (n_flip_pixels, n_pixels, max errors dict)."""
-    margin = ref["margin"]
     dC = np.abs(got["color"] - ref["color"]).max(axis=0)
     dD = np.abs(got["depth"] - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-3)
     dA = np.abs(got["alpha"] - ref["alpha"])
     bad = (dC > COLOR_TOL) | (dD > DEPTH_TOL) | (dA > ALPHA_TOL)
-    flip = margin < MARGIN
+    flip = near_threshold(ref)
     hard = bad & ~flip
     errs = dict(color=float(dC.max()), depth=float(dD.max()), alpha=float(dA.max()),
-                color_nonflip=float(dC[~flip].max()) if (~flip).any() else 0.0)
+                color_nonflip=float(dC[~flip].max()) if (~flip).any() else 0.0,
+                near_threshold=int(flip.sum()))
     assert not hard.any(), (
-        f"{label}: {int(hard.sum())} pixels out of tolerance with margin >= {MARGIN}; "
+        f"{label}: {int(hard.sum())} pixels out of tolerance away from every threshold; "
         f"worst colour {dC[~flip].max():.3g}, depth {dD[~flip].max():.3g}, alpha {dA[~flip].max():.3g}")
     return int((bad & flip).sum()), int(bad.size), errs
 

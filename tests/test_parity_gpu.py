@@ -36,11 +36,13 @@ def test_forward_parity_reduced(name):
     sc = REDUCED[name]()
     got, _ = U.gpu_forward(sc)
     ref = oracle.render(sc)
-    flips = total = 0
+    flips = total = near = 0
     for v, (r, g) in enumerate(zip(ref, got)):
-        f, n, _ = U.compare_images(r, g, f"{name} view {v}")
-        flips, total = flips + f, total + n
+        f, n, e = U.compare_images(r, g, f"{name} view {v}")
+        flips, total, near = flips + f, total + n, near + e["near_threshold"]
     assert flips <= max(2, U.FLIP_SHARE * total), f"{flips} threshold-flip pixels of {total}"
+    # the per-pixel tolerance holds on all but a small share of the pixels
+    assert near <= 0.01 * total, f"{near} of {total} pixels near a threshold"
 
 
 @pytest.mark.parametrize("name", list(REDUCED))
@@ -202,13 +204,15 @@ def test_full_size_sampled_pixels(name):
     pix, gCs, gDs, gAs = scenes.sparse_pixel_grads(sc, per_view, seed=11)
     got, state = U.gpu_forward(sc)
     ref = oracle.render(sc, pixels=pix, brute=True)
-    flips = total = 0
+    flips = total = near = 0
     for v, (r, g) in enumerate(zip(ref, got)):
         sel = {k: (g[k].reshape(3, -1)[:, pix[v]] if k == "color" else g[k].reshape(-1)[pix[v]])
                for k in ("color", "depth", "alpha")}
-        f, n, _ = U.compare_images(r, sel, f"{name} view {v}")
-        flips, total = flips + f, total + n
+        f, n, e = U.compare_images(r, sel, f"{name} view {v}")
+        flips, total, near = flips + f, total + n, near + e["near_threshold"]
     assert flips <= max(2, U.FLIP_SHARE * total * 10), f"{flips} threshold-flip pixels of {total}"
+    # deep lists at full size: more close depth pairs per pixel, still a small share
+    assert near <= 0.05 * total, f"{near} of {total} pixels near a threshold"
     # sparse upstream gradients: dense on the GPU, listed pixels for the oracle
     gC, gD, gA = [], [], []
     for v, c in enumerate(sc.cameras):
@@ -362,7 +366,7 @@ def test_median_depth_forward_and_backward(name):
     for v, (r, m) in enumerate(zip(ref, R.split_views(med, cams))):
         got = m.cpu().numpy().astype(np.float64)
         err = np.abs(got - r["median_depth"]) / np.maximum(np.abs(r["median_depth"]), 1e-3)
-        flip = (r["median_margin"] < U.MARGIN) | (r["margin"] < U.MARGIN)
+        flip = (r["median_margin"] < U.MARGIN) | U.near_threshold(r)
         bad = err > U.DEPTH_TOL
         assert not (bad & ~flip).any(), f"view {v}: {int((bad & ~flip).sum())} median pixels off"
         flips += int((bad & flip).sum())
@@ -413,7 +417,7 @@ def test_densify_stats_against_oracle(name):
     got = {k: v.cpu().numpy().astype(np.float64) for k, v in dens.items()}
     _, rg = oracle.render_backward(sc, gC, gD, gA, want_screen=True)
     ref = oracle.densify_stats(sc, rg["screen"])
-    sure = ref["margin"] > U.MARGIN * 10
+    sure = ref["margin"] > 1e-3
     assert sure.mean() > 0.99
     np.testing.assert_array_equal(got["count"][sure], ref["count"][sure])
     assert U.rel_l2(got["grad"], ref["grad"]) < U.GRAD_TOL

@@ -50,7 +50,7 @@ def gpu_surfels(sc, tile=16, binning="tile"):
 
 
 def compare_surfels(ref, got, label):
-    flip = ref["margin"] < U.MARGIN
+    flip = ref["margin"] < U.SURFEL_MARGIN
     err_c = np.abs(got["color"] - ref["color"]).max(0)
     err_n = np.abs(got["normal"] - ref["normal"]).max(0)
     err_a = np.abs(got["alpha"] - ref["alpha"])
