@@ -42,6 +42,12 @@ STAGE_SLEEP_CYCLES = 4_000_000   # about 2 ms of GPU sleep before each stage-tim
 BWD_OPS_PER_PAIR = 48   # the same for the blend backward (before the per-warp reduction)
 SURFEL_FWD_OPS_PER_PAIR = 47   # surfels: ray-disk intersection + compositing with normal and distortion
 SURFEL_BWD_OPS_PER_PAIR = 85   # surfels: recomputed intersection + its backward
+# MUFU (SFU) operations per composited pair: ex2 of alpha in the forward; ex2 and the
+# reciprocal of 1 - alpha in the backward
+MUFU_PER_PAIR = {"blend_fwd": 1, "blend_bwd": 2}
+MUFU_PER_SM_CLK = 16   # SFU lanes per SM per clock (4 per SM sub-partition)
+# peak device allocation allowed for the in-the-wild window (32 x 1920x1080, 2M Gaussians)
+HBM_BUDGET_BYTES = {"outdoor": 32 * 10**9}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -73,6 +79,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    p.add_argument("--extra-workloads", default="uneven,outdoor",
+                   help="comma-separated workloads also measured after the headline one (rank 0 of a 1-GPU run, "
+                        "graph replay, autotuned tile and binning), or 'none'")
     return p.parse_args()
 
 
@@ -373,9 +382,10 @@ class Window:
                                    densify=self.dens)
 
 
-def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, binning="tile", tiles=1):
+def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, binning="tile", tiles=1, sfu_peak=None):
     """Every stage against its bound: the blends against the FP32 lanes
-    (composited pairs x FP32 instructions per pair), the rest against HBM with
+    (composited pairs x FP32 instructions per pair) and, beside it, the SFU
+    (composited pairs x MUFU operations per pair), the rest against HBM with
     the bytes the host can count -- a lower bound for the preprocesses, whose
     records of visible pairs are counted on the device only."""
     K = (scene.sh_degree + 1) ** 2
@@ -385,6 +395,10 @@ def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, bin
     for s in ("blend_fwd", "blend_bwd"):
         a = pairs * ops[s] / (stage_ms[s] * 1e-3) / 1e9
         out[s] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Gop/s", "frac": a / alu_peak}
+        if sfu_peak and s in MUFU_PER_PAIR and stage_ms[s] > 0:
+            m = pairs * MUFU_PER_PAIR[s] / (stage_ms[s] * 1e-3) / 1e9
+            out[s]["sfu"] = {"achieved": m, "peak": sfu_peak, "unit": "Gop/s", "frac": m / sfu_peak,
+                             "work": f"{MUFU_PER_PAIR[s]} MUFU per composited pair"}
     hbm = {
         # parameters once, a 4-byte count per pair, 12 bytes per emitted key
         "preprocess": (param_b + 4 * VN + 12 * keys, "lower bound: + 64 B of records per visible pair"),
@@ -442,9 +456,9 @@ def time_steps(torch, fn, K, flush, events_per_step=None):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source has not changed since the capture."""
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    if the kernel's source has not changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     name = "blend.cu" if "blend" in kernel else ("binning.cu" if kernel in ("sort", "duplicate") else "preprocess.cu")
     src = os.path.join(ROOT, "paper_2411_17660_b300", "csrc", name)
@@ -456,9 +470,88 @@ def traffic_for(kernel: str):
         if line.startswith("#"):
             continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("source_sha") == sha:
+        if f.get("kernel") == kernel and f.get("source_sha") == sha and f.get("workload") == workload:
             return float(f["dram_bytes_per_launch"])
     return None
+
+
+def step_memory(torch, scene, win):
+    """Peak device allocation of the step: every tensor of the window
+    (parameters, targets, images, gradients, workspace) plus whatever the step
+    allocates on the fly, read after the timed steps (the peak statistics
+    were reset once the window was set up)."""
+    peak = torch.cuda.max_memory_allocated()
+    out = {"peak_allocated_bytes": int(peak), "workspace_bytes": int(win.ws.numel() * win.ws.element_size()),
+           "note": "torch.cuda.max_memory_allocated() over the timed steps: parameters, targets, images, "
+                   "gradients and the library's workspace (the library allocates nothing itself); "
+                   "excludes the bench's 256 MB L2-flush buffer"}
+    budget = HBM_BUDGET_BYTES.get(scene.name.split("-")[0])
+    if budget:
+        out["budget_bytes"] = budget
+        out["within_budget"] = peak - L2_FLUSH_BYTES <= budget
+    return out
+
+
+def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W=3):
+    """Another workload, measured like the headline one: tile size and
+    binning from the autotuner, stage times from eager steps queued behind a
+    GPU sleep, the step as one replayed CUDA graph, the peak allocation."""
+    from paper_2411_17660_b300 import autotune as A
+    scene = make_scene(name)
+    params = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).cuda() for k in R.PARAM_NAMES}
+    cams = [R.Intrinsics(c.H, c.W, c.fx, c.fy, c.cx, c.cy) for c in scene.cameras]
+    vm = torch.from_numpy(np.stack([c.T_cw for c in scene.cameras]).astype(np.float32)).cuda()
+    tuned = A.tune(params, scene.sh_degree, cams, vm)
+    del params, vm
+    torch.cuda.empty_cache()
+    rast = R.GaussianRasterizer(tuned["tile"], binning=tuned["binning"])
+    win = Window(scene, rast)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    for _ in range(W):
+        flush()
+        win.step()
+    ev_sets = [[torch.cuda.Event(enable_timing=True) for _ in range(B.STAGE_EVENTS)] for _ in range(K)]
+    for es in ev_sets:    # stages a path skips keep these recordings (zero length)
+        for e in es:
+            e.record()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush()
+        torch.cuda._sleep(STAGE_SLEEP_CYCLES)
+        rast.ctx.set_stage_events([e.cuda_event for e in ev_sets[k]])
+        win.step()
+    torch.cuda.synchronize()
+    rast.ctx.set_stage_events(None)
+    eager = statistics.mean(time_steps(torch, win.step, K, flush))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        win.step()
+    for _ in range(3):
+        flush()
+        graph.replay()
+    replay = statistics.mean(time_steps(torch, graph.replay, K, flush))
+    info = rast.info(win.ws)
+    if info.status != 0:
+        raise RuntimeError(f"{name}: device status {B.STATUS.get(info.status)}")
+    stage_ms = {}
+    for k, st in enumerate(B.STAGES):
+        a, b = B.STAGE_SPANS[k]
+        stage_ms[st] = statistics.mean(ev_sets[i][a].elapsed_time(ev_sets[i][b]) for i in range(K))
+    ops = {"blend_fwd": FWD_OPS_PER_PAIR, "blend_bwd": BWD_OPS_PER_PAIR}
+    roof = stage_rooflines(stage_ms, ops, info.pairs_contributing, alu_peak, peaks["hbm_gbs"], scene, win.P,
+                           info.keys, tuned["binning"], info.tiles, sfu_peak)
+    out = {"config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene),
+                      "gaussians": scene.N, "sh_degree": scene.sh_degree, "tile": tuned["tile"],
+                      "binning": tuned["binning"], "autotune_ms": tuned["ms"],
+                      "step": f"forward + L1 colour/depth loss + backward (params + {scene.V} poses)",
+                      "launch": "one CUDA graph per step, replayed", "steps": K, "warmup": W},
+           "value": win.P / (replay / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": replay,
+           "mapping_it_per_s": 1000.0 / replay, "eager_ms_per_step": eager,
+           "stages_ms": stage_ms, "keys": info.keys, "pairs_contributing": info.pairs_contributing,
+           "stage_rooflines": roof, "memory": step_memory(torch, scene, win)}
+    del graph, win
+    return out
 
 
 def main():
@@ -484,9 +577,11 @@ def main():
     rast = R.GaussianRasterizer(tile, binning=args.binning)
     opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify,
                 fuse_l1=not args.separate_loss)
-    win = Window(scene, rast, **opts)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_buf.fill_(1.0)
+    win = Window(scene, rast, **opts)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
     K, W = args.steps, args.warmup
 
     for _ in range(max(W, 3)):
@@ -530,6 +625,7 @@ def main():
     info = rast.info(win.ws)
     if info.status != 0:
         raise RuntimeError(f"device status {B.STATUS.get(info.status)} during the timed steps")
+    memory = step_memory(torch, scene, win)
     stage_ms = {}
     for k, name in enumerate(B.STAGES):
         a, b = B.STAGE_SPANS[k]
@@ -553,7 +649,7 @@ def main():
         per_view = dist_max(world, statistics.mean(pv))
 
     # the same step captured once in a CUDA graph and replayed
-    graph_ms = None
+    graph_ms, graph = None, None
     if not args.no_graph:
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -580,6 +676,7 @@ def main():
     peaks = load_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * peaks["sm_max_mhz"] * 1e6 / 1e9   # Gop/s (FP32 lanes x clock)
+    sfu_peak = n_sm * MUFU_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e9   # Gop/s (SFU lanes x clock)
     pairs = info.pairs_contributing
     dominant = max(("blend_fwd", "blend_bwd", "sort", "preprocess", "preprocess_bwd"), key=lambda s: stage_ms[s])
     ops = {"blend_fwd": FWD_OPS_PER_PAIR, "blend_bwd": BWD_OPS_PER_PAIR}
@@ -589,14 +686,14 @@ def main():
         achieved = pairs * ops[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
         roof = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
                 "frac": achieved / alu_peak,
-                "traffic": traffic_for(dominant) if args.primitive == "gaussians" else None,
+                "traffic": traffic_for(dominant, scene.name) if args.primitive == "gaussians" else None,
                 "peak_note": f"FP32 lanes: {n_sm} SMs x 128 x {peaks['sm_max_mhz']:.0f} MHz (max clock)",
                 "work": f"{pairs} composited pairs x {ops[dominant]} FP32 ops"}
     else:
         roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": None, "traffic": traffic_for(dominant)}
+                "frac": None, "traffic": traffic_for(dominant, scene.name)}
     stage_roof = stage_rooflines(stage_ms, ops, pairs, alu_peak, peaks["hbm_gbs"], scene, win.P, info.keys,
-                                 args.binning, info.tiles)
+                                 args.binning, info.tiles, sfu_peak if args.primitive == "gaussians" else None)
 
     P_all = win.P * world
     # headline: the step as one replayed CUDA graph (the batched path's launch
@@ -626,6 +723,7 @@ def main():
         "stage_timing": "device time per stage from CUDA events, in steps queued behind a ~2 ms GPU sleep "
                         "so that host launch gaps do not count",
         "keys": info.keys, "pairs_contributing": pairs,
+        "memory": memory,
         "roofline": roof,
         "stage_rooflines": stage_roof,
         "graph_replay": None if graph_ms is None else {
@@ -638,6 +736,7 @@ def main():
     }
     if args.density_ops:
         line["density_ops"] = measure_density(torch, win, K, W, flush, peaks["hbm_gbs"])
+
     if rank == 0 and not args.no_cpu:
         imgs = None
         if args.primitive == "gaussians":   # the oracle renders Gaussians
@@ -646,6 +745,15 @@ def main():
             imgs = [(c.reshape(3, -1).cpu().numpy().astype(np.float64), d.reshape(-1).cpu().numpy().astype(np.float64))
                     for c, d in zip(cols, deps)]
         line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, imgs)
+    extras = [w for w in args.extra_workloads.split(",") if w and w != "none" and w != scene.name]
+    if extras and world == 1 and args.primitive == "gaussians":
+        del win, graph
+        torch.cuda.empty_cache()
+        line["workloads"] = {}
+        for name in extras:
+            line["workloads"][name] = measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak,
+                                                       K=min(K, 5), W=3)
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -726,8 +834,26 @@ def measure_e2e(torch, R, scene, win, K, W, flush):
     torch.cuda.synchronize()
     ms = time_steps(torch, e2e_step, K, flush)
     m = statistics.mean(ms)
+    # the same with every parameter gradient read back as well
+    out_grads = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in win.grads.items()}
+    d2h_all = d2h + sum(t.numel() * 4 for t in out_grads.values())
+
+    def e2e_step_grads():
+        e2e_step()
+        for k, t in out_grads.items():
+            t.copy_(win.grads[k], non_blocking=True)
+
+    for _ in range(2):
+        flush()
+        e2e_step_grads()
+    torch.cuda.synchronize()
+    mg = statistics.mean(time_steps(torch, e2e_step_grads, K, flush))
     return {"value": win.P / (m / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": m,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "returns": "the loss and the pose gradients: the parameter gradients stay on the device, where the "
+                       "mapper's optimiser consumes them",
+            "with_param_grads": {"value": win.P / (mg / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": mg,
+                                 "d2h_bytes_per_step": d2h_all}}
 
 
 if __name__ == "__main__":

@@ -21,14 +21,13 @@
 // of global atomics per (warp, Gaussian); when at most four lanes touch a
 // Gaussian they issue their atomics directly instead.
 //
-// In the backward, a lane's pixels share their column, hence dx: the
-// per-pixel arithmetic of two of them runs on packed FP32 pairs (one
-// fma.rn.f32x2 for both pixels, the same rounding as two scalar ones, so that
-// the decisions stay bit-identical to the forward's scalar ones).  Its staged entries hold every
+// A lane's pixels share their column, hence dx: the per-pixel arithmetic
+// of two of them runs on packed FP32 pairs (one fma.rn.f32x2 for both
+// pixels, the same rounding as two scalar ones, so that the forward and the
+// backward take bit-identical decisions).  The staged entries hold every
 // operand that both pixels use as a duplicated pair, so that one 128-bit
-// shared load yields two ready register pairs.  The forward stays scalar: it
-// skips a pixel row's work whenever no lane of the warp needs it, which
-// saves more than packing would.
+// shared load yields two ready register pairs.  The forward runs its pair
+// without branches; the backward branches on the rows its warp reaches.
 #include "kernels.cuh"
 
 namespace gsr {
@@ -237,74 +236,94 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 // L1: the epilogue also takes the L1 loss terms of its pixels (gsr_render_l1),
 // with the expressions of the stand-alone L1 kernel, so that the gradients
 // match it bit for bit.
+//
+// A lane's two pixels (rows y and y + 4 of its column) run as one packed
+// FP32 pair, without branches: a pixel that an entry does not reach, or that
+// has stopped, composites it with w = 0, which leaves its sums unchanged.
+// The staged entries hold the operands that both pixels use as duplicated
+// pairs (as in the backward), so one 128-bit shared load yields two ready
+// register pairs.
 template <int TS, bool MED, bool L1>
 __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     constexpr int BH = FwdBlock<TS>::H, NR = BH / kRowStep;
+    static_assert(NR == 2, "a lane composites one pair of rows");
     using S = BlendShape<TS, BH>;
-    __shared__ float4 sA[S::WARPS][32], sB[S::WARPS][32], sC[S::WARPS][32];
+    // per slot: (-ur, -ur, -vr, -vr), (m00, m00, m01, m01), (m11, m11, l, l),
+    // (r, r, g, g), (b, b, z, z); sX: (s_max, list index)
+    __shared__ float4 sF[S::WARPS][kEntryQuads][32];
+    __shared__ float2 sX[S::WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.sorted;
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
+    const float2 lx2 = make_float2(lxf, lxf);
+    const float2 neg2 = make_float2(-1.f, -1.f);
 
-    float T[NR], C0[NR], C1[NR], C2[NR], D[NR], Zm[NR];
-    uint32_t last[NR], mi[NR], ncon = 0;
-    bool done[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-        T[q] = 1.f;
-        C0[q] = C1[q] = C2[q] = D[q] = Zm[q] = 0.f;
-        last[q] = mi[q] = 0;
-        done[q] = !(wt.px < vp.W && wt.py + q * kRowStep < vp.H);
-    }
+    // A row that lies outside the view, or has met the transmittance stop,
+    // sits at an infinite row offset: its s is not finite (inf or NaN), so no
+    // entry reaches it.  T never falls below the stop, so an entry that
+    // reaches no row leaves Tn = T and cannot trigger the stop either.
+    const float kInf = __int_as_float(0x7f800000);
+    float2 ly2 = make_float2(wt.px < vp.W && wt.py < vp.H ? lyf : kInf,
+                             wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + (float)kRowStep : kInf);
+    float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0, D = C0, Zm = C0;
+    uint32_t last[NR] = {0u, 0u}, mi[NR] = {0u, 0u}, ncon = 0;
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
-        bool all_done = true;
-#pragma unroll
-        for (int q = 0; q < NR; ++q) all_done &= done[q];
-        if (__all_sync(kFull, all_done)) break;
+        if (__all_sync(kFull, ly2.x == kInf && ly2.y == kInf)) break;
         const int n = stage_chunk<BH>(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
-                                         [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
-                                             uint32_t idx, uint32_t) {
-                                      sA[warp][slot] = make_float4(ur, vr, r1.x, r1.y);
-                                      sB[warp][slot] = make_float4(r1.z, r1.w, log2o, r2.w);
-                                      sC[warp][slot] = make_float4(r2.x, r2.y, r2.z, __uint_as_float(idx));
-                                  });
+                                      [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
+                                          uint32_t idx, uint32_t) {
+                                          float4(&e)[kEntryQuads][32] = sF[warp];
+                                          e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
+                                          e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
+                                          e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
+                                          e[3][slot] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                                          e[4][slot] = make_float4(r2.z, r2.z, r2.w, r2.w);
+                                          sX[warp][slot] = make_float2(r1.w, __uint_as_float(idx));
+                                      });
+#pragma unroll 2
         for (int j = 0; j < n; ++j) {
-            const float4 a = sA[warp][j], b = sB[warp][j];
-            const float m00dx = __fmul_rn(a.z, __fsub_rn(lxf, a.x));
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                if (done[q]) continue;
-                float p1, p2;
-                const float s = pair_s(m00dx, __fsub_rn(lyf + (float)(q * kRowStep), a.y), a.w, b.x, p1, p2);
-                if (s <= b.y) {
-                    const float alpha = fminf(kAlphaMax, ex2_approx(__fsub_rn(b.z, s)));
-                    const float w = alpha * T[q];
-                    const float Tn = T[q] - w;   // T (1 - alpha)
-                    if (Tn < kTStop) {
-                        done[q] = true;
-                    } else {
-                        const float4 c = sC[warp][j];
-                        C0[q] = fmaf(w, c.x, C0[q]);
-                        C1[q] = fmaf(w, c.y, C1[q]);
-                        C2[q] = fmaf(w, c.z, C2[q]);
-                        D[q] = fmaf(w, b.w, D[q]);
-                        if (MED && T[q] > 0.5f) {
-                            Zm[q] = b.w;
-                            mi[q] = __float_as_uint(c.w) + 1u;
-                        }
-                        T[q] = Tn;
-                        last[q] = __float_as_uint(c.w) + 1u;
-                        ++ncon;
-                    }
-                }
+            const float4 e0 = sF[warp][0][j], e1 = sF[warp][1][j], e2 = sF[warp][2][j];
+            const float2 x = sX[warp][j];
+            const float2 m00dx = __fmul2_rn(lo2(e1), __fadd2_rn(lx2, lo2(e0)));
+            const float2 dy = __fadd2_rn(ly2, hi2(e0));
+            float2 p1, p2;
+            const float2 s = pair_s2(m00dx, dy, hi2(e1), lo2(e2), p1, p2);
+            const float2 arg = __ffma2_rn(s, neg2, hi2(e2));    // log2(sigma) - s
+            const float2 al = make_float2(s.x <= x.x ? fminf(kAlphaMax, ex2_approx(arg.x)) : 0.f,
+                                          s.y <= x.x ? fminf(kAlphaMax, ex2_approx(arg.y)) : 0.f);
+            float2 w = __fmul2_rn(al, T);
+            const float2 Tn = __ffma2_rn(w, neg2, T);              // T (1 - alpha)
+            const bool st0 = Tn.x < kTStop, st1 = Tn.y < kTStop;   // stop before this entry
+            w.x = st0 ? 0.f : w.x;
+            w.y = st1 ? 0.f : w.y;
+            ly2.x = st0 ? kInf : ly2.x;
+            ly2.y = st1 ? kInf : ly2.y;
+            const float4 e3 = sF[warp][3][j], e4 = sF[warp][4][j];
+            C0 = __ffma2_rn(w, lo2(e3), C0);
+            C1 = __ffma2_rn(w, hi2(e3), C1);
+            C2 = __ffma2_rn(w, lo2(e4), C2);
+            D = __ffma2_rn(w, hi2(e4), D);
+            // composited <=> w > 0 (alpha >= 1/255 where s <= s_max, T >= the stop)
+            const bool k0 = w.x > 0.f, k1 = w.y > 0.f;
+            const uint32_t id1 = __float_as_uint(x.y) + 1u;
+            if (MED) {
+                if (k0 && T.x > 0.5f) Zm.x = e4.z, mi[0] = id1;
+                if (k1 && T.y > 0.5f) Zm.y = e4.z, mi[1] = id1;
             }
+            T.x = st0 ? T.x : Tn.x;
+            T.y = st1 ? T.y : Tn.y;
+            last[0] = k0 ? id1 : last[0];
+            last[1] = k1 ? id1 : last[1];
+            ncon += (uint32_t)k0 + (uint32_t)k1;
         }
         __syncwarp();
     }
+    const float Ta[NR] = {T.x, T.y}, C0a[NR] = {C0.x, C0.y}, C1a[NR] = {C1.x, C1.y}, C2a[NR] = {C2.x, C2.y},
+                Da[NR] = {D.x, D.y}, Zma[NR] = {Zm.x, Zm.y};
     // L1: the targets of the lane's pixels, loaded together before any store
     // (a store to a gradient image could otherwise alias the next load)
     float tgt[L1 ? NR : 1][4];
@@ -325,15 +344,15 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
         const int py = wt.py + q * kRowStep;
         if (wt.px < vp.W && py < vp.H) {
             const size_t HW = (size_t)vp.H * vp.W, pix = (size_t)py * vp.W + wt.px;
-            vp.color[pix] = C0[q];
-            vp.color[HW + pix] = C1[q];
-            vp.color[2 * HW + pix] = C2[q];
-            if (vp.depth) vp.depth[pix] = D[q];
-            if (vp.alpha) vp.alpha[pix] = 1.f - T[q];
-            ws.T_final[vp.pixel_offset + pix] = T[q];
+            vp.color[pix] = C0a[q];
+            vp.color[HW + pix] = C1a[q];
+            vp.color[2 * HW + pix] = C2a[q];
+            if (vp.depth) vp.depth[pix] = Da[q];
+            if (vp.alpha) vp.alpha[pix] = 1.f - Ta[q];
+            ws.T_final[vp.pixel_offset + pix] = Ta[q];
             ws.last[vp.pixel_offset + pix] = last[q];
             if (MED) {
-                if (vp.median_depth) vp.median_depth[pix] = Zm[q];
+                if (vp.median_depth) vp.median_depth[pix] = Zma[q];
                 ws.median[vp.pixel_offset + pix] = mi[q];
             }
         }
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
             const int py = wt.py + q * kRowStep;
             if (wt.px < vp.W && py < vp.H) {
                 const size_t pix = (size_t)py * vp.W + wt.px;
-                const float c[3] = {C0[q], C1[q], C2[q]};
+                const float c[3] = {C0a[q], C1a[q], C2a[q]};
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     const float d = c[ch] - tgt[q][ch];
@@ -361,7 +380,7 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
                 }
                 float g = 0.f;
                 if (dterm) {
-                    const float d = D[q] - tgt[q][3];
+                    const float d = Da[q] - tgt[q][3];
                     part += fabsf(d) * kd;
                     g = sgn(d) * kd;
                 }
