@@ -73,7 +73,10 @@ def parse():
                    help="also time the density-control calls (ADC, MCMC relocation and noise) at 2M Gaussians")
     p.add_argument("--binning", default="tile", choices=["tile", "radix"],
                    help="tile binning strategy: per-tile counting sort (default) or onesweep radix sort")
-    p.add_argument("--autotune", action="store_true", help="pick the tile size and binning with the autotuner first")
+    p.add_argument("--autotune", action="store_true",
+                   help="pick the tile size, binning and entry batch with the autotuner first")
+    p.add_argument("--batch", type=int, default=32, choices=[32, 64],
+                   help="list entries a blend warp stages per round")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -81,7 +84,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     p.add_argument("--extra-workloads", default="uneven,outdoor",
                    help="comma-separated workloads also measured after the headline one (rank 0 of a 1-GPU run, "
-                        "graph replay, autotuned tile and binning), or 'none'")
+                        "graph replay, autotuned tile, binning and batch), or 'none'")
     return p.parse_args()
 
 
@@ -493,8 +496,8 @@ def step_memory(torch, scene, win):
 
 
 def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W=3):
-    """Another workload, measured like the headline one: tile size and
-    binning from the autotuner, stage times from eager steps queued behind a
+    """Another workload, measured like the headline one: tile size, binning
+    and entry batch from the autotuner, stage times from eager steps queued behind a
     GPU sleep, the step as one replayed CUDA graph, the peak allocation."""
     from paper_2411_17660_b300 import autotune as A
     scene = make_scene(name)
@@ -504,7 +507,7 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
     tuned = A.tune(params, scene.sh_degree, cams, vm)
     del params, vm
     torch.cuda.empty_cache()
-    rast = R.GaussianRasterizer(tuned["tile"], binning=tuned["binning"])
+    rast = R.GaussianRasterizer(tuned["tile"], binning=tuned["binning"], batch=tuned["batch"])
     win = Window(scene, rast)
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
@@ -543,7 +546,7 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
                            info.keys, tuned["binning"], info.tiles, sfu_peak)
     out = {"config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene),
                       "gaussians": scene.N, "sh_degree": scene.sh_degree, "tile": tuned["tile"],
-                      "binning": tuned["binning"], "autotune_ms": tuned["ms"],
+                      "binning": tuned["binning"], "batch": tuned["batch"], "autotune_ms": tuned["ms"],
                       "step": f"forward + L1 colour/depth loss + backward (params + {scene.V} poses)",
                       "launch": "one CUDA graph per step, replayed", "steps": K, "warmup": W},
            "value": win.P / (replay / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": replay,
@@ -572,9 +575,9 @@ def main():
         from paper_2411_17660_b300 import autotune as A
         w0 = Window(scene, R.GaussianRasterizer(16, binning=args.binning), loss=args.loss, primitive=args.primitive)
         tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
-        tile, args.binning = tuned["tile"], tuned["binning"]
+        tile, args.binning, args.batch = tuned["tile"], tuned["binning"], tuned["batch"]
         del w0
-    rast = R.GaussianRasterizer(tile, binning=args.binning)
+    rast = R.GaussianRasterizer(tile, binning=args.binning, batch=args.batch)
     opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify,
                 fuse_l1=not args.separate_loss)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -705,7 +708,8 @@ def main():
         "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
-                   "sh_degree": scene.sh_degree, "tile": tile, "binning": args.binning, "autotune": tuned,
+                   "sh_degree": scene.sh_degree, "tile": tile, "binning": args.binning, "batch": args.batch,
+                   "autotune": tuned,
                    "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
                    "loss_in_forward_blend": win.fuse_l1,
                    "primitive": args.primitive,

@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 5
+#define GSR_ABI_VERSION 6
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -68,29 +68,38 @@ typedef struct CUstream_st *gsr_stream;
 
 typedef struct gsr_ctx gsr_ctx;
 
-/* Library configuration, fixed for the lifetime of a context. */
+/* Library configuration of a context (gsr_autotune may replace tile,
+ * binning and batch with the fastest it measured). */
 typedef struct {
     int tile;              /* screen tile edge in pixels: 8, 16 or 32 (0 = 16) */
     uint32_t spin_limit;   /* iterations before a bounded device wait gives up (0 = default) */
     int flags;             /* 0, or GSR_TEST_STALL_SORT (test hook, see below) */
     int binning;           /* GSR_BIN_TILE (0, default) or GSR_BIN_RADIX */
+    int batch;             /* depth-sorted list entries a blend warp stages per round: 32 or 64
+                              (0 = 32); 64 needs a tile of 8 or 16 (GSR_EINVAL otherwise).
+                              The images do not depend on it, only the speed. */
 } gsr_config;
 
 /* Test hook for the bounded-wait path: the first tile of the first radix-sort
  * pass never publishes its digit counts, so the next tile's look-back wait
  * runs out after spin_limit iterations and the call reports GSR_ETIMEOUT
- * (outputs undefined).  Only GSR_BIN_RADIX has an inter-block wait.  Never set
- * outside tests. */
+ * (outputs undefined).  Only the onesweep passes wait on other blocks: all of
+ * GSR_BIN_RADIX's, and GSR_BIN_TILE's beyond 32,768 tiles.  Never set outside
+ * tests. */
 #define GSR_TEST_STALL_SORT 1
 
 /* Tile binning strategies; both give the same list order (by tile, then
  * depth, then Gaussian index) and so bit-identical results.
- * GSR_BIN_TILE: a counting sort on the tile (the preprocess counts each
- *   tile's keys, a scan gives each tile its place, the duplication fills it
- *   with atomics) and a sort of each tile's (depth, index) words in shared
- *   memory; no kernel waits on another block.
- * GSR_BIN_RADIX: one stable onesweep LSD radix sort of all (tile, depth)
- *   keys, 8 bits per pass, with a bounded decoupled look-back. */
+ * GSR_BIN_TILE: the preprocess emits each pair's (tile, depth, index) keys
+ *   (one slot reservation per warp); with up to 32,768 tiles a count kernel
+ *   counts them per tile (shared-memory counts per block, one atomic per
+ *   block and tile, the last block scans the counts into the ranges) and a
+ *   scatter kernel groups them by tile; beyond, onesweep passes over the tile
+ *   bits group them; then each tile's (depth, index) words are sorted in
+ *   registers or shared memory.
+ * GSR_BIN_RADIX: a scan of the per-pair tile counts and a duplication kernel
+ *   emit the keys, then one stable onesweep LSD radix sort of all (tile,
+ *   depth) keys, 8 bits per pass, with a bounded decoupled look-back. */
 #define GSR_BIN_TILE 0
 #define GSR_BIN_RADIX 1
 
@@ -145,10 +154,11 @@ typedef struct {
     /* Densification statistics of the batch (adaptive density control of
      * 3DGS, used by the paper's mapper), [N] each, all NULL or all set.  A
      * Gaussian is visible in a view when it is not culled and its cutoff
-     * ellipse (d^2 <= min(9, 2 ln(255 sigma))) contains a pixel centre
-     * (decided with the tile coverage's conservative inflation of at most
-     * 0.2 % + 0.02 in d^2).  With accumulate != 0, grad and count add and
-     * radius takes the maximum, so the arrays can gather several batches. */
+     * ellipse (d^2 <= min(9, 2 ln(255 sigma))) meets the rectangle
+     * [0, W-1] x [0, H-1] spanned by the pixel centres (decided in FP32 from
+     * the exact minimum of d^2 over that rectangle).  With accumulate != 0,
+     * grad and count add and radius takes the maximum, so the arrays can
+     * gather several batches. */
     float *densify_grad;      /* sum over visible views of |(dL/du, dL/dv)|, pixels */
     float *densify_count;     /* number of visible views */
     float *densify_radius;    /* max over visible views of 3 sqrt(lambda_max(Sigma')), pixels */
@@ -172,7 +182,7 @@ typedef struct {
 } gsr_l1_view;
 
 /* Creates a context (host memory only).  cfg may be NULL for defaults.
- * Returns GSR_EINVAL for an unsupported tile size. */
+ * Returns GSR_EINVAL for an unsupported tile size, binning or batch. */
 gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out);
 
 /* Frees a context.  NULL is ignored. */
@@ -212,6 +222,49 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
  * and render again) or GSR_ETIMEOUT. */
 gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info *info,
                          gsr_stream stream);
+
+/* The device status word of ws alone: waits for stream and returns the first
+ * device error that the calls on ws recorded (GSR_ECAPACITY, GSR_ETIMEOUT,
+ * GSR_EINTERNAL), or GSR_OK; the same value as gsr_read_info's info.status.
+ * Its own failures are GSR_EINVAL (bad arguments) and GSR_ECUDA, with a
+ * message in gsr_last_error. */
+gsr_status gsr_get_status(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_stream stream);
+
+/* One configuration timed by gsr_autotune. */
+typedef struct {
+    int tile, binning, batch;   /* the candidate (see gsr_config) */
+    float ms;                   /* best of reps forward + backward times (CUDA events), or -1 */
+    int32_t status;             /* GSR_OK, or why it was not timed (GSR_ECAPACITY: its keys
+                                   exceed the workspace; a synchronous error code) */
+} gsr_tune_entry;
+
+/* Autotuner of the batched render (the paper's mapper renders a batch of
+ * keyframes every iteration, Supp. Sec. 1.2; tile size and per-warp entry
+ * batch trade sort work against blend work differently for every scene and
+ * set of views).  Times forward + backward on the caller's own Gaussians,
+ * views and workspace for every candidate (tile 8, 16, 32) x (GSR_BIN_TILE,
+ * GSR_BIN_RADIX) x (batch 32, 64; 64 not at tile 32), best of reps (1..100)
+ * after one warm-up run, the rendered colour serving as the upstream
+ * gradient, and leaves the fastest configuration in ctx (ties: the earlier
+ * candidate in that order).  The candidates' results are identical images;
+ * only their speed differs.
+ * - views' color/depth/alpha receive renders and grads (all arrays, pose
+ *   outputs not used) receives gradients: pass scratch buffers.
+ * - ws must be large enough for the candidate with the most keys (tile 8):
+ *   a candidate whose keys do not fit is skipped with status GSR_ECAPACITY.
+ *   After tuning, size workspaces again with gsr_workspace_size: the tile
+ *   size changes the layout.
+ * - entries (host, may be NULL when max_entries is 0) receives up to
+ *   max_entries candidates in the order above, *n_entries (may be NULL)
+ *   their number.
+ * - It synchronises the stream after every run (it reads the device status
+ *   and the event times), so it cannot be captured in a CUDA graph.
+ * Returns GSR_OK when at least one candidate ran; otherwise the first
+ * candidate's failure (the context keeps its configuration).  A context
+ * created with test flags is rejected (GSR_EINVAL). */
+gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V,
+                        const gsr_grads *grads, void *ws, size_t ws_bytes, int reps,
+                        gsr_tune_entry *entries, int max_entries, int *n_entries, gsr_stream stream);
 
 /* L1 loss front end (the L1 terms of Eq. "rnd_loss"): for each view,
  * loss += color_weight * mean|C - C*| + depth_weight * mean|D - D*| over its
@@ -306,7 +359,9 @@ gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events);
  * that must not allocate).  It renders exactly as gsr_render, but its scratch
  * is a static device array of GSR_NOALLOC_SCRATCH_BYTES inside the library,
  * held on every device that loads the library until the process exits.  No
- * device memory is allocated by the call.
+ * device memory is allocated by the call.  Each build of the library
+ * (libgsr.so, libgsr_checked.so) holds its own array; a process that loads
+ * both holds both, and the builds never share one.
  * - Scenes whose smallest workspace (gsr_workspace_size with key_capacity 1)
  *   exceeds GSR_NOALLOC_SCRATCH_BYTES are rejected with GSR_EINVAL.  The key
  *   capacity is whatever fits in the rest of the array.
@@ -399,7 +454,7 @@ int gsr_abi_version(void);
 /* sizeof of the ABI structs, for binding checks: 0 gsr_config, 1
  * gsr_gaussians, 2 gsr_view, 3 gsr_view_grad, 4 gsr_grads, 5 gsr_info,
  * 6 gsr_l1_view, 7 gsr_surfel_out, 8 gsr_surfel_grad, 9 gsr_adc_params,
- * 10 gsr_gaussians_out; 0 for other values. */
+ * 10 gsr_gaussians_out, 11 gsr_tune_entry; 0 for other values. */
 size_t gsr_abi_sizeof(int which);
 
 #ifdef __cplusplus

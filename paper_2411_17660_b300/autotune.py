@@ -1,47 +1,43 @@
-"""Autotuner of the batched rasteriser's tile size and binning strategy.
+"""Autotuner of the batched rasteriser: tile size, binning strategy and the
+blends' per-warp entry batch.
 
 The screen tile (8, 16 or 32 pixels) sets how many (Gaussian, tile) keys the
 sort handles and how many warps share a tile's depth-sorted list; the binning
-strategy ("tile": radix passes over the tile bits and a sort inside each
-tile; "radix": radix passes over tile and depth bits) trades fewer global
-passes against per-tile sorts that grow with the keys per tile.  Which pair
-is fastest depends on the scene (Gaussian footprints) and the views.  The
-tuner times one forward + backward per candidate on the caller's own inputs
-(CUDA events on the current stream, after warm-up) and keeps the fastest,
-cached per (GPU, N, SH degree, view sizes).  The images do not depend on
-either choice, so it changes only speed.
-
-The per-warp entry batch of the blend kernels is the warp width (32 entries
-per chunk, one per lane) and is not a tuning parameter.
+strategy ("tile": grouping by tile and a sort inside each tile; "radix":
+radix passes over tile and depth bits) trades fewer global passes against
+per-tile sorts that grow with the keys per tile; the batch (32 or 64 list
+entries staged per warp and round in both blends) trades staging rounds and
+loads in flight against entries staged past a warp's transmittance stop.
+Which combination is fastest depends on the scene (Gaussian footprints) and
+the views.  The timing runs in the library (gsr_autotune): forward +
+backward per candidate on the caller's own inputs, CUDA events on the
+stream, best of a few after a warm-up run.  This module sizes the workspace
+for the candidate with the most keys and caches the choice per (GPU, N, SH
+degree, view sizes) in an optional JSON file.  The images do not depend on
+any of the three choices, so tuning changes only speed.
 """
 from __future__ import annotations
 
 import json
 import os
-from typing import Callable, Dict, Iterable, Optional, Sequence
+from typing import Dict, Optional, Sequence
 
 TILES = (8, 16, 32)
 BINNINGS = ("tile", "radix")
-CANDIDATES = tuple(f"{t}/{b}" for t in TILES for b in BINNINGS)   # "tile size/binning"
+BATCHES = (32, 64)
+# "tile size/binning/batch", in the order the library times them (64 is not offered at tile 32)
+CANDIDATES = tuple(f"{t}/{b}/{k}" for t in TILES for b in BINNINGS for k in BATCHES if not (t == 32 and k == 64))
 
 
 def parse(candidate: str):
-    """("16/tile") -> (16, "tile")."""
-    t, b = candidate.split("/")
-    return int(t), b
+    """("16/tile/32") -> (16, "tile", 32)."""
+    t, b, k = candidate.split("/")
+    return int(t), b, int(k)
 
 
 def signature(gpu: str, N: int, sh_degree: int, cams: Sequence) -> str:
     views = ",".join(f"{c.W}x{c.H}" for c in cams)
     return f"{gpu}|N={N}|deg={sh_degree}|views={views}"
-
-
-def choose(time_ms: Callable[[object], float], candidates: Iterable = CANDIDATES) -> Dict[str, object]:
-    """Times every candidate once with time_ms(candidate) and returns the
-    fastest (ties go to the earlier candidate) with all timings."""
-    times = {c: float(time_ms(c)) for c in candidates}
-    best = min(times, key=lambda c: (times[c], list(times).index(c)))
-    return {"best": best, "ms": times}
 
 
 class TileCache:
@@ -66,49 +62,44 @@ class TileCache:
             os.replace(tmp, self.path)
 
 
-def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = None, reps: int = 3,
-         warmup: int = 2, candidates: Iterable[str] = CANDIDATES) -> Dict[str, object]:
-    """Times forward + backward (upstream gradient of ones on the colour) for
-    each "tile size/binning" candidate on these inputs and returns
-    {"tile": size, "binning": strategy, "ms": {candidate: ms}}."""
+def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = None,
+         reps: int = 3) -> Dict[str, object]:
+    """Times every candidate with gsr_autotune on these inputs and returns
+    {"tile": size, "binning": strategy, "batch": entries, "ms": {candidate: ms
+    or None when it could not run}}."""
     import torch
 
+    from . import binding as B
     from . import render as R
 
     gpu = torch.cuda.get_device_name()
-    key = signature(gpu, int(params["means"].shape[1]), sh_degree, cams)
+    N = int(params["means"].shape[1])
+    key = signature(gpu, N, sh_degree, cams)
     if cache is not None and cache.get(key) is not None:
         return cache.get(key)
+    dev = params["means"].device
+    # a workspace with room for the keys of the smallest tile (the most keys)
+    sizing = R.GaussianRasterizer(8)
+    _, _, _, ws = sizing.render_forward(params, sh_degree, cams, viewmats)
+    keys = sizing.info(ws).keys
+    del ws
+    rast = R.GaussianRasterizer(8)
+    ws = rast.alloc_workspace(N, cams, int(keys * 1.1) + 8192, dev)
     P = R.pixel_offsets(cams)[-1]
-    d_color = torch.ones(3 * P, device=params["means"].device)
+    color, depth, alpha = (torch.empty(3 * P, device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
     grads = {k: torch.empty_like(v) for k, v in params.items()}
-    d_pose = torch.empty(len(cams), 6, device=params["means"].device)
-
-    def time_ms(candidate: str) -> float:
-        tile, binning = parse(candidate)
-        rast = R.GaussianRasterizer(tile, binning=binning)
-        color, depth, alpha, ws = rast.render_forward(params, sh_degree, cams, viewmats)
-        ws = rast.alloc_workspace(int(params["means"].shape[1]), cams, int(rast.info(ws).keys * 1.1) + 8192)
-
-        def step():
-            rast.forward_raw(params, sh_degree, cams, viewmats, ws, color, depth, alpha)
-            rast.backward_raw(params, sh_degree, cams, viewmats, ws, d_color, None, None, grads, d_pose)
-
-        for _ in range(warmup):
-            step()
-        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        best = float("inf")
-        for _ in range(reps):
-            start.record()
-            step()
-            end.record()
-            end.synchronize()
-            best = min(best, start.elapsed_time(end))
-        return best
-
-    chosen = choose(time_ms, candidates)
-    tile, binning = parse(chosen["best"])
-    result = {"tile": tile, "binning": binning, "ms": chosen["ms"]}
+    g = R.gaussians_struct(*[params[k] for k in R.PARAM_NAMES], sh_degree)
+    views = R.view_structs(cams, viewmats, color, depth, alpha)
+    out = B.Grads(*[grads[k].data_ptr() for k in R.PARAM_NAMES], 0, 0, 0, 0)
+    st, entries = rast.ctx.autotune(g, views, out, ws.data_ptr(), ws.numel(), reps,
+                                    torch.cuda.current_stream().cuda_stream)
+    rast.ctx.check(st, "gsr_autotune")
+    name = {B.BIN_TILE: "tile", B.BIN_RADIX: "radix"}
+    times = {f"{e.tile}/{name[e.binning]}/{e.batch}": (float(e.ms) if e.status == B.OK else None) for e in entries}
+    ran = {c: t for c, t in times.items() if t is not None}
+    best = min(ran, key=lambda c: (ran[c], list(times).index(c)))
+    tile, binning, batch = parse(best)
+    result = {"tile": tile, "binning": binning, "batch": batch, "ms": times}
     if cache is not None:
         cache.put(key, result)
     return result

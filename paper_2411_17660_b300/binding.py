@@ -17,7 +17,7 @@ LIB_PATH = os.environ.get("GSR_LIBRARY") or os.path.join(_PKG, "_build", "libgsr
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
-ABI_VERSION = 5   # GSR_ABI_VERSION these structs follow
+ABI_VERSION = 6   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
@@ -33,7 +33,7 @@ _p = ctypes.c_void_p
 
 class Config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("flags", ctypes.c_int),
-                ("binning", ctypes.c_int)]
+                ("binning", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class Gaussians(ctypes.Structure):
@@ -83,8 +83,13 @@ class GaussiansOut(ctypes.Structure):
                 ("sh", _p)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("binning", ctypes.c_int), ("batch", ctypes.c_int), ("ms", ctypes.c_float),
+                ("status", ctypes.c_int32)]
+
+
 ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View, SurfelOut, SurfelGrad, AdcParams,
-               GaussiansOut]
+               GaussiansOut, TuneEntry]
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -119,6 +124,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gsr_render_backward": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View),
                                          ctypes.POINTER(ViewGrad), c_int, ctypes.POINTER(Grads), _p, c_size, _p]),
         "gsr_read_info": (c_int, [_p, _p, c_size, ctypes.POINTER(Info), _p]),
+        "gsr_get_status": (c_int, [_p, _p, c_size, _p]),
+        "gsr_autotune": (c_int, [_p, ctypes.POINTER(Gaussians), ctypes.POINTER(View), c_int, ctypes.POINTER(Grads),
+                                 _p, c_size, c_int, ctypes.POINTER(TuneEntry), c_int, ctypes.POINTER(c_int), _p]),
         "gsr_l1_loss": (c_int, [_p, ctypes.POINTER(View), ctypes.POINTER(L1View), c_int, ctypes.c_float,
                                 ctypes.c_float, _p, _p]),
         "gsr_set_stage_events": (c_int, [_p, ctypes.POINTER(_p)]),
@@ -155,13 +163,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 class Context:
     """Owns one gsr_ctx (host memory only)."""
 
-    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: int = BIN_TILE):
+    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: int = BIN_TILE,
+                 batch: int = 32):
         self.lib = load()
-        cfg = Config(tile, spin_limit, flags, binning)
+        cfg = Config(tile, spin_limit, flags, binning, batch)
         h = _p()
         st = self.lib.gsr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:
-            raise GsrError(st, f"gsr_create(tile={tile})")
+            raise GsrError(st, f"gsr_create(tile={tile}, binning={binning}, batch={batch})")
         self.h = h
         self.tile = tile
 
@@ -218,6 +227,19 @@ class Context:
         status_ptr: device int32 receiving the device-side status, or 0."""
         arr = (View * len(views))(*views)
         return self.lib.gsr_render_noalloc(self.h, ctypes.byref(g), arr, len(views), status_ptr or None, stream)
+
+    def get_status(self, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+        """gsr_get_status: the workspace's device status (after the stream)."""
+        return self.lib.gsr_get_status(self.h, ws_ptr, ws_bytes, stream)
+
+    def autotune(self, g: Gaussians, views, grads: Grads, ws_ptr: int, ws_bytes: int, reps: int, stream: int):
+        """gsr_autotune; returns (status, [TuneEntry])."""
+        arr = (View * len(views))(*views)
+        entries = (TuneEntry * 16)()
+        n = ctypes.c_int(0)
+        st = self.lib.gsr_autotune(self.h, ctypes.byref(g), arr, len(views), ctypes.byref(grads), ws_ptr, ws_bytes,
+                                   reps, entries, 16, ctypes.byref(n), stream)
+        return st, list(entries[:n.value])
 
     def read_info(self, ws_ptr: int, ws_bytes: int, stream: int) -> Info:
         info = Info()

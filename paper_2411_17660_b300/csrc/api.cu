@@ -19,12 +19,14 @@ struct gsr_ctx {
     uint32_t spin = gsr::kDefaultSpin;
     int flags = 0;
     int binning = GSR_BIN_TILE;
+    int batch = 32;   // list entries a blend warp stages per round (32 or 64)
     int sm_count = 0;
     std::string err;
     struct Rec {
         const void *ws;
         size_t bytes;
         int N, V, deg;
+        int tile, binning;   // the configuration that rendered it (gsr_autotune changes the context's)
         std::vector<int> dims;
         bool median;   // the forward recorded the median-depth contributors
         bool surfels;  // the forward rendered surfels
@@ -287,10 +289,11 @@ bool want_median(const gsr_view *views, int V) {
     return false;
 }
 
-void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile) {
+void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile, int batch = 32) {
     memset(&vt, 0, sizeof vt);
     vt.V = V;
     vt.tile = tile;
+    vt.batch = batch;
     uint32_t toff = 0, poff = 0;
     for (int v = 0; v < V; ++v) {
         ViewParams &p = vt.v[v];
@@ -330,7 +333,7 @@ void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads
 // Gaussians and views (and of the same kind).
 void remember_forward(gsr_ctx *ctx, const void *ws_ptr, size_t ws_bytes, const gsr_gaussians *gs,
                       const gsr_view *views, int V, bool median, bool surfels) {
-    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, {}, median, surfels};
+    gsr_ctx::Rec r{ws_ptr, ws_bytes, gs->N, V, gs->sh_degree, ctx->tile, ctx->binning, {}, median, surfels};
     for (int v = 0; v < V; ++v) {
         r.dims.push_back(views[v].H);
         r.dims.push_back(views[v].W);
@@ -349,7 +352,8 @@ const gsr_ctx::Rec *find_forward(gsr_ctx *ctx, const void *ws_ptr, size_t ws_byt
     const gsr_ctx::Rec *rec = nullptr;
     for (const auto &r : ctx->recs)
         if (r.ws == ws_ptr) rec = &r;
-    bool match = rec && rec->bytes == ws_bytes && rec->N == gs->N && rec->V == V && rec->deg == gs->sh_degree;
+    bool match = rec && rec->bytes == ws_bytes && rec->N == gs->N && rec->V == V && rec->deg == gs->sh_degree &&
+                 rec->tile == ctx->tile && rec->binning == ctx->binning;
     for (int v = 0; match && v < V; ++v)
         match = rec->dims[2 * v] == views[v].H && rec->dims[2 * v + 1] == views[v].W;
     return match ? rec : nullptr;
@@ -381,9 +385,11 @@ extern "C" {
 gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     if (!out) return GSR_EINVAL;
     *out = nullptr;
-    int tile = 16, flags = 0, binning = GSR_BIN_TILE;
+    int tile = 16, flags = 0, binning = GSR_BIN_TILE, batch = 32;
     uint32_t spin = kDefaultSpin;
     if (cfg) {
+        if (cfg->batch != 0 && cfg->batch != 32 && cfg->batch != 64) return GSR_EINVAL;
+        if (cfg->batch != 0) batch = cfg->batch;
         if (cfg->tile != 0) tile = cfg->tile;
         if (cfg->spin_limit != 0) spin = cfg->spin_limit;
         if (cfg->flags & ~GSR_TEST_STALL_SORT) return GSR_EINVAL;
@@ -392,12 +398,14 @@ gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
         binning = cfg->binning;
     }
     if (tile != 8 && tile != 16 && tile != 32) return GSR_EINVAL;
+    if (tile == 32 && batch == 64) return GSR_EINVAL;   // the blends' staging would exceed 48 KB of shared memory
     gsr_ctx *c = new (std::nothrow) gsr_ctx;
     if (!c) return GSR_EINVAL;
     c->tile = tile;
     c->spin = spin;
     c->flags = flags;
     c->binning = binning;
+    c->batch = batch;
     *out = c;
     return GSR_OK;
 }
@@ -446,7 +454,7 @@ gsr_status render_impl(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vi
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
     if (l1) {
         for (int v = 0; v < V; ++v) {
             vt.v[v].l1_target_color = l1->targets[v].target_color;
@@ -529,7 +537,7 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, grads, V, ctx->tile);
+    fill_views(vt, views, grads, V, ctx->tile, ctx->batch);
     const Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     GradPtrs gout;
@@ -573,7 +581,7 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
     if (extra)
         for (int v = 0; v < V; ++v) {
             vt.v[v].normal = extra[v].normal;
@@ -631,7 +639,7 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, grads, V, ctx->tile);
+    fill_views(vt, views, grads, V, ctx->tile, ctx->batch);
     if (extra)
         for (int v = 0; v < V; ++v) {
             vt.v[v].d_normal = extra[v].d_normal;
@@ -682,6 +690,103 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
     return GSR_OK;
 }
 
+gsr_status gsr_get_status(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_stream stream) {
+    gsr_info info;
+    const gsr_status s = gsr_read_info(ctx, ws, ws_bytes, &info, stream);
+    return s != GSR_OK ? s : static_cast<gsr_status>(info.status);
+}
+
+namespace {
+
+// Forward + backward of one tuning candidate on the caller's buffers: the
+// rendered colour serves as its own upstream gradient.
+gsr_status tune_step(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, const gsr_grads *grads,
+                     void *ws, size_t ws_bytes, gsr_stream stream) {
+    gsr_view_grad vg[GSR_MAX_VIEWS];
+    for (int v = 0; v < V; ++v) vg[v] = gsr_view_grad{views[v].color, nullptr, nullptr, nullptr, nullptr};
+    gsr_status s = gsr_render(ctx, gs, views, V, ws, ws_bytes, stream);
+    if (s != GSR_OK) return s;
+    return gsr_render_backward(ctx, gs, views, vg, V, grads, ws, ws_bytes, stream);
+}
+
+}  // namespace
+
+gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *views, int V, const gsr_grads *grads,
+                        void *ws, size_t ws_bytes, int reps, gsr_tune_entry *entries, int max_entries,
+                        int *n_entries, gsr_stream stream) {
+    if (!ctx) return GSR_EINVAL;
+    if (!grads || (max_entries > 0 && !entries) || max_entries < 0 || reps < 1 || reps > 100)
+        return fail(ctx, GSR_EINVAL, "gsr_autotune: grads must be non-NULL, 1 <= reps <= 100, entries for max_entries");
+    gsr_status s = check_views(ctx, views, V, true);
+    if (s != GSR_OK) return s;
+    if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
+    if (ctx->flags) return fail(ctx, GSR_EINVAL, "gsr_autotune: a context with test flags cannot be tuned");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int tile0 = ctx->tile, binning0 = ctx->binning, batch0 = ctx->batch;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ctx, e, "gsr_autotune: event");
+    }
+    static const int kTiles[] = {8, 16, 32}, kBinnings[] = {GSR_BIN_TILE, GSR_BIN_RADIX}, kBatches[] = {32, 64};
+    int n = 0, best = -1;
+    float best_ms = 0.f;
+    int best_cfg[3] = {tile0, binning0, batch0};
+    gsr_status first_fail = GSR_OK, hard = GSR_OK;
+    for (int tile : kTiles)
+        for (int binning : kBinnings)
+            for (int batch : kBatches) {
+                if (hard != GSR_OK || (tile == 32 && batch == 64)) continue;   // 32/64: not supported (shared memory)
+                ctx->tile = tile;
+                ctx->binning = binning;
+                ctx->batch = batch;
+                gsr_tune_entry r{tile, binning, batch, -1.f, GSR_OK};
+                // the warm-up run also tells whether the keys fit this workspace
+                gsr_status cs = tune_step(ctx, gs, views, V, grads, ws, ws_bytes, stream);
+                gsr_info info{};
+                if (cs == GSR_OK) cs = gsr_read_info(ctx, ws, ws_bytes, &info, stream);
+                if (cs == GSR_OK) cs = static_cast<gsr_status>(info.status);
+                for (int k = 0; cs == GSR_OK && k < reps; ++k) {
+                    float ms = 0.f;
+                    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { cs = cuda_fail(ctx, e, "gsr_autotune: record"); break; }
+                    cs = tune_step(ctx, gs, views, V, grads, ws, ws_bytes, stream);
+                    if (cs != GSR_OK) break;
+                    if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                        (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+                        cs = cuda_fail(ctx, e, "gsr_autotune: timing");
+                        break;
+                    }
+                    r.ms = k == 0 ? ms : std::min(r.ms, ms);
+                }
+                r.status = cs;
+                if (cs != GSR_OK) {
+                    r.ms = -1.f;
+                    if (first_fail == GSR_OK) first_fail = cs;
+                    if (cs == GSR_ECUDA) hard = cs;
+                } else if (best < 0 || r.ms < best_ms) {
+                    best = n;
+                    best_ms = r.ms;
+                    best_cfg[0] = tile;
+                    best_cfg[1] = binning;
+                    best_cfg[2] = batch;
+                }
+                if (n < max_entries) entries[n] = r;
+                ++n;
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_entries) *n_entries = std::min(n, max_entries);
+    ctx->tile = best_cfg[0];
+    ctx->binning = best_cfg[1];
+    ctx->batch = best_cfg[2];
+    if (hard != GSR_OK) return hard;
+    if (best < 0) return fail(ctx, first_fail, "gsr_autotune: no candidate ran (%s); grow the workspace",
+                              gsr_status_string(first_fail));
+    return GSR_OK;
+}
+
 gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *targets, int V, float color_weight,
                        float depth_weight, float *loss, gsr_stream stream) {
     if (!ctx) return GSR_EINVAL;
@@ -692,7 +797,7 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
         if (!targets[v].target_color || !targets[v].d_color)
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
     CallTrace tr("gsr_l1_loss");
     cudaError_t e = launch_l1_loss(vt, targets, color_weight, depth_weight, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "l1 loss");
@@ -711,7 +816,7 @@ gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view 
         if (!targets[v].target_color || !targets[v].d_color)
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
     CallTrace tr("gsr_rgbd_loss");
     cudaError_t e = launch_rgbd_loss(vt, targets, lambda1, lambda2, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rgbd loss");
@@ -835,6 +940,7 @@ size_t gsr_abi_sizeof(int which) {
         case 8: return sizeof(gsr_surfel_grad);
         case 9: return sizeof(gsr_adc_params);
         case 10: return sizeof(gsr_gaussians_out);
+        case 11: return sizeof(gsr_tune_entry);
     }
     return 0;
 }

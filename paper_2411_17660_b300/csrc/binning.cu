@@ -1,22 +1,24 @@
 // binning.cu -- tile binning of the projected Gaussians: every (view,
 // Gaussian) pair becomes one key per screen tile it touches, the keys are put
 // in (global tile, FP32 depth, Gaussian id) order, and every tile gets its
-// [start, end) range of the sorted list.  An exclusive scan of the per-pair
-// tile counts places each pair's keys; then one of two strategies, with the
-// same result:
+// [start, end) range of the sorted list.  Two strategies, with the same
+// result:
 //
-// radix: keys (tile << 32 | depth bits) with the Gaussian id as value, one
-//   stable hand-written onesweep LSD radix sort over all used bits (8 per
-//   pass; equal depths keep the pair order, i.e. the id order), and a boundary
-//   pass for the ranges.
-// per-tile (default): u32 tile keys with (depth bits << 32 | id) words as
-//   values, grouped by tile, after which each tile's words -- unique, since a
-//   Gaussian meets a tile once -- are sorted in registers (a warp) or shared
-//   memory (a block), which orders them by depth and then id.  Grouping: with
-//   up to 65,536 tiles the preprocess counts the keys of every tile as it
-//   emits them, one block scans the counts into the ranges, and each key
-//   takes the next slot of its tile (bucket_binning); beyond, the onesweep
-//   sort runs over the tile bits only and the boundary pass gives the ranges.
+// radix: an exclusive scan of the per-pair tile counts places each pair's
+//   keys, a duplication kernel emits them as (tile << 32 | depth bits) with
+//   the Gaussian id as value, one stable hand-written onesweep LSD radix sort
+//   runs over all used bits (8 per pass; equal depths keep the pair order,
+//   i.e. the id order), and a boundary pass gives the ranges.
+// per-tile (default): the preprocess emits u32 tile keys with (depth bits <<
+//   32 | id) words as values, grouped here by tile, after which each tile's
+//   words -- unique, since a Gaussian meets a tile once -- are sorted in
+//   registers (a warp) or shared memory (a block), which orders them by depth
+//   and then id.  Grouping: with up to 32,768 tiles a count kernel counts
+//   each block's slice of the keys per tile in shared memory and adds them
+//   with one atomic per (block, tile), its last block scans the counts into
+//   the ranges, and a scatter kernel places each key in its tile's slots
+//   (bucket_binning); beyond, the onesweep sort runs over the tile bits only
+//   and the boundary pass gives the ranges.
 //
 // All sizes the host cannot know (the key count) are read on the device, so
 // either sequence needs no host sync and can be captured in a CUDA graph.

@@ -101,6 +101,10 @@ struct BwdBlock {
 template <int TS>
 struct FwdBlock {
     static constexpr int H = kSubH;
+    // 36 resident warps (56 registers): the measured register need of the
+    // kernel; the compiler's own choice of 58 would round to 64 and leave 32
+    static constexpr int MIN_BLOCKS =
+        1152 / BlendShape<TS, H>::THREADS < 32 ? 1152 / BlendShape<TS, H>::THREADS : 32;
 };
 
 // Whether min over the warp's block of pixel centres of s can reach s_max.
@@ -204,31 +208,47 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     return w;
 }
 
-// Loads entry idx of the tile list (lane-parallel), tests it against the
-// warp's block of BH rows and compacts the survivors into the warp's slots in
-// list order; Stage writes one survivor's slot.  Returns the number of
-// survivors.
-template <int BH, typename Stage>
-__device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, size_t vN, uint32_t idx, uint32_t end,
+// Loads entries [base, base + 32 CH) of the tile list (lane-parallel: entry
+// base + 32 k + lane on each lane, k < CH), tests each against the warp's
+// block of BH rows and compacts the survivors into the warp's slots in list
+// order; Stage writes one survivor's slot.  Returns the number of survivors.
+// CH = 2 (the 64-entry batch) halves the staging rounds (and the warp's
+// done tests between them), at the price of staging up to 64 entries past a
+// warp's transmittance stop.
+template <int BH, int CH, typename Stage>
+__device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, size_t vN, uint32_t base, uint32_t end,
                                            int X0, int Y0, Stage &&write) {
-    bool keep = false;
-    float4 r0, r1;
-    float ur = 0.f, vr = 0.f;
-    size_t gi = 0;
-    const uint32_t g = idx < end ? vals[idx] : 0xffffffffu;
-    if (idx < end) (void)GSR_CHECK(ws.hdr, g < ws.N);   // a listed id >= N: only after another error
-    if (g < ws.N) {
-        gi = vN + g;
-        r0 = ws.rec0[gi];
-        r1 = ws.rec1[gi];
-        ur = __fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z);
-        vr = __fadd_rn(__fsub_rn(r0.y, (float)Y0), r0.w);
-        keep = touches_block<BH>(ur, vr, r1.x, r1.y, r1.z, r1.w);
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t g[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        const uint32_t idx = base + 32u * k + lane;
+        g[k] = idx < end ? vals[idx] : 0xffffffffu;
+        if (idx < end) (void)GSR_CHECK(ws.hdr, g[k] < ws.N);   // a listed id >= N: only after another error
     }
-    const unsigned ballot = __ballot_sync(kFull, keep);
-    if (keep) write(__popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, idx, g);
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        bool keep = false;
+        float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ur = 0.f, vr = 0.f;
+        if (g[k] < ws.N) {
+            const float4 r0 = ws.rec0[vN + g[k]];
+            r1 = ws.rec1[vN + g[k]];
+            ur = __fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z);
+            vr = __fadd_rn(__fsub_rn(r0.y, (float)Y0), r0.w);
+            keep = touches_block<BH>(ur, vr, r1.x, r1.y, r1.z, r1.w);
+        }
+        const unsigned ballot = __ballot_sync(kFull, keep);
+        if (keep) {
+            const size_t gi = vN + g[k];
+            write(n + __popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, base + 32u * k + lane,
+                  g[k]);
+        }
+        n += __popc(ballot);
+    }
     __syncwarp();
-    return __popc(ballot);
+    return n;
 }
 
 // MED: also record, per pixel, the median-depth contributor (the last one
@@ -243,16 +263,16 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 // The staged entries hold the operands that both pixels use as duplicated
 // pairs (as in the backward), so one 128-bit shared load yields two ready
 // register pairs.
-template <int TS, bool MED, bool L1>
-__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
+template <int TS, int CH, bool MED, bool L1>
+__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdBlock<TS>::MIN_BLOCKS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
     constexpr int BH = FwdBlock<TS>::H, NR = BH / kRowStep;
     static_assert(NR == 2, "a lane composites one pair of rows");
     using S = BlendShape<TS, BH>;
     // per slot: (-ur, -ur, -vr, -vr), (m00, m00, m01, m01), (m11, m11, l, l),
     // (r, r, g, g), (b, b, z, z); sX: (s_max, list index)
-    __shared__ float4 sF[S::WARPS][kEntryQuads][32];
-    __shared__ float2 sX[S::WARPS][32];
+    __shared__ float4 sF[S::WARPS][kEntryQuads][32 * CH];
+    __shared__ float2 sX[S::WARPS][32 * CH];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
@@ -271,12 +291,12 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS) blen
                              wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + (float)kRowStep : kInf);
     float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0, D = C0, Zm = C0;
     uint32_t last[NR] = {0u, 0u}, mi[NR] = {0u, 0u}, ncon = 0;
-    for (uint32_t base = wt.range.x; base < wt.range.y; base += 32) {
+    for (uint32_t base = wt.range.x; base < wt.range.y; base += 32 * CH) {
         if (__all_sync(kFull, ly2.x == kInf && ly2.y == kInf)) break;
-        const int n = stage_chunk<BH>(ws, vals, vN, base + lane, wt.range.y, wt.X0, wt.Y0,
+        const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t) {
-                                          float4(&e)[kEntryQuads][32] = sF[warp];
+                                          float4(&e)[kEntryQuads][32 * CH] = sF[warp];
                                           e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
                                           e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
                                           e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
@@ -434,14 +454,14 @@ __device__ __forceinline__ void pair_sums(float2 (&A)[kVGGrads], float2 dp1, flo
 // MED: dL/d(median depth) goes to the z of each pixel's median contributor.
 // A lane owns NR = BH / 4 pixel rows of its column; rows 2p and 2p + 1 (y + 8p
 // and y + 8p + 4) form pair p, whose arithmetic runs on packed FP32 pairs.
-template <int TS, bool MED>
+template <int TS, int CH, bool MED>
 __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdBlock<TS>::MIN_BLOCKS)
     blend_bwd_kernel(const __grid_constant__ ViewTable vt, const Ws ws) {
     constexpr int BH = BwdBlock<TS>::H;
     constexpr int NR = BH / kRowStep, NP = NR / 2;
     using S = BlendShape<TS, BH>;
-    __shared__ float4 sE[S::WARPS][kEntryQuads][32];
-    __shared__ float4 sX[S::WARPS][32];  // (s_max, list index, Gaussian index, -)
+    __shared__ float4 sE[S::WARPS][kEntryQuads][32 * CH];
+    __shared__ float4 sX[S::WARPS][32 * CH];  // (s_max, list index, Gaussian index, -)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
@@ -494,11 +514,11 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     const size_t row = (size_t)ws.V * kVGGrads;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
-        const uint32_t begin = end - wt.range.x > 32u ? end - 32u : wt.range.x;
-        const int n = stage_chunk<BH>(ws, vals, vN, begin + lane, end, wt.X0, wt.Y0,
+        const uint32_t begin = end - wt.range.x > 32u * CH ? end - 32u * CH : wt.range.x;
+        const int n = stage_chunk<BH, CH>(ws, vals, vN, begin, end, wt.X0, wt.Y0,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t g) {
-                                          float4(&e)[kEntryQuads][32] = sE[warp];
+                                          float4(&e)[kEntryQuads][32 * CH] = sE[warp];
                                           e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
                                           e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
                                           e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
@@ -658,31 +678,32 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     }
 }
 
-template <int TS>
+template <int TS, int CH>
 cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
     constexpr int T = BlendShape<TS, FwdBlock<TS>::H>::THREADS;
     const bool l1 = vt.l1_loss != nullptr;
     if (med && l1)
-        blend_fwd_kernel<TS, true, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     else if (med)
-        blend_fwd_kernel<TS, true, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     else if (l1)
-        blend_fwd_kernel<TS, false, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, false, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
-template <int TS>
+template <int TS, int CH>
 cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].d_median_depth != nullptr;
+    constexpr int T = BlendShape<TS, BwdBlock<TS>::H>::THREADS;
     if (med)
-        blend_bwd_kernel<TS, true><<<vt.total_tiles, BlendShape<TS, BwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, CH, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     else
-        blend_bwd_kernel<TS, false><<<vt.total_tiles, BlendShape<TS, BwdBlock<TS>::H>::THREADS, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, CH, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
@@ -691,18 +712,19 @@ cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
 cudaError_t launch_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     if (vt.total_tiles == 0) return cudaSuccess;
     switch (vt.tile) {
-        case 8: return launch_fwd_t<8>(vt, ws, st);
-        case 32: return launch_fwd_t<32>(vt, ws, st);
-        default: return launch_fwd_t<16>(vt, ws, st);
+        // the 64-entry batch at tile 32 would need more than 48 KB of static shared memory
+        case 8: return vt.batch == 64 ? launch_fwd_t<8, 2>(vt, ws, st) : launch_fwd_t<8, 1>(vt, ws, st);
+        case 32: return launch_fwd_t<32, 1>(vt, ws, st);
+        default: return vt.batch == 64 ? launch_fwd_t<16, 2>(vt, ws, st) : launch_fwd_t<16, 1>(vt, ws, st);
     }
 }
 
 cudaError_t launch_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     if (vt.total_tiles == 0) return cudaSuccess;
     switch (vt.tile) {
-        case 8: return launch_bwd_t<8>(vt, ws, st);
-        case 32: return launch_bwd_t<32>(vt, ws, st);
-        default: return launch_bwd_t<16>(vt, ws, st);
+        case 8: return vt.batch == 64 ? launch_bwd_t<8, 2>(vt, ws, st) : launch_bwd_t<8, 1>(vt, ws, st);
+        case 32: return launch_bwd_t<32, 1>(vt, ws, st);
+        default: return vt.batch == 64 ? launch_bwd_t<16, 2>(vt, ws, st) : launch_bwd_t<16, 1>(vt, ws, st);
     }
 }
 

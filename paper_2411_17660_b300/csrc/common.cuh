@@ -61,6 +61,7 @@ struct ViewParams {
 struct ViewTable {
     int V;
     int tile;
+    int batch;                // list entries a blend warp stages per round: 32 or 64
     uint32_t total_tiles;
     uint32_t total_pixels;
     float *l1_loss;           // fused L1 loss: the device scalar it adds to, or NULL

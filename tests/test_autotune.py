@@ -1,19 +1,15 @@
-"""Host logic of the tile-size autotuner (no GPU)."""
+"""Host logic of the autotuner (no GPU): candidate list, cache, signature.
+The timing itself runs in the library (gsr_autotune, tests/test_parity_gpu.py)."""
 from paper_2411_17660_b300 import autotune as A
 from paper_2411_17660_b300.render import Intrinsics
 
 
-def test_choose_picks_fastest_and_breaks_ties_in_order():
-    times = {"8/tile": 3.0, "8/radix": 2.5, "16/tile": 1.5, "16/radix": 1.7, "32/tile": 2.0, "32/radix": 1.6}
-    r = A.choose(lambda c: times[c])
-    assert r["best"] == "16/tile" and r["ms"] == times
-    r = A.choose(lambda c: 1.0)
-    assert r["best"] == A.CANDIDATES[0]
-
-
-def test_candidates_cover_every_tile_size_and_binning():
-    assert {A.parse(c) for c in A.CANDIDATES} == {(t, b) for t in A.TILES for b in A.BINNINGS}
-    assert A.parse("32/radix") == (32, "radix")
+def test_candidates_cover_every_tile_binning_and_batch():
+    want = {(t, b, k) for t in A.TILES for b in A.BINNINGS for k in A.BATCHES if not (t == 32 and k == 64)}
+    assert {A.parse(c) for c in A.CANDIDATES} == want and len(A.CANDIDATES) == len(want) == 10
+    assert A.parse("32/radix/32") == (32, "radix", 32)
+    # the library's order: tile, then binning, then batch
+    assert A.CANDIDATES[:3] == ("8/tile/32", "8/tile/64", "8/radix/32")
 
 
 def test_signature_distinguishes_views_and_sizes():
@@ -28,6 +24,6 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "tiles.json")
     c = A.TileCache(path)
     assert c.get("k") is None
-    c.put("k", {"tile": 32, "ms": {"8": 1.0}})
+    c.put("k", {"tile": 32, "binning": "radix", "batch": 32, "ms": {"8/tile/32": 1.0}})
     again = A.TileCache(path)
     assert again.get("k")["tile"] == 32

@@ -184,6 +184,58 @@ def test_radix_binning_capacity_overflow_is_reported():
     assert info.status == B.ECAPACITY and info.keys > info.key_capacity
 
 
+@pytest.mark.parametrize("tile,binning", [(16, "tile"), (8, "radix"), (16, "radix")])
+def test_entry_batch_64_gives_identical_images_and_gradients(tile, binning):
+    """The blends staging 64 list entries per warp and round (gsr_config.batch)
+    render bit-identical images; the backward's gradients differ only in the
+    order of their FP32 sums."""
+    for name in ("window", "uneven"):
+        sc = REDUCED[name]()
+        a, sa = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning, batch=32))
+        b, sb = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning, batch=64))
+        _assert_same_images(a, b)
+        gC, gD, gA = U.upstream(sc)
+        ga = U.gpu_backward(sc, sa, gC, gD, gA)
+        gb = U.gpu_backward(sc, sb, gC, gD, gA)
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
+            assert U.rel_l2(gb[k], ga[k]) < 1e-5, (name, k)
+
+
+def test_entry_batch_64_is_refused_at_tile_32():
+    with pytest.raises(B.GsrError):
+        R.GaussianRasterizer(32, batch=64)
+
+
+def test_bucket_binning_capacity_overflow_with_tile_order():
+    """The default per-tile binning (bucket grouping, blends in most-keys-first
+    tile order) on a workspace too small for the keys: only the keys that fit
+    are grouped and the ranges are clamped, so the forward and the backward
+    stay in bounds and report GSR_ECAPACITY; the same context then renders
+    correctly on a workspace with room."""
+    sc = REDUCED["uneven"]()
+    params, cams, vm = U.to_device(sc)
+    rast = R.GaussianRasterizer(16)
+    small = rast.alloc_workspace(sc.N, cams, key_capacity=3072)
+    P = sum(c.H * c.W for c in cams)
+    color, depth, alpha = (torch.empty(3 * P, device="cuda"), torch.empty(P, device="cuda"),
+                           torch.empty(P, device="cuda"))
+    rast.forward_raw(params, sc.sh_degree, cams, vm, small, color, depth, alpha)
+    info = rast.info(small)
+    assert info.tiles <= 32768, "the bucket grouping runs up to 32,768 tiles"
+    assert info.status == B.ECAPACITY and info.keys > info.key_capacity
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    d_pose = torch.empty(len(cams), 6, device="cuda")
+    rast.backward_raw(params, sc.sh_degree, cams, vm, small, torch.ones(3 * P, device="cuda"), None, None,
+                      grads, d_pose)
+    torch.cuda.synchronize()
+    assert rast.info(small).status == B.ECAPACITY
+    c2, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+    assert rast.info(ws).status == B.OK
+    ref = U.gpu_forward(sc)[0]
+    for v, c in enumerate(R.split_views(c2, cams, 3)):
+        np.testing.assert_array_equal(c.cpu().numpy(), ref[v]["color"])
+
+
 @pytest.mark.parametrize("name", ["window", "uneven"])
 def test_strategies_agree_on_surfels(name):
     from tests.test_surfel_gpu import gpu_surfels, surfel_scene

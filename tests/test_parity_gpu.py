@@ -107,7 +107,10 @@ def test_capacity_overflow_is_reported_then_grown():
     rast.forward_raw(params, sc.sh_degree, cams, vm, small, color, None, None)
     info = rast.info(small)
     assert info.status == B.ECAPACITY and info.keys > info.key_capacity
+    assert rast.ctx.get_status(small.data_ptr(), small.numel(), torch.cuda.current_stream().cuda_stream) == \
+        B.ECAPACITY
     c2, _, _, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
+    assert rast.ctx.get_status(ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream) == B.OK
     assert rast.info(ws).status == B.OK
     ref = U.gpu_forward(sc)[0]
     for v, c in enumerate(R.split_views(c2, cams, 3)):
@@ -224,14 +227,25 @@ def test_full_size_sampled_pixels(name):
     U.compare_grads(orc, gpu, label=name)
 
 
-@pytest.mark.parametrize("fused", [False, True])
-def test_cuda_graph_replay_matches_eager(fused):
+GRAPH_SCENES = {
+    "window": lambda: REDUCED["window"](),
+    # an uneven batch: 16 keyframes of resolutions drawn from {320x240, 640x480, 1200x680} (scaled by 0.3)
+    "uneven16": lambda: scenes.config_uneven(N=30000, V=16, res_scale=0.3),
+}
+
+
+@pytest.mark.parametrize("name,binning,fused", [("window", "tile", False), ("window", "tile", True),
+                                                ("uneven16", "tile", True), ("uneven16", "radix", True)])
+def test_cuda_graph_replay_matches_eager(name, binning, fused):
     """Forward + loss + backward captured once in a CUDA graph, replayed on
     changed inputs (same buffers), equals the eager calls on those inputs;
     fused: the L1 loss taken in the forward blend (gsr_render_l1), as the
-    benchmark runs it."""
-    sc = REDUCED["window"]()
-    rast = R.GaussianRasterizer(16)
+    benchmark runs it.  uneven16: a 16-keyframe batch of mixed resolutions,
+    with both binning strategies (the radix one is the autotuner's choice for
+    the full-size uneven batch)."""
+    sc = GRAPH_SCENES[name]()
+    assert name != "uneven16" or (sc.V == 16 and len({(c.H, c.W) for c in sc.cameras}) == 3)
+    rast = R.GaussianRasterizer(16, binning=binning)
     params, cams, vm = U.to_device(sc)
     color, depth, alpha, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
     ws = rast.alloc_workspace(sc.N, cams, int(rast.info(ws).keys * 2) + 8192)
@@ -279,13 +293,62 @@ def test_cuda_graph_replay_matches_eager(fused):
 
 
 def test_autotuner_picks_a_candidate_and_caches(tmp_path):
+    """gsr_autotune (through the C ABI) times all ten candidates on the
+    caller's inputs, leaves the fastest in the context, and the Python side
+    caches the choice; the tuned context renders the same images."""
     from paper_2411_17660_b300 import autotune as A
     sc = REDUCED["uneven"]()
     params, cams, vm = U.to_device(sc)
     cache = A.TileCache(str(tmp_path / "tiles.json"))
     r = A.tune(params, sc.sh_degree, cams, vm, cache=cache, reps=2)
-    assert r["tile"] in A.TILES and r["binning"] in A.BINNINGS and set(r["ms"]) == set(A.CANDIDATES)
+    assert r["tile"] in A.TILES and r["binning"] in A.BINNINGS and r["batch"] in A.BATCHES
+    assert list(r["ms"]) == list(A.CANDIDATES) and all(t is not None and t > 0 for t in r["ms"].values())
+    assert r["ms"][f"{r['tile']}/{r['binning']}/{r['batch']}"] == min(r["ms"].values())
     assert A.tune(params, sc.sh_degree, cams, vm, cache=cache) == r
+    tuned = R.GaussianRasterizer(r["tile"], binning=r["binning"], batch=r["batch"])
+    _assert_same_images_as_default(sc, tuned)
+
+
+def _assert_same_images_as_default(sc, rast):
+    got = U.gpu_forward(sc, rast=rast)[0]
+    ref = U.gpu_forward(sc)[0]
+    for a, b in zip(got, ref):
+        for k in ("color", "depth", "alpha"):
+            np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_autotune_skips_candidates_whose_keys_do_not_fit():
+    """A workspace sized for tile 16's keys: the tile-8 candidates report
+    GSR_ECAPACITY and are skipped, the others run, and the context keeps the
+    fastest of those."""
+    sc = REDUCED["window"]()
+    params, cams, vm = U.to_device(sc)
+    rast = R.GaussianRasterizer(16)
+    _, _, _, ws0 = rast.render_forward(params, sc.sh_degree, cams, vm)
+    keys16 = rast.info(ws0).keys
+    rast8 = R.GaussianRasterizer(8)
+    _, _, _, ws8 = rast8.render_forward(params, sc.sh_degree, cams, vm)
+    assert rast8.info(ws8).keys > 1.5 * keys16
+    ws = rast.alloc_workspace(sc.N, cams, int(keys16 * 1.05) + 3072)
+    P = R.pixel_offsets(cams)[-1]
+    color = torch.empty(3 * P, device="cuda")
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    g = R.gaussians_struct(*[params[k] for k in R.PARAM_NAMES], sc.sh_degree)
+    out = B.Grads(*[grads[k].data_ptr() for k in R.PARAM_NAMES], 0, 0, 0, 0)
+    st, entries = rast.ctx.autotune(g, R.view_structs(cams, vm, color), out, ws.data_ptr(), ws.numel(), 1,
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == B.OK and len(entries) == 10
+    for e in entries:
+        assert (e.status == B.ECAPACITY) == (e.tile == 8), (e.tile, e.binning, e.batch, e.status)
+        assert (e.ms > 0) == (e.status == B.OK)
+    best = min((e for e in entries if e.status == B.OK), key=lambda e: e.ms)
+    # the tuned context renders with its new configuration on a fresh workspace
+    color2, _, _, ws2 = rast.render_forward(params, sc.sh_degree, cams, vm)
+    assert rast.ctx.get_status(ws2.data_ptr(), ws2.numel(), torch.cuda.current_stream().cuda_stream) == B.OK
+    ref = U.gpu_forward(sc)[0]
+    for v, c in enumerate(R.split_views(color2, cams, 3)):
+        np.testing.assert_array_equal(c.cpu().numpy(), ref[v]["color"])
+    assert best.tile in (16, 32)
 
 
 @pytest.mark.parametrize("deg", [1, 2])
