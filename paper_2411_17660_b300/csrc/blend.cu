@@ -290,7 +290,10 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdB
     float2 ly2 = make_float2(wt.px < vp.W && wt.py < vp.H ? lyf : kInf,
                              wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + (float)kRowStep : kInf);
     float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0, D = C0, Zm = C0;
-    uint32_t last[NR] = {0u, 0u}, mi[NR] = {0u, 0u}, ncon = 0;
+    // last: the list position of the entry the pixel stopped at, or the
+    // list's end -- the backward's contributors are the entries before it
+    // that reach the pixel (every one of them was composited)
+    uint32_t last[NR] = {wt.range.y, wt.range.y}, mi[NR] = {0u, 0u}, ncon = 0;
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32 * CH) {
         if (__all_sync(kFull, ly2.x == kInf && ly2.y == kInf)) break;
         const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0,
@@ -312,33 +315,32 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdB
             const float2 dy = __fadd2_rn(ly2, hi2(e0));
             float2 p1, p2;
             const float2 s = pair_s2(m00dx, dy, hi2(e1), lo2(e2), p1, p2);
+            const bool c0 = s.x <= x.x, c1 = s.y <= x.x;           // the entry reaches the pixel
             const float2 arg = __ffma2_rn(s, neg2, hi2(e2));    // log2(sigma) - s
-            const float2 al = make_float2(s.x <= x.x ? fminf(kAlphaMax, ex2_approx(arg.x)) : 0.f,
-                                          s.y <= x.x ? fminf(kAlphaMax, ex2_approx(arg.y)) : 0.f);
+            const float2 al = make_float2(c0 ? fminf(kAlphaMax, ex2_approx(arg.x)) : 0.f,
+                                          c1 ? fminf(kAlphaMax, ex2_approx(arg.y)) : 0.f);
             float2 w = __fmul2_rn(al, T);
-            const float2 Tn = __ffma2_rn(w, neg2, T);              // T (1 - alpha)
+            float2 Tn = __ffma2_rn(w, neg2, T);                    // T (1 - alpha)
+            ncon += (uint32_t)c0 + (uint32_t)c1;
             const bool st0 = Tn.x < kTStop, st1 = Tn.y < kTStop;   // stop before this entry
-            w.x = st0 ? 0.f : w.x;
-            w.y = st1 ? 0.f : w.y;
-            ly2.x = st0 ? kInf : ly2.x;
-            ly2.y = st1 ? kInf : ly2.y;
+            if (__any_sync(kFull, st0 || st1)) {
+                // rare: a pixel of the warp meets the stop; it keeps its T and
+                // takes nothing more (its row moves to the infinite offset)
+                const uint32_t idx = __float_as_uint(x.y);
+                if (st0) w.x = 0.f, Tn.x = T.x, ly2.x = kInf, last[0] = idx, --ncon;
+                if (st1) w.y = 0.f, Tn.y = T.y, ly2.y = kInf, last[1] = idx, --ncon;
+            }
             const float4 e3 = sF[warp][3][j], e4 = sF[warp][4][j];
             C0 = __ffma2_rn(w, lo2(e3), C0);
             C1 = __ffma2_rn(w, hi2(e3), C1);
             C2 = __ffma2_rn(w, lo2(e4), C2);
             D = __ffma2_rn(w, hi2(e4), D);
-            // composited <=> w > 0 (alpha >= 1/255 where s <= s_max, T >= the stop)
-            const bool k0 = w.x > 0.f, k1 = w.y > 0.f;
-            const uint32_t id1 = __float_as_uint(x.y) + 1u;
-            if (MED) {
-                if (k0 && T.x > 0.5f) Zm.x = e4.z, mi[0] = id1;
-                if (k1 && T.y > 0.5f) Zm.y = e4.z, mi[1] = id1;
+            if (MED) {   // a stopping entry has T < 0.01, so c is enough here
+                const uint32_t id1 = __float_as_uint(x.y) + 1u;
+                if (c0 && T.x > 0.5f) Zm.x = e4.z, mi[0] = id1;
+                if (c1 && T.y > 0.5f) Zm.y = e4.z, mi[1] = id1;
             }
-            T.x = st0 ? T.x : Tn.x;
-            T.y = st1 ? T.y : Tn.y;
-            last[0] = k0 ? id1 : last[0];
-            last[1] = k1 ? id1 : last[1];
-            ncon += (uint32_t)k0 + (uint32_t)k1;
+            T = Tn;
         }
         __syncwarp();
     }

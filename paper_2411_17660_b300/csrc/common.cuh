@@ -120,7 +120,7 @@ struct Ws {
     uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
     uint2 *ranges;           // [total_tiles] [start, end) in the sorted list
     float *T_final;          // [total_pixels]
-    uint32_t *last;          // [total_pixels] last contributor index + 1
+    uint32_t *last;          // [total_pixels] list position where the pixel stopped, or its tile list's end
     uint32_t *median;        // [total_pixels] median-depth contributor index + 1 (0: none)
     float *vg_grads;         // [N][V][10] screen-space gradients of each (Gaussian, view)
     float *pose_partials;    // [V][pose_blocks][6]
