@@ -385,12 +385,13 @@ class Window:
                                    densify=self.dens)
 
 
-def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, binning="tile", tiles=1, sfu_peak=None):
+def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, binning="tile", tiles=1, sfu_peak=None,
+                    visible=0):
     """Every stage against its bound: the blends against the FP32 lanes
     (composited pairs x FP32 instructions per pair) and, beside it, the SFU
     (composited pairs x MUFU operations per pair), the rest against HBM with
-    the bytes the host can count -- a lower bound for the preprocesses, whose
-    records of visible pairs are counted on the device only."""
+    their algorithmic bytes: what the stage must read and write once, from
+    the Gaussian, pair, visible-pair (counted on the device) and key counts."""
     K = (scene.sh_degree + 1) ** 2
     param_b = scene.N * 4 * (3 + 3 + 4 + 1 + 3 * K)
     VN = scene.V * scene.N
@@ -403,15 +404,24 @@ def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, bin
             out[s]["sfu"] = {"achieved": m, "peak": sfu_peak, "unit": "Gop/s", "frac": m / sfu_peak,
                              "work": f"{MUFU_PER_PAIR[s]} MUFU per composited pair"}
     hbm = {
-        # parameters once, a 4-byte count per pair, 12 bytes per emitted key
-        "preprocess": (param_b + 4 * VN + 12 * keys, "lower bound: + 64 B of records per visible pair"),
+        # parameters once; per pair its tile count and densification radius; per visible pair its
+        # four records and its cleared gradient row; per emitted key its tile and word (per-tile binning)
+        "preprocess": (param_b + 8 * VN + 104 * visible + (12 * keys if binning == "tile" else 0),
+                       "parameters once + 8 B per pair + 104 B per visible pair (records, cleared gradient row)"
+                       + (" + 12 B per key" if binning == "tile" else "")),
         # per-tile: count reads tile ids; scatter reads tile ids and words, writes words; tile sort
         # reads words, writes ids.  radix: 24 B per key per 8-bit pass (sort) + 8 (ranges)
         "sort": (36 * keys, "36 B per key") if binning == "tile" else
                 (24 * keys * ((32 + max(1, (tiles - 1).bit_length()) + 7) // 8), "24 B per key per pass"),
-        # parameters in, gradients out, a 4-byte count per pair
-        "preprocess_bwd": (2 * param_b + 4 * VN, "lower bound: + 40 B of screen gradients per visible pair"),
+        # parameters in, gradients out, a count per pair, each visible pair's gradient row read and cleared
+        "preprocess_bwd": (2 * param_b + 4 * VN + 80 * visible,
+                           "2 x parameters + 4 B per pair + 80 B per visible pair (gradient row read and cleared)"),
     }
+    if binning != "tile":
+        # radix: counts read by the scan and the duplication, the spans' records (rec0, rec1, rec3,
+        # depth) read per visible pair, 12 B written per key
+        hbm["scan_duplicate"] = (8 * VN + 52 * visible + 12 * keys,
+                                 "8 B per pair + 52 B per visible pair + 12 B per key")
     for s, (b, note) in hbm.items():
         if s not in stage_ms or stage_ms[s] <= 0:
             continue
@@ -543,7 +553,7 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
         stage_ms[st] = statistics.mean(ev_sets[i][a].elapsed_time(ev_sets[i][b]) for i in range(K))
     ops = {"blend_fwd": FWD_OPS_PER_PAIR, "blend_bwd": BWD_OPS_PER_PAIR}
     roof = stage_rooflines(stage_ms, ops, info.pairs_contributing, alu_peak, peaks["hbm_gbs"], scene, win.P,
-                           info.keys, tuned["binning"], info.tiles, sfu_peak)
+                           info.keys, tuned["binning"], info.tiles, sfu_peak, info.pairs_visible)
     out = {"config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene),
                       "gaussians": scene.N, "sh_degree": scene.sh_degree, "tile": tuned["tile"],
                       "binning": tuned["binning"], "batch": tuned["batch"], "autotune_ms": tuned["ms"],
@@ -552,6 +562,7 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
            "value": win.P / (replay / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": replay,
            "mapping_it_per_s": 1000.0 / replay, "eager_ms_per_step": eager,
            "stages_ms": stage_ms, "keys": info.keys, "pairs_contributing": info.pairs_contributing,
+           "pairs_visible": info.pairs_visible,
            "stage_rooflines": roof, "memory": step_memory(torch, scene, win)}
     del graph, win
     return out
@@ -696,7 +707,8 @@ def main():
         roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "traffic": traffic_for(dominant, scene.name)}
     stage_roof = stage_rooflines(stage_ms, ops, pairs, alu_peak, peaks["hbm_gbs"], scene, win.P, info.keys,
-                                 args.binning, info.tiles, sfu_peak if args.primitive == "gaussians" else None)
+                                 args.binning, info.tiles, sfu_peak if args.primitive == "gaussians" else None,
+                                 info.pairs_visible)
 
     P_all = win.P * world
     # headline: the step as one replayed CUDA graph (the batched path's launch
@@ -726,7 +738,7 @@ def main():
         "stages_ms": stage_ms,
         "stage_timing": "device time per stage from CUDA events, in steps queued behind a ~2 ms GPU sleep "
                         "so that host launch gaps do not count",
-        "keys": info.keys, "pairs_contributing": pairs,
+        "keys": info.keys, "pairs_contributing": pairs, "pairs_visible": info.pairs_visible,
         "memory": memory,
         "roofline": roof,
         "stage_rooflines": stage_roof,

@@ -171,6 +171,9 @@ typedef struct {
     uint32_t key_capacity;       /* keys the workspace holds */
     uint32_t tiles;              /* screen tiles over all views */
     uint64_t pairs_contributing; /* (pixel, Gaussian) pairs composited by the last render */
+    uint32_t pairs_visible;      /* (view, Gaussian) pairs of the last Gaussian render that reach a
+                                    pixel centre and got tile keys (0 for surfels) */
+    uint32_t reserved;           /* 0 */
 } gsr_info;
 
 /* Target images for the L1 loss front end (device). */

@@ -687,6 +687,8 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
     info->key_capacity = h.key_capacity;
     info->tiles = h.tiles;
     info->pairs_contributing = h.pairs_contrib;
+    info->pairs_visible = h.pairs_visible;
+    info->reserved = 0;
     return GSR_OK;
 }
 

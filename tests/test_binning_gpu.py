@@ -75,15 +75,24 @@ def test_keys_reserved_in_the_preprocess_match_the_scan(name):
     the radix path's scan total, and repeated renders must agree bit for bit."""
     sc = REDUCED[name]()
     params, cams, vm = U.to_device(sc)
-    counts, images = [], []
+    counts, images, visible = [], [], []
     for binning in ("radix", "tile", "tile", "tile"):
         rast = R.GaussianRasterizer(16, binning=binning)
         c, d, a, ws = rast.render_forward(params, sc.sh_degree, cams, vm)
         info = rast.info(ws)
         assert info.status == B.OK
         counts.append(info.keys)
+        visible.append(info.pairs_visible)
         images.append([t.cpu().numpy() for t in (c, d, a)])
     assert len(set(counts)) == 1 and counts[0] > 0
+    # the visible-pair count is the binning's too, and adds up over the views rendered alone
+    assert len(set(visible)) == 1 and 0 < visible[0] <= sc.V * sc.N
+    alone = 0
+    for v in range(sc.V):
+        rast = R.GaussianRasterizer(16)
+        _, _, _, ws = rast.render_forward(params, sc.sh_degree, cams[v:v + 1], vm[v:v + 1].contiguous())
+        alone += rast.info(ws).pairs_visible
+    assert alone == visible[0]
     for im in images[2:]:
         for x, y in zip(images[1], im):
             np.testing.assert_array_equal(x, y)
