@@ -323,23 +323,29 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdB
             float2 Tn = __ffma2_rn(w, neg2, T);                    // T (1 - alpha)
             ncon += (uint32_t)c0 + (uint32_t)c1;
             const bool st0 = Tn.x < kTStop, st1 = Tn.y < kTStop;   // stop before this entry
-            if (__any_sync(kFull, st0 || st1)) {
-                // rare: a pixel of the warp meets the stop; it keeps its T and
-                // takes nothing more (its row moves to the infinite offset)
-                const uint32_t idx = __float_as_uint(x.y);
-                if (st0) w.x = 0.f, Tn.x = T.x, ly2.x = kInf, last[0] = idx, --ncon;
-                if (st1) w.y = 0.f, Tn.y = T.y, ly2.y = kInf, last[1] = idx, --ncon;
-            }
             const float4 e3 = sF[warp][3][j], e4 = sF[warp][4][j];
-            C0 = __ffma2_rn(w, lo2(e3), C0);
-            C1 = __ffma2_rn(w, hi2(e3), C1);
-            C2 = __ffma2_rn(w, lo2(e4), C2);
-            D = __ffma2_rn(w, hi2(e4), D);
             if (MED) {   // a stopping entry has T < 0.01, so c is enough here
                 const uint32_t id1 = __float_as_uint(x.y) + 1u;
                 if (c0 && T.x > 0.5f) Zm.x = e4.z, mi[0] = id1;
                 if (c1 && T.y > 0.5f) Zm.y = e4.z, mi[1] = id1;
             }
+            if (__builtin_expect(__any_sync(kFull, st0 || st1), 0)) {
+                // rare: a pixel of the warp meets the stop; it keeps its T and
+                // takes nothing more (its row moves to the infinite offset)
+                const uint32_t idx = __float_as_uint(x.y);
+                if (st0) w.x = 0.f, Tn.x = T.x, ly2.x = kInf, last[0] = idx, --ncon;
+                if (st1) w.y = 0.f, Tn.y = T.y, ly2.y = kInf, last[1] = idx, --ncon;
+                C0 = __ffma2_rn(w, lo2(e3), C0);
+                C1 = __ffma2_rn(w, hi2(e3), C1);
+                C2 = __ffma2_rn(w, lo2(e4), C2);
+                D = __ffma2_rn(w, hi2(e4), D);
+                T = Tn;
+                continue;
+            }
+            C0 = __ffma2_rn(w, lo2(e3), C0);
+            C1 = __ffma2_rn(w, hi2(e3), C1);
+            C2 = __ffma2_rn(w, lo2(e4), C2);
+            D = __ffma2_rn(w, hi2(e4), D);
             T = Tn;
         }
         __syncwarp();
