@@ -55,6 +55,41 @@ def test_backward_parity_reduced(name):
     U.compare_grads(ref, got, label=name)
 
 
+def _opaque_stack(seed=31, N=2500, H=60, W=80, f=70.0):
+    """A dense stack of nearly opaque Gaussians in front of one view, so that
+    most pixels meet the transmittance stop part-way down their lists."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    base = scenes.config_small(seed=seed, N=N, H=H, W=W, f=f)
+    z = rng.uniform(2.0, 5.0, N)
+    xy = rng.uniform(-0.9, 0.9, (2, N)) * z * np.array([[W / (2 * f)], [H / (2 * f)]])
+    return dataclasses.replace(
+        base, means=np.ascontiguousarray(np.stack([xy[0], xy[1], z]).astype(np.float32)),
+        log_scales=np.ascontiguousarray(rng.normal(-1.9, 0.3, (3, N)).astype(np.float32)),
+        opacity_logits=np.ascontiguousarray(rng.normal(4.0, 0.5, N).astype(np.float32)))
+
+
+def test_transmittance_stop_forward_and_backward():
+    """Pixels that stop part-way down their lists: the forward keeps the stop
+    position, and the backward's contributors (the entries before it that
+    reach the pixel) give the oracle's gradients."""
+    sc = _opaque_stack()
+    got, state = U.gpu_forward(sc)
+    ref = oracle.render(sc)
+    stopped = ref[0]["T"] < 2e-4
+    assert stopped.mean() > 0.3, "most pixels should meet the stop"
+    n_ref = int(ref[0]["ncontrib"].sum())
+    U.compare_images(ref[0], got[0], "opaque stack")
+    info = state[0].info(state[4])
+    flips = (ref[0]["margin"] < U.MARGIN) | (ref[0]["zmargin"] < U.ZMARGIN)
+    # composited pairs counted by the forward = the oracle's contributors (up to flips)
+    assert abs(info.pairs_contributing - n_ref) <= int(flips.sum()) * 4
+    gC, gD, gA = U.upstream(sc)
+    g = U.gpu_backward(sc, state, gC, gD, gA)
+    _, gref = oracle.render_backward(sc, gC, gD, gA)
+    U.compare_grads(gref, g, label="opaque stack")
+
+
 def test_tile_size_invariance():
     sc = REDUCED["room"]()
     outs = [U.gpu_forward(sc, tile=t)[0][0] for t in (8, 16, 32)]
