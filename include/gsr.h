@@ -173,7 +173,11 @@ typedef struct {
     uint64_t pairs_contributing; /* (pixel, Gaussian) pairs composited by the last render */
     uint32_t pairs_visible;      /* (view, Gaussian) pairs of the last Gaussian render that reach a
                                     pixel centre and got tile keys (0 for surfels) */
-    uint32_t reserved;           /* 0 */
+    uint32_t pairs_backward;     /* checked build (libgsr_checked.so) only, else 0: the (pixel,
+                                    Gaussian) pairs the backward since that render took as
+                                    contributors, saturated at 2^32 - 1; equal to
+                                    pairs_contributing after one backward, as the two kernels take
+                                    the same decisions */
 } gsr_info;
 
 /* Target images for the L1 loss front end (device). */

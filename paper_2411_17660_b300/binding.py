@@ -59,7 +59,7 @@ class Grads(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("keys", ctypes.c_uint32), ("key_capacity", ctypes.c_uint32),
                 ("tiles", ctypes.c_uint32), ("pairs_contributing", ctypes.c_uint64), ("pairs_visible", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("pairs_backward", ctypes.c_uint32)]
 
 
 class L1View(ctypes.Structure):

@@ -688,7 +688,7 @@ gsr_status gsr_read_info(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_info
     info->tiles = h.tiles;
     info->pairs_contributing = h.pairs_contrib;
     info->pairs_visible = h.pairs_visible;
-    info->reserved = 0;
+    info->pairs_backward = h.pairs_bwd > 0xffffffffull ? 0xffffffffu : (uint32_t)h.pairs_bwd;
     return GSR_OK;
 }
 

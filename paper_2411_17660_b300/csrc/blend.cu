@@ -179,6 +179,15 @@ __device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane
     return d;
 }
 
+// Both blends form a pixel's row offset from the mean relative to the last
+// row above it that is a multiple of kRowOrigin (the first row of a 16-row
+// band), whatever their own warp blocks: the forward's 8-row blocks and the
+// backward's 16-row ones (or 8-row ones at tile 8) then form s with the same
+// FP32 operations for every pixel, so the two kernels take the same
+// decisions, at every tile size.
+constexpr int kRowOrigin = 16;
+__device__ __forceinline__ int row_origin(int Y0) { return Y0 - Y0 % kRowOrigin; }
+
 struct WarpTile {
     int v;
     int X0, Y0;         // pixel of lane 0 (origin of the warp's block)
@@ -215,9 +224,12 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
 // CH = 2 (the 64-entry batch) halves the staging rounds (and the warp's
 // done tests between them), at the price of staging up to 64 entries past a
 // warp's transmittance stop.
+// vr is the mean's row offset from row Yr (the origin the per-pixel offsets
+// are formed from); the block test takes it relative to the block's first
+// row Y0 >= Yr.
 template <int BH, int CH, typename Stage>
 __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, size_t vN, uint32_t base, uint32_t end,
-                                           int X0, int Y0, Stage &&write) {
+                                           int X0, int Y0, int Yr, Stage &&write) {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t g[CH];
 #pragma unroll
@@ -236,8 +248,8 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
             const float4 r0 = ws.rec0[vN + g[k]];
             r1 = ws.rec1[vN + g[k]];
             ur = __fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z);
-            vr = __fadd_rn(__fsub_rn(r0.y, (float)Y0), r0.w);
-            keep = touches_block<BH>(ur, vr, r1.x, r1.y, r1.z, r1.w);
+            vr = __fadd_rn(__fsub_rn(r0.y, (float)Yr), r0.w);
+            keep = touches_block<BH>(ur, Y0 == Yr ? vr : __fsub_rn(vr, (float)(Y0 - Yr)), r1.x, r1.y, r1.z, r1.w);
         }
         const unsigned ballot = __ballot_sync(kFull, keep);
         if (keep) {
@@ -286,9 +298,11 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdB
     // sits at an infinite row offset: its s is not finite (inf or NaN), so no
     // entry reaches it.  T never falls below the stop, so an entry that
     // reaches no row leaves Tn = T and cannot trigger the stop either.
+    const int Yr = row_origin(wt.Y0);
+    const float yoff = (float)(wt.Y0 - Yr);
     const float kInf = __int_as_float(0x7f800000);
-    float2 ly2 = make_float2(wt.px < vp.W && wt.py < vp.H ? lyf : kInf,
-                             wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + (float)kRowStep : kInf);
+    float2 ly2 = make_float2(wt.px < vp.W && wt.py < vp.H ? lyf + yoff : kInf,
+                             wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + yoff + (float)kRowStep : kInf);
     float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0, D = C0, Zm = C0;
     // last: the list position of the entry the pixel stopped at, or the
     // list's end -- the backward's contributors are the entries before it
@@ -296,7 +310,7 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdB
     uint32_t last[NR] = {wt.range.y, wt.range.y}, mi[NR] = {0u, 0u}, ncon = 0;
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32 * CH) {
         if (__all_sync(kFull, ly2.x == kInf && ly2.y == kInf)) break;
-        const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0,
+        const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0, Yr,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t) {
                                           float4(&e)[kEntryQuads][32 * CH] = sF[warp];
@@ -479,6 +493,8 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     const float2 lx2 = make_float2(lxf, lxf);
     const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
     const float2 m2ln2 = make_float2(-2.f * kLn2, -2.f * kLn2);
+    const int Yr = row_origin(wt.Y0);             // the row offsets' origin (see row_origin)
+    const float yoff = (float)(wt.Y0 - Yr);
 
     // per pixel (pair p: .x row 2p, .y row 2p + 1): Q = gC . (colour behind)
     // + gD (depth behind), normalised by the transmittance in front of the
@@ -518,12 +534,15 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
         Q[p] = make_float2(0.f, 0.f);
     }
     const uint32_t wlast = __reduce_max_sync(kFull, lmax);
+#ifdef GSR_CHECKED
+    unsigned long long nbwd = 0;   // the contributor pairs this warp takes (the same in every lane)
+#endif
     float *grads = ws.vg_grads + (size_t)wt.v * kVGGrads;   // + g V 10: (Gaussian, view) rows of 10
     const size_t row = (size_t)ws.V * kVGGrads;
 
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u * CH ? end - 32u * CH : wt.range.x;
-        const int n = stage_chunk<BH, CH>(ws, vals, vN, begin, end, wt.X0, wt.Y0,
+        const int n = stage_chunk<BH, CH>(ws, vals, vN, begin, end, wt.X0, wt.Y0, Yr,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t g) {
                                           float4(&e)[kEntryQuads][32 * CH] = sE[warp];
@@ -546,7 +565,8 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             unsigned m[NR], cmask = 0u;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const float2 ly = make_float2(lyf + (float)(2 * p * kRowStep), lyf + (float)((2 * p + 1) * kRowStep));
+                const float2 ly = make_float2(lyf + yoff + (float)(2 * p * kRowStep),
+                                              lyf + yoff + (float)((2 * p + 1) * kRowStep));
                 dy[p] = __fadd2_rn(ly, hi2(e0));
                 s[p] = pair_s2(m00dx, dy[p], hi2(e1), lo2(e2), p1[p], p2[p]);
                 c[2 * p] = eidx < last[2 * p] && s[p].x <= x.x;
@@ -556,6 +576,10 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 cmask |= m[2 * p] | m[2 * p + 1];
             }
             if (cmask == 0u) continue;
+#ifdef GSR_CHECKED
+#pragma unroll
+            for (int r = 0; r < NR; ++r) nbwd += (unsigned long long)__popc(m[r]);
+#endif
             const float4 e3 = sE[warp][3][j], e4 = sE[warp][4][j];
             float2 A[kVGGrads];
             // Both rows of pair p, packed.  Branch-free: a pixel without a
@@ -684,6 +708,9 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
         __syncwarp();
         end = begin;
     }
+#ifdef GSR_CHECKED
+    if (lane == 0 && nbwd) atomicAdd(&ws.hdr->pairs_bwd, nbwd);
+#endif
 }
 
 template <int TS, int CH>

@@ -86,7 +86,9 @@ struct WsHeader {
     uint32_t bwd_groups;            // preprocess backward: groups taken (reset by the pose reduction)
     uint32_t pre_items;             // preprocess forward: work items taken (zeroed by the init kernel)
     uint32_t pairs_visible;         // (view, Gaussian) pairs with tile keys (records written), Gaussians only
-    uint32_t pad[64 - 11 - kMaxPasses];
+    uint32_t pad0;
+    unsigned long long pairs_bwd;   // checked builds: contributor pairs the blend backward took
+    uint32_t pad[64 - 14 - kMaxPasses];
 };
 static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
 

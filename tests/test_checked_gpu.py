@@ -29,6 +29,6 @@ def test_parity_subset_on_the_checked_build():
     assert which.returncode == 0 and which.stdout.strip() == lib, which.stderr[-2000:]
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_parity_gpu.py", "tests/test_binning_gpu.py",
                         "tests/test_surfel_gpu.py", "-q", "-x", "-p", "no:cacheprovider", "-m", "gpu", "-k",
-                        "reduced or strategies or capacity or surfel or tiny"],
+                        "reduced or strategies or capacity or surfel or tiny or decisions"],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=1500)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]

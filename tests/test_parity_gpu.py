@@ -90,6 +90,23 @@ def test_transmittance_stop_forward_and_backward():
     U.compare_grads(gref, g, label="opaque stack")
 
 
+@pytest.mark.parametrize("tile,binning", [(8, "tile"), (16, "tile"), (32, "tile"), (16, "radix")])
+def test_decisions_backward_equals_forward(tile, binning):
+    """The checked build counts the backward's contributor pairs: they are
+    exactly the forward's composited pairs (both kernels form every s with
+    the same FP32 operations), at every tile size, also where pixels stop."""
+    if not B.LIB_PATH.endswith("libgsr_checked.so"):
+        pytest.skip("the backward's pair count is kept by the checked build (tests/test_checked_gpu.py)")
+    for sc in (REDUCED["window"](), REDUCED["uneven"](), REDUCED["outdoor"](), _opaque_stack()):
+        _, state = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning))
+        gC, gD, gA = U.upstream(sc)
+        U.gpu_backward(sc, state, gC, gD, gA)
+        info = state[0].info(state[4])
+        assert info.status == B.OK
+        assert info.pairs_backward == info.pairs_contributing > 0, (sc.name, info.pairs_backward,
+                                                                     info.pairs_contributing)
+
+
 def test_tile_size_invariance():
     sc = REDUCED["room"]()
     outs = [U.gpu_forward(sc, tile=t)[0][0] for t in (8, 16, 32)]
