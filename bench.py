@@ -445,12 +445,16 @@ def launches_per_step(rast, win):
     # tile bits and the ranges -- and adds 2 tile sorts; the L1 loss fused into
     # the forward blend has no kernel of its own
     loss = 0 if win.fuse_l1 else 1
-    group = 2 if tiles <= 32768 else 2 + (tbits + 7) // 8
+    # beyond 32,768 tiles, and with radix binning, two kernels also list the
+    # blends' tile order up to 65,536 tiles (the bucket count lists it
+    # itself); not for surfels
+    order = 0 if win.surfels or tiles > 65536 else 2
+    group = 2 if tiles <= 32768 else 2 + (tbits + 7) // 8 + order
     if rast.binning == "tile" and not win.surfels:
         return 6 + loss + group + 2
     if rast.binning == "tile":   # surfels: scan + duplicate, then the same grouping
         return 10 + loss + group + 2
-    return 12 + loss + (32 + tbits + 7) // 8
+    return 12 + loss + (32 + tbits + 7) // 8 + order
 
 
 def time_steps(torch, fn, K, flush, events_per_step=None):

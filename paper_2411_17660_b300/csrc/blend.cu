@@ -200,7 +200,7 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     using S = BlendShape<TS, BH>;
     WarpTile w;
     uint32_t tile = blockIdx.x;
-    if (ws.order_tiles) {   // the bucket scan's order: tiles with the most keys first
+    if (ws.order_tiles) {   // tiles with the most keys first (bucket scan or launch_tile_order)
         const uint32_t t = ws.tile_order[blockIdx.x];
         tile = t < vt.total_tiles ? t : blockIdx.x;
     }

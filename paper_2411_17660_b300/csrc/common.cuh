@@ -86,7 +86,7 @@ struct WsHeader {
     uint32_t bwd_groups;            // preprocess backward: groups taken (reset by the pose reduction)
     uint32_t pre_items;             // preprocess forward: work items taken (zeroed by the init kernel)
     uint32_t pairs_visible;         // (view, Gaussian) pairs with tile keys (records written), Gaussians only
-    uint32_t pad0;
+    uint32_t order_counter;         // tile-order count kernel: blocks done (zeroed by the init kernel)
     unsigned long long pairs_bwd;   // checked builds: contributor pairs the blend backward took
     uint32_t pad[64 - 14 - kMaxPasses];
 };
@@ -118,7 +118,8 @@ struct Ws {
     int bin_tile;
     uint32_t *hist;          // [kMaxPasses][256]
     uint32_t *tile_cursor;   // [total_tiles] bucket binning: keys per tile, then each tile's next free slot
-    uint32_t *tile_order;    // [total_tiles] bucket binning: the blends' launch order, most keys first
+    uint32_t *tile_order;    // [total_tiles] the blends' launch order, most keys first
+    uint32_t *order_bins;    // [2][33] tile counts by key-count bit length, then each bin's next slot
     int order_tiles;         // the blends take their tiles from tile_order
     uint32_t *lookback;      // [2][lb_tiles][256] look-back flags, by pass parity
     uint2 *ranges;           // [total_tiles] [start, end) in the sorted list
@@ -149,6 +150,8 @@ __host__ __device__ __forceinline__ bool keys_in_preprocess(const Ws &w) { retur
 // duplication for surfels -- are grouped by tile with counting kernels
 // instead of the onesweep passes over the tile bits.
 constexpr uint32_t kBucketMaxTiles = 1u << 15;
+// Up to this many tiles the blends take them most keys first.
+constexpr uint32_t kOrderMaxTiles = 1u << 16;
 __host__ __device__ __forceinline__ bool bucket_binning(const Ws &w) {
     return w.bin_tile && w.total_tiles <= kBucketMaxTiles;
 }
