@@ -28,6 +28,8 @@
 // operand that both pixels use as a duplicated pair, so that one 128-bit
 // shared load yields two ready register pairs.  The forward runs its pair
 // without branches; the backward branches on the rows its warp reaches.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace gsr {
@@ -49,24 +51,49 @@ struct BlendShape {
     static constexpr int THREADS = WARPS * 32;
 };
 
-// s = 0.5 log2(e) d^2 of a pixel at offset (dx, dy) from the mean, with the
-// Cholesky factor m of 0.5 log2(e) Sigma'^-1: p1 = m00 dx + m01 dy, p2 = m11 dy
-// (m00dx = m00 dx, shared by the rows of a column).  Round-to-nearest
-// intrinsics: the forward and the backward take bit-identical decisions.
-__device__ __forceinline__ float pair_s(float m00dx, float dy, float m01, float m11, float &p1, float &p2) {
-    p1 = __fmaf_rn(m01, dy, m00dx);
-    p2 = __fmul_rn(m11, dy);
-    return __fmaf_rn(p1, p1, __fmul_rn(p2, p2));
+// s = 0.5 log2(e) d^2 = p1^2 + p2^2, with the Cholesky factor m of
+// 0.5 log2(e) Sigma'^-1 and the mean at offset (ur, vr) from the origin of
+// the pixel offsets (x, y): p1 = m00 (x - ur) + m01 (y - vr) = m00 x + m01 y + a
+// and p2 = m11 (y - vr) = m11 y + b.  The constants a, b are formed once per
+// staged entry; a pixel then needs three FMAs for p1, p2.  Round-to-nearest
+// intrinsics throughout, so that the forward and the backward take
+// bit-identical decisions.
+__device__ __forceinline__ void lin_consts(float ur, float vr, float m00, float m01, float m11, float &a, float &b) {
+    a = -__fmaf_rn(m01, vr, __fmul_rn(m00, ur));
+    b = -__fmul_rn(m11, vr);
 }
 
+// Forward: staged entry of a warp's slot k, three float4 (no duplicated
+// pairs: the blend forward is bound by the bytes its shared-memory loads
+// deliver to the warp, 128 per clock and SM, so each entry is loaded once
+// as plain scalars).
+//   q0 = (m00, a, m01, m11)   Cholesky factor of 0.5 log2(e) Sigma'^-1, constant a
+//   q1 = (b, s_max, l, list index as bits)   l = log2(opacity)
+//   q2 = (r, g, b, z)
+constexpr int kFwdQuads = 3;
 // Backward: staged entry of a warp's slot k, five float4 of pairs and one
-// float2.
-//   e0 = (-ur, -ur, -vr, -vr)  mean relative to the warp's block origin
-//   e1 = (m00, m00, m01, m01)  Cholesky factor of 0.5 log2(e) Sigma'^-1
-//   e2 = (m11, m11, l, l)      l = log2(opacity)
+// float4, so that one 128-bit shared load yields two ready register pairs
+// (the backward has arithmetic enough per entry that its shared loads are
+// not what bounds it).
+//   e0 = (-ur, -ur, -vr, -vr)  mean relative to the offsets' origin
+//   e1 = (m00, m00, m01, m01)
+//   e2 = (m11, m11, l, l)
 //   e3 = (r, r, g, g), e4 = (b, b, z, z)
-//   x  = (s_max, list index as bits)
-constexpr int kEntryQuads = 5;
+//   x  = (s_max, list index, Gaussian index, -)
+constexpr int kBwdQuads = 5;
+
+// Below this log2(opacity), 2^(log2(opacity) - s) stays under the 0.99
+// alpha clamp for every s >= 0 even with ex2.approx's error (a relative
+// 2^-21 at most against the 1.5e-5 margin), so the clamp is the identity.
+constexpr float kLog2ClampFree = -0.01452f;   // log2(0.99) = -0.0144996, less 2e-5
+
+// 1.0f where a <= b, else 0.0f (also for a NaN): one instruction that gives
+// both the cutoff mask that scales alpha and the composited-pair count.
+__device__ __forceinline__ float le_mask(float a, float b) {
+    float r;
+    asm("set.le.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 
 template <int R>
 struct RowTag {
@@ -76,13 +103,12 @@ struct RowTag {
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
-// s = 0.5 log2(e) d^2 of a lane's two pixels at offsets (dx, dy.x) and
-// (dx, dy.y) from the mean, with the Cholesky factor m of 0.5 log2(e)
-// Sigma'^-1.  Round-to-nearest throughout: the forward and the backward take
-// bit-identical decisions.
-__device__ __forceinline__ float2 pair_s2(float2 m00dx, float2 dy, float2 m01, float2 m11, float2 &p1, float2 &p2) {
-    p1 = __ffma2_rn(m01, dy, m00dx);
-    p2 = __fmul2_rn(m11, dy);
+// s of a lane's two pixels, at rows ly.x and ly.y of one column: t = m00 x +
+// a (the same for both pixels) comes from the caller, once per entry.
+__device__ __forceinline__ float2 pair_s2(float2 t, float2 ly, float2 m01, float2 m11, float2 b, float2 &p1,
+                                          float2 &p2) {
+    p1 = __ffma2_rn(m01, ly, t);
+    p2 = __ffma2_rn(m11, ly, b);
     return __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
 }
 
@@ -96,15 +122,21 @@ struct BwdBlock {
     static constexpr int MIN_BLOCKS = 768 / BlendShape<TS, H>::THREADS;
 };
 
-// Forward block height: 8 rows (16 measured slower: the forward has no
-// per-Gaussian reduction to share, and its taller blocks cull less).
-template <int TS>
+// Forward block height: 16 rows (two packed row pairs per lane) when the
+// tile is at least that tall, as in the backward: the per-entry work that
+// does not depend on the pixel (shared loads, the linear forms' constant,
+// the stop vote, the loop) and the staging then serve twice the pixels.
+// The median-depth variant keeps one row pair per lane: its per-pixel
+// median state would not fit the registers of two.
+template <int TS, bool MED>
 struct FwdBlock {
-    static constexpr int H = kSubH;
-    // 36 resident warps (56 registers): the measured register need of the
-    // kernel; the compiler's own choice of 58 would round to 64 and leave 32
-    static constexpr int MIN_BLOCKS =
-        1152 / BlendShape<TS, H>::THREADS < 32 ? 1152 / BlendShape<TS, H>::THREADS : 32;
+    static constexpr int H = TS >= 16 && !MED ? 16 : kSubH;
+    // resident warps: 32 (64 registers) with two row pairs per lane, 36 (56
+    // registers) with one
+    static constexpr int WARPS_PER_SM = H == 16 ? 32 : 36;
+    static constexpr int MIN_BLOCKS = WARPS_PER_SM * 32 / BlendShape<TS, H>::THREADS < 32
+                                          ? WARPS_PER_SM * 32 / BlendShape<TS, H>::THREADS
+                                          : 32;
 };
 
 // Whether min over the warp's block of pixel centres of s can reach s_max.
@@ -269,103 +301,146 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 // with the expressions of the stand-alone L1 kernel, so that the gradients
 // match it bit for bit.
 //
-// A lane's two pixels (rows y and y + 4 of its column) run as one packed
-// FP32 pair, without branches: a pixel that an entry does not reach, or that
-// has stopped, composites it with w = 0, which leaves its sums unchanged.
-// The staged entries hold the operands that both pixels use as duplicated
-// pairs (as in the backward), so one 128-bit shared load yields two ready
-// register pairs.
+// A lane's two pixels (rows y and y + 4 of its column) share the entry's
+// scalars; the terms that are already pairs (s, alpha, w, T, the pair
+// count) run as packed FP32 pairs, without branches: a pixel that an entry
+// does not reach, or that has stopped, composites it with w = 0, which leaves
+// its sums unchanged.
 template <int TS, int CH, bool MED, bool L1>
-__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS>::H>::THREADS, FwdBlock<TS>::MIN_BLOCKS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
+__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED>::H>::THREADS, FwdBlock<TS, MED>::MIN_BLOCKS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                            const Ws ws) {
-    constexpr int BH = FwdBlock<TS>::H, NR = BH / kRowStep;
-    static_assert(NR == 2, "a lane composites one pair of rows");
+    constexpr int BH = FwdBlock<TS, MED>::H, NR = BH / kRowStep, NP = NR / 2;
     using S = BlendShape<TS, BH>;
-    // per slot: (-ur, -ur, -vr, -vr), (m00, m00, m01, m01), (m11, m11, l, l),
-    // (r, r, g, g), (b, b, z, z); sX: (s_max, list index)
-    __shared__ float4 sF[S::WARPS][kEntryQuads][32 * CH];
-    __shared__ float2 sX[S::WARPS][32 * CH];
+    __shared__ float4 sF[S::WARPS][kFwdQuads][32 * CH];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.sorted;
     const size_t vN = (size_t)wt.v * ws.N;
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
-    const float2 lx2 = make_float2(lxf, lxf);
     const float2 neg2 = make_float2(-1.f, -1.f);
 
     // A row that lies outside the view, or has met the transmittance stop,
-    // sits at an infinite row offset: its s is not finite (inf or NaN), so no
-    // entry reaches it.  T never falls below the stop, so an entry that
-    // reaches no row leaves Tn = T and cannot trigger the stop either.
+    // sits at the row offset kFar (the largest finite float): its p2 = m11
+    // kFar + b overflows (m11 > 0 is a Cholesky diagonal, far above 1e-19)
+    // and p1 is finite or infinite but never NaN, so s = +inf, which no
+    // entry reaches and whose 2^(l - s) is 0.  T never falls below the stop,
+    // so an entry that reaches no row leaves Tn = T and cannot trigger the
+    // stop either.
     const int Yr = row_origin(wt.Y0);
     const float yoff = (float)(wt.Y0 - Yr);
-    const float kInf = __int_as_float(0x7f800000);
-    float2 ly2 = make_float2(wt.px < vp.W && wt.py < vp.H ? lyf + yoff : kInf,
-                             wt.px < vp.W && wt.py + kRowStep < vp.H ? lyf + yoff + (float)kRowStep : kInf);
-    float2 T = make_float2(1.f, 1.f), C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0, D = C0, Zm = C0;
+    const float kFar = 0x1.fffffep127f;
+    // per pixel (pair p: .x row 2p, .y row 2p + 1, i.e. rows y + 8p and y + 8p + 4)
+    float2 ly[NP], T[NP], C0[NP], C1[NP], C2[NP], D[NP], Zm[NP], cnt[NP];
     // last: the list position of the entry the pixel stopped at, or the
     // list's end -- the backward's contributors are the entries before it
     // that reach the pixel (every one of them was composited)
-    uint32_t last[NR] = {wt.range.y, wt.range.y}, mi[NR] = {0u, 0u}, ncon = 0;
+    uint32_t last[NR], mi[NR];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int r0 = 2 * p * kRowStep, r1 = r0 + kRowStep;
+        ly[p] = make_float2(wt.px < vp.W && wt.py + r0 < vp.H ? lyf + yoff + (float)r0 : kFar,
+                            wt.px < vp.W && wt.py + r1 < vp.H ? lyf + yoff + (float)r1 : kFar);
+        T[p] = make_float2(1.f, 1.f);
+        C0[p] = C1[p] = C2[p] = D[p] = Zm[p] = cnt[p] = make_float2(0.f, 0.f);   // cnt: composited pairs (exact in FP32)
+        last[2 * p] = last[2 * p + 1] = wt.range.y;
+        mi[2 * p] = mi[2 * p + 1] = 0u;
+    }
+    const float4(&F)[kFwdQuads][32 * CH] = sF[warp];
+    auto all_stopped = [&]() {
+        bool far = true;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) far = far && ly[p].x == kFar && ly[p].y == kFar;
+        return __all_sync(kFull, far);
+    };
+
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32 * CH) {
-        if (__all_sync(kFull, ly2.x == kInf && ly2.y == kInf)) break;
+        if (all_stopped()) break;
+        bool clamp_chunk = false;
         const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0, Yr,
-                                      [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
-                                          uint32_t idx, uint32_t) {
-                                          float4(&e)[kEntryQuads][32 * CH] = sF[warp];
-                                          e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
-                                          e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
-                                          e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
-                                          e[3][slot] = make_float4(r2.x, r2.x, r2.y, r2.y);
-                                          e[4][slot] = make_float4(r2.z, r2.z, r2.w, r2.w);
-                                          sX[warp][slot] = make_float2(r1.w, __uint_as_float(idx));
-                                      });
+                                          [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
+                                              uint32_t idx, uint32_t) {
+                                              float a, b;
+                                              lin_consts(ur, vr, r1.x, r1.y, r1.z, a, b);
+                                              clamp_chunk |= log2o > kLog2ClampFree;
+                                              sF[warp][0][slot] = make_float4(r1.x, a, r1.y, r1.z);
+                                              sF[warp][1][slot] = make_float4(b, r1.w, log2o, __uint_as_float(idx));
+                                              sF[warp][2][slot] = r2;
+                                          });
+        // the entries in list order, with the stop rule
+        auto run = [&](auto clamp) {
 #pragma unroll 2
-        for (int j = 0; j < n; ++j) {
-            const float4 e0 = sF[warp][0][j], e1 = sF[warp][1][j], e2 = sF[warp][2][j];
-            const float2 x = sX[warp][j];
-            const float2 m00dx = __fmul2_rn(lo2(e1), __fadd2_rn(lx2, lo2(e0)));
-            const float2 dy = __fadd2_rn(ly2, hi2(e0));
-            float2 p1, p2;
-            const float2 s = pair_s2(m00dx, dy, hi2(e1), lo2(e2), p1, p2);
-            const bool c0 = s.x <= x.x, c1 = s.y <= x.x;           // the entry reaches the pixel
-            const float2 arg = __ffma2_rn(s, neg2, hi2(e2));    // log2(sigma) - s
-            const float2 al = make_float2(c0 ? fminf(kAlphaMax, ex2_approx(arg.x)) : 0.f,
-                                          c1 ? fminf(kAlphaMax, ex2_approx(arg.y)) : 0.f);
-            float2 w = __fmul2_rn(al, T);
-            float2 Tn = __ffma2_rn(w, neg2, T);                    // T (1 - alpha)
-            ncon += (uint32_t)c0 + (uint32_t)c1;
-            const bool st0 = Tn.x < kTStop, st1 = Tn.y < kTStop;   // stop before this entry
-            const float4 e3 = sF[warp][3][j], e4 = sF[warp][4][j];
-            if (MED) {   // a stopping entry has T < 0.01, so c is enough here
-                const uint32_t id1 = __float_as_uint(x.y) + 1u;
-                if (c0 && T.x > 0.5f) Zm.x = e4.z, mi[0] = id1;
-                if (c1 && T.y > 0.5f) Zm.y = e4.z, mi[1] = id1;
+            for (int j = 0; j < n; ++j) {
+                const float4 q0 = F[0][j], q1 = F[1][j];
+                // s with the same FP32 operations as the backward
+                const float t = __fmaf_rn(q0.x, lxf, q0.y);                     // m00 x + a
+                float2 w[NP], Tn[NP], m[NP];
+                bool st = false;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float2 p1 = make_float2(__fmaf_rn(q0.z, ly[p].x, t), __fmaf_rn(q0.z, ly[p].y, t));
+                    const float2 p2 = make_float2(__fmaf_rn(q0.w, ly[p].x, q1.x), __fmaf_rn(q0.w, ly[p].y, q1.x));
+                    const float2 s = __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
+                    m[p] = make_float2(le_mask(s.x, q1.y), le_mask(s.y, q1.y));   // the entry reaches the pixel
+                    // alpha = min(0.99, 2^(log2(sigma) - s)), times the mask;
+                    // chunks whose Gaussians all lie below kLog2ClampFree skip the clamp
+                    float2 e = make_float2(ex2_approx(__fmaf_rn(s.x, -1.f, q1.z)),
+                                           ex2_approx(__fmaf_rn(s.y, -1.f, q1.z)));
+                    if constexpr (decltype(clamp)::value) e = make_float2(fminf(kAlphaMax, e.x), fminf(kAlphaMax, e.y));
+                    w[p] = __fmul2_rn(__fmul2_rn(e, m[p]), T[p]);
+                    Tn[p] = __ffma2_rn(w[p], neg2, T[p]);                    // T (1 - alpha)
+                    st = st || Tn[p].x < kTStop || Tn[p].y < kTStop;          // stop before this entry
+                }
+                if (MED) {   // a stopping entry has T < 0.01, so the reach mask is enough here
+                    const uint32_t id1 = __float_as_uint(q1.w) + 1u;
+                    const float z = F[2][j].w;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (m[p].x != 0.f && T[p].x > 0.5f) Zm[p].x = z, mi[2 * p] = id1;
+                        if (m[p].y != 0.f && T[p].y > 0.5f) Zm[p].y = z, mi[2 * p + 1] = id1;
+                    }
+                }
+                if (__builtin_expect(__any_sync(kFull, st), 0)) {
+                    // a pixel of the warp meets the stop; it keeps its T and
+                    // takes nothing more (its row moves to the far offset)
+                    const uint32_t idx = __float_as_uint(q1.w);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (Tn[p].x < kTStop) w[p].x = 0.f, Tn[p].x = T[p].x, ly[p].x = kFar, last[2 * p] = idx, m[p].x = 0.f;
+                        if (Tn[p].y < kTStop)
+                            w[p].y = 0.f, Tn[p].y = T[p].y, ly[p].y = kFar, last[2 * p + 1] = idx, m[p].y = 0.f;
+                    }
+                }
+                const float4 q2 = F[2][j];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    cnt[p] = __fadd2_rn(cnt[p], m[p]);
+                    C0[p].x = __fmaf_rn(w[p].x, q2.x, C0[p].x), C0[p].y = __fmaf_rn(w[p].y, q2.x, C0[p].y);
+                    C1[p].x = __fmaf_rn(w[p].x, q2.y, C1[p].x), C1[p].y = __fmaf_rn(w[p].y, q2.y, C1[p].y);
+                    C2[p].x = __fmaf_rn(w[p].x, q2.z, C2[p].x), C2[p].y = __fmaf_rn(w[p].y, q2.z, C2[p].y);
+                    D[p].x = __fmaf_rn(w[p].x, q2.w, D[p].x), D[p].y = __fmaf_rn(w[p].y, q2.w, D[p].y);
+                    T[p] = Tn[p];
+                }
             }
-            if (__builtin_expect(__any_sync(kFull, st0 || st1), 0)) {
-                // rare: a pixel of the warp meets the stop; it keeps its T and
-                // takes nothing more (its row moves to the infinite offset)
-                const uint32_t idx = __float_as_uint(x.y);
-                if (st0) w.x = 0.f, Tn.x = T.x, ly2.x = kInf, last[0] = idx, --ncon;
-                if (st1) w.y = 0.f, Tn.y = T.y, ly2.y = kInf, last[1] = idx, --ncon;
-                C0 = __ffma2_rn(w, lo2(e3), C0);
-                C1 = __ffma2_rn(w, hi2(e3), C1);
-                C2 = __ffma2_rn(w, lo2(e4), C2);
-                D = __ffma2_rn(w, hi2(e4), D);
-                T = Tn;
-                continue;
-            }
-            C0 = __ffma2_rn(w, lo2(e3), C0);
-            C1 = __ffma2_rn(w, hi2(e3), C1);
-            C2 = __ffma2_rn(w, lo2(e4), C2);
-            D = __ffma2_rn(w, hi2(e4), D);
-            T = Tn;
-        }
+        };
+        if (__any_sync(kFull, clamp_chunk))
+            run(std::true_type{});
+        else
+            run(std::false_type{});
         __syncwarp();
     }
-    const float Ta[NR] = {T.x, T.y}, C0a[NR] = {C0.x, C0.y}, C1a[NR] = {C1.x, C1.y}, C2a[NR] = {C2.x, C2.y},
-                Da[NR] = {D.x, D.y}, Zma[NR] = {Zm.x, Zm.y};
+    uint32_t ncon = 0;
+    float Ta[NR], C0a[NR], C1a[NR], C2a[NR], Da[NR], Zma[NR];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        ncon += (uint32_t)cnt[p].x + (uint32_t)cnt[p].y;
+        Ta[2 * p] = T[p].x, Ta[2 * p + 1] = T[p].y;
+        C0a[2 * p] = C0[p].x, C0a[2 * p + 1] = C0[p].y;
+        C1a[2 * p] = C1[p].x, C1a[2 * p + 1] = C1[p].y;
+        C2a[2 * p] = C2[p].x, C2a[2 * p + 1] = C2[p].y;
+        Da[2 * p] = D[p].x, Da[2 * p + 1] = D[p].y;
+        Zma[2 * p] = Zm[p].x, Zma[2 * p + 1] = Zm[p].y;
+    }
     // L1: the targets of the lane's pixels, loaded together before any store
     // (a store to a gradient image could otherwise alias the next load)
     float tgt[L1 ? NR : 1][4];
@@ -482,7 +557,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     constexpr int BH = BwdBlock<TS>::H;
     constexpr int NR = BH / kRowStep, NP = NR / 2;
     using S = BlendShape<TS, BH>;
-    __shared__ float4 sE[S::WARPS][kEntryQuads][32 * CH];
+    __shared__ float4 sE[S::WARPS][kBwdQuads][32 * CH];
     __shared__ float4 sX[S::WARPS][32 * CH];  // (s_max, list index, Gaussian index, -)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
@@ -545,7 +620,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
         const int n = stage_chunk<BH, CH>(ws, vals, vN, begin, end, wt.X0, wt.Y0, Yr,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t g) {
-                                          float4(&e)[kEntryQuads][32 * CH] = sE[warp];
+                                          float4(&e)[kBwdQuads][32 * CH] = sE[warp];
                                           e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
                                           e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
                                           e[2][slot] = make_float4(r1.z, r1.z, log2o, log2o);
@@ -558,8 +633,12 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
             const float4 x = sX[warp][j];
             const uint32_t eidx = __float_as_uint(x.y);
-            const float2 dx = __fadd2_rn(lx2, lo2(e0));
-            const float2 m00dx = __fmul2_rn(lo2(e1), dx);
+            const float dx = __fadd_rn(lxf, e0.x);                    // the gradient's column offset
+            // the constants a, b of lin_consts, and t = m00 x + a: the same
+            // FP32 operations as the forward (negation is exact)
+            const float2 a2 = __ffma2_rn(hi2(e1), hi2(e0), __fmul2_rn(lo2(e1), lo2(e0)));
+            const float2 b2 = __fmul2_rn(lo2(e2), hi2(e0));
+            const float2 t = __ffma2_rn(lo2(e1), lx2, a2);
             float2 dy[NP], s[NP], p1[NP], p2[NP];
             bool c[NR];
             unsigned m[NR], cmask = 0u;
@@ -568,7 +647,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 const float2 ly = make_float2(lyf + yoff + (float)(2 * p * kRowStep),
                                               lyf + yoff + (float)((2 * p + 1) * kRowStep));
                 dy[p] = __fadd2_rn(ly, hi2(e0));
-                s[p] = pair_s2(m00dx, dy[p], hi2(e1), lo2(e2), p1[p], p2[p]);
+                s[p] = pair_s2(t, ly, hi2(e1), lo2(e2), b2, p1[p], p2[p]);
                 c[2 * p] = eidx < last[2 * p] && s[p].x <= x.x;
                 c[2 * p + 1] = eidx < last[2 * p + 1] && s[p].y <= x.x;
                 m[2 * p] = __ballot_sync(kFull, c[2 * p]);
@@ -683,7 +762,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             float gv[kVGGrads];
             gv[0] = A[0].x + A[0].y;                                    // du, dv follow from these and m
             gv[1] = A[1].x + A[1].y;
-            gv[2] = dx.x * gv[0];
+            gv[2] = dx * gv[0];
 #pragma unroll
             for (int k = 3; k < kVGGrads; ++k) gv[k] = A[k].x + A[k].y;
             if (MED) {
@@ -717,16 +796,17 @@ template <int TS, int CH>
 cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
-    constexpr int T = BlendShape<TS, FwdBlock<TS>::H>::THREADS;
+    constexpr int TM = BlendShape<TS, FwdBlock<TS, true>::H>::THREADS;    // with median depth
+    constexpr int TP = BlendShape<TS, FwdBlock<TS, false>::H>::THREADS;   // without
     const bool l1 = vt.l1_loss != nullptr;
     if (med && l1)
-        blend_fwd_kernel<TS, CH, true, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, true><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
     else if (med)
-        blend_fwd_kernel<TS, CH, true, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, false><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
     else if (l1)
-        blend_fwd_kernel<TS, CH, false, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, true><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, CH, false, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, false><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
