@@ -149,7 +149,7 @@ __device__ __forceinline__ bool touches_block(float ur, float vr, float m00, flo
     const float dx0 = -ur, dx1 = (float)(kSubW - 1) - ur;
     const float dy0 = -vr, dy1 = (float)(BH - 1) - vr;
     const float a0 = m00 * dx0, a1 = m00 * dx1;
-    const float inv_den = 1.0f / (m01 * m01 + m11 * m11);
+    const float inv_den = rcp_approx(m01 * m01 + m11 * m11);   // m11 > 0
     auto f = [&](float dy) {
         const float t = m01 * dy;
         const float p = fmaxf(0.f, fmaxf(a0 + t, -(a1 + t)));

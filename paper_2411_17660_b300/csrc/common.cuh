@@ -212,13 +212,19 @@ __device__ __forceinline__ void dot3_plus(float w0, float w1, float w2, float t,
 }
 
 // f*(xh+xl)/(zh+zl) + c as hi + lo (double-float), for pixel coordinates
-// whose fractional part must survive |u| up to thousands of pixels.
-__device__ __forceinline__ void project_coord(float f, float c, float xh, float xl, float zh, float zl,
+// whose fractional part must survive |u| up to thousands of pixels.  rz is
+// an approximation of 1/zh (rcp.approx: within about one unit in the last
+// place): the quotient's high part q1 = xh rz is then within a few units of
+// xh/zh, the FMA forms its remainder xh - q1 zh with an error of about
+// 2^-46 |xh| at most, and the low part q2 = remainder rz corrects q1, so
+// q1 + q2 carries the quotient to about 2^-44 -- far below the 2^-24 of the
+// pixel coordinate's low part.
+__device__ __forceinline__ void project_coord(float f, float c, float xh, float xl, float zh, float zl, float rz,
                                               float &hi, float &lo) {
-    const float q1 = __fdiv_rn(xh, zh);
-    float r = __fmaf_rn(-q1, zh, xh);          // exact remainder xh - q1*zh
+    const float q1 = __fmul_rn(xh, rz);
+    float r = __fmaf_rn(-q1, zh, xh);          // remainder xh - q1*zh
     r = __fadd_rn(r, __fsub_rn(xl, __fmul_rn(q1, zl)));
-    const float q2 = __fdiv_rn(r, zh);
+    const float q2 = __fmul_rn(r, rz);
     float p, pe;
     two_prod(f, q1, p, pe);
     pe = __fmaf_rn(f, q2, pe);
@@ -252,6 +258,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

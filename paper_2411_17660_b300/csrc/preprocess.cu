@@ -22,6 +22,8 @@ namespace gsr {
 
 constexpr int kPreWarps = 8;
 constexpr int kPreThreads = 32 * kPreWarps;
+// Resident blocks per SM of the forward kernel (its register budget).
+constexpr int kPreFwdBlocksPerSM = 3;
 
 // ------------------------------------------------------------------ forward
 // Warp-queue forward: persistent warps take batches of 32 Gaussians (one per
@@ -130,7 +132,7 @@ __device__ __forceinline__ bool preprocess_fwd_pair(const ViewTable &vt, const G
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
+__global__ void __launch_bounds__(kPreThreads, kPreFwdBlocksPerSM) preprocess_fwd_kernel(const __grid_constant__ ViewTable vt,
                                                                      const GaussianPtrs gp, const Ws ws,
                                                                      int item_views) {
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
@@ -171,8 +173,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
                 const ViewParams &vp = vt.v[v];
                 float rad = 0.f;
                 if (G.alive && project_view(G, s_pose[v], vp, p)) {
-                    project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, uh, ul);
-                    project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, vh, vl);
+                    project_coord(vp.fx, vp.cx, p.xh, p.xl, p.zh, p.zl, p.rz, uh, ul);
+                    project_coord(vp.fy, vp.cy, p.yh, p.yl, p.zh, p.zl, p.rz, vh, vl);
                     vis = isfinite(uh) && isfinite(vh);
                     // densification visibility: the cutoff ellipse meets the
                     // rectangle of pixel centres.  The same minimum, with the
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_fwd_kernel(const __
                 // the SH view direction, from the camera centre to the mean
                 const Pose &ps = s_pose[v];
                 float dx = G.mx - ps.C[0], dy = G.my - ps.C[1], dz = G.mz - ps.C[2];
-                const float rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+                const float rn = rsqrt_approx(dx * dx + dy * dy + dz * dz);
                 q.dx[k] = dx * rn;
                 q.dy[k] = dy * rn;
                 q.dz[k] = dz * rn;
@@ -356,7 +358,7 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
 
     // pixel mean and depth: the blend returns the sums of dL/dp1 and dL/dp2
     // (p = m d, d = pixel - mean), so dL/du = -m00 S1, dL/dv = -(m01 S1 + m11 S2)
-    const float x = p.xh, y = p.yh, z = p.zh, rz = 1.0f / z;
+    const float x = p.xh, y = p.yh, z = p.zh, rz = p.rz;
     const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
     const float dvv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
     dpc[0] += du * vp.fx * rz;
@@ -364,9 +366,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     dpc[2] += -(du * vp.fx * x + dvv * vp.fy * y) * rz * rz + sg[9];
 
     // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
-    const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = 1.0f / det, iC = 1.0f / C;
+    const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = rcp_approx(det), iC = rcp_approx(C);
     const float dl00 = kSqrtHalfLog2e * sg[2], dl01 = kSqrtHalfLog2e * sg[3], dl11 = kSqrtHalfLog2e * sg[4];
-    const float rdc = 1.0f / sqrtf(det * C);
+    const float rdc = rsqrt_approx(det * C);
     const float dA = -0.5f * C * idet * (dl00 * p.l00 + dl01 * p.l01);
     const float dB = dl00 * p.l00 * B * idet + dl01 * (p.l01 * B * idet - rdc);
     const float dC = dl00 * 0.5f * p.l00 * (iC - A * idet) - dl01 * 0.5f * p.l01 * (A * idet + iC) -
@@ -804,8 +806,6 @@ cudaError_t launch_pose_reduce(const ViewTable &vt, const Ws &ws, int accumulate
     return cudaGetLastError();
 }
 
-// Resident blocks per SM of the forward kernel (registers allow 3).
-constexpr int kPreFwdBlocksPerSM = 3;
 
 template <int DEG>
 static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, const Ws &ws, int sm_count,

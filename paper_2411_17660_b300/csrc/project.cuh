@@ -63,11 +63,13 @@ __device__ __forceinline__ void gauss_pre(const GaussianPtrs &gp, int g, GaussPr
               isfinite(G.s[0] + G.s[1] + G.s[2]) && qn2 > 0.f && isfinite(qn2);
 }
 
-// Camera pose in shared memory: W row-major (9), t (3), centre C = -W^T t (3).
+// Camera pose in shared memory: W row-major (9), t (3), centre C = -W^T t
+// (3), and the view's Jacobian clamp limits on x/z and y/z.
 struct Pose {
     float W[3][3];
     float t[3];
     float C[3];
+    float limx, limy;
 };
 
 // dL/dq of the raw quaternion from dL/dR of R(q / |q|).
@@ -101,6 +103,9 @@ __device__ __forceinline__ void load_poses(const ViewTable &vt, Pose *s_pose) {
     if (threadIdx.x < (unsigned)vt.V) {
         Pose &p = s_pose[threadIdx.x];
         for (int j = 0; j < 3; ++j) p.C[j] = -(p.W[0][j] * p.t[0] + p.W[1][j] * p.t[1] + p.W[2][j] * p.t[2]);
+        const ViewParams &vp = vt.v[threadIdx.x];
+        p.limx = kFovClamp * 0.5f * (float)vp.W / vp.fx;
+        p.limy = kFovClamp * 0.5f * (float)vp.H / vp.fy;
     }
     __syncthreads();
 }
@@ -111,7 +116,7 @@ __device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, floa
     dx = G.mx - ps.C[0];
     dy = G.my - ps.C[1];
     dz = G.mz - ps.C[2];
-    rn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    rn = rsqrt_approx(dx * dx + dy * dy + dz * dz);
     dx *= rn;
     dy *= rn;
     dz *= rn;
@@ -121,6 +126,7 @@ __device__ __forceinline__ void view_dir(const GaussPre &G, const Pose &ps, floa
 
 struct Proj {
     float xh, yh, zh, xl, yl, zl;  // camera-frame mean, hi + lo
+    float rz;                      // 1/zh (rcp.approx)
     bool clx, cly;
     float txz, tyz;                // clamped x/z, y/z
     float J00, J02, J11, J12;
@@ -139,9 +145,9 @@ __device__ __forceinline__ bool project_view(const GaussPre &G, const Pose &ps, 
     dot3_plus(ps.W[2][0], ps.W[2][1], ps.W[2][2], ps.t[2], G.mx, G.my, G.mz, p.zh, p.zl);
     const float z = p.zh;
     if (!(z > kNearZ) || !isfinite(z)) return false;
-    const float limx = kFovClamp * 0.5f * (float)vp.W / vp.fx;
-    const float limy = kFovClamp * 0.5f * (float)vp.H / vp.fy;
-    const float rz = 1.0f / z;
+    const float limx = ps.limx, limy = ps.limy;
+    const float rz = rcp_approx(z);
+    p.rz = rz;
     float tx = p.xh * rz, ty = p.yh * rz;
     p.clx = (tx < -limx) || (tx > limx);
     p.cly = (ty < -limy) || (ty > limy);
@@ -170,9 +176,13 @@ __device__ __forceinline__ bool project_view(const GaussPre &G, const Pose &ps, 
     p.syy = c0 + kDilation;
     p.det = (m01 * m01 + m02 * m02 + m12 * m12) + kDilation * (a0 + c0) + kDilation * kDilation;
     if (!(p.det > 0.f) || !isfinite(p.det) || !isfinite(p.sxx + p.syy + p.sxy)) return false;
-    p.l11 = 1.0f / sqrtf(p.syy);
-    p.l00 = sqrtf(p.syy / p.det);
-    p.l01 = -p.sxy / sqrtf(p.det * p.syy);
+    // l11 = 1/sqrt(Syy), l00 = sqrt(Syy/det) = Syy / sqrt(det Syy),
+    // l01 = -Sxy / sqrt(det Syy), from two approximate reciprocal square roots
+    // (a few units in the last place)
+    const float rds = rsqrt_approx(p.det * p.syy);
+    p.l11 = rsqrt_approx(p.syy);
+    p.l00 = p.syy * rds;
+    p.l01 = -p.sxy * rds;
     return isfinite(p.l00) && isfinite(p.l01);
 }
 
@@ -184,7 +194,7 @@ __device__ __forceinline__ bool project_view(const GaussPre &G, const Pose &ps, 
 __device__ __forceinline__ float quad_min_over_box(float dx0, float dx1, float dy0, float dy1, float m00, float m01,
                                                    float m11) {
     const float a0 = m00 * dx0, a1 = m00 * dx1;
-    const float inv_den = 1.0f / (m01 * m01 + m11 * m11);
+    const float inv_den = rcp_approx(m01 * m01 + m11 * m11);   // m11 > 0
     auto f = [&](float dy) {
         const float t = m01 * dy;
         const float p = fmaxf(0.f, fmaxf(a0 + t, -(a1 + t)));

@@ -34,12 +34,13 @@ __device__ __forceinline__ uint32_t visit_tile_spans(float u, float v, float sxx
     yhi = fminf(yhi, (float)(H - 1));
     if (!(ylo <= yhi)) return 0u;
     const int py0 = (int)ylo, py1 = (int)yhi;
+    const int tsh = 31 - __clz(TS);   // TS is a power of two; the coordinates are >= 0
     const float isyy = rcp_approx(syy);
     const float kx = __fmul_rn(sxy, isyy);
     const float sc = __fmul_rn(kHalfLog2e, rcp_approx(__fmul_rn(m00, m00)));   // det/Syy, from the stable factor
     const float dyp = __fmul_rn(__fmul_rn(sxy, sqrt_approx(r2)), rcp_approx(sqrt_approx(sxx)));
     uint32_t count = 0;
-    for (int ty = py0 / TS; ty <= py1 / TS; ++ty) {
+    for (int ty = py0 >> tsh; ty <= py1 >> tsh; ++ty) {
         const int yb0 = max(ty * TS, py0), yb1 = min(ty * TS + TS - 1, py1);
         const float dy0 = __fsub_rn((float)yb0, v), dy1 = __fsub_rn((float)yb1, v);
         const float dyr = fminf(fmaxf(dyp, dy0), dy1);
@@ -53,7 +54,7 @@ __device__ __forceinline__ uint32_t visit_tile_spans(float u, float v, float sxx
         xlo = fmaxf(xlo, 0.f);
         xhi = fminf(xhi, (float)(W - 1));
         if (!(xlo <= xhi)) continue;
-        const int tx0 = (int)xlo / TS, tx1 = (int)xhi / TS;
+        const int tx0 = (int)xlo >> tsh, tx1 = (int)xhi >> tsh;
         f(ty, tx0, tx1);
         count += (uint32_t)(tx1 - tx0 + 1);
     }

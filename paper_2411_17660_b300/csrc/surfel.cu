@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(128) surfel_pre_fwd_kernel(const __grid_consta
             const float zmin = z - 3.f * sqrtf(a[2] * a[2] + b[2] * b[2]);
             if (z > kNearZ && zmin > kNearZ && isfinite(zmin)) {
                 float uh, ul, vh, vl;
-                project_coord(vp.fx, vp.cx, xh, xl, zh, zl, uh, ul);
-                project_coord(vp.fy, vp.cy, yh, yl, zh, zl, vh, vl);
+                const float rzh = rcp_approx(zh);
+                project_coord(vp.fx, vp.cx, xh, xl, zh, zl, rzh, uh, ul);
+                project_coord(vp.fy, vp.cy, yh, yl, zh, zl, rzh, vh, vl);
                 // the screen region rho3 <= d2max: the projected circle u^2 + v^2 = d2max, bounded
                 // by its dual conic D = M diag(d2max, d2max, -1) M^T with M taken relative to the
                 // projected centre (its first two rows then have no p column)
