@@ -117,9 +117,10 @@ __device__ __forceinline__ float2 pair_s2(float2 t, float2 ly, float2 m01, float
 template <int TS>
 struct BwdBlock {
     static constexpr int H = TS >= 16 ? 16 : kSubH;
-    // resident blocks per SM asked of the compiler: 24 warps, 80 registers
-    // (measured faster than the uncapped 115 with their lower occupancy)
-    static constexpr int MIN_BLOCKS = 768 / BlendShape<TS, H>::THREADS;
+    // resident blocks per SM asked of the compiler: 28 warps, 72 registers
+    // (window: 0.2340 ms against 0.2356 with 24 warps at 80 registers; the
+    // uncapped 115 registers, with their lower occupancy, were slower still)
+    static constexpr int MIN_BLOCKS = 896 / BlendShape<TS, H>::THREADS;
 };
 
 // Forward block height: 16 rows (two packed row pairs per lane) when the
@@ -184,9 +185,9 @@ __device__ __forceinline__ void butterfly_level(const float *in, float *out, int
 }
 
 // Sums 10 per-lane values over the warp with 12 shuffles (instead of 50):
-// afterwards lane l holds the total of component comp (valid = true) and
-// its partner lane l^1 holds the same total.
-__device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane, int &comp, bool &valid) {
+// afterwards lane l holds the total of component sum10_slot(l) (where that
+// slot is valid), and its partner lane l^1 holds the same total.
+__device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane) {
     static_assert(kVGGrads == 10, "butterfly is laid out for 10 values");
     float a[5], b[3], c[2];
     butterfly_level<10, 16>(v, a, lane);
@@ -195,6 +196,13 @@ __device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane
     float d;
     butterfly_level<2, 2>(c, &d, lane);
     d += __shfl_xor_sync(kFull, d, 1);
+    return d;
+}
+
+// The component that warp_sum10 leaves in lane `lane`, and whether it is one
+// (the halving of 10 values leaves some lanes without a component); it
+// depends on the lane alone, so callers form it once.
+__device__ __forceinline__ void sum10_slot(int lane, int &comp, bool &valid) {
     int base = 0, left = 10;
     const int lev[4] = {16, 8, 4, 2}, half[4] = {5, 3, 2, 1};
 #pragma unroll
@@ -208,7 +216,6 @@ __device__ __forceinline__ float warp_sum10(const float (&v)[kVGGrads], int lane
     }
     comp = base;
     valid = left == 1;
-    return d;
 }
 
 // Both blends form a pixel's row offset from the mean relative to the last
@@ -609,6 +616,17 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
         Q[p] = make_float2(0.f, 0.f);
     }
     const uint32_t wlast = __reduce_max_sync(kFull, lmax);
+    // the lane's component of the warp sums, and whether it writes it (one
+    // lane of each partner pair)
+    int sum_comp;
+    bool sum_writer;
+    sum10_slot(lane, sum_comp, sum_writer);
+    sum_writer = sum_writer && (lane & 1) == 0;
+    // the lane's row offsets from the origin, per pair
+    float2 lyp[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+        lyp[p] = make_float2(lyf + yoff + (float)(2 * p * kRowStep), lyf + yoff + (float)((2 * p + 1) * kRowStep));
 #ifdef GSR_CHECKED
     unsigned long long nbwd = 0;   // the contributor pairs this warp takes (the same in every lane)
 #endif
@@ -617,9 +635,11 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
 
     for (uint32_t end = wlast; end > wt.range.x;) {
         const uint32_t begin = end - wt.range.x > 32u * CH ? end - 32u * CH : wt.range.x;
+        bool clamp_chunk = false;
         const int n = stage_chunk<BH, CH>(ws, vals, vN, begin, end, wt.X0, wt.Y0, Yr,
                                       [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
                                           uint32_t idx, uint32_t g) {
+                                          clamp_chunk |= log2o > kLog2ClampFree;
                                           float4(&e)[kBwdQuads][32 * CH] = sE[warp];
                                           e[0][slot] = make_float4(-ur, -ur, -vr, -vr);
                                           e[1][slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
@@ -629,7 +649,9 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                                           sX[warp][slot] = make_float4(r1.w, __uint_as_float(idx),
                                                                        __uint_as_float(g), 0.f);
                                       });
-        for (int j = n - 1; j >= 0; --j) {
+        // entry j; CLAMP: the chunk holds a Gaussian that can reach the alpha clamp
+        auto entry = [&](int j, auto clamp) {
+            constexpr bool CLAMP = decltype(clamp)::value;
             const float4 e0 = sE[warp][0][j], e1 = sE[warp][1][j], e2 = sE[warp][2][j];
             const float4 x = sX[warp][j];
             const uint32_t eidx = __float_as_uint(x.y);
@@ -644,8 +666,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
             unsigned m[NR], cmask = 0u;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const float2 ly = make_float2(lyf + yoff + (float)(2 * p * kRowStep),
-                                              lyf + yoff + (float)((2 * p + 1) * kRowStep));
+                const float2 ly = lyp[p];
                 dy[p] = __fadd2_rn(ly, hi2(e0));
                 s[p] = pair_s2(t, ly, hi2(e1), lo2(e2), b2, p1[p], p2[p]);
                 c[2 * p] = eidx < last[2 * p] && s[p].x <= x.x;
@@ -654,7 +675,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 m[2 * p + 1] = __ballot_sync(kFull, c[2 * p + 1]);
                 cmask |= m[2 * p] | m[2 * p + 1];
             }
-            if (cmask == 0u) continue;
+            if (cmask == 0u) return;
 #ifdef GSR_CHECKED
 #pragma unroll
             for (int r = 0; r < NR; ++r) nbwd += (unsigned long long)__popc(m[r]);
@@ -668,7 +689,8 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 const float2 arg = __ffma2_rn(s[p], neg2, hi2(e2));
                 const float2 raw = make_float2(c[2 * p] ? ex2_approx(arg.x) : 0.f,
                                                c[2 * p + 1] ? ex2_approx(arg.y) : 0.f);
-                const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                float2 al = raw;
+                if constexpr (CLAMP) al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
                 const float2 om = __ffma2_rn(al, neg2, one2);
                 const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
                 const float2 Ti = __fmul2_rn(T[p], rom);
@@ -684,17 +706,19 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 T[p] = Ti;
                 // no gradient to position or opacity through the 0.99 clamp
                 glo = __fmul2_rn(dA, raw);                              // dL/d ln(sigma)
-                glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
-                glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+                if constexpr (CLAMP) {
+                    glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
+                    glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
+                }
                 const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
                 dp1 = __fmul2_rn(p1[p], ds2);
                 dp2 = __fmul2_rn(p2[p], ds2);
             };
-            bool all_rows = false;
-            if constexpr (NP == 2) all_rows = m[0] != 0u && m[1] != 0u && m[2] != 0u && m[3] != 0u;
-            if (all_rows) {
-                // every row reached: both pairs in one straight run, so that
-                // their independent chains interleave
+            if constexpr (NP == 2) {
+                // both pairs in one straight run, so that their independent
+                // chains interleave (measured faster than skipping the pairs
+                // and rows the entry does not reach: that took more registers
+                // than the 80 of 24 resident warps)
                 float2 dp1[NP], dp2[NP], glo[NP], w[NP];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) packed(p, dp1[p], dp2[p], glo[p], w[p]);
@@ -731,7 +755,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                             const float gBq = R ? gB[p].y : gB[p].x, gZq = R ? gZ[p].y : gZ[p].x;
                             const float gAq = R ? gA[p].y : gA[p].x;
                             const float raw = cq ? ex2_approx(__fmaf_rn(sq, -1.f, e2.z)) : 0.f;
-                            const float al = fminf(kAlphaMax, raw);
+                            const float al = CLAMP ? fminf(kAlphaMax, raw) : raw;
                             const float rom = rcp_approx(__fmaf_rn(al, -1.f, 1.f));
                             const float Ti = Tq * rom;
                             const float wq = al * Ti;
@@ -740,7 +764,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                             const float dA = fmaf(Ti, dgq, gAq * rom);
                             Qq = fmaf(al, dgq, Qq);
                             Tq = Ti;
-                            const float gl = raw <= kAlphaMax ? dA * raw : 0.f;
+                            const float gl = !CLAMP || raw <= kAlphaMax ? dA * raw : 0.f;
                             const float ds2 = (-2.f * kLn2) * gl;
                             auto put = [](float v) { return R ? make_float2(0.f, v) : make_float2(v, 0.f); };
                             dp1 = put(p1q * ds2);
@@ -778,11 +802,14 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                     for (int k = 0; k < kVGGrads; ++k) atomicAdd(gp + k, gv[k]);
                 }
             } else {
-                int comp;
-                bool valid;
-                const float sum = warp_sum10(gv, lane, comp, valid);
-                if (valid && (lane & 1) == 0) atomicAdd(gp + comp, sum);
+                const float sum = warp_sum10(gv, lane);
+                if (sum_writer) atomicAdd(gp + sum_comp, sum);
             }
+        };
+        if (__any_sync(kFull, clamp_chunk)) {
+            for (int j = n - 1; j >= 0; --j) entry(j, std::true_type{});
+        } else {
+            for (int j = n - 1; j >= 0; --j) entry(j, std::false_type{});
         }
         __syncwarp();
         end = begin;

@@ -34,10 +34,13 @@ constexpr int kPreFwdBlocksPerSM = 3;
 // records.  Warps never wait for each other, and the expensive part runs
 // with full warps however few pairs are visible.
 constexpr int kQueue = 64;   // a warp's queue: up to 31 waiting + 32 appended
-// Views of one forward work item: 4, or 2 when 4 would leave the warps fewer
-// than kPreItemsPerWarp items each (the window: 0.060 -> 0.057 ms; 2 on the
-// 16- and 32-view workloads measured 7 % slower, 1 view per item slower still).
+// Views of one forward work item: 8, or 2 when 8 would leave the warps fewer
+// than kPreItemsPerWarp items each (the window: 0.060 -> 0.057 ms with 2
+// instead of 4; on the 16- and 32-view workloads 2 measured 7 % slower than
+// 4, 1 view per item slower still, and 8 faster than 4: uneven 0.387 ->
+// 0.372 ms, outdoor 2.406 -> 2.391 ms).
 constexpr int kPreItemsPerWarp = 4;
+constexpr int kPreItemViews = 8;
 
 struct WarpQueue {
     float uh[kQueue], vh[kQueue], ul[kQueue], vl[kQueue];
@@ -812,7 +815,8 @@ static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
                                   cudaStream_t st) {
     const long long batches = ((long long)gp.N + 31) / 32;
     const long long max_warps = (long long)sm_count * kPreFwdBlocksPerSM * kPreWarps;
-    const int item_views = batches * ((vt.V + 3) / 4) < kPreItemsPerWarp * max_warps ? 2 : 4;
+    const int item_views =
+        batches * ((vt.V + kPreItemViews - 1) / kPreItemViews) < kPreItemsPerWarp * max_warps ? 2 : kPreItemViews;
     const long long items = batches * ((vt.V + item_views - 1) / item_views);
     const long long need = (items + kPreWarps - 1) / kPreWarps;
     const unsigned blocks = (unsigned)std::min<long long>(need, (long long)sm_count * kPreFwdBlocksPerSM);
