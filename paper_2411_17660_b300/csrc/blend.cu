@@ -2,16 +2,16 @@
 // "rendering": C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j)) and its
 // back-to-front backward.
 //
-// One CTA per screen tile (all views concatenated), one warp per 8x8 block
-// of pixels in the forward (two pixels per lane) and per 8x16 block in the
-// backward (four pixels per lane, where the tile is that tall: the warp's
-// per-Gaussian reduction then serves twice the pixels).  Each warp walks its tile's depth-sorted
-// list in chunks of 32 entries: the 32 lanes load one entry each, keep only
-// the Gaussians whose cutoff ellipse reaches the warp's 8x8 block (an exact
-// convex minimum of d^2 over the block), compact the survivors into the
-// warp's shared-memory slots with a ballot, and then every lane composites
-// them for its two pixels.  A warp leaves as soon as all its lanes have hit the
-// transmittance stop; warps never wait for each other.
+// One CTA per screen tile (all views concatenated), one warp per 8x16 block
+// of pixels (four pixels per lane) where the tile is that tall, else per 8x8
+// block (two pixels per lane; also the forward's median-depth variant).
+// Each warp walks its tile's depth-sorted list in chunks of 32 entries: the
+// 32 lanes load one entry each, keep only the Gaussians whose cutoff ellipse
+// reaches the warp's block (an exact convex minimum of d^2 over the block),
+// compact the survivors into the warp's shared-memory slots with a ballot,
+// and then every lane composites them for its pixels.  A warp leaves as soon
+// as all its lanes have hit the transmittance stop; warps never wait for each
+// other.
 //
 // The backward recomputes the blend state from the stored final
 // transmittance and last contributor: walking back, T_i = T_{i+1}/(1-alpha_i)
@@ -21,13 +21,14 @@
 // of global atomics per (warp, Gaussian); when at most four lanes touch a
 // Gaussian they issue their atomics directly instead.
 //
-// A lane's pixels share their column, hence dx: the per-pixel arithmetic
-// of two of them runs on packed FP32 pairs (one fma.rn.f32x2 for both
-// pixels, the same rounding as two scalar ones, so that the forward and the
-// backward take bit-identical decisions).  The staged entries hold every
-// operand that both pixels use as a duplicated pair, so that one 128-bit
-// shared load yields two ready register pairs.  The forward runs its pair
-// without branches; the backward branches on the rows its warp reaches.
+// A lane's pixels share their column: rows y, y + 4 (and y + 8, y + 12) form
+// row pairs whose per-pixel terms run on packed FP32 pairs (fma.rn.f32x2, the
+// same rounding as two scalar operations), and both kernels form s from the
+// same linear forms, so the forward and the backward take bit-identical
+// decisions.  The forward stages each entry as plain scalars (its shared
+// loads would otherwise bound it); the backward stages duplicated operand
+// pairs, so that one 128-bit shared load yields two ready register pairs.
+// Both run their row pairs without branches.
 #include <type_traits>
 
 #include "kernels.cuh"
