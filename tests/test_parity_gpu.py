@@ -90,6 +90,50 @@ def test_transmittance_stop_forward_and_backward():
     U.compare_grads(gref, g, label="opaque stack")
 
 
+def _axis_band(seed=37, N=1500, H=60, W=96, f=70.0):
+    """Unrotated Gaussians whose means lie on the camera's y = 0 plane: their
+    projected covariances have an exactly zero off-diagonal (m01 = 0), so a
+    row that has met the stop evaluates 0 times its far row offset.  The left
+    half of the band is translucent (opacity about 0.92: its tiles' chunks skip
+    the 0.99 clamp), the right half opaque (above 0.99: clamped chunks); both
+    are dense enough that most band pixels meet the transmittance stop."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    base = scenes.config_small(seed=seed, N=N, H=H, W=W, f=f)
+    while True:
+        z = rng.uniform(2.0, 5.0, N)
+        if scenes.distinct_f32(z):
+            break
+    u = rng.uniform(-0.95, 0.95, N)
+    x = u * z * W / (2 * f)
+    logit = np.where(u < 0.0, rng.normal(2.5, 0.2, N), rng.normal(5.5, 0.3, N))
+    quats = np.zeros((4, N), np.float32)
+    quats[0] = rng.uniform(0.5, 2.0, N)   # unnormalised identity rotations
+    return dataclasses.replace(
+        base, means=np.ascontiguousarray(np.stack([x, np.zeros(N), z]).astype(np.float32)),
+        log_scales=np.ascontiguousarray(rng.normal(-2.0, 0.25, (3, N)).astype(np.float32)),
+        quats=quats, opacity_logits=np.ascontiguousarray(logit.astype(np.float32)))
+
+
+def test_stop_with_zero_off_diagonal_and_both_clamp_paths():
+    """Stopped rows with m01 = 0, and chunks with and without a Gaussian that
+    reaches the alpha clamp: finite images equal to the oracle's, forward and
+    backward, and the oracle sees both opacity ranges composited."""
+    sc = _axis_band()
+    got, state = U.gpu_forward(sc)
+    for key in ("color", "depth", "alpha"):
+        assert np.isfinite(got[0][key]).all(), key
+    ref = oracle.render(sc)
+    assert (ref[0]["T"] < 2e-4).mean() > 0.15, "band pixels should meet the stop"
+    U.compare_images(ref[0], got[0], "axis band")
+    gC, gD, gA = U.upstream(sc)
+    g = U.gpu_backward(sc, state, gC, gD, gA)
+    for k, v in g.items():
+        assert np.isfinite(v).all(), k
+    _, gref = oracle.render_backward(sc, gC, gD, gA)
+    U.compare_grads(gref, g, label="axis band")
+
+
 @pytest.mark.parametrize("tile,binning", [(8, "tile"), (16, "tile"), (32, "tile"), (16, "radix")])
 def test_decisions_backward_equals_forward(tile, binning):
     """The checked build counts the backward's contributor pairs: they are
@@ -97,7 +141,7 @@ def test_decisions_backward_equals_forward(tile, binning):
     the same FP32 operations), at every tile size, also where pixels stop."""
     if not B.LIB_PATH.endswith("libgsr_checked.so"):
         pytest.skip("the backward's pair count is kept by the checked build (tests/test_checked_gpu.py)")
-    for sc in (REDUCED["window"](), REDUCED["uneven"](), REDUCED["outdoor"](), _opaque_stack()):
+    for sc in (REDUCED["window"](), REDUCED["uneven"](), REDUCED["outdoor"](), _opaque_stack(), _axis_band()):
         _, state = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning))
         gC, gD, gA = U.upstream(sc)
         U.gpu_backward(sc, state, gC, gD, gA)
