@@ -118,10 +118,11 @@ __device__ __forceinline__ float2 pair_s2(float2 t, float2 ly, float2 m01, float
 template <int TS>
 struct BwdBlock {
     static constexpr int H = TS >= 16 ? 16 : kSubH;
-    // resident blocks per SM asked of the compiler: 28 warps, 72 registers
-    // (window: 0.2340 ms against 0.2356 with 24 warps at 80 registers; the
-    // uncapped 115 registers, with their lower occupancy, were slower still)
-    static constexpr int MIN_BLOCKS = 896 / BlendShape<TS, H>::THREADS;
+    // resident blocks per SM asked of the compiler: 24 warps, 80 registers
+    // (window: 0.2227 ms against 0.2306 with 28 warps at 72 registers, which
+    // spill; the uncapped 115 registers, with their lower occupancy, were
+    // slower still)
+    static constexpr int MIN_BLOCKS = 768 / BlendShape<TS, H>::THREADS;
 };
 
 // Forward block height: 16 rows (two packed row pairs per lane) when the
@@ -716,17 +717,29 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                 dp2 = __fmul2_rn(p2[p], ds2);
             };
             if constexpr (NP == 2) {
-                // both pairs in one straight run, so that their independent
-                // chains interleave (measured faster than skipping the pairs
-                // and rows the entry does not reach: that took more registers
-                // than the 80 of 24 resident warps)
-                float2 dp1[NP], dp2[NP], glo[NP], w[NP];
+                // Both pairs in one straight run where the entry reaches rows
+                // of both halves of the block in the warp, so that their
+                // independent chains interleave; only the reached pair where
+                // it reaches one half (a warp-uniform branch).  Rows the entry
+                // does not reach within a computed pair run with alpha = 0.
+                // (Scalar paths for single reached rows took more registers
+                // than the 80 of 24 resident warps.)
+                const bool h0 = (m[0] | m[1]) != 0u, h1 = (m[2] | m[3]) != 0u;
+                if (h0 && h1) {
+                    float2 dp1[NP], dp2[NP], glo[NP], w[NP];
 #pragma unroll
-                for (int p = 0; p < NP; ++p) packed(p, dp1[p], dp2[p], glo[p], w[p]);
-                pair_sums<true>(A, dp1[0], dp2[0], glo[0], w[0], dy[0], gR[0], gG[0], gB[0], gZ[0]);
-#pragma unroll
-                for (int p = 1; p < NP; ++p)
-                    pair_sums<false>(A, dp1[p], dp2[p], glo[p], w[p], dy[p], gR[p], gG[p], gB[p], gZ[p]);
+                    for (int p = 0; p < NP; ++p) packed(p, dp1[p], dp2[p], glo[p], w[p]);
+                    pair_sums<true>(A, dp1[0], dp2[0], glo[0], w[0], dy[0], gR[0], gG[0], gB[0], gZ[0]);
+                    pair_sums<false>(A, dp1[1], dp2[1], glo[1], w[1], dy[1], gR[1], gG[1], gB[1], gZ[1]);
+                } else if (h0) {
+                    float2 dp1, dp2, glo, w;
+                    packed(0, dp1, dp2, glo, w);
+                    pair_sums<true>(A, dp1, dp2, glo, w, dy[0], gR[0], gG[0], gB[0], gZ[0]);
+                } else {
+                    float2 dp1, dp2, glo, w;
+                    packed(1, dp1, dp2, glo, w);
+                    pair_sums<true>(A, dp1, dp2, glo, w, dy[1], gR[1], gG[1], gB[1], gZ[1]);
+                }
             } else {
                 // pair 0 sets the sums (to zero when it is not reached), later pairs add
 #pragma unroll
