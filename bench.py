@@ -77,6 +77,8 @@ def parse():
                    help="pick the tile size, binning and entry batch with the autotuner first")
     p.add_argument("--batch", type=int, default=32, choices=[32, 64],
                    help="list entries a blend warp stages per round")
+    p.add_argument("--fwd-rows", type=int, default=0, choices=[0, 8, 16],
+                   help="pixel rows of a forward blend warp's block (0: the library's default, 16)")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -521,7 +523,8 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
     tuned = A.tune(params, scene.sh_degree, cams, vm)
     del params, vm
     torch.cuda.empty_cache()
-    rast = R.GaussianRasterizer(tuned["tile"], binning=tuned["binning"], batch=tuned["batch"])
+    rast = R.GaussianRasterizer(tuned["tile"], binning=tuned["binning"], batch=tuned["batch"],
+                                fwd_rows=tuned["fwd_rows"])
     win = Window(scene, rast)
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
@@ -560,7 +563,8 @@ def measure_workload(name, torch, B, R, flush, peaks, alu_peak, sfu_peak, K=5, W
                            info.keys, tuned["binning"], info.tiles, sfu_peak, info.pairs_visible)
     out = {"config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene),
                       "gaussians": scene.N, "sh_degree": scene.sh_degree, "tile": tuned["tile"],
-                      "binning": tuned["binning"], "batch": tuned["batch"], "autotune_ms": tuned["ms"],
+                      "binning": tuned["binning"], "batch": tuned["batch"], "fwd_rows": tuned["fwd_rows"],
+                      "autotune_ms": tuned["ms"],
                       "step": f"forward + L1 colour/depth loss + backward (params + {scene.V} poses)",
                       "launch": "one CUDA graph per step, replayed", "steps": K, "warmup": W},
            "value": win.P / (replay / 1000) / 1e6, "unit": "Mpix/s", "ms_per_step": replay,
@@ -591,8 +595,9 @@ def main():
         w0 = Window(scene, R.GaussianRasterizer(16, binning=args.binning), loss=args.loss, primitive=args.primitive)
         tuned = A.tune(w0.params, scene.sh_degree, w0.cams, w0.vm)
         tile, args.binning, args.batch = tuned["tile"], tuned["binning"], tuned["batch"]
+        args.fwd_rows = tuned["fwd_rows"]
         del w0
-    rast = R.GaussianRasterizer(tile, binning=args.binning, batch=args.batch)
+    rast = R.GaussianRasterizer(tile, binning=args.binning, batch=args.batch, fwd_rows=args.fwd_rows)
     opts = dict(loss=args.loss, primitive=args.primitive, median=args.median, densify=args.densify,
                 fuse_l1=not args.separate_loss)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -725,6 +730,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "views": scene.V, "resolution": resolution(scene), "gaussians": scene.N,
                    "sh_degree": scene.sh_degree, "tile": tile, "binning": args.binning, "batch": args.batch,
+                   "fwd_rows": rast.fwd_rows,
                    "autotune": tuned,
                    "step": f"forward + {LOSS_NAMES[args.loss]} + backward (params + {scene.V} poses)",
                    "loss_in_forward_blend": win.fuse_l1,

@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define GSR_ABI_VERSION 6
+#define GSR_ABI_VERSION 7
 #define GSR_MAX_VIEWS 64
 
 typedef enum {
@@ -69,7 +69,7 @@ typedef struct CUstream_st *gsr_stream;
 typedef struct gsr_ctx gsr_ctx;
 
 /* Library configuration of a context (gsr_autotune may replace tile,
- * binning and batch with the fastest it measured). */
+ * binning, batch and fwd_rows with the fastest it measured). */
 typedef struct {
     int tile;              /* screen tile edge in pixels: 8, 16 or 32 (0 = 16) */
     uint32_t spin_limit;   /* iterations before a bounded device wait gives up (0 = default) */
@@ -78,6 +78,11 @@ typedef struct {
     int batch;             /* depth-sorted list entries a blend warp stages per round: 32 or 64
                               (0 = 32); 64 needs a tile of 8 or 16 (GSR_EINVAL otherwise).
                               The images do not depend on it, only the speed. */
+    int fwd_rows;          /* pixel rows of a forward blend warp's block (8 columns wide): 8 or
+                              16 (0 = 16, or 8 at tile 8); 16 needs a tile of 16 or 32
+                              (GSR_EINVAL otherwise).  Taller blocks share each staged entry
+                              among more pixels, shorter ones evaluate fewer entries that do
+                              not reach a pixel; the images do not depend on it. */
 } gsr_config;
 
 /* Test hook for the bounded-wait path: the first tile of the first radix-sort
@@ -189,7 +194,7 @@ typedef struct {
 } gsr_l1_view;
 
 /* Creates a context (host memory only).  cfg may be NULL for defaults.
- * Returns GSR_EINVAL for an unsupported tile size, binning or batch. */
+ * Returns GSR_EINVAL for an unsupported tile size, binning, batch or fwd_rows. */
 gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out);
 
 /* Frees a context.  NULL is ignored. */
@@ -239,7 +244,7 @@ gsr_status gsr_get_status(gsr_ctx *ctx, const void *ws, size_t ws_bytes, gsr_str
 
 /* One configuration timed by gsr_autotune. */
 typedef struct {
-    int tile, binning, batch;   /* the candidate (see gsr_config) */
+    int tile, binning, batch, fwd_rows;   /* the candidate (see gsr_config) */
     float ms;                   /* best of reps forward + backward times (CUDA events), or -1 */
     int32_t status;             /* GSR_OK, or why it was not timed (GSR_ECAPACITY: its keys
                                    exceed the workspace; a synchronous error code) */
@@ -250,7 +255,8 @@ typedef struct {
  * batch trade sort work against blend work differently for every scene and
  * set of views).  Times forward + backward on the caller's own Gaussians,
  * views and workspace for every candidate (tile 8, 16, 32) x (GSR_BIN_TILE,
- * GSR_BIN_RADIX) x (batch 32, 64; 64 not at tile 32), best of reps (1..100)
+ * GSR_BIN_RADIX) x (batch 32, 64; 64 not at tile 32) x (fwd_rows 16, 8; 16
+ * not at tile 8), best of reps (1..100)
  * after one warm-up run, the rendered colour serving as the upstream
  * gradient, and leaves the fastest configuration in ctx (ties: the earlier
  * candidate in that order).  The candidates' results are identical images;

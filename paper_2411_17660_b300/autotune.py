@@ -1,5 +1,5 @@
-"""Autotuner of the batched rasteriser: tile size, binning strategy and the
-blends' per-warp entry batch.
+"""Autotuner of the batched rasteriser: tile size, binning strategy, the
+blends' per-warp entry batch and the forward blend's block height.
 
 The screen tile (8, 16 or 32 pixels) sets how many (Gaussian, tile) keys the
 sort handles and how many warps share a tile's depth-sorted list; the binning
@@ -7,14 +7,16 @@ strategy ("tile": grouping by tile and a sort inside each tile; "radix":
 radix passes over tile and depth bits) trades fewer global passes against
 per-tile sorts that grow with the keys per tile; the batch (32 or 64 list
 entries staged per warp and round in both blends) trades staging rounds and
-loads in flight against entries staged past a warp's transmittance stop.
-Which combination is fastest depends on the scene (Gaussian footprints) and
+loads in flight against entries staged past a warp's transmittance stop;
+the forward blend's warp block of 8 columns by 16 or 8 rows trades entries
+shared among more pixels against evaluations of entries that reach no pixel
+of the block.  Which combination is fastest depends on the scene (Gaussian footprints) and
 the views.  The timing runs in the library (gsr_autotune): forward +
 backward per candidate on the caller's own inputs, CUDA events on the
 stream, best of a few after a warm-up run.  This module sizes the workspace
 for the candidate with the most keys and caches the choice per (GPU, N, SH
 degree, view sizes) in an optional JSON file.  The images do not depend on
-any of the three choices, so tuning changes only speed.
+any of the choices, so tuning changes only speed.
 """
 from __future__ import annotations
 
@@ -25,14 +27,17 @@ from typing import Dict, Optional, Sequence
 TILES = (8, 16, 32)
 BINNINGS = ("tile", "radix")
 BATCHES = (32, 64)
-# "tile size/binning/batch", in the order the library times them (64 is not offered at tile 32)
-CANDIDATES = tuple(f"{t}/{b}/{k}" for t in TILES for b in BINNINGS for k in BATCHES if not (t == 32 and k == 64))
+FWD_ROWS = (16, 8)
+# "tile size/binning/batch/forward rows", in the order the library times them (64 is not
+# offered at tile 32, 16 rows not at tile 8)
+CANDIDATES = tuple(f"{t}/{b}/{k}/{r}" for t in TILES for b in BINNINGS for k in BATCHES for r in FWD_ROWS
+                   if not (t == 32 and k == 64) and not (t == 8 and r == 16))
 
 
 def parse(candidate: str):
-    """("16/tile/32") -> (16, "tile", 32)."""
-    t, b, k = candidate.split("/")
-    return int(t), b, int(k)
+    """("16/tile/32/8") -> (16, "tile", 32, 8)."""
+    t, b, k, r = candidate.split("/")
+    return int(t), b, int(k), int(r)
 
 
 def signature(gpu: str, N: int, sh_degree: int, cams: Sequence) -> str:
@@ -65,8 +70,8 @@ class TileCache:
 def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = None,
          reps: int = 3) -> Dict[str, object]:
     """Times every candidate with gsr_autotune on these inputs and returns
-    {"tile": size, "binning": strategy, "batch": entries, "ms": {candidate: ms
-    or None when it could not run}}."""
+    {"tile": size, "binning": strategy, "batch": entries, "fwd_rows": rows,
+    "ms": {candidate: ms or None when it could not run}}."""
     import torch
 
     from . import binding as B
@@ -75,7 +80,7 @@ def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = No
     gpu = torch.cuda.get_device_name()
     N = int(params["means"].shape[1])
     key = signature(gpu, N, sh_degree, cams)
-    if cache is not None and cache.get(key) is not None:
+    if cache is not None and cache.get(key) is not None and "fwd_rows" in cache.get(key):
         return cache.get(key)
     dev = params["means"].device
     # a workspace with room for the keys of the smallest tile (the most keys)
@@ -95,11 +100,12 @@ def tune(params, sh_degree: int, cams, viewmats, cache: Optional[TileCache] = No
                                     torch.cuda.current_stream().cuda_stream)
     rast.ctx.check(st, "gsr_autotune")
     name = {B.BIN_TILE: "tile", B.BIN_RADIX: "radix"}
-    times = {f"{e.tile}/{name[e.binning]}/{e.batch}": (float(e.ms) if e.status == B.OK else None) for e in entries}
+    times = {f"{e.tile}/{name[e.binning]}/{e.batch}/{e.fwd_rows}": (float(e.ms) if e.status == B.OK else None)
+             for e in entries}
     ran = {c: t for c, t in times.items() if t is not None}
     best = min(ran, key=lambda c: (ran[c], list(times).index(c)))
-    tile, binning, batch = parse(best)
-    result = {"tile": tile, "binning": binning, "batch": batch, "ms": times}
+    tile, binning, batch, rows = parse(best)
+    result = {"tile": tile, "binning": binning, "batch": batch, "fwd_rows": rows, "ms": times}
     if cache is not None:
         cache.put(key, result)
     return result

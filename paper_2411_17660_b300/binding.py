@@ -17,7 +17,7 @@ LIB_PATH = os.environ.get("GSR_LIBRARY") or os.path.join(_PKG, "_build", "libgsr
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gsr.h")
 
 MAX_VIEWS = 64
-ABI_VERSION = 6   # GSR_ABI_VERSION these structs follow
+ABI_VERSION = 7   # GSR_ABI_VERSION these structs follow
 STATUS = {0: "GSR_OK", -1: "GSR_EINVAL", -2: "GSR_ECAPACITY", -3: "GSR_ECUDA", -4: "GSR_ETIMEOUT",
           -5: "GSR_ENOTREADY", -6: "GSR_EINTERNAL"}
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOTREADY, EINTERNAL = 0, -1, -2, -3, -4, -5, -6
@@ -33,7 +33,7 @@ _p = ctypes.c_void_p
 
 class Config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("flags", ctypes.c_int),
-                ("binning", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("binning", ctypes.c_int), ("batch", ctypes.c_int), ("fwd_rows", ctypes.c_int)]
 
 
 class Gaussians(ctypes.Structure):
@@ -85,8 +85,8 @@ class GaussiansOut(ctypes.Structure):
 
 
 class TuneEntry(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("binning", ctypes.c_int), ("batch", ctypes.c_int), ("ms", ctypes.c_float),
-                ("status", ctypes.c_int32)]
+    _fields_ = [("tile", ctypes.c_int), ("binning", ctypes.c_int), ("batch", ctypes.c_int), ("fwd_rows", ctypes.c_int),
+                ("ms", ctypes.c_float), ("status", ctypes.c_int32)]
 
 
 ABI_STRUCTS = [Config, Gaussians, View, ViewGrad, Grads, Info, L1View, SurfelOut, SurfelGrad, AdcParams,
@@ -165,13 +165,13 @@ class Context:
     """Owns one gsr_ctx (host memory only)."""
 
     def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: int = BIN_TILE,
-                 batch: int = 32):
+                 batch: int = 32, fwd_rows: int = 0):
         self.lib = load()
-        cfg = Config(tile, spin_limit, flags, binning, batch)
+        cfg = Config(tile, spin_limit, flags, binning, batch, fwd_rows)
         h = _p()
         st = self.lib.gsr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:
-            raise GsrError(st, f"gsr_create(tile={tile}, binning={binning}, batch={batch})")
+            raise GsrError(st, f"gsr_create(tile={tile}, binning={binning}, batch={batch}, fwd_rows={fwd_rows})")
         self.h = h
         self.tile = tile
 
@@ -236,10 +236,10 @@ class Context:
     def autotune(self, g: Gaussians, views, grads: Grads, ws_ptr: int, ws_bytes: int, reps: int, stream: int):
         """gsr_autotune; returns (status, [TuneEntry])."""
         arr = (View * len(views))(*views)
-        entries = (TuneEntry * 16)()
+        entries = (TuneEntry * 32)()
         n = ctypes.c_int(0)
         st = self.lib.gsr_autotune(self.h, ctypes.byref(g), arr, len(views), ctypes.byref(grads), ws_ptr, ws_bytes,
-                                   reps, entries, 16, ctypes.byref(n), stream)
+                                   reps, entries, 32, ctypes.byref(n), stream)
         return st, list(entries[:n.value])
 
     def read_info(self, ws_ptr: int, ws_bytes: int, stream: int) -> Info:

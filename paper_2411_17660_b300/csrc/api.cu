@@ -20,6 +20,7 @@ struct gsr_ctx {
     int flags = 0;
     int binning = GSR_BIN_TILE;
     int batch = 32;   // list entries a blend warp stages per round (32 or 64)
+    int fwd_rows = 16;   // pixel rows of a forward blend warp's block (8, or 16 at tiles 16 and 32)
     int sm_count = 0;
     std::string err;
     struct Rec {
@@ -300,11 +301,13 @@ bool want_median(const gsr_view *views, int V) {
     return false;
 }
 
-void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile, int batch = 32) {
+void fill_views(ViewTable &vt, const gsr_view *views, const gsr_view_grad *grads, int V, int tile, int batch = 32,
+                int fwd_rows = 16) {
     memset(&vt, 0, sizeof vt);
     vt.V = V;
     vt.tile = tile;
     vt.batch = batch;
+    vt.fwd_rows = tile == 8 ? 8 : fwd_rows;
     uint32_t toff = 0, poff = 0;
     for (int v = 0; v < V; ++v) {
         ViewParams &p = vt.v[v];
@@ -396,11 +399,13 @@ extern "C" {
 gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     if (!out) return GSR_EINVAL;
     *out = nullptr;
-    int tile = 16, flags = 0, binning = GSR_BIN_TILE, batch = 32;
+    int tile = 16, flags = 0, binning = GSR_BIN_TILE, batch = 32, fwd_rows = 0;
     uint32_t spin = kDefaultSpin;
     if (cfg) {
         if (cfg->batch != 0 && cfg->batch != 32 && cfg->batch != 64) return GSR_EINVAL;
         if (cfg->batch != 0) batch = cfg->batch;
+        if (cfg->fwd_rows != 0 && cfg->fwd_rows != 8 && cfg->fwd_rows != 16) return GSR_EINVAL;
+        fwd_rows = cfg->fwd_rows;
         if (cfg->tile != 0) tile = cfg->tile;
         if (cfg->spin_limit != 0) spin = cfg->spin_limit;
         if (cfg->flags & ~GSR_TEST_STALL_SORT) return GSR_EINVAL;
@@ -410,6 +415,8 @@ gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     }
     if (tile != 8 && tile != 16 && tile != 32) return GSR_EINVAL;
     if (tile == 32 && batch == 64) return GSR_EINVAL;   // the blends' staging would exceed 48 KB of shared memory
+    if (tile == 8 && fwd_rows == 16) return GSR_EINVAL;  // a tile of 8 rows holds no 16-row block
+    if (fwd_rows == 0) fwd_rows = tile == 8 ? 8 : 16;
     gsr_ctx *c = new (std::nothrow) gsr_ctx;
     if (!c) return GSR_EINVAL;
     c->tile = tile;
@@ -417,6 +424,7 @@ gsr_status gsr_create(const gsr_config *cfg, gsr_ctx **out) {
     c->flags = flags;
     c->binning = binning;
     c->batch = batch;
+    c->fwd_rows = fwd_rows;
     *out = c;
     return GSR_OK;
 }
@@ -465,7 +473,7 @@ gsr_status render_impl(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *vi
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     if (l1) {
         for (int v = 0; v < V; ++v) {
             vt.v[v].l1_target_color = l1->targets[v].target_color;
@@ -548,7 +556,7 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, grads, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, grads, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     const Ws w = make_ws(ws_ptr, L, gs->N, V, *ctx);
     const GaussianPtrs gp = gaussian_ptrs(gs);
     GradPtrs gout;
@@ -592,7 +600,7 @@ gsr_status gsr_render_surfels(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_v
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     if (extra)
         for (int v = 0; v < V; ++v) {
             vt.v[v].normal = extra[v].normal;
@@ -650,7 +658,7 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
     Layout L;
     make_layout(gs->N, views, V, ctx->tile, cap, L);
     ViewTable vt;
-    fill_views(vt, views, grads, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, grads, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     if (extra)
         for (int v = 0; v < V; ++v) {
             vt.v[v].d_normal = extra[v].d_normal;
@@ -735,7 +743,7 @@ gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *v
     if ((s = check_gaussians(ctx, gs, V)) != GSR_OK) return s;
     if (ctx->flags) return fail(ctx, GSR_EINVAL, "gsr_autotune: a context with test flags cannot be tuned");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int tile0 = ctx->tile, binning0 = ctx->binning, batch0 = ctx->batch;
+    const int tile0 = ctx->tile, binning0 = ctx->binning, batch0 = ctx->batch, rows0 = ctx->fwd_rows;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -743,19 +751,23 @@ gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *v
         if (e0) cudaEventDestroy(e0);
         return cuda_fail(ctx, e, "gsr_autotune: event");
     }
-    static const int kTiles[] = {8, 16, 32}, kBinnings[] = {GSR_BIN_TILE, GSR_BIN_RADIX}, kBatches[] = {32, 64};
+    static const int kTiles[] = {8, 16, 32}, kBinnings[] = {GSR_BIN_TILE, GSR_BIN_RADIX}, kBatches[] = {32, 64},
+                     kRows[] = {16, 8};
     int n = 0, best = -1;
     float best_ms = 0.f;
-    int best_cfg[3] = {tile0, binning0, batch0};
+    int best_cfg[4] = {tile0, binning0, batch0, rows0};
     gsr_status first_fail = GSR_OK, hard = GSR_OK;
     for (int tile : kTiles)
         for (int binning : kBinnings)
-            for (int batch : kBatches) {
+            for (int batch : kBatches)
+                for (int rows : kRows) {
                 if (hard != GSR_OK || (tile == 32 && batch == 64)) continue;   // 32/64: not supported (shared memory)
+                if (tile == 8 && rows == 16) continue;                          // no 16-row block in an 8-row tile
                 ctx->tile = tile;
                 ctx->binning = binning;
                 ctx->batch = batch;
-                gsr_tune_entry r{tile, binning, batch, -1.f, GSR_OK};
+                ctx->fwd_rows = rows;
+                gsr_tune_entry r{tile, binning, batch, rows, -1.f, GSR_OK};
                 // the warm-up run also tells whether the keys fit this workspace
                 gsr_status cs = tune_step(ctx, gs, views, V, grads, ws, ws_bytes, stream);
                 gsr_info info{};
@@ -784,6 +796,7 @@ gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *v
                     best_cfg[0] = tile;
                     best_cfg[1] = binning;
                     best_cfg[2] = batch;
+                    best_cfg[3] = rows;
                 }
                 if (n < max_entries) entries[n] = r;
                 ++n;
@@ -794,6 +807,7 @@ gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_view *v
     ctx->tile = best_cfg[0];
     ctx->binning = best_cfg[1];
     ctx->batch = best_cfg[2];
+    ctx->fwd_rows = best_cfg[3];
     if (hard != GSR_OK) return hard;
     if (best < 0) return fail(ctx, first_fail, "gsr_autotune: no candidate ran (%s); grow the workspace",
                               gsr_status_string(first_fail));
@@ -810,7 +824,7 @@ gsr_status gsr_l1_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view *t
         if (!targets[v].target_color || !targets[v].d_color)
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     CallTrace tr("gsr_l1_loss");
     cudaError_t e = launch_l1_loss(vt, targets, color_weight, depth_weight, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "l1 loss");
@@ -829,7 +843,7 @@ gsr_status gsr_rgbd_loss(gsr_ctx *ctx, const gsr_view *views, const gsr_l1_view 
         if (!targets[v].target_color || !targets[v].d_color)
             return fail(ctx, GSR_EINVAL, "view %d: target_color and d_color must be non-NULL", v);
     ViewTable vt;
-    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch);
+    fill_views(vt, views, nullptr, V, ctx->tile, ctx->batch, ctx->fwd_rows);
     CallTrace tr("gsr_rgbd_loss");
     cudaError_t e = launch_rgbd_loss(vt, targets, lambda1, lambda2, loss, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rgbd loss");

@@ -129,11 +129,14 @@ struct BwdBlock {
 // tile is at least that tall, as in the backward: the per-entry work that
 // does not depend on the pixel (shared loads, the linear forms' constant,
 // the stop vote, the loop) and the staging then serve twice the pixels.
+// ROWS is the configured block height (gsr_config.fwd_rows: 16 shares each
+// staged entry among twice the pixels, 8 evaluates fewer entries that reach
+// no pixel; which is faster depends on the scene, so the autotuner picks).
 // The median-depth variant keeps one row pair per lane: its per-pixel
 // median state would not fit the registers of two.
-template <int TS, bool MED>
+template <int TS, bool MED, int ROWS>
 struct FwdBlock {
-    static constexpr int H = TS >= 16 && !MED ? 16 : kSubH;
+    static constexpr int H = TS >= 16 && !MED && ROWS == 16 ? 16 : kSubH;
     // resident warps: 32 (64 registers) with two row pairs per lane, 36 (56
     // registers) with one
     static constexpr int WARPS_PER_SM = H == 16 ? 32 : 36;
@@ -315,10 +318,10 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
 // count) run as packed FP32 pairs, without branches: a pixel that an entry
 // does not reach, or that has stopped, composites it with w = 0, which leaves
 // its sums unchanged.
-template <int TS, int CH, bool MED, bool L1>
-__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED>::H>::THREADS, FwdBlock<TS, MED>::MIN_BLOCKS) blend_fwd_kernel(const __grid_constant__ ViewTable vt,
-                                                                           const Ws ws) {
-    constexpr int BH = FwdBlock<TS, MED>::H, NR = BH / kRowStep, NP = NR / 2;
+template <int TS, int CH, bool MED, bool L1, int ROWS>
+__global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::THREADS, FwdBlock<TS, MED, ROWS>::MIN_BLOCKS)
+    blend_fwd_kernel(const __grid_constant__ ViewTable vt, const Ws ws) {
+    constexpr int BH = FwdBlock<TS, MED, ROWS>::H, NR = BH / kRowStep, NP = NR / 2;
     using S = BlendShape<TS, BH>;
     __shared__ float4 sF[S::WARPS][kFwdQuads][32 * CH];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -833,22 +836,32 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
 #endif
 }
 
+// The median-depth variant has 8-row blocks at either ROWS (FwdBlock), so
+// it is instantiated once, with ROWS 8.
+template <int TS, int CH, int ROWS>
+cudaError_t launch_fwd_rows(const ViewTable &vt, const Ws &ws, cudaStream_t st, bool med, bool l1) {
+    constexpr int TM = BlendShape<TS, FwdBlock<TS, true, 8>::H>::THREADS;       // with median depth
+    constexpr int TP = BlendShape<TS, FwdBlock<TS, false, ROWS>::H>::THREADS;   // without
+    if (med && l1)
+        blend_fwd_kernel<TS, CH, true, true, 8><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
+    else if (med)
+        blend_fwd_kernel<TS, CH, true, false, 8><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
+    else if (l1)
+        blend_fwd_kernel<TS, CH, false, true, ROWS><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
+    else
+        blend_fwd_kernel<TS, CH, false, false, ROWS><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
+    return cudaGetLastError();
+}
+
 template <int TS, int CH>
 cudaError_t launch_fwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].median_depth != nullptr;
-    constexpr int TM = BlendShape<TS, FwdBlock<TS, true>::H>::THREADS;    // with median depth
-    constexpr int TP = BlendShape<TS, FwdBlock<TS, false>::H>::THREADS;   // without
     const bool l1 = vt.l1_loss != nullptr;
-    if (med && l1)
-        blend_fwd_kernel<TS, CH, true, true><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
-    else if (med)
-        blend_fwd_kernel<TS, CH, true, false><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
-    else if (l1)
-        blend_fwd_kernel<TS, CH, false, true><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
-    else
-        blend_fwd_kernel<TS, CH, false, false><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
-    return cudaGetLastError();
+    if constexpr (TS >= 16) {
+        if (vt.fwd_rows == 16) return launch_fwd_rows<TS, CH, 16>(vt, ws, st, med, l1);
+    }
+    return launch_fwd_rows<TS, CH, 8>(vt, ws, st, med, l1);
 }
 
 template <int TS, int CH>

@@ -62,6 +62,7 @@ struct ViewTable {
     int V;
     int tile;
     int batch;                // list entries a blend warp stages per round: 32 or 64
+    int fwd_rows;             // pixel rows of a forward blend warp's block: 8 or 16 (16 needs tile >= 16)
     uint32_t total_tiles;
     uint32_t total_pixels;
     float *l1_loss;           // fused L1 loss: the device scalar it adds to, or NULL

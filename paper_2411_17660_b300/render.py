@@ -99,13 +99,16 @@ def split_views(flat: torch.Tensor, cams, channels: int = 1):
 class GaussianRasterizer:
     """Batched differentiable Gaussian rasteriser over a keyframe window."""
 
-    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: str = "tile", batch: int = 32):
+    def __init__(self, tile: int = 16, spin_limit: int = 0, flags: int = 0, binning: str = "tile", batch: int = 32,
+                 fwd_rows: int = 0):
         if binning not in ("tile", "radix"):
             raise ValueError(f"binning must be 'tile' or 'radix', not {binning!r}")
-        self.ctx = _b.Context(tile, spin_limit, flags, _b.BIN_TILE if binning == "tile" else _b.BIN_RADIX, batch)
+        self.ctx = _b.Context(tile, spin_limit, flags, _b.BIN_TILE if binning == "tile" else _b.BIN_RADIX, batch,
+                              fwd_rows)
         self.tile = tile
         self.binning = binning
         self.batch = batch
+        self.fwd_rows = fwd_rows or (8 if tile == 8 else 16)
         self._cap_hint = {}
 
     # ------------------------------------------------------------ workspace

@@ -4,12 +4,14 @@ from paper_2411_17660_b300 import autotune as A
 from paper_2411_17660_b300.render import Intrinsics
 
 
-def test_candidates_cover_every_tile_binning_and_batch():
-    want = {(t, b, k) for t in A.TILES for b in A.BINNINGS for k in A.BATCHES if not (t == 32 and k == 64)}
-    assert {A.parse(c) for c in A.CANDIDATES} == want and len(A.CANDIDATES) == len(want) == 10
-    assert A.parse("32/radix/32") == (32, "radix", 32)
-    # the library's order: tile, then binning, then batch
-    assert A.CANDIDATES[:3] == ("8/tile/32", "8/tile/64", "8/radix/32")
+def test_candidates_cover_every_tile_binning_batch_and_block_height():
+    want = {(t, b, k, r) for t in A.TILES for b in A.BINNINGS for k in A.BATCHES for r in A.FWD_ROWS
+            if not (t == 32 and k == 64) and not (t == 8 and r == 16)}
+    assert {A.parse(c) for c in A.CANDIDATES} == want and len(A.CANDIDATES) == len(want) == 16
+    assert A.parse("32/radix/32/8") == (32, "radix", 32, 8)
+    # the library's order: tile, then binning, then batch, then forward rows
+    assert A.CANDIDATES[:3] == ("8/tile/32/8", "8/tile/64/8", "8/radix/32/8")
+    assert A.CANDIDATES[4:6] == ("16/tile/32/16", "16/tile/32/8")
 
 
 def test_signature_distinguishes_views_and_sizes():
@@ -24,6 +26,6 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "tiles.json")
     c = A.TileCache(path)
     assert c.get("k") is None
-    c.put("k", {"tile": 32, "binning": "radix", "batch": 32, "ms": {"8/tile/32": 1.0}})
+    c.put("k", {"tile": 32, "binning": "radix", "batch": 32, "fwd_rows": 8, "ms": {"8/tile/32/8": 1.0}})
     again = A.TileCache(path)
     assert again.get("k")["tile"] == 32

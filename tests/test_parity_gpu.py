@@ -134,15 +134,16 @@ def test_stop_with_zero_off_diagonal_and_both_clamp_paths():
     U.compare_grads(gref, g, label="axis band")
 
 
-@pytest.mark.parametrize("tile,binning", [(8, "tile"), (16, "tile"), (32, "tile"), (16, "radix")])
-def test_decisions_backward_equals_forward(tile, binning):
+@pytest.mark.parametrize("tile,binning,rows", [(8, "tile", 8), (16, "tile", 16), (16, "tile", 8), (32, "tile", 16),
+                                               (32, "tile", 8), (16, "radix", 16)])
+def test_decisions_backward_equals_forward(tile, binning, rows):
     """The checked build counts the backward's contributor pairs: they are
     exactly the forward's composited pairs (both kernels form every s with
     the same FP32 operations), at every tile size, also where pixels stop."""
     if not B.LIB_PATH.endswith("libgsr_checked.so"):
         pytest.skip("the backward's pair count is kept by the checked build (tests/test_checked_gpu.py)")
     for sc in (REDUCED["window"](), REDUCED["uneven"](), REDUCED["outdoor"](), _opaque_stack(), _axis_band()):
-        _, state = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning))
+        _, state = U.gpu_forward(sc, rast=R.GaussianRasterizer(tile, binning=binning, fwd_rows=rows))
         gC, gD, gA = U.upstream(sc)
         U.gpu_backward(sc, state, gC, gD, gA)
         info = state[0].info(state[4])
@@ -152,8 +153,11 @@ def test_decisions_backward_equals_forward(tile, binning):
 
 
 def test_tile_size_invariance():
+    """Tile size and the forward's warp-block height change which entries a
+    warp stages, never a pixel's arithmetic: bit-identical images."""
     sc = REDUCED["room"]()
     outs = [U.gpu_forward(sc, tile=t)[0][0] for t in (8, 16, 32)]
+    outs += [U.gpu_forward(sc, rast=R.GaussianRasterizer(t, fwd_rows=8))[0][0] for t in (16, 32)]
     for o in outs[1:]:
         for k in ("color", "depth", "alpha"):
             np.testing.assert_array_equal(o[k], outs[0][k])
@@ -389,7 +393,7 @@ def test_cuda_graph_replay_matches_eager(name, binning, fused):
 
 
 def test_autotuner_picks_a_candidate_and_caches(tmp_path):
-    """gsr_autotune (through the C ABI) times all ten candidates on the
+    """gsr_autotune (through the C ABI) times all sixteen candidates on the
     caller's inputs, leaves the fastest in the context, and the Python side
     caches the choice; the tuned context renders the same images."""
     from paper_2411_17660_b300 import autotune as A
@@ -398,10 +402,11 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path):
     cache = A.TileCache(str(tmp_path / "tiles.json"))
     r = A.tune(params, sc.sh_degree, cams, vm, cache=cache, reps=2)
     assert r["tile"] in A.TILES and r["binning"] in A.BINNINGS and r["batch"] in A.BATCHES
+    assert r["fwd_rows"] in A.FWD_ROWS
     assert list(r["ms"]) == list(A.CANDIDATES) and all(t is not None and t > 0 for t in r["ms"].values())
-    assert r["ms"][f"{r['tile']}/{r['binning']}/{r['batch']}"] == min(r["ms"].values())
+    assert r["ms"][f"{r['tile']}/{r['binning']}/{r['batch']}/{r['fwd_rows']}"] == min(r["ms"].values())
     assert A.tune(params, sc.sh_degree, cams, vm, cache=cache) == r
-    tuned = R.GaussianRasterizer(r["tile"], binning=r["binning"], batch=r["batch"])
+    tuned = R.GaussianRasterizer(r["tile"], binning=r["binning"], batch=r["batch"], fwd_rows=r["fwd_rows"])
     _assert_same_images_as_default(sc, tuned)
 
 
@@ -417,6 +422,7 @@ def test_autotune_skips_candidates_whose_keys_do_not_fit():
     """A workspace sized for tile 16's keys: the tile-8 candidates report
     GSR_ECAPACITY and are skipped, the others run, and the context keeps the
     fastest of those."""
+    from paper_2411_17660_b300 import autotune as A
     sc = REDUCED["window"]()
     params, cams, vm = U.to_device(sc)
     rast = R.GaussianRasterizer(16)
@@ -433,9 +439,9 @@ def test_autotune_skips_candidates_whose_keys_do_not_fit():
     out = B.Grads(*[grads[k].data_ptr() for k in R.PARAM_NAMES], 0, 0, 0, 0)
     st, entries = rast.ctx.autotune(g, R.view_structs(cams, vm, color), out, ws.data_ptr(), ws.numel(), 1,
                                     torch.cuda.current_stream().cuda_stream)
-    assert st == B.OK and len(entries) == 10
+    assert st == B.OK and len(entries) == len(A.CANDIDATES) == 16
     for e in entries:
-        assert (e.status == B.ECAPACITY) == (e.tile == 8), (e.tile, e.binning, e.batch, e.status)
+        assert (e.status == B.ECAPACITY) == (e.tile == 8), (e.tile, e.binning, e.batch, e.fwd_rows, e.status)
         assert (e.ms > 0) == (e.status == B.OK)
     best = min((e for e in entries if e.status == B.OK), key=lambda e: e.ms)
     # the tuned context renders with its new configuration on a fresh workspace
