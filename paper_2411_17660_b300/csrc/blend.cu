@@ -175,18 +175,28 @@ __device__ __forceinline__ bool touches_block(float ur, float vr, float m00, flo
 
 // One level of a transposing butterfly: L values per lane become ceil(L/2)
 // values, each summed over the lane pair (lane, lane ^ LEVEL).  The lower
-// lane keeps the first half, the upper lane the second (zero-padded).
+// lane keeps the first half, the upper lane the second (zero-padded).  The
+// sums run two at a time on packed FP32 pairs.
 template <int L, int LEVEL>
 __device__ __forceinline__ void butterfly_level(const float *in, float *out, int lane) {
     constexpr int H = (L + 1) / 2;
     const bool hi = (lane & LEVEL) != 0;
+    float keep[H], recv[H];
 #pragma unroll
     for (int i = 0; i < H; ++i) {
         const float lo_keep = in[i];
         const float hi_keep = (H + i < L) ? in[H + i] : 0.f;
         const float send = hi ? lo_keep : hi_keep;
-        out[i] = (hi ? hi_keep : lo_keep) + __shfl_xor_sync(kFull, send, LEVEL);
+        keep[i] = hi ? hi_keep : lo_keep;
+        recv[i] = __shfl_xor_sync(kFull, send, LEVEL);
     }
+#pragma unroll
+    for (int i = 0; i + 1 < H; i += 2) {
+        const float2 r = __fadd2_rn(make_float2(keep[i], keep[i + 1]), make_float2(recv[i], recv[i + 1]));
+        out[i] = r.x;
+        out[i + 1] = r.y;
+    }
+    if constexpr (H % 2 == 1) out[H - 1] = __fadd_rn(keep[H - 1], recv[H - 1]);
 }
 
 // Sums 10 per-lane values over the warp with 12 shuffles (instead of 50):
@@ -579,7 +589,6 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     const float lxf = (float)(lane & (kSubW - 1)), lyf = (float)(lane / kSubW);
     const float2 lx2 = make_float2(lxf, lxf);
     const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
-    const float2 m2ln2 = make_float2(-2.f * kLn2, -2.f * kLn2);
     const int Yr = row_origin(wt.Y0);             // the row offsets' origin (see row_origin)
     const float yoff = (float)(wt.Y0 - Yr);
 
@@ -715,9 +724,10 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                     glo.x = raw.x <= kAlphaMax ? glo.x : 0.f;
                     glo.y = raw.y <= kAlphaMax ? glo.y : 0.f;
                 }
-                const float2 ds2 = __fmul2_rn(glo, m2ln2);              // 2 dL/ds
-                dp1 = __fmul2_rn(p1[p], ds2);
-                dp2 = __fmul2_rn(p2[p], ds2);
+                // dL/dp = 2 p dL/ds = -2 ln 2 p glo: the factor -2 ln 2 is
+                // applied once per (view, Gaussian) by the preprocess backward
+                dp1 = __fmul2_rn(p1[p], glo);
+                dp2 = __fmul2_rn(p2[p], glo);
             };
             if constexpr (NP == 2) {
                 // Both pairs in one straight run where the entry reaches rows
@@ -782,7 +792,7 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
                             Qq = fmaf(al, dgq, Qq);
                             Tq = Ti;
                             const float gl = !CLAMP || raw <= kAlphaMax ? dA * raw : 0.f;
-                            const float ds2 = (-2.f * kLn2) * gl;
+                            const float ds2 = gl;   // without -2 ln 2, as in the packed path
                             auto put = [](float v) { return R ? make_float2(0.f, v) : make_float2(v, 0.f); };
                             dp1 = put(p1q * ds2);
                             dp2 = put(p2q * ds2);

@@ -22,6 +22,9 @@ constexpr float kFovClamp = 1.3f;
 // The blend works with s = 0.5*log2(e)*d^2, so exp(-d^2/2) = 2^-s.
 constexpr float kHalfLog2e = 0.721347520444481703680f;      // 0.5 / ln 2
 constexpr float kSqrtHalfLog2e = 0.849321800288019133f;     // sqrt(0.5 / ln 2)
+// Scale of the blend backward's position and conic-factor sums (gradient
+// row components 0..4): -2 ln 2 sqrt(0.5 / ln 2) = -sqrt(2 ln 2)
+constexpr float kRowScale = -1.17741002251547466f;
 constexpr float kLn2 = 0.693147180559945309417f;
 constexpr float kLog2_255 = 7.99435343685885793f;           // log2(255)
 

@@ -362,15 +362,18 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     // pixel mean and depth: the blend returns the sums of dL/dp1 and dL/dp2
     // (p = m d, d = pixel - mean), so dL/du = -m00 S1, dL/dv = -(m01 S1 + m11 S2)
     const float x = p.xh, y = p.yh, z = p.zh, rz = p.rz;
-    const float du = -kSqrtHalfLog2e * p.l00 * sg[0];
-    const float dvv = -kSqrtHalfLog2e * (p.l01 * sg[0] + p.l11 * sg[1]);
+    // The blend sums dL/dp1, dL/dp2 and their products with the offsets
+    // without the factor -2 ln 2 of dL/dp = 2 p dL/ds (dL/ds = -ln 2 dL/d ln
+    // sigma, per pixel), which comes in here, once per (view, Gaussian).
+    const float du = -kRowScale * p.l00 * sg[0];
+    const float dvv = -kRowScale * (p.l01 * sg[0] + p.l11 * sg[1]);
     dpc[0] += du * vp.fx * rz;
     dpc[1] += dvv * vp.fy * rz;
     dpc[2] += -(du * vp.fx * x + dvv * vp.fy * y) * rz * rz + sg[9];
 
     // Cholesky factor of Sigma'^-1 -> Sigma' = [[A, B], [B, C]]
     const float A = p.sxx, B = p.sxy, C = p.syy, det = p.det, idet = rcp_approx(det), iC = rcp_approx(C);
-    const float dl00 = kSqrtHalfLog2e * sg[2], dl01 = kSqrtHalfLog2e * sg[3], dl11 = kSqrtHalfLog2e * sg[4];
+    const float dl00 = kRowScale * sg[2], dl01 = kRowScale * sg[3], dl11 = kRowScale * sg[4];
     const float rdc = rsqrt_approx(det * C);
     const float dA = -0.5f * C * idet * (dl00 * p.l00 + dl01 * p.l01);
     const float dB = dl00 * p.l00 * B * idet + dl01 * (p.l01 * B * idet - rdc);
