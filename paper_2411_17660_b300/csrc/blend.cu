@@ -376,8 +376,9 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::TH
         return __all_sync(kFull, far);
     };
 
+    bool stopped_all = false;
     for (uint32_t base = wt.range.x; base < wt.range.y; base += 32 * CH) {
-        if (all_stopped()) break;
+        if (stopped_all || all_stopped()) break;
         bool clamp_chunk = false;
         const int n = stage_chunk<BH, CH>(ws, vals, vN, base, wt.range.y, wt.X0, wt.Y0, Yr,
                                           [&](int slot, float ur, float vr, float4 r1, float4 r2, float log2o,
@@ -431,6 +432,14 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::TH
                         if (Tn[p].x < kTStop) w[p].x = 0.f, Tn[p].x = T[p].x, ly[p].x = kFar, last[2 * p] = idx, m[p].x = 0.f;
                         if (Tn[p].y < kTStop)
                             w[p].y = 0.f, Tn[p].y = T[p].y, ly[p].y = kFar, last[2 * p + 1] = idx, m[p].y = 0.f;
+                    }
+                    // every pixel of the warp has stopped: this entry adds
+                    // nothing (w = 0 and Tn = T everywhere), nor does any
+                    // later one, so the warp leaves the chunk (and then the
+                    // list) here instead of at the chunk's end
+                    if (all_stopped()) {
+                        stopped_all = true;
+                        break;
                     }
                 }
                 const float4 q2 = F[2][j];
