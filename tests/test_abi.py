@@ -48,6 +48,12 @@ def test_create_rejects_bad_config(lib):
             B.Context(tile)
     with pytest.raises(B.GsrError):
         B.Context(16, flags=4)
+    # the forward blend's block height: 8 everywhere, 16 at tiles 16 and 32 (0: the default)
+    for tile, rows in ((8, 8), (16, 8), (16, 16), (32, 8), (32, 16), (8, 0), (16, 0)):
+        B.Context(tile, fwd_rows=rows)
+    for tile, rows in ((8, 16), (16, 4), (16, 12), (32, 32)):
+        with pytest.raises(B.GsrError):
+            B.Context(tile, fwd_rows=rows)
 
 
 def _view(H=32, W=48):
