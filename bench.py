@@ -407,21 +407,24 @@ def stage_rooflines(stage_ms, ops, pairs, alu_peak, hbm_gbs, scene, P, keys, bin
                              "work": f"{MUFU_PER_PAIR[s]} MUFU per composited pair"}
     hbm = {
         # parameters once; per pair its tile count and densification radius; per visible pair its
-        # four records and its cleared gradient row; per emitted key its tile and word (per-tile binning)
-        "preprocess": (param_b + 8 * VN + 104 * visible + (12 * keys if binning == "tile" else 0),
-                       "parameters once + 8 B per pair + 104 B per visible pair (records, cleared gradient row)"
+        # 64-byte record; per emitted key its tile and word (per-tile binning).  The gradient rows are
+        # cleared by the backward after use, not here.
+        "preprocess": (param_b + 8 * VN + 64 * visible + (12 * keys if binning == "tile" else 0),
+                       "parameters once + 8 B per pair + 64 B per visible pair (record)"
                        + (" + 12 B per key" if binning == "tile" else "")),
         # per-tile: count reads tile ids; scatter reads tile ids and words, writes words; tile sort
         # reads words, writes ids.  radix: 24 B per key per 8-bit pass (sort) + 8 (ranges)
         "sort": (36 * keys, "36 B per key") if binning == "tile" else
                 (24 * keys * ((32 + max(1, (tiles - 1).bit_length()) + 7) // 8), "24 B per key per pass"),
-        # parameters in, gradients out, a count per pair, each visible pair's gradient row read and cleared
-        "preprocess_bwd": (2 * param_b + 4 * VN + 80 * visible,
-                           "2 x parameters + 4 B per pair + 80 B per visible pair (gradient row read and cleared)"),
+        # parameters in, gradients out, a count per pair, each visible pair's gradient row read and
+        # cleared and its stored colour read
+        "preprocess_bwd": (2 * param_b + 4 * VN + 96 * visible,
+                           "2 x parameters + 4 B per pair + 96 B per visible pair (gradient row read and cleared, "
+                           "colour read)"),
     }
     if binning != "tile":
-        # radix: counts read by the scan and the duplication, the spans' records (rec0, rec1, rec3,
-        # depth) read per visible pair, 12 B written per key
+        # radix: counts read by the scan and the duplication, the record fields the spans use (centre,
+        # factor, s_max, covariance, depth) read per visible pair, 12 B written per key
         hbm["scan_duplicate"] = (8 * VN + 52 * visible + 12 * keys,
                                  "8 B per pair + 52 B per visible pair + 12 B per key")
     for s, (b, note) in hbm.items():

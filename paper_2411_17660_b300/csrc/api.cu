@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <new>
@@ -64,7 +65,7 @@ struct CallTrace {
 };
 
 struct Layout {
-    size_t hdr, counts, offsets, scan_partials, rec0, rec1, rec2, rec3, rec4, rec5, radius, aux;
+    size_t hdr, counts, offsets, scan_partials, rec, rec4, rec5, radius, aux;
     size_t keys0, keys1, vals0, vals1, hist, tile_cursor, tile_order, order_bins, lookback, ranges, T_final, last, median,
         vg_grads, pose_partials;
     size_t total;
@@ -100,10 +101,7 @@ void make_layout(int N, const gsr_view *views, int V, int tile, size_t cap, Layo
     L.counts = take(4 * L.VN);
     L.offsets = take(4 * L.VN);
     L.scan_partials = take(8ull * L.scan_blocks);
-    L.rec0 = take(16 * L.VN);
-    L.rec1 = take(16 * L.VN);
-    L.rec2 = take(16 * L.VN);
-    L.rec3 = take(16 * L.VN);
+    L.rec = take(64 * L.VN);
     L.rec4 = take(16 * L.VN);
     L.rec5 = take(16 * L.VN);
     L.radius = take(4 * L.VN);
@@ -172,10 +170,7 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     w.counts = reinterpret_cast<uint32_t *>(b + L.counts);
     w.offsets = reinterpret_cast<uint32_t *>(b + L.offsets);
     w.scan_partials = reinterpret_cast<unsigned long long *>(b + L.scan_partials);
-    w.rec0 = reinterpret_cast<float4 *>(b + L.rec0);
-    w.rec1 = reinterpret_cast<float4 *>(b + L.rec1);
-    w.rec2 = reinterpret_cast<float4 *>(b + L.rec2);
-    w.rec3 = reinterpret_cast<float4 *>(b + L.rec3);
+    w.rec = reinterpret_cast<float4 *>(b + L.rec);
     w.radius = reinterpret_cast<float *>(b + L.radius);
     w.rec4 = reinterpret_cast<float4 *>(b + L.rec4);
     w.rec5 = reinterpret_cast<float4 *>(b + L.rec5);
@@ -213,13 +208,15 @@ Ws make_ws(void *base, const Layout &L, int N, int V, const gsr_ctx &ctx) {
     return w;
 }
 
-// Clears the header, the radix histograms of the sort, the bucket grouping's
-// tile counters (tile_counts, when it runs) and the fused loss's scalar
-// (loss, when there is one).
+// Clears the header (all but its record of clean gradient rows, which ends
+// it), the radix histograms of the sort, the bucket grouping's tile counters
+// (tile_counts, when it runs) and the fused loss's scalar (loss, when there
+// is one).
 __global__ void __launch_bounds__(1024) init_header_kernel(WsHeader *h, uint32_t cap, uint32_t tiles, uint32_t *hist,
                                                            uint32_t *tile_counts, float *loss, uint32_t *order_bins) {
     uint32_t *p = reinterpret_cast<uint32_t *>(h);
-    for (int i = threadIdx.x; i < (int)(sizeof(WsHeader) / 4); i += blockDim.x) p[i] = 0u;
+    static_assert(offsetof(WsHeader, rows_clean) == sizeof(WsHeader) - 4 * kRowsCleanWords, "record ends the header");
+    for (int i = threadIdx.x; i < (int)(sizeof(WsHeader) / 4) - kRowsCleanWords; i += blockDim.x) p[i] = 0u;
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) hist[i] = 0u;
     for (int i = threadIdx.x; i < 2 * 33; i += blockDim.x) order_bins[i] = 0u;
     if (tile_counts)
@@ -571,8 +568,9 @@ gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *gs, const gsr_
     gout.densify_radius = out->densify_radius;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-    // the per-pair gradient rows were cleared by the forward (and by the last
-    // backward after reading them), so nothing is cleared here
+    // the per-pair gradient rows are zero here: cleared by the last backward
+    // after reading them, or by the forward when the header did not record
+    // them as clean (rows_known_clean in common.cuh)
     CallTrace tr("gsr_render_backward");
     ctx->mark(6, st);
     ctx->mark(7, st);

@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const __grid_constant__ 
     const uint32_t off_k = ws.offsets[i];
     const uint32_t v = (uint32_t)(i / ws.N), g = (uint32_t)(i - (size_t)v * ws.N);
     const ViewParams &vp = vt.v[v];
-    const float4 r0 = ws.rec0[i], r1 = ws.rec1[i], r3 = ws.rec3[i];
-    const unsigned long long zbits = __float_as_uint(ws.rec2[i].w);
+    const float4 *rec = ws.rec + 4 * i;
+    const float4 r0 = rec[0], r1 = rec[1], r3 = rec[3];
+    const unsigned long long zbits = __float_as_uint(rec[2].w);
     unsigned long long *keys = ws.keys[0];
     uint32_t *vals = ws.vals[0];
     const uint32_t cap = ws.cap;

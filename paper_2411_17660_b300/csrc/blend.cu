@@ -299,17 +299,17 @@ __device__ __forceinline__ int stage_chunk(const Ws &ws, const uint32_t *vals, s
         float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);
         float ur = 0.f, vr = 0.f;
         if (g[k] < ws.N) {
-            const float4 r0 = ws.rec0[vN + g[k]];
-            r1 = ws.rec1[vN + g[k]];
+            const float4 *rec = ws.rec + 4 * (vN + g[k]);
+            const float4 r0 = rec[0];
+            r1 = rec[1];
             ur = __fadd_rn(__fsub_rn(r0.x, (float)X0), r0.z);
             vr = __fadd_rn(__fsub_rn(r0.y, (float)Yr), r0.w);
             keep = touches_block<BH>(ur, Y0 == Yr ? vr : __fsub_rn(vr, (float)(Y0 - Yr)), r1.x, r1.y, r1.z, r1.w);
         }
         const unsigned ballot = __ballot_sync(kFull, keep);
         if (keep) {
-            const size_t gi = vN + g[k];
-            write(n + __popc(ballot & lanemask_lt()), ur, vr, r1, ws.rec2[gi], ws.rec3[gi].x, base + 32u * k + lane,
-                  g[k]);
+            const float4 *rec = ws.rec + 4 * (vN + g[k]);
+            write(n + __popc(ballot & lanemask_lt()), ur, vr, r1, rec[2], rec[3].x, base + 32u * k + lane, g[k]);
         }
         n += __popc(ballot);
     }
@@ -335,6 +335,8 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::TH
     using S = BlendShape<TS, BH>;
     __shared__ float4 sF[S::WARPS][kFwdQuads][32 * CH];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the preprocess left this layout's gradient rows zero (rows_known_clean)
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_rows_clean(ws, true);
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.sorted;
@@ -591,6 +593,8 @@ __global__ void __launch_bounds__(BlendShape<TS, BwdBlock<TS>::H>::THREADS, BwdB
     __shared__ float4 sE[S::WARPS][kBwdQuads][32 * CH];
     __shared__ float4 sX[S::WARPS][32 * CH];  // (s_max, list index, Gaussian index, -)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the rows fill up here until the preprocess backward clears them again
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_rows_clean(ws, false);
     const WarpTile wt = warp_tile<TS, BH>(vt, ws);
     const ViewParams &vp = vt.v[wt.v];
     const uint32_t *vals = ws.sorted;

@@ -79,6 +79,8 @@ struct GaussianPtrs {
 };
 
 // Device-side state at the start of the workspace.
+constexpr int kRowsCleanWords = 8;
+
 struct WsHeader {
     int32_t status;                 // first device error (gsr_status)
     uint32_t key_capacity;
@@ -92,7 +94,11 @@ struct WsHeader {
     uint32_t pairs_visible;         // (view, Gaussian) pairs with tile keys (records written), Gaussians only
     uint32_t order_counter;         // tile-order count kernel: blocks done (zeroed by the init kernel)
     unsigned long long pairs_bwd;   // checked builds: contributor pairs the blend backward took
-    uint32_t pad[64 - 14 - kMaxPasses];
+    uint32_t pad[64 - 14 - kMaxPasses - kRowsCleanWords];
+    // The layout whose screen-gradient rows are known to be all zero (tag,
+    // byte offset of the rows in the workspace, N, V, row stride); kept by the
+    // init kernel, see rows_known_clean below.
+    uint32_t rows_clean[kRowsCleanWords];
 };
 static_assert(sizeof(WsHeader) == 256, "header must stay one 256-byte block");
 
@@ -102,10 +108,12 @@ struct Ws {
     uint32_t *counts;        // [V*N] tiles touched by (view, Gaussian)
     uint32_t *offsets;       // [V*N] exclusive scan of counts
     unsigned long long *scan_partials;  // [scan_blocks]
-    float4 *rec0;            // [V*N] (u_hi, v_hi, u_lo, v_lo)
-    float4 *rec1;            // [V*N] (m00, m01, m11, s_max)
-    float4 *rec2;            // [V*N] (r, g, b, z)
-    float4 *rec3;            // [V*N] (log2 opacity, Sxx, Sxy, Syy)
+    // [V*N][4] one 64-byte record per pair: rec[4i] (u_hi, v_hi, u_lo, v_lo),
+    // rec[4i+1] (m00, m01, m11, s_max), rec[4i+2] (r, g, b, z), rec[4i+3]
+    // (log2 opacity, Sxx, Sxy, Syy); a pair's record fills whole 32-byte
+    // sectors, so writing the visible pairs' records never leaves a sector
+    // partly written (which L2 would complete with a read from DRAM)
+    float4 *rec;
     float *radius;           // [V*N] 3 sqrt(lambda_max(Sigma')) if the pair is visible for densification, else 0
     float4 *rec4;            // [V*N] surfels: (n_x, n_y, n_z, 0) normal towards the camera
     float4 *rec5;            // [V*N] surfels: (x_lo, y_lo, x_hi, y_hi) pixel bounds of the cutoff region
@@ -139,6 +147,48 @@ struct Ws {
     uint32_t spin_limit;
     int test_flags;
 };
+
+// Screen-gradient rows.  The blend backward accumulates into the rows of the
+// visible pairs, which must start at zero; the preprocess backward clears
+// every row it reads.  So between iterations on one layout the rows stay
+// zero, and the forward clears them only when the header does not record
+// this layout as clean: a fresh or foreign workspace, another layout (N, V,
+// image sizes or key capacity moved the rows), surfel rows, or a backward
+// whose preprocess half did not run.  The Gaussian blend forward records
+// the layout once the preprocess has cleared (or found clean) the rows; the
+// blend backward withdraws the record and the pose reduction after the
+// preprocess backward restores it; the surfel forward withdraws it.
+constexpr uint32_t kRowsCleanTag0 = 0x52c3e9a1u, kRowsCleanTag1 = 0x0d7b46f5u;
+
+__device__ __forceinline__ void rows_clean_record(const Ws &ws, uint32_t (&d)[kRowsCleanWords]) {
+    const unsigned long long off =
+        (unsigned long long)(reinterpret_cast<const char *>(ws.vg_grads) - reinterpret_cast<const char *>(ws.hdr));
+    d[0] = kRowsCleanTag0;
+    d[1] = kRowsCleanTag1;
+    d[2] = (uint32_t)off;
+    d[3] = (uint32_t)(off >> 32);
+    d[4] = ws.N;
+    d[5] = ws.V;
+    d[6] = ws.vg_stride;
+    d[7] = 0u;
+}
+
+__device__ __forceinline__ bool rows_known_clean(const Ws &ws) {
+    uint32_t d[kRowsCleanWords];
+    rows_clean_record(ws, d);
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < kRowsCleanWords; ++k) same &= ws.hdr->rows_clean[k] == d[k];
+    return same;
+}
+
+// One thread records the layout as clean (or withdraws the record).
+__device__ __forceinline__ void set_rows_clean(const Ws &ws, bool clean) {
+    uint32_t d[kRowsCleanWords];
+    rows_clean_record(ws, d);
+#pragma unroll
+    for (int k = 0; k < kRowsCleanWords; ++k) ws.hdr->rows_clean[k] = clean ? d[k] : 0u;
+}
 
 // Gaussians (not surfels) binned per tile emit their tile keys in the
 // preprocess: each warp reserves its pairs' keys with one atomic on the key

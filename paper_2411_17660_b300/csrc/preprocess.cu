@@ -123,15 +123,21 @@ __device__ __forceinline__ bool preprocess_fwd_pair(const ViewTable &vt, const G
         for (int j = 0; j < K; ++j) acc = fmaf(cf[c][j], Y[j], acc);
         rgb[c] = fmaxf(acc, 0.f);
     }
-    ws.rec0[i] = make_float4(puh, pvh, q.ul[k], q.vl[k]);
-    ws.rec1[i] = make_float4(m00, q.m01[k], q.m11[k], smax);
-    ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
-    ws.rec3[i] = make_float4(log2o, sxx, sxy, syy);
-    // the backward's blend accumulates this pair's screen gradients with atomics
-    float2 *row = reinterpret_cast<float2 *>(ws.vg_grads + ((size_t)pg * ws.V + pv) * kVGGrads);
-#pragma unroll
-    for (int k = 0; k < kVGGrads / 2; ++k) row[k] = make_float2(0.f, 0.f);
+    float4 *rec = ws.rec + 4 * i;
+    rec[0] = make_float4(puh, pvh, q.ul[k], q.vl[k]);
+    rec[1] = make_float4(m00, q.m01[k], q.m11[k], smax);
+    rec[2] = make_float4(rgb[0], rgb[1], rgb[2], q.zh[k]);
+    rec[3] = make_float4(log2o, sxx, sxy, syy);
     return true;
+}
+
+// The grid's share of zeroing every (Gaussian, view) gradient row (kept out
+// of line: it runs only when a layout's rows are not known clean).
+__device__ __noinline__ void clear_rows(const Ws &ws) {
+    float2 *rows = reinterpret_cast<float2 *>(ws.vg_grads);
+    const size_t n = (size_t)ws.N * ws.V * (kVGGrads / 2);
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        rows[k] = make_float2(0.f, 0.f);
 }
 
 template <int DEG>
@@ -141,6 +147,12 @@ __global__ void __launch_bounds__(kPreThreads, kPreFwdBlocksPerSM) preprocess_fw
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
     __shared__ WarpQueue s_q[kPreWarps];
     load_poses(vt, s_pose);
+    // The blend backward accumulates the visible pairs' screen gradients into
+    // rows that must be zero; unless the header records this layout's rows
+    // as clean, all blocks clear them first (their last use was the blend
+    // backward of another layout, or nothing).  Clearing only the visible
+    // pairs' rows in every forward cost the outdoor preprocess 0.55 of 2.4 ms.
+    if (!rows_known_clean(ws)) clear_rows(ws);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpQueue &q = s_q[warp];
     const size_t N = (size_t)gp.N;
@@ -301,6 +313,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     constexpr int K = BwdAcc<DEG>::K;
     const size_t N = (size_t)gp.N;
     const size_t i = (size_t)v * N + g;
+    // the forward's colour, loaded first: its latency overlaps the projection
+    // (the blend's screen gradients loaded here too: uneven 0.805 -> 0.827 ms)
+    const float4 rgb = __ldg(ws.rec + 4 * i + 2);
     GaussPre G;
     gauss_pre(gp, g, G);
     Proj p;
@@ -310,6 +325,9 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     for (int k = 0; k < 9; ++k) dM[k] = 0.f;
     float dlno = 0.f;
     if (!project_view(G, ps, vp, p)) {   // same decision as the forward; kept for safety
+        float2 *row = reinterpret_cast<float2 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kVGGrads);
+#pragma unroll
+        for (int c = 0; c < kVGGrads / 2; ++c) row[c] = make_float2(0.f, 0.f);   // rows stay clean
 #pragma unroll
         for (int k = 0; k < BwdAcc<DEG>::NS; ++k) part[k] = 0.f;
 #pragma unroll
@@ -332,7 +350,6 @@ __device__ __forceinline__ void pair_backward(const GaussianPtrs &gp, const Ws &
     view_dir(G, ps, dx, dy, dz, rn);
     float Y[K];
     sh_eval<DEG>(dx, dy, dz, Y);
-    const float4 rgb = ws.rec2[i];
     const float dr0 = rgb.x > 0.f ? sg[6] : 0.f, dr1 = rgb.y > 0.f ? sg[7] : 0.f, dr2 = rgb.z > 0.f ? sg[8] : 0.f;
     float wk[K];
     const float *shg = gp.sh + g;
@@ -808,7 +825,11 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(const __grid_constant_
     }
     float *dst = vt.v[v].d_pose;
     if (threadIdx.x < 6 && dst) dst[threadIdx.x] = accumulate ? dst[threadIdx.x] + s[0][threadIdx.x] : s[0][threadIdx.x];
-    if (v == 0 && threadIdx.x == 0) ws.hdr->bwd_groups = 0u;   // for the next backward on this workspace
+    if (v == 0 && threadIdx.x == 0) {
+        ws.hdr->bwd_groups = 0u;   // for the next backward on this workspace
+        // the preprocess backward has cleared every row the blend backward wrote
+        if (!ws.surfels) set_rows_clean(ws, true);
+    }
 }
 
 // ------------------------------------------------------------------ launchers

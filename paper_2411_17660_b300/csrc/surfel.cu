@@ -7,11 +7,12 @@
 // Per (view, Gaussian) the preprocess computes, in the camera frame,
 // a = s_u W t_u, b = s_v W t_v, p = W mu + t (compensated) and the normal,
 // and bounds the screen region rho <= d2max by the projected disk (dual
-// conic) and the low-pass disk.  Records:
-//   rec0 = (u_hi, v_hi, u_lo, v_lo)   projected centre (double-float)
-//   rec1 = (a_x, a_y, a_z, b_x)
-//   rec2 = (r, g, b, p_z)              p_z: the depth key of the sort
-//   rec3 = (log2 sigma, s_max, b_y, b_z)
+// conic) and the low-pass disk.  Records (rec[4i + k], one 64-byte record
+// per pair, then two more arrays):
+//   k = 0: (u_hi, v_hi, u_lo, v_lo)   projected centre (double-float)
+//   k = 1: (a_x, a_y, a_z, b_x)
+//   k = 2: (r, g, b, p_z)              p_z: the depth key of the sort
+//   k = 3: (log2 sigma, s_max, b_y, b_z)
 //   rec4 = (n_x, n_y, n_z, 0)
 //   rec5 = (x_lo, y_lo, x_hi, y_hi)    pixel-centre bounds of the cutoff region
 // For a pixel (x, y) = (X0 + lx, Y0 + ly) of a warp's 8x8 block the planes
@@ -48,6 +49,8 @@ __global__ void __launch_bounds__(128) surfel_pre_fwd_kernel(const __grid_consta
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ Pose s_pose[GSR_MAX_VIEWS];
     load_poses(vt, s_pose);
+    // surfel rows overwrite the Gaussian layout's (rows_known_clean)
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_rows_clean(ws, false);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= gp.N) return;
     const size_t N = (size_t)gp.N;
@@ -119,10 +122,11 @@ __global__ void __launch_bounds__(128) surfel_pre_fwd_kernel(const __grid_consta
                         for (int k = 0; k < K; ++k) acc = fmaf(__ldg(shc + (size_t)k * 3 * N), Y[k], acc);
                         rgb[c] = fmaxf(acc, 0.f);
                     }
-                    ws.rec0[i] = make_float4(uh, vh, ul, vl);
-                    ws.rec1[i] = make_float4(a[0], a[1], a[2], b[0]);
-                    ws.rec2[i] = make_float4(rgb[0], rgb[1], rgb[2], zh);
-                    ws.rec3[i] = make_float4(G.log2o, G.smax, b[1], b[2]);
+                    float4 *rec = ws.rec + 4 * i;
+                    rec[0] = make_float4(uh, vh, ul, vl);
+                    rec[1] = make_float4(a[0], a[1], a[2], b[0]);
+                    rec[2] = make_float4(rgb[0], rgb[1], rgb[2], zh);
+                    rec[3] = make_float4(G.log2o, G.smax, b[1], b[2]);
                     ws.rec4[i] = make_float4(n[0], n[1], n[2], 0.f);
                     ws.rec5[i] = rect;
                     float4 *row = reinterpret_cast<float4 *>(ws.vg_grads + ((size_t)g * ws.V + v) * kSG);
@@ -214,7 +218,8 @@ __device__ __forceinline__ Tile tile_of(const ViewTable &vt, const Ws &ws) {
 
 __device__ __forceinline__ void stage_entry(float4 (*sE)[32], const Ws &ws, const ViewParams &vp, int X0, int Y0,
                                             int slot, size_t gi, uint32_t idx, uint32_t g) {
-    const float4 r0 = ws.rec0[gi], r1 = ws.rec1[gi], r2 = ws.rec2[gi], r3 = ws.rec3[gi], r4 = ws.rec4[gi];
+    const float4 *rec = ws.rec + 4 * gi;
+    const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3], r4 = ws.rec4[gi];
     const float ox = (float)X0 - vp.cx, oy = (float)Y0 - vp.cy;
     // (a_x, a_y, a_z, b_x) = r1, (b_y, b_z) = r3.zw
     sE[0][slot] = make_float4(vp.fx * r1.x - ox * r1.z, vp.fx * r1.w - ox * r3.w, vp.fy * r1.y - oy * r1.z,
@@ -589,7 +594,7 @@ __global__ void __launch_bounds__(kPB) surfel_pre_bwd_kernel(const __grid_consta
             view_dir(G, ps, dx, dy, dz, rn);
             float Y[K];
             sh_eval<DEG>(dx, dy, dz, Y);
-            const float4 rgb = ws.rec2[(size_t)v * N + g];
+            const float4 rgb = ws.rec[4 * ((size_t)v * N + g) + 2];
             const float dr0 = rgb.x > 0.f ? sg[10] : 0.f, dr1 = rgb.y > 0.f ? sg[11] : 0.f,
                         dr2 = rgb.z > 0.f ? sg[12] : 0.f;
             float wk[K];

@@ -134,6 +134,117 @@ def test_stop_with_zero_off_diagonal_and_both_clamp_paths():
     U.compare_grads(gref, g, label="axis band")
 
 
+def _edge_stress(seed=41, N=3000, H=48, W=64, f=60.0):
+    """Gaussians around the image borders (centres from 0.6 image widths
+    outside to 0.6 inside past the far edge), beyond the Jacobian clamp, and
+    at the near plane, anisotropic with opacities across the alpha cutoff,
+    seen by three cameras 2.6 km from the world origin (large coordinates
+    whose camera transform cancels).  The forward's conservative cull must
+    keep every pair whose cutoff ellipse reaches a pixel centre."""
+    import dataclasses
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(seed)
+    base = scenes.config_small(seed=seed, N=N, H=H, W=W, f=f)
+    near = rng.uniform(size=N) < 0.2
+    z = np.where(near, rng.uniform(0.19, 0.26, N), rng.uniform(0.3, 8.0, N))
+    u = rng.uniform(-0.6 * W, 1.6 * W, N)
+    v = rng.uniform(-0.6 * H, 1.6 * H, N)
+    O = np.array([2000.0, -700.0, 1500.0])
+    means = np.stack([(u - W / 2) * z / f, (v - H / 2) * z / f, z]) + O[:, None]
+    rots = [np.eye(3), Rotation.from_rotvec([0.0, 0.3, 0.0]).as_matrix(),
+            Rotation.from_rotvec([-0.25, 0.0, 0.2]).as_matrix()]
+    centres = [O, O + np.array([0.5, 0.2, -0.3]), O + np.array([-0.3, 0.1, 0.2])]
+    cams = [scenes.Camera(H, W, f, f, W / 2, H / 2, scenes.pose_from_c2w(Rm, C)) for Rm, C in zip(rots, centres)]
+    sc = dataclasses.replace(
+        base, means=np.ascontiguousarray(means.astype(np.float32)),
+        log_scales=np.ascontiguousarray(np.minimum(rng.normal(-2.5, 1.0, (3, N)), 0.5).astype(np.float32)),
+        quats=np.ascontiguousarray(rng.normal(size=(4, N)).astype(np.float32)),
+        opacity_logits=np.ascontiguousarray(rng.normal(0.0, 3.0, N).astype(np.float32)))
+    return sc.with_cameras(cams)
+
+
+def test_conservative_cull_keeps_every_reaching_pair():
+    """The preprocess culls (view, Gaussian) pairs with FP32 bounds before
+    the exact projection: on pairs placed at the borders, past the Jacobian
+    clamp and at the near plane, the images equal the oracle's and so does
+    every Gaussian's count of views whose cutoff ellipse reaches a pixel
+    centre (a culled pair gets radius 0)."""
+    sc = _edge_stress()
+    got, state = U.gpu_forward(sc)
+    ref = oracle.render(sc)
+    for v in range(sc.V):
+        U.compare_images(ref[v], got[v], f"edge stress view {v}")
+    # the scene reaches the cases: visible pairs centred outside the image,
+    # clamped ones, near-plane ones
+    outside = clamped = near = 0
+    for c in sc.cameras:
+        P = oracle.project(sc, camera=c)
+        for g in np.nonzero(P["valid"])[0]:
+            d2max = min(9.0, 2.0 * np.log(255.0 * P["opacity"][g]))
+            if not d2max >= 0:
+                continue
+            q = oracle._quad_min_over_box(P["conic0"][g], P["conic1"][g], P["conic2"][g], P["u"][g], P["v"][g],
+                                          0.0, c.W - 1.0, 0.0, c.H - 1.0)
+            if q > d2max:
+                continue
+            outside += not (0 <= P["u"][g] <= c.W - 1 and 0 <= P["v"][g] <= c.H - 1)
+            clamped += bool(P["clamp_x"][g] or P["clamp_y"][g])
+            near += P["z"][g] < 0.26
+    assert outside > 300 and clamped > 100 and near > 20, (outside, clamped, near)
+    rast, params, cams, vm, ws, color, depth, alpha = state
+    gC, gD, gA = U.upstream(sc)
+    flat = lambda arrs: torch.from_numpy(np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in arrs])).cuda()
+    dens = {k: torch.full((sc.N,), np.nan, device="cuda") for k in ("grad", "count", "radius")}
+    grads = {k: torch.empty_like(x) for k, x in params.items()}
+    rast.backward_raw(params, sc.sh_degree, cams, vm, ws, flat(gC), flat(gD), flat(gA), grads, None, densify=dens)
+    torch.cuda.synchronize()
+    count = dens["count"].cpu().numpy()
+    _, rg = oracle.render_backward(sc, gC, gD, gA, want_screen=True)
+    ref_d = oracle.densify_stats(sc, rg["screen"])
+    sure = ref_d["margin"] > 1e-3
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(count[sure], ref_d["count"][sure])
+
+
+def test_gradient_rows_clean_record():
+    """The forward clears the screen-gradient rows only when the workspace
+    header does not record this layout's rows as clean.  A workspace of
+    garbage, a surfel forward and backward (whose rows stay filled) in
+    between, a smaller Gaussian set on the same workspace, and back-to-back
+    iterations all give the gradients of a fresh workspace."""
+    sc = REDUCED["window"]()
+    gC, gD, gA = U.upstream(sc)
+    _, ref_state = U.gpu_forward(sc)
+    ref = U.gpu_backward(sc, ref_state, gC, gD, gA)
+    rast, params, cams, vm, ws = ref_state[:5]
+
+    def step(scene, prm, ws):
+        color, depth, alpha, ws2 = rast.render_forward(prm, scene.sh_degree, cams, vm, ws=ws, grow=False)
+        assert ws2 is ws and rast.info(ws).status == B.OK
+        return U.gpu_backward(scene, (rast, prm, cams, vm, ws, color, depth, alpha), gC, gD, gA)
+
+    def same(a, b, label):
+        for k in a:
+            assert U.rel_l2(b[k], a[k]) < 1e-5, (label, k, U.rel_l2(b[k], a[k]))
+
+    ws.fill_(255)   # every float NaN, no record
+    same(ref, step(sc, params, ws), "garbage workspace")
+    same(ref, step(sc, params, ws), "second iteration")
+    P = R.pixel_offsets(cams)[-1]
+    bufs = [torch.empty(n * P, device="cuda") for n in (3, 1, 1, 3, 1)]
+    rast.surfels_forward_raw(params, sc.sh_degree, cams, vm, ws, *bufs)
+    ups = [torch.rand(n * P, device="cuda") - 0.5 for n in (3, 1, 1, 3, 1)]
+    sg = {k: torch.empty_like(x) for k, x in params.items()}
+    rast.surfels_backward_raw(params, sc.sh_degree, cams, vm, ws, *ups, sg, None)
+    same(ref, step(sc, params, ws), "after surfels")
+    sub = sc.subset(np.arange(0, sc.N, 2))
+    _, sub_state = U.gpu_forward(sub)
+    sub_ref = U.gpu_backward(sub, sub_state, gC, gD, gA)
+    sub_params = U.to_device(sub)[0]
+    same(sub_ref, step(sub, sub_params, ws), "smaller set, same workspace")
+    same(ref, step(sc, params, ws), "full set again")
+
+
 @pytest.mark.parametrize("tile,binning,rows", [(8, "tile", 8), (16, "tile", 16), (16, "tile", 8), (32, "tile", 16),
                                                (32, "tile", 8), (16, "radix", 16)])
 def test_decisions_backward_equals_forward(tile, binning, rows):
