@@ -403,14 +403,15 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::TH
                 bool st = false;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    const float2 p1 = make_float2(__fmaf_rn(q0.z, ly[p].x, t), __fmaf_rn(q0.z, ly[p].y, t));
-                    const float2 p2 = make_float2(__fmaf_rn(q0.w, ly[p].x, q1.x), __fmaf_rn(q0.w, ly[p].y, q1.x));
+                    // packed: each half is the same fma.rn as the scalar form
+                    const float2 p1 = __ffma2_rn(make_float2(q0.z, q0.z), ly[p], make_float2(t, t));
+                    const float2 p2 = __ffma2_rn(make_float2(q0.w, q0.w), ly[p], make_float2(q1.x, q1.x));
                     const float2 s = __ffma2_rn(p1, p1, __fmul2_rn(p2, p2));
                     m[p] = make_float2(le_mask(s.x, q1.y), le_mask(s.y, q1.y));   // the entry reaches the pixel
                     // alpha = min(0.99, 2^(log2(sigma) - s)), times the mask;
                     // chunks whose Gaussians all lie below kLog2ClampFree skip the clamp
-                    float2 e = make_float2(ex2_approx(__fmaf_rn(s.x, -1.f, q1.z)),
-                                           ex2_approx(__fmaf_rn(s.y, -1.f, q1.z)));
+                    const float2 earg = __ffma2_rn(s, neg2, make_float2(q1.z, q1.z));   // 0.0877 -> 0.0855 ms
+                    float2 e = make_float2(ex2_approx(earg.x), ex2_approx(earg.y));
                     if constexpr (decltype(clamp)::value) e = make_float2(fminf(kAlphaMax, e.x), fminf(kAlphaMax, e.y));
                     w[p] = __fmul2_rn(__fmul2_rn(e, m[p]), T[p]);
                     Tn[p] = __ffma2_rn(w[p], neg2, T[p]);                    // T (1 - alpha)
@@ -448,10 +449,12 @@ __global__ void __launch_bounds__(BlendShape<TS, FwdBlock<TS, MED, ROWS>::H>::TH
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                     cnt[p] = __fadd2_rn(cnt[p], m[p]);
-                    C0[p].x = __fmaf_rn(w[p].x, q2.x, C0[p].x), C0[p].y = __fmaf_rn(w[p].y, q2.x, C0[p].y);
-                    C1[p].x = __fmaf_rn(w[p].x, q2.y, C1[p].x), C1[p].y = __fmaf_rn(w[p].y, q2.y, C1[p].y);
-                    C2[p].x = __fmaf_rn(w[p].x, q2.z, C2[p].x), C2[p].y = __fmaf_rn(w[p].y, q2.z, C2[p].y);
-                    D[p].x = __fmaf_rn(w[p].x, q2.w, D[p].x), D[p].y = __fmaf_rn(w[p].y, q2.w, D[p].y);
+                    // colour and depth sums of both rows, packed (window blend forward
+                    // 0.0898 -> 0.0877 ms with the linear forms above)
+                    C0[p] = __ffma2_rn(w[p], make_float2(q2.x, q2.x), C0[p]);
+                    C1[p] = __ffma2_rn(w[p], make_float2(q2.y, q2.y), C1[p]);
+                    C2[p] = __ffma2_rn(w[p], make_float2(q2.z, q2.z), C2[p]);
+                    D[p] = __ffma2_rn(w[p], make_float2(q2.w, q2.w), D[p]);
                     T[p] = Tn[p];
                 }
             }
