@@ -34,13 +34,15 @@ constexpr int kPreFwdBlocksPerSM = 3;
 // records.  Warps never wait for each other, and the expensive part runs
 // with full warps however few pairs are visible.
 constexpr int kQueue = 64;   // a warp's queue: up to 31 waiting + 32 appended
-// Views of one forward work item: 8, or 2 when 8 would leave the warps fewer
-// than kPreItemsPerWarp items each (the window: 0.060 -> 0.057 ms with 2
-// instead of 4; on the 16- and 32-view workloads 2 measured 7 % slower than
-// 4, 1 view per item slower still, and 8 faster than 4: uneven 0.387 ->
-// 0.372 ms, outdoor 2.406 -> 2.391 ms).
+// Views of one forward work item: 8, or kPreSmallItemViews when 8 would leave
+// the warps fewer than kPreItemsPerWarp items each (the window, with the
+// forward no longer clearing gradient rows: 4-view items 0.0472 ms against
+// 0.0487 with 2 and 0.0512 with 8; on the 16- and 32-view workloads 2
+// measured 7 % slower than 4, 1 view per item slower still, and 8 faster
+// than 4: uneven 0.387 -> 0.372 ms, outdoor 2.406 -> 2.391 ms).
 constexpr int kPreItemsPerWarp = 4;
 constexpr int kPreItemViews = 8;
+constexpr int kPreSmallItemViews = 4;
 
 struct WarpQueue {
     float uh[kQueue], vh[kQueue], ul[kQueue], vl[kQueue];
@@ -845,7 +847,7 @@ static cudaError_t launch_pre_fwd(const ViewTable &vt, const GaussianPtrs &gp, c
     const long long batches = ((long long)gp.N + 31) / 32;
     const long long max_warps = (long long)sm_count * kPreFwdBlocksPerSM * kPreWarps;
     const int item_views =
-        batches * ((vt.V + kPreItemViews - 1) / kPreItemViews) < kPreItemsPerWarp * max_warps ? 2 : kPreItemViews;
+        batches * ((vt.V + kPreItemViews - 1) / kPreItemViews) < kPreItemsPerWarp * max_warps ? kPreSmallItemViews : kPreItemViews;
     const long long items = batches * ((vt.V + item_views - 1) / item_views);
     const long long need = (items + kPreWarps - 1) / kPreWarps;
     const unsigned blocks = (unsigned)std::min<long long>(need, (long long)sm_count * kPreFwdBlocksPerSM);
