@@ -303,7 +303,7 @@ struct BwdAcc {
     // shared-memory floats of the partials and of the run totals (one view
     // needs neither: each pair is finished by its own thread)
     __host__ __device__ static constexpr int parts(int VW) { return VW == 1 ? 0 : NVP * kPreThreads; }
-    __host__ __device__ static constexpr int tots(int VW) { return VW == 1 ? 0 : 13 * kPreThreads; }
+    __host__ __device__ static constexpr int tots(int VW, int GBT) { return VW == 1 ? 0 : 13 * GBT; }
 };
 
 // Backward of one visible (view, Gaussian) pair; writes its NV partials to
@@ -494,7 +494,7 @@ static size_t bwd_smem_bytes() {
     using S = BwdShape<VW>;
     constexpr size_t NS = BwdAcc<DEG>::NS;
     return sizeof(unsigned long long) * S::GBT +
-           sizeof(float) * (BwdAcc<DEG>::parts(VW) + 6 * kPreThreads + BwdAcc<DEG>::tots(VW) + 2 * NS + 6 * VW) +
+           sizeof(float) * (BwdAcc<DEG>::parts(VW) + 6 * kPreThreads + BwdAcc<DEG>::tots(VW, S::GBT) + 2 * NS + 6 * VW) +
            sizeof(int) * (S::LC + 5 * S::GBT);
 }
 
@@ -557,8 +557,8 @@ __device__ __forceinline__ void preprocess_bwd_group(const ViewTable &vt, const 
     unsigned long long *s_mask = smem_u64;             // [GBT] visible views of each Gaussian
     float *s_part = reinterpret_cast<float *>(s_mask + GBT);   // [256][NVP] per-pair partials of a chunk
     float *s_pose = s_part + BwdAcc<DEG>::parts(VW);   // [6][256] per-pair pose twists
-    float *s_tot = s_pose + 6 * kPreThreads;           // [256][13] totals of the runs that end in a chunk
-    float *s_carry = s_tot + BwdAcc<DEG>::tots(VW);    // [2][NS] partial sums of a run cut by a chunk's end
+    float *s_tot = s_pose + 6 * kPreThreads;           // [GBT][13] each Gaussian's view-summed totals
+    float *s_carry = s_tot + BwdAcc<DEG>::tots(VW, GBT);   // [2][NS] partial sums of a run cut by a chunk's end
     float *s_vpose = s_carry + 2 * NS;                 // [VW][6] pose partials per view
     int *s_item = reinterpret_cast<int *>(s_vpose + 6 * VW);   // [LC] (Gaussian << 8 | view) per list position
     int *s_first = s_item + S::LC;                     // [GBT] list position of each Gaussian's run
@@ -697,7 +697,7 @@ __device__ __forceinline__ void preprocess_bwd_group(const ViewTable &vt, const 
             if (c0 + p + 1 < first + s_cnt[gl]) {
                 carry_out[k] = x;   // continues in the next chunk
             } else if (k < 13) {
-                s_tot[j * 13 + k] = x;
+                s_tot[gl * 13 + k] = x;
             } else if (k == NV) {
                 s_dgrad[gl] = x;
             } else {
@@ -747,16 +747,14 @@ __device__ __forceinline__ void preprocess_bwd_group(const ViewTable &vt, const 
                 for (int c = 0; c < 6; ++c) s_vpose[v * 6 + c] += pv[c];
         }
         __syncthreads();
-        // Gaussians whose runs ended in this chunk
-        for (int j = tid; j < nruns; j += kPreThreads) {
-            const int p = s_end[j], gl = s_item[c0 + p] >> 8;
-            if (c0 + p + 1 < s_first[gl] + s_cnt[gl]) continue;
-            float acc[13];
-#pragma unroll
-            for (int k = 0; k < 13; ++k) acc[k] = s_tot[j * 13 + k];
-            bwd_finish(gp, out, gbase + gl, acc);
-        }
-        __syncthreads();
+    }
+    // The parameter gradients of every Gaussian visible somewhere, from its
+    // totals, once the group's list is done: all threads at once, instead of
+    // the few whose Gaussians' runs ended in a chunk while the rest waited at
+    // the chunk's barrier.
+    if constexpr (VW != 1) {
+        for (int gl = tid; gl < GBT; gl += kPreThreads)
+            if (gbase + gl < gp.N && s_cnt[gl] != 0) bwd_finish(gp, out, gbase + gl, s_tot + gl * 13);
     }
 
     // Gaussians visible in no view: zero gradients
