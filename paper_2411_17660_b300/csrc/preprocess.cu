@@ -712,21 +712,34 @@ __device__ __forceinline__ void preprocess_bwd_group(const ViewTable &vt, const 
         // the walk would keep most of the block waiting at its barrier
         // (uneven, 16 views: the warps take 0.799 against 0.854 ms).
         if (VW >= 32) {
-            // one thread per view walks the runs ending in this chunk and
-            // picks its view's entry from the Gaussian's mask
-            for (int v = tid; v < vt.V; v += kPreThreads) {
+            // eight lanes per view walk the runs ending in this chunk (lane
+            // part of the eight takes runs part, part + 8, ...) and pick
+            // their view's entry from the Gaussian's mask; a fixed xor tree
+            // adds the eight sums (one thread per view left 7/8 of the block
+            // at the barrier: outdoor 4.06 -> 3.76 ms)
+            const int part = lane & 7;
+            for (int v = tid >> 3; v < VW; v += kPreThreads / 8) {   // the same trip count in a warp
                 float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int j = 0; j < nruns; ++j) {
-                    const int gl = s_item[c0 + s_end[j]] >> 8;
-                    const unsigned long long m = s_mask[gl];
-                    if (!((m >> v) & 1ull)) continue;
-                    const int pos = s_first[gl] + __popcll(m & ((1ull << v) - 1ull)) - c0;
-                    if (pos < 0 || pos >= n) continue;   // in an earlier or a later chunk
+                if (v < vt.V) {
+                    for (int j = part; j < nruns; j += 8) {
+                        const int gl = s_item[c0 + s_end[j]] >> 8;
+                        const unsigned long long m = s_mask[gl];
+                        if (!((m >> v) & 1ull)) continue;
+                        const int pos = s_first[gl] + __popcll(m & ((1ull << v) - 1ull)) - c0;
+                        if (pos < 0 || pos >= n) continue;   // in an earlier or a later chunk
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) pv[c] += s_pose[c * kPreThreads + pos];
+                        for (int c = 0; c < 6; ++c) pv[c] += s_pose[c * kPreThreads + pos];
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < 6; ++c) s_vpose[v * 6 + c] += pv[c];
+                for (int c = 0; c < 6; ++c) {
+                    pv[c] += __shfl_xor_sync(0xffffffffu, pv[c], 4);
+                    pv[c] += __shfl_xor_sync(0xffffffffu, pv[c], 2);
+                    pv[c] += __shfl_xor_sync(0xffffffffu, pv[c], 1);
+                }
+                if (part == 0 && v < vt.V)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) s_vpose[v * 6 + c] += pv[c];
             }
         } else
         // warp w takes views w, w + 8, ...: lanes stride the chunk, then a butterfly
