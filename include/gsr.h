@@ -16,7 +16,12 @@
  * caller, except where marked "host".  The library allocates no device
  * memory: the caller provides one workspace buffer per render (size from
  * gsr_workspace_size) and must pass the same workspace, Gaussians and views
- * to gsr_render_backward as to the gsr_render it differentiates.  All calls
+ * to gsr_render_backward as to the gsr_render it differentiates.  A
+ * workspace may start with any content and may be reused for other scenes;
+ * between iterations on one layout it keeps its per-pair gradient rows zero
+ * (the backward clears them after use, and its header records the layout
+ * whose rows are clean, so that the next gsr_render need not clear them;
+ * on any other layout or content gsr_render clears them all).  All calls
  * enqueue work on the given stream and return without synchronising, except
  * gsr_read_info, which waits for the stream.
  *
@@ -359,8 +364,8 @@ gsr_status gsr_render_surfels_backward(gsr_ctx *ctx, const gsr_gaussians *gs, co
  * launch and events[1+k] after forward stage k (0 preprocess, 1 scan + key
  * duplication, 2 radix sort, 3 tile ranges, 4 blend); gsr_render_backward
  * records events[6] before its first launch and events[7+k] after backward
- * stage k (0 gradient clear, 1 blend backward, 2 preprocess backward with the
- * pose reduction).  Elapsed times between consecutive events are the stage
+ * stage k (0 empty: the gradient rows are already zero, 1 blend backward, 2
+ * preprocess backward with the pose reduction).  Elapsed times between consecutive events are the stage
  * durations on the device. */
 #define GSR_STAGE_EVENTS 10
 gsr_status gsr_set_stage_events(gsr_ctx *ctx, void *const *events);

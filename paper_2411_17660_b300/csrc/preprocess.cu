@@ -2,14 +2,16 @@
 // (activation, camera transform, EWA projection, SH colour, exact tile count)
 // and its backward (projection/SH chain rule, per-view SE(3) pose reduction).
 //
-// Forward: a block owns 256 / VW Gaussians (VW = min(V, 8), a power of two)
-// and takes the views VW at a time; it projects every pair, compacts the
+// Forward: persistent warps take work items of 32 Gaussians (one per lane)
+// and up to 8 views; each warp projects every pair of an item, queues the
 // visible ones in shared memory and gives the expensive part (tile count, SH
-// colour, records) to full warps of visible pairs.
-// Backward: a block owns 32 Gaussians; it compacts the visible (view,
-// Gaussian) pairs so that its warps work on visible pairs only, and sums the
-// per-pair gradients over views in shared memory in a fixed order, so the
-// result does not depend on timing.
+// colour, the pair's 64-byte record, per-tile keys) to full warps of visible
+// pairs.
+// Backward: persistent blocks take groups of Gaussians with all their views;
+// a group's visible (view, Gaussian) pairs are compacted Gaussian-major so
+// that warps work on visible pairs only, the per-pair gradients are summed
+// over views in shared memory in a fixed order (the result does not depend on
+// timing), and each pair's screen-gradient row is cleared after it is read.
 #include <algorithm>
 #include <mutex>
 
