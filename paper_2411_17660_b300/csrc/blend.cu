@@ -2,7 +2,8 @@
 // "rendering": C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j)) and its
 // back-to-front backward.
 //
-// One CTA per screen tile (all views concatenated), one warp per 8x16 block
+// One CTA per screen tile of up to 16x16 pixels, four CTAs of 16x16 per
+// tile of 32 (all views concatenated), one warp per 8x16 block
 // of pixels (four pixels per lane) where the tile is that tall, else per 8x8
 // block (two pixels per lane; also the forward's median-depth variant).
 // Each warp walks its tile's depth-sorted list in chunks of 32 entries: the
@@ -43,11 +44,18 @@ namespace {
 constexpr int kSubW = 8, kSubH = 8, kRowStep = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
+// A CTA covers a CS x CS square of a tile (CS = the tile side up to 16):
+// tiles of 32 are blended by four CTAs of 16 x 16, each reading the whole
+// tile list, so that a CTA's slot on the SM is held only as long as its two
+// (or four) warps work rather than until the slowest of eight finishes.
 template <int TS, int BH = kSubH>
 struct BlendShape {
-    static_assert(TS % kSubW == 0 && TS % BH == 0, "a tile holds whole warp blocks");
-    static constexpr int WX = TS / kSubW;
-    static constexpr int WY = TS / BH;
+    static constexpr int CS = TS > 16 ? 16 : TS;   // CTA side
+    static constexpr int SUB = TS / CS;            // CTAs per tile side
+    static constexpr int CTAS = SUB * SUB;         // CTAs per tile
+    static_assert(TS % CS == 0 && CS % kSubW == 0 && CS % BH == 0, "a CTA holds whole warp blocks");
+    static constexpr int WX = CS / kSubW;
+    static constexpr int WY = CS / BH;
     static constexpr int WARPS = WX * WY;
     static constexpr int THREADS = WARPS * 32;
 };
@@ -253,18 +261,19 @@ template <int TS, int BH = kSubH>
 __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws) {
     using S = BlendShape<TS, BH>;
     WarpTile w;
-    uint32_t tile = blockIdx.x;
+    const uint32_t slot = blockIdx.x / S::CTAS, q = blockIdx.x % S::CTAS;   // tile slot, CTA in the tile
+    uint32_t tile = slot;
     if (ws.order_tiles) {   // tiles with the most keys first (bucket scan or launch_tile_order)
-        const uint32_t t = ws.tile_order[blockIdx.x];
-        tile = t < vt.total_tiles ? t : blockIdx.x;
+        const uint32_t t = ws.tile_order[slot];
+        tile = t < vt.total_tiles ? t : slot;
     }
     w.v = view_of_tile(vt, tile);
     const ViewParams &vp = vt.v[w.v];
     const uint32_t lt = tile - vp.tile_offset;
     const int tx = (int)(lt % (uint32_t)vp.tiles_x), ty = (int)(lt / (uint32_t)vp.tiles_x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    w.X0 = tx * TS + (warp % S::WX) * kSubW;
-    w.Y0 = ty * TS + (warp / S::WX) * BH;
+    w.X0 = tx * TS + (int)(q % S::SUB) * S::CS + (warp % S::WX) * kSubW;
+    w.Y0 = ty * TS + (int)(q / S::SUB) * S::CS + (warp / S::WX) * BH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
     w.range = checked_range(ws.ranges, tile, ws.hdr, ws.cap);
@@ -868,14 +877,15 @@ template <int TS, int CH, int ROWS>
 cudaError_t launch_fwd_rows(const ViewTable &vt, const Ws &ws, cudaStream_t st, bool med, bool l1) {
     constexpr int TM = BlendShape<TS, FwdBlock<TS, true, 8>::H>::THREADS;       // with median depth
     constexpr int TP = BlendShape<TS, FwdBlock<TS, false, ROWS>::H>::THREADS;   // without
+    const unsigned ctas = vt.total_tiles * BlendShape<TS>::CTAS;
     if (med && l1)
-        blend_fwd_kernel<TS, CH, true, true, 8><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, true, 8><<<ctas, TM, 0, st>>>(vt, ws);
     else if (med)
-        blend_fwd_kernel<TS, CH, true, false, 8><<<vt.total_tiles, TM, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, false, 8><<<ctas, TM, 0, st>>>(vt, ws);
     else if (l1)
-        blend_fwd_kernel<TS, CH, false, true, ROWS><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, true, ROWS><<<ctas, TP, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, CH, false, false, ROWS><<<vt.total_tiles, TP, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, false, ROWS><<<ctas, TP, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
@@ -895,10 +905,11 @@ cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].d_median_depth != nullptr;
     constexpr int T = BlendShape<TS, BwdBlock<TS>::H>::THREADS;
+    const unsigned ctas = vt.total_tiles * BlendShape<TS>::CTAS;
     if (med)
-        blend_bwd_kernel<TS, CH, true><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, CH, true><<<ctas, T, 0, st>>>(vt, ws);
     else
-        blend_bwd_kernel<TS, CH, false><<<vt.total_tiles, T, 0, st>>>(vt, ws);
+        blend_bwd_kernel<TS, CH, false><<<ctas, T, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
