@@ -2,10 +2,10 @@
 // "rendering": C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j)) and its
 // back-to-front backward.
 //
-// One CTA per screen tile of up to 16x16 pixels, four CTAs of 16x16 per
-// tile of 32 (all views concatenated), one warp per 8x16 block
-// of pixels (four pixels per lane) where the tile is that tall, else per 8x8
-// block (two pixels per lane; also the forward's median-depth variant).
+// One CTA of one warp per block of pixels of a screen tile (all views
+// concatenated; the blocks of a tile are consecutive CTAs): 8x16 blocks
+// (four pixels per lane) where the tile is that tall, else 8x8 blocks (two
+// pixels per lane; also the forward's median-depth variant).
 // Each warp walks its tile's depth-sorted list in chunks of 32 entries: the
 // 32 lanes load one entry each, keep only the Gaussians whose cutoff ellipse
 // reaches the warp's block (an exact convex minimum of d^2 over the block),
@@ -44,20 +44,19 @@ namespace {
 constexpr int kSubW = 8, kSubH = 8, kRowStep = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
-// A CTA covers a CS x CS square of a tile (CS = the tile side up to 16):
-// tiles of 32 are blended by four CTAs of 16 x 16, each reading the whole
-// tile list, so that a CTA's slot on the SM is held only as long as its two
-// (or four) warps work rather than until the slowest of eight finishes.
+// A CTA is one warp with its block of 8 columns and BH rows; the blocks of a
+// tile are consecutive CTAs, each reading the whole tile list.  A CTA's slot
+// on the SM is then held only while its own warp works, not until the
+// slowest warp of its tile finishes (window blend backward 0.2190 -> 0.2120
+// ms against a CTA per tile of 16; at tile 32 against a CTA per 16 x 16 or
+// per tile, uneven blend backward 1.525 -> 1.477, 1.590 ms).
 template <int TS, int BH = kSubH>
 struct BlendShape {
-    static constexpr int CS = TS > 16 ? 16 : TS;   // CTA side
-    static constexpr int SUB = TS / CS;            // CTAs per tile side
-    static constexpr int CTAS = SUB * SUB;         // CTAs per tile
-    static_assert(TS % CS == 0 && CS % kSubW == 0 && CS % BH == 0, "a CTA holds whole warp blocks");
-    static constexpr int WX = CS / kSubW;
-    static constexpr int WY = CS / BH;
-    static constexpr int WARPS = WX * WY;
-    static constexpr int THREADS = WARPS * 32;
+    static_assert(TS % kSubW == 0 && TS % BH == 0, "a tile holds whole warp blocks");
+    static constexpr int CX = TS / kSubW;          // CTAs (warp blocks) per tile row
+    static constexpr int CTAS = CX * (TS / BH);    // CTAs per tile
+    static constexpr int WARPS = 1;
+    static constexpr int THREADS = 32;
 };
 
 // s = 0.5 log2(e) d^2 = p1^2 + p2^2, with the Cholesky factor m of
@@ -261,7 +260,7 @@ template <int TS, int BH = kSubH>
 __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws) {
     using S = BlendShape<TS, BH>;
     WarpTile w;
-    const uint32_t slot = blockIdx.x / S::CTAS, q = blockIdx.x % S::CTAS;   // tile slot, CTA in the tile
+    const uint32_t slot = blockIdx.x / S::CTAS, q = blockIdx.x % S::CTAS;   // tile slot, block in the tile
     uint32_t tile = slot;
     if (ws.order_tiles) {   // tiles with the most keys first (bucket scan or launch_tile_order)
         const uint32_t t = ws.tile_order[slot];
@@ -271,9 +270,9 @@ __device__ __forceinline__ WarpTile warp_tile(const ViewTable &vt, const Ws &ws)
     const ViewParams &vp = vt.v[w.v];
     const uint32_t lt = tile - vp.tile_offset;
     const int tx = (int)(lt % (uint32_t)vp.tiles_x), ty = (int)(lt / (uint32_t)vp.tiles_x);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    w.X0 = tx * TS + (int)(q % S::SUB) * S::CS + (warp % S::WX) * kSubW;
-    w.Y0 = ty * TS + (int)(q / S::SUB) * S::CS + (warp / S::WX) * BH;
+    const int lane = threadIdx.x & 31;
+    w.X0 = tx * TS + (int)(q % S::CX) * kSubW;
+    w.Y0 = ty * TS + (int)(q / S::CX) * BH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
     w.range = checked_range(ws.ranges, tile, ws.hdr, ws.cap);
@@ -877,15 +876,16 @@ template <int TS, int CH, int ROWS>
 cudaError_t launch_fwd_rows(const ViewTable &vt, const Ws &ws, cudaStream_t st, bool med, bool l1) {
     constexpr int TM = BlendShape<TS, FwdBlock<TS, true, 8>::H>::THREADS;       // with median depth
     constexpr int TP = BlendShape<TS, FwdBlock<TS, false, ROWS>::H>::THREADS;   // without
-    const unsigned ctas = vt.total_tiles * BlendShape<TS>::CTAS;
+    const unsigned cm = vt.total_tiles * BlendShape<TS, FwdBlock<TS, true, 8>::H>::CTAS;
+    const unsigned cp = vt.total_tiles * BlendShape<TS, FwdBlock<TS, false, ROWS>::H>::CTAS;
     if (med && l1)
-        blend_fwd_kernel<TS, CH, true, true, 8><<<ctas, TM, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, true, 8><<<cm, TM, 0, st>>>(vt, ws);
     else if (med)
-        blend_fwd_kernel<TS, CH, true, false, 8><<<ctas, TM, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, true, false, 8><<<cm, TM, 0, st>>>(vt, ws);
     else if (l1)
-        blend_fwd_kernel<TS, CH, false, true, ROWS><<<ctas, TP, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, true, ROWS><<<cp, TP, 0, st>>>(vt, ws);
     else
-        blend_fwd_kernel<TS, CH, false, false, ROWS><<<ctas, TP, 0, st>>>(vt, ws);
+        blend_fwd_kernel<TS, CH, false, false, ROWS><<<cp, TP, 0, st>>>(vt, ws);
     return cudaGetLastError();
 }
 
@@ -905,7 +905,7 @@ cudaError_t launch_bwd_t(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     bool med = false;
     for (int v = 0; v < vt.V; ++v) med |= vt.v[v].d_median_depth != nullptr;
     constexpr int T = BlendShape<TS, BwdBlock<TS>::H>::THREADS;
-    const unsigned ctas = vt.total_tiles * BlendShape<TS>::CTAS;
+    const unsigned ctas = vt.total_tiles * BlendShape<TS, BwdBlock<TS>::H>::CTAS;
     if (med)
         blend_bwd_kernel<TS, CH, true><<<ctas, T, 0, st>>>(vt, ws);
     else
