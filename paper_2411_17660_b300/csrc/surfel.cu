@@ -36,7 +36,10 @@ constexpr float kLowPass = 2.0f;   // rho2 = 2 |pixel - centre|^2
 
 template <int TS>
 struct Shape {
-    static constexpr int WX = TS / kSubW, WY = TS / kSubH, WARPS = WX * WY, THREADS = WARPS * 32;
+    // one CTA of one warp per 8x8 block; a tile's blocks are consecutive CTAs
+    // (an SM slot is held only while its warp works, as in the Gaussian blends)
+    static constexpr int WX = 1, WY = 1, WARPS = 1, THREADS = 32;
+    static constexpr int CX = TS / kSubW, CTAS = CX * (TS / kSubH);   // blocks per tile row, per tile
     // resident blocks per SM asked of the backward: three quarters of full occupancy, at least 1
     static constexpr int BWD_BLOCKS = 1024 / THREADS * 3 / 4 > 0 ? 1024 / THREADS * 3 / 4 : 1;
 };
@@ -202,14 +205,14 @@ struct Tile {
 template <int TS>
 __device__ __forceinline__ Tile tile_of(const ViewTable &vt, const Ws &ws) {
     Tile w;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = blockIdx.x / Shape<TS>::CTAS, q = blockIdx.x % Shape<TS>::CTAS;
     w.v = view_of_tile(vt, tile);
     const ViewParams &vp = vt.v[w.v];
     const uint32_t lt = tile - vp.tile_offset;
     const int tx = (int)(lt % (uint32_t)vp.tiles_x), ty = (int)(lt / (uint32_t)vp.tiles_x);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    w.X0 = tx * TS + (warp % Shape<TS>::WX) * kSubW;
-    w.Y0 = ty * TS + (warp / Shape<TS>::WX) * kSubH;
+    const int lane = threadIdx.x & 31;
+    w.X0 = tx * TS + (int)(q % Shape<TS>::CX) * kSubW;
+    w.Y0 = ty * TS + (int)(q / Shape<TS>::CX) * kSubH;
     w.px = w.X0 + (lane & (kSubW - 1));
     w.py = w.Y0 + lane / kSubW;
     w.range = checked_range(ws.ranges, tile, ws.hdr, ws.cap);
@@ -722,9 +725,9 @@ cudaError_t launch_surfel_preprocess_bwd(const ViewTable &vt, const GaussianPtrs
 cudaError_t launch_surfel_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     if (vt.total_tiles == 0) return cudaSuccess;
     switch (vt.tile) {
-        case 8: surfel_blend_fwd_kernel<8><<<vt.total_tiles, Shape<8>::THREADS, 0, st>>>(vt, ws); break;
-        case 32: surfel_blend_fwd_kernel<32><<<vt.total_tiles, Shape<32>::THREADS, 0, st>>>(vt, ws); break;
-        default: surfel_blend_fwd_kernel<16><<<vt.total_tiles, Shape<16>::THREADS, 0, st>>>(vt, ws); break;
+        case 8: surfel_blend_fwd_kernel<8><<<vt.total_tiles * Shape<8>::CTAS, Shape<8>::THREADS, 0, st>>>(vt, ws); break;
+        case 32: surfel_blend_fwd_kernel<32><<<vt.total_tiles * Shape<32>::CTAS, Shape<32>::THREADS, 0, st>>>(vt, ws); break;
+        default: surfel_blend_fwd_kernel<16><<<vt.total_tiles * Shape<16>::CTAS, Shape<16>::THREADS, 0, st>>>(vt, ws); break;
     }
     return cudaGetLastError();
 }
@@ -732,9 +735,9 @@ cudaError_t launch_surfel_blend_fwd(const ViewTable &vt, const Ws &ws, cudaStrea
 cudaError_t launch_surfel_blend_bwd(const ViewTable &vt, const Ws &ws, cudaStream_t st) {
     if (vt.total_tiles == 0) return cudaSuccess;
     switch (vt.tile) {
-        case 8: surfel_blend_bwd_kernel<8><<<vt.total_tiles, Shape<8>::THREADS, 0, st>>>(vt, ws); break;
-        case 32: surfel_blend_bwd_kernel<32><<<vt.total_tiles, Shape<32>::THREADS, 0, st>>>(vt, ws); break;
-        default: surfel_blend_bwd_kernel<16><<<vt.total_tiles, Shape<16>::THREADS, 0, st>>>(vt, ws); break;
+        case 8: surfel_blend_bwd_kernel<8><<<vt.total_tiles * Shape<8>::CTAS, Shape<8>::THREADS, 0, st>>>(vt, ws); break;
+        case 32: surfel_blend_bwd_kernel<32><<<vt.total_tiles * Shape<32>::CTAS, Shape<32>::THREADS, 0, st>>>(vt, ws); break;
+        default: surfel_blend_bwd_kernel<16><<<vt.total_tiles * Shape<16>::CTAS, Shape<16>::THREADS, 0, st>>>(vt, ws); break;
     }
     return cudaGetLastError();
 }
