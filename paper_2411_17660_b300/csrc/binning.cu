@@ -654,14 +654,15 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_scatter_kernel(const Ws
 // After the tile-key passes, tile t's (depth bits << 32 | id) words sit in
 // words[start, end) in pair order; ascending words are the list order.  Up to
 // kWarpSortMax words a warp sorts them in registers (a bitonic network over
-// 32 E words, word e * 32 + lane in lane's x[e]); up to kBlockSortMid the
-// block of the tile's warp sorts them in shared memory by a radix sort of the
-// depth bits; beyond, a block with kBlockSortCap words of shared memory does,
-// as runs merged pairwise through the free word buffer when there are more.
-// The ids go to ws.sorted.
+// 32 E words, word e * 32 + lane in lane's x[e]); beyond, a block with
+// kBlockSortCap words of shared memory sorts them by a radix sort of the
+// depth bits, as runs merged pairwise through the free word buffer when there
+// are more.  (Tiles of 513 to 2,048 words sorted by the block of the tile's
+// warp held that block's other warps until they were done: window sort
+// 0.0498 -> 0.0473 ms with those tiles in the big-tile kernel and blocks of
+// two warps instead of eight.)  The ids go to ws.sorted.
 constexpr int kWarpSortMax = 512;
-constexpr int kBlockSortMid = 2048;
-constexpr int kTilesPerSortBlock = 8;   // one warp each
+constexpr int kTilesPerSortBlock = 2;   // one warp each
 constexpr int kBlockSortCap = 16384;
 constexpr int kBigSortThreads = 1024;
 constexpr size_t kBigSortSmem = kBlockSortCap * sizeof(unsigned long long) + (kBigSortThreads / 32) * kRadix * 4;
@@ -874,16 +875,9 @@ __device__ __forceinline__ void block_sort_run(const unsigned long long *src, ui
     __syncthreads();
 }
 
-// Tiles of up to kBlockSortMid keys: warp w of block b takes tile
-// 8 b + w if it holds at most kWarpSortMax keys; then the block sorts, one
-// after another, those of its 8 tiles that hold more (and at most
-// kBlockSortMid).
+// Tiles of up to kWarpSortMax keys: warp w of block b takes tile
+// kTilesPerSortBlock b + w.
 __global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(const Ws ws) {
-    constexpr int THREADS = 32 * kTilesPerSortBlock;
-    __shared__ unsigned long long s_sort[kBlockSortMid];
-    __shared__ uint32_t s_whist[kTilesPerSortBlock][kRadix];
-    __shared__ uint32_t s_red[2 * kTilesPerSortBlock];
-    __shared__ uint2 s_range[kTilesPerSortBlock];
     const int lane = threadIdx.x & 31;
     const uint32_t t0 = blockIdx.x * kTilesPerSortBlock;
     const unsigned long long *words = ws.keys[ws.passes & 1];
@@ -891,7 +885,6 @@ __global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(cons
     {
         const uint32_t t = t0 + (threadIdx.x >> 5);
         const uint2 r = t < ws.total_tiles ? checked_range(ws.ranges, t, ws.hdr, ws.cap) : make_uint2(0u, 0u);
-        if (lane == 0) s_range[threadIdx.x >> 5] = r;
         const uint32_t n = r.y - r.x;
         if (n == 1) {
             if (lane == 0) ids[r.x] = (uint32_t)words[r.x];
@@ -906,14 +899,6 @@ __global__ void __launch_bounds__(32 * kTilesPerSortBlock) tile_sort_kernel(cons
         } else if (n > 256 && n <= kWarpSortMax) {   // 512 words: measured 10.4 -> 9.0 ms of outdoor tile sorts
             warp_sort_tile<16>(words + r.x, ids + r.x, n, lane);
         }
-    }
-    __syncthreads();
-    for (int w = 0; w < kTilesPerSortBlock; ++w) {
-        const uint2 r = s_range[w];
-        const uint32_t n = r.y - r.x;
-        if (n > (uint32_t)kWarpSortMax && n <= (uint32_t)kBlockSortMid)
-            block_sort_run<THREADS, kBlockSortMid / THREADS>(words + r.x, n, s_sort, s_whist, s_red, nullptr,
-                                                              ids + r.x);
     }
 }
 
@@ -941,7 +926,7 @@ __device__ __forceinline__ void block_merge(const unsigned long long *A, uint32_
     }
 }
 
-// Tiles of more than kBlockSortMid keys, a block each in turn.  Block b
+// Tiles of more than kWarpSortMax keys, a block each in turn.  Block b
 // looks at tiles b, b + G, b + 2G, ... (G blocks), a thread per tile at a
 // time, and lists the big ones in shared memory first.
 __global__ void __launch_bounds__(kBigSortThreads) tile_sort_big_kernel(const Ws ws) {
@@ -959,7 +944,7 @@ __global__ void __launch_bounds__(kBigSortThreads) tile_sort_big_kernel(const Ws
         const size_t tt = first + threadIdx.x * G;
         if (tt < ws.total_tiles) {
             const uint2 r = checked_range(ws.ranges, (uint32_t)tt, ws.hdr, ws.cap);
-            if (r.y - r.x > (uint32_t)kBlockSortMid) s_big[atomicAdd(&s_nbig, 1u)] = (uint32_t)tt;
+            if (r.y - r.x > (uint32_t)kWarpSortMax) s_big[atomicAdd(&s_nbig, 1u)] = (uint32_t)tt;
         }
         __syncthreads();
         const uint32_t nbig = s_nbig;
