@@ -38,7 +38,7 @@ template <int TS>
 struct Shape {
     // one CTA of one warp per 8x8 block; a tile's blocks are consecutive CTAs
     // (an SM slot is held only while its warp works, as in the Gaussian blends)
-    static constexpr int WX = 1, WY = 1, WARPS = 1, THREADS = 32;
+    static constexpr int WARPS = 1, THREADS = 32;
     static constexpr int CX = TS / kSubW, CTAS = CX * (TS / kSubH);   // blocks per tile row, per tile
     // resident blocks per SM asked of the backward: three quarters of full occupancy, at least 1
     static constexpr int BWD_BLOCKS = 1024 / THREADS * 3 / 4 > 0 ? 1024 / THREADS * 3 / 4 : 1;
